@@ -1,0 +1,219 @@
+"""Seeded synthetic inputs for the cut-cell MAC projection step.
+
+This module describes *problems*, never how they are solved: grid sizes, the box, the
+immersed body, the physical constants, the box boundary types, solver settings, and the
+random draws (initial velocity perturbations, the mixes of cases used for batched and
+served runs).  Both the CUDA library's tests/bench and the FP64 oracle read their inputs
+from here; neither the capacities, nor the operators, nor the time step live here.
+
+Conventions shared by every consumer:
+
+* A case has ``nx x ny`` pressure cells on ``[x0, x1] x [y0, y1]``.
+* Every field is exchanged as a padded array of shape ``(ny + 3, nx + 3)`` (x fastest):
+  array element ``[j + 1, i + 1]`` holds index ``(i, j)`` with ``i`` in ``[-1, nx + 1]`` and
+  ``j`` in ``[-1, ny + 1]``.  Index ``(i, j)`` means the pressure cell ``i, j``, the x-face
+  ``x0 + i*hx`` (u), the y-face ``y0 + j*hy`` (v) or the node ``(x0 + i*hx, y0 + j*hy)``
+  depending on the field.
+* Box sides are numbered W=0, E=1, S=2, N=3.  A side is either ``DIRICHLET`` (prescribed
+  normal component ``bc_un`` and tangential component ``bc_ut``; an inflow is a Dirichlet
+  side with ``bc_un = U_inf``) or ``OUTFLOW`` (zero-gradient velocity, pressure zero).
+* The time step is ``dt = CFL * min(hx, hy) / U_inf`` and the viscosity
+  ``mu = rho * U_inf * L / Re`` with ``L`` the cylinder diameter or the airfoil chord.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+SEED = 2211106980
+
+SIDE_W, SIDE_E, SIDE_S, SIDE_N = 0, 1, 2, 3
+BC_DIRICHLET, BC_OUTFLOW = 0, 1
+
+GEOM_NONE, GEOM_CIRCLE, GEOM_NACA, GEOM_HALFPLANE = 0, 1, 2, 3
+
+
+@dataclasses.dataclass
+class Geometry:
+    kind: int = GEOM_NONE
+    # circle: fluid where |x - c| > r
+    cx: float = 0.0
+    cy: float = 0.0
+    r: float = 0.0
+    # symmetric NACA 4-digit 00tt: leading edge at (le_x, le_y), chord, angle of attack
+    naca_tt: int = 12
+    chord: float = 1.0
+    aoa_deg: float = 0.0
+    le_x: float = 0.0
+    le_y: float = 0.0
+    closed_te: int = 1
+    # half plane: fluid where hp_nx * x + hp_ny * y > hp_off
+    hp_nx: float = 1.0
+    hp_ny: float = 0.0
+    hp_off: float = 0.0
+
+
+@dataclasses.dataclass
+class Case:
+    name: str
+    nx: int
+    ny: int
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    rho: float
+    mu: float
+    dt: float
+    u_inf: float
+    bc_type: Tuple[int, int, int, int]
+    bc_un: Tuple[float, float, float, float]
+    bc_ut: Tuple[float, float, float, float]
+    geom: Geometry
+    steps: int = 1
+    precision: str = "fp64"        # "fp64" or "mixed"
+    precond: str = "jacobi"        # "jacobi" or "chebyshev"
+    cheb_degree: int = 4
+    tol_p: float = 1e-10
+    tol_h: float = 1e-10
+    tol_inner: float = 1e-5
+    max_iter_p: int = 20000
+    max_iter_h: int = 2000
+    perturb_sigma: float = 0.0
+    seed: int = SEED
+    literal_offdiag: int = 0
+
+    @property
+    def hx(self) -> float:
+        return (self.x1 - self.x0) / self.nx
+
+    @property
+    def hy(self) -> float:
+        return (self.y1 - self.y0) / self.ny
+
+    @property
+    def shape(self) -> Tuple[int, int]:
+        return (self.ny + 3, self.nx + 3)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+
+def flow_past_body_bc(u_inf: float = 1.0):
+    """West inflow (u = U_inf, v = 0), outflow on east, south and north."""
+    return ((BC_DIRICHLET, BC_OUTFLOW, BC_OUTFLOW, BC_OUTFLOW),
+            (u_inf, 0.0, 0.0, 0.0), (0.0, 0.0, 0.0, 0.0))
+
+
+def closed_box_bc(lid: float = 0.0):
+    """Four no-slip walls; the north wall slides with tangential speed ``lid``."""
+    return ((BC_DIRICHLET,) * 4, (0.0, 0.0, 0.0, 0.0), (0.0, 0.0, 0.0, lid))
+
+
+def make_case(name, nx, ny, box, geom, re, cfl, lref, *, u_inf=1.0, rho=1.0, bc=None,
+              **kw) -> Case:
+    x0, x1, y0, y1 = box
+    hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
+    dt = cfl * min(hx, hy) / u_inf
+    mu = rho * u_inf * lref / re
+    bt, bn, bu = bc if bc is not None else flow_past_body_bc(u_inf)
+    return Case(name=name, nx=nx, ny=ny, x0=x0, x1=x1, y0=y0, y1=y1, rho=rho, mu=mu, dt=dt,
+                u_inf=u_inf, bc_type=tuple(bt), bc_un=tuple(bn), bc_ut=tuple(bu), geom=geom, **kw)
+
+
+def cylinder_re40_128x64() -> Case:
+    """FP64 single case: 128x64 on [-2,6]x[-2,2], circle D=1 at the origin, Re 40, CFL 0.5,
+    100 steps, Jacobi-PCG to 1e-10."""
+    return make_case("cylinder_re40_128x64", 128, 64, (-2.0, 6.0, -2.0, 2.0),
+                     Geometry(kind=GEOM_CIRCLE, cx=0.0, cy=0.0, r=0.5), re=40.0, cfl=0.5,
+                     lref=1.0, steps=100)
+
+
+def cylinder_re100_1024x512() -> Case:
+    """FP64 vortex-shedding case: 1024x512 on [-4,12]x[-4,4], circle D=1, Re 100, CFL 0.5,
+    2000 steps, N(0, 1e-3) velocity perturbation, Jacobi-PCG to 1e-10."""
+    return make_case("cylinder_re100_1024x512", 1024, 512, (-4.0, 12.0, -4.0, 4.0),
+                     Geometry(kind=GEOM_CIRCLE, cx=0.0, cy=0.0, r=0.5), re=100.0, cfl=0.5,
+                     lref=1.0, steps=2000, perturb_sigma=1e-3)
+
+
+def naca0012_re1000_2048x1024() -> Case:
+    """Mixed-precision airfoil: NACA0012, chord 1, 4 deg, leading edge at the origin,
+    Re 1000, 2048x1024 on [-2,6]x[-2,2], 1000 steps, Chebyshev-PCG FP32 inner with FP64
+    refinement to 1e-10."""
+    return make_case("naca0012_re1000_2048x1024", 2048, 1024, (-2.0, 6.0, -2.0, 2.0),
+                     Geometry(kind=GEOM_NACA, naca_tt=12, chord=1.0, aoa_deg=4.0),
+                     re=1000.0, cfl=0.5, lref=1.0, steps=1000, precision="mixed",
+                     precond="chebyshev")
+
+
+def batch_cases(n: int = 64, seed: int = SEED, steps: int = 500,
+                nx_range=(256, 1024)) -> List[Case]:
+    """Batched mix: half cylinders (D ~ U[0.5,1.5], centre ~ U[-0.5,0.5]^2), half NACA00tt
+    (tt uniform in 08..18, AoA ~ U[0,10] deg); nx log-uniform in ``nx_range`` rounded to a
+    multiple of 16, ny = nx/2, box [-2,6]x[-2,2]; Re ~ U[40,1000]; mixed precision."""
+    out = []
+    for k in range(n):
+        rng = np.random.default_rng(seed + k)
+        nx = int(round(math.exp(rng.uniform(math.log(nx_range[0]), math.log(nx_range[1]))) / 16.0)) * 16
+        nx = max(nx, 16)
+        ny = nx // 2
+        re = float(rng.uniform(40.0, 1000.0))
+        if k % 2 == 0:
+            d = float(rng.uniform(0.5, 1.5))
+            c = rng.uniform(-0.5, 0.5, size=2)
+            geom = Geometry(kind=GEOM_CIRCLE, cx=float(c[0]), cy=float(c[1]), r=0.5 * d)
+            lref = d
+        else:
+            tt = int(rng.integers(8, 19))
+            aoa = float(rng.uniform(0.0, 10.0))
+            geom = Geometry(kind=GEOM_NACA, naca_tt=tt, chord=1.0, aoa_deg=aoa)
+            lref = 1.0
+        out.append(make_case(f"batch{k:03d}", nx, ny, (-2.0, 6.0, -2.0, 2.0), geom, re=re,
+                             cfl=0.5, lref=lref, steps=steps, precision="mixed",
+                             precond="chebyshev", seed=seed + k))
+    return out
+
+
+def serving_requests(n: int = 1000, lam: float = 20.0, seed: int = SEED,
+                     nx_range=(128, 2048), steps_range=(200, 5000)):
+    """Request stream: exponential inter-arrival times with rate ``lam`` per second;
+    geometry and Re drawn like ``batch_cases``; nx log-uniform in ``nx_range``; steps
+    uniform in ``steps_range``.  Returns a list of (arrival_time_s, Case)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / lam, size=n)
+    t = np.cumsum(gaps)
+    reqs = []
+    for k in range(n):
+        c = batch_cases(1, seed=seed + 100000 + k, nx_range=nx_range)[0]
+        r2 = np.random.default_rng(seed + 200000 + k)
+        c.steps = int(r2.integers(steps_range[0], steps_range[1] + 1))
+        c.name = f"req{k:04d}"
+        reqs.append((float(t[k]), c))
+    return reqs
+
+
+def perturbation(case: Case) -> Tuple[np.ndarray, np.ndarray]:
+    """Seeded N(0, sigma^2) draws for the u and v arrays (padded shape).  Consumers add them
+    on the velocity unknowns whose staggered control volume holds fluid."""
+    rng = np.random.default_rng(case.seed)
+    pu = rng.standard_normal(case.shape) * case.perturb_sigma
+    pv = rng.standard_normal(case.shape) * case.perturb_sigma
+    return pu, pv
+
+
+def random_field(case: Case, seed: int, scale: float = 1.0) -> np.ndarray:
+    """A seeded N(0, scale^2) padded array, for operator parity inputs."""
+    return np.random.default_rng(seed).standard_normal(case.shape) * scale
+
+
+def small_cylinder(nx=16, ny=8, box=(-2.0, 2.0, -1.0, 1.0), r=0.37, cx=0.05, cy=-0.03,
+                   re=40.0, cfl=0.5, bc=None, **kw) -> Case:
+    """A small off-centre cylinder case for dense and brute-force tests."""
+    return make_case(f"small_cyl_{nx}x{ny}", nx, ny, box,
+                     Geometry(kind=GEOM_CIRCLE, cx=cx, cy=cy, r=r), re=re, cfl=cfl,
+                     lref=2 * r, bc=bc, **kw)
