@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput of the cut-cell MAC projection step on GB300, in MAC cell-steps/s.
+
+Workload (one GPU): the 1024x512 Re 100 cylinder on [-4,12]x[-4,4] in FP64 with the seeded
+N(0, 1e-3) velocity perturbation, Jacobi-PCG to 1e-10 (the configuration the metric is
+quoted on).  A "step" is one whole PmII projection step (predictor with AB2 convection and
+Crank-Nicolson viscosity, Helmholtz PCG, divergence, Poisson PCG, projection and pressure
+update) over the case.  The state is device resident; L2 is flushed (256 MiB write)
+between timed steps, outside each step's CUDA-event interval.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank advances its own replica of the case
+(the case is not split: replicas only) and ``value`` is the sum over ranks.
+``--impl reference`` times the FP64 CPU oracle on this machine's host cores on bounded
+samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MAC cell-steps/s single & batched; HBM GB/s frac; p50/p99 solve latency"
+UNIT = "cell-steps/s"
+WORKLOAD = "cylinder_re100_1024x512"
+
+# Algorithmic cost of one Jacobi-PCG iteration per cell (FP64): K p (4 differences, 4
+# products, 3 sums), p.q, x += a p, r -= a q, z = D^-1 r, r.z, r.r, p = z + b p.
+PCG_FLOPS_PER_CELL_ITER = 24
+# x, r and p each read and written once per iteration (8-byte words).
+PCG_BYTES_PER_CELL_ITER = 48
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clock x 2 flop x
+# 2.07 GHz (the probe measured 1.20 TFLOP/s of dependent-chain-free FMAs).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def _traffic_from_profile():
+    """DRAM bytes per launch of the Poisson PCG from the committed ncu summary, if the
+    kernel source still matches the hash recorded with the counters."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "pcg_poisson_fp64_cylinder.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    src = open(os.path.join(ROOT, "paper_2211_10698_gb300", "csrc", "pcg.cu"), "rb").read()
+    if vals.get("pcg.cu sha256") != hashlib.sha256(src).hexdigest()[:16]:
+        return None, None
+    try:
+        return float(vals["dram bytes per iteration per cell"]), vals
+    except (KeyError, ValueError):
+        return None, None
+
+
+class Clocks:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for r in csv.reader(fh):
+                if len(r) >= 9:
+                    rows.append([x.strip() for x in r])
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+class _OracleSampler:
+    """Bounded samples of the oracle on the workload.  One sample is one oracle step from the
+    initial state with the Poisson PCG capped at a few iterations; samples at two caps give
+    the fixed cost a of a step (predictor, Helmholtz PCG, projection) and the cost b of one
+    Poisson iteration, so that a whole step costs a + b * (Poisson iterations per step)."""
+
+    def __init__(self, case):
+        import copy
+
+        import oracle
+        from paper_2211_10698_gb300 import inputs
+
+        self.case = case
+        self.pu, self.pv = inputs.perturbation(case)
+        self.o = {}
+        for n in (5, 45):
+            c2 = copy.deepcopy(case)
+            c2.max_iter_p = n
+            self.o[n] = oracle.Oracle(c2)
+        self.pts = []
+
+    def sample(self, n):
+        o = self.o[n]
+        st = o.init_state(pu=self.pu, pv=self.pv)
+        t0 = time.perf_counter()
+        hist, _ = o.step(st, 1)
+        self.pts.append((hist[0]["iters_p"], time.perf_counter() - t0))
+        return self.pts[-1]
+
+    def fit(self, pts=None):
+        import numpy as np
+
+        pts = self.pts if pts is None else pts
+        n = np.array([p[0] for p in pts], float)
+        t = np.array([p[1] for p in pts], float)
+        b, a = np.polyfit(n, t, 1)
+        return float(a), float(b)
+
+
+def _cpu_sample(case, iters_per_step):
+    s = _OracleSampler(case)
+    s.sample(5)
+    s.sample(45)
+    a, b = s.fit()
+    t_step = a + b * iters_per_step
+    (n1, t1), (n2, t2) = s.pts
+    return dict(value=case.cells / t_step, unit=UNIT, cores=1, kind="oracle",
+                sample=(f"{WORKLOAD}: 2 oracle steps from the initial state with the Poisson PCG capped at "
+                        f"{n1} and {n2} iterations ({t1:.1f} s, {t2:.1f} s); whole step = {a:.2f} s + "
+                        f"{b:.4f} s/iteration x {iters_per_step:.0f} oracle Poisson iterations per step"),
+                seconds_per_step=t_step)
+
+
+def _oracle_iters_per_step(skip=3):
+    path = os.path.join(ROOT, "tests", "golden", "c2_oracle_iterations.json")
+    with open(path) as f:
+        rows = json.load(f)["steps"]
+    use = [r["iters_p"] for r in rows[skip:]] or [r["iters_p"] for r in rows]
+    return sum(use) / len(use), len(use)
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_2211_10698_gb300 import inputs
+
+    case = inputs.cylinder_re100_1024x512()
+    iters, nrows = _oracle_iters_per_step()
+    sampler = _OracleSampler(case)
+    for k in range(args.warmup):
+        sampler.sample(5 if k % 2 == 0 else 45)
+    timed = [sampler.sample(5 if k % 2 == 0 else 45) for k in range(max(args.steps, 2))]
+    a, b = sampler.fit(timed)
+    sec_step = a + b * iters
+    secs = sec_step * len(timed)
+    value = case.cells / sec_step
+    vals = [dict(sample=(f"{WORKLOAD}: {len(timed)} oracle steps from the initial state with the Poisson PCG "
+                         f"capped alternately at 5 and 45 iterations; whole step = {a:.2f} s + {b:.4f} s/iteration "
+                         f"x {iters:.0f} oracle Poisson iterations per step (tests/golden/c2_oracle_iterations.json)"))] * len(timed)
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * secs / len(vals), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD, nx=case.nx, ny=case.ny, precision="fp64", precond="jacobi",
+                            tol_p=case.tol_p, oracle_poisson_iters_per_step=iters),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=vals[-1]["sample"]),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2211_10698_gb300 import ccm, inputs
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    case = inputs.cylinder_re100_1024x512()
+    stream = torch.cuda.current_stream()
+    g = ccm.Case(case, stream=stream.cuda_stream, allocator=ccm.TorchAllocator())
+    pu, pv = inputs.perturbation(case)
+    g.set_field(ccm.CCM_F_U, g.get_field(ccm.CCM_F_U) + pu)
+    g.set_field(ccm.CCM_F_V, g.get_field(ccm.CCM_F_V) + pv)
+    g.step(args.warmup)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    g.enable_kernel_timing(True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = Clocks(local)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        g.step_async(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    st = g.read_stats()
+    kt = g.kernel_timing()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = world * case.cells * args.steps / (t_ms * 1e-3)
+    iters_p = st["iters_p"] / args.steps
+    iters_h = st["iters_h"] / args.steps
+
+    # end to end through the C ABI with host (pinned) buffers: upload U, V, P, one step,
+    # download U, V, P
+    shape = case.shape
+    hb = [torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
+    fields = (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P)
+    for f, buf in zip(fields, hb):
+        g.get_field(f, out=buf)
+    g.enable_kernel_timing(False)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for f, buf in zip(fields, hb):
+            g.set_field(f, buf)
+        g.step(1)
+        for f, buf in zip(fields, hb):
+            g.get_field(f, out=buf)
+    e2e_s = time.perf_counter() - e0
+    e2e_val = world * case.cells * args.e2e_steps / e2e_s if args.e2e_steps > 0 else None
+    nbytes = 3 * shape[0] * shape[1] * 8
+
+    peaks, peak_kind = _peaks()
+    launches = max(kt["poisson_launches"], 1)
+    avg_ms = kt["poisson_ms"] / launches
+    iters_per_launch = kt["poisson_iters"] / launches
+    flops = PCG_FLOPS_PER_CELL_ITER * case.cells * iters_per_launch
+    bytes_alg = PCG_BYTES_PER_CELL_ITER * case.cells * iters_per_launch
+    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
+    achieved_gbs = bytes_alg / (avg_ms * 1e-3) / 1e9
+    frac_alu = achieved_tf / FP64_PEAK_TFLOPS
+    frac_hbm = achieved_gbs / peaks["hbm_gbs"]
+    traffic_pc, prof = _traffic_from_profile()
+    traffic = traffic_pc * case.cells * iters_per_launch if traffic_pc is not None else None
+    if frac_alu >= frac_hbm:
+        roof = dict(bound="alu", achieved=achieved_tf, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=frac_alu,
+                    traffic=traffic, kernel="k_pcg_poisson<double>",
+                    peak_source="FP64 unit count x clock (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)")
+    else:
+        roof = dict(bound="hbm", achieved=achieved_gbs, peak=peaks["hbm_gbs"], unit="GB/s", frac=frac_hbm,
+                    traffic=traffic, kernel="k_pcg_poisson<double>", peak_source=f"{peak_kind} hbm_gbs")
+    roof_alt = dict(hbm_achieved_gbs=achieved_gbs, hbm_peak_gbs=peaks["hbm_gbs"], hbm_frac=frac_hbm,
+                    fp64_achieved_tflops=achieved_tf, fp64_peak_tflops=FP64_PEAK_TFLOPS, fp64_frac=frac_alu,
+                    avg_launch_ms=avg_ms, iters_per_launch=iters_per_launch,
+                    us_per_iteration=1e3 * avg_ms / max(iters_per_launch, 1), peak_kind=peak_kind)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            oi, _ = _oracle_iters_per_step()
+        except (OSError, KeyError, ValueError):
+            oi = iters_p
+        cpu = _cpu_sample(case, oi)
+        cpu.pop("seconds_per_step", None)
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                    dtype="f64", data="synthetic",
+                    config=dict(workload=WORKLOAD, nx=case.nx, ny=case.ny, cells=case.cells, precision="fp64",
+                                precond="jacobi", tol_p=case.tol_p, tol_h=case.tol_h, parallelism=f"replicas{world}",
+                                l2="flushed between timed steps (256 MiB write, outside the step events)",
+                                poisson_iters_per_step=iters_p, helmholtz_iters_per_step=iters_h),
+                    roofline=roof, roofline_detail=roof_alt, cpu_baseline=cpu,
+                    e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes,
+                             steps=args.e2e_steps),
+                    gpu_launches=int(kt["kernel_launches"]), clocks=clocks,
+                    wall_s=wall, step_ms_min=min(step_ms), step_ms_max=max(step_ms),
+                    max_div=st["max_div"], kinetic=st["kinetic"], converged=bool(st["converged"]))
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

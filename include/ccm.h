@@ -1,0 +1,216 @@
+/*
+ * ccm.h - C ABI of libccm, a GB300 (sm_103a) implementation of one projection time step of
+ * the conservative Cartesian cut-cell method for the incompressible Navier-Stokes equations
+ * on staggered (MAC) grids (Quiros Rodriguez, Fullana, Le Chenadec, Sayadi,
+ * arXiv 2211.10698).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns a ccm_status; nothing else crosses the ABI (no exceptions, no exit).
+ *    On failure ccm_last_error() returns a message for the calling thread.
+ *  - A case owns all of its device memory.  Host pointers passed in are read or written
+ *    during the call only and never retained.  Sizes are element counts and are checked
+ *    (CCM_E_INVALID on mismatch).
+ *  - A case is not thread-safe; different cases may be used from different threads.
+ *  - Every field crosses the ABI as a float64 array of (ny+3) x (nx+3) elements, x
+ *    fastest ("padded layout"): element (j+1)*(nx+3) + (i+1) holds index (i, j), i in
+ *    [-1, nx+1], j in [-1, ny+1].  Index (i, j) names the pressure cell (i, j), the x-face
+ *    at x0 + i*hx (u), the y-face at y0 + j*hy (v) or the node (x0 + i*hx, y0 + j*hy),
+ *    depending on the field.
+ *  - Box sides are W=0, E=1, S=2, N=3.  A DIRICHLET side prescribes the normal velocity
+ *    component bc_un and the tangential component bc_ut (an inflow is a Dirichlet side);
+ *    an OUTFLOW side has zero-gradient velocity and zero pressure (Sec. 5.1).
+ *  - The immersed body is fixed and no-slip (Dirichlet data D = 0 in Eqs. divergence,
+ *    diag, offdiag, convective) and must stay two cells away from every box side.
+ */
+#ifndef CCM_H
+#define CCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CCM_VERSION 1
+
+typedef struct ccm_case_s* ccm_case;
+
+typedef enum {
+  CCM_OK = 0,
+  CCM_E_INVALID = 1,        /* bad argument, size or configuration */
+  CCM_E_OOM = 2,            /* device allocation failed */
+  CCM_E_CUDA = 3,           /* CUDA runtime error (message in ccm_last_error) */
+  CCM_E_NOT_CONVERGED = 4,  /* a PCG reached its iteration limit; state stays usable */
+  CCM_E_NONFINITE = 5,      /* NaN or Inf detected in the fields */
+  CCM_E_TIMEOUT = 6,        /* a device-wide barrier gave up waiting; context still usable */
+  CCM_E_STATE = 7           /* call out of order (e.g. step before set_geometry) */
+} ccm_status;
+
+enum { CCM_SIDE_W = 0, CCM_SIDE_E = 1, CCM_SIDE_S = 2, CCM_SIDE_N = 3 };
+enum { CCM_BC_DIRICHLET = 0, CCM_BC_OUTFLOW = 1 };
+enum { CCM_FP64 = 0, CCM_MIXED = 1 };         /* MIXED: FP32 inner Poisson PCG, FP64 refinement */
+enum { CCM_JACOBI = 0, CCM_CHEBYSHEV = 1 };
+enum { CCM_GEOM_NONE = 0, CCM_GEOM_CIRCLE = 1, CCM_GEOM_NACA = 2, CCM_GEOM_HALFPLANE = 3 };
+
+/* Device allocator hooks (optional).  When alloc is NULL the library uses cudaMalloc. */
+typedef void* (*ccm_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*ccm_free_fn)(void* ptr, void* ctx);
+
+/* Case description: the mesh of Sec. 3.1 (uniform spacing), the fluid constants of Sec. 4,
+ * the time step, the box boundary data and the solver settings. */
+typedef struct {
+  int nx, ny;                 /* pressure cells */
+  double x0, x1, y0, y1;      /* box */
+  double rho, mu, dt;         /* density, dynamic viscosity, time step tau */
+  int bc_type[4];             /* CCM_BC_* per side */
+  double bc_un[4], bc_ut[4];  /* Dirichlet normal / tangential velocity per side */
+  int precision;              /* CCM_FP64 or CCM_MIXED */
+  int precond;                /* Poisson preconditioner: CCM_JACOBI or CCM_CHEBYSHEV */
+  int cheb_degree;            /* Chebyshev polynomial degree (>= 1) */
+  double tol_p, tol_h;        /* relative residual targets, Poisson and Helmholtz */
+  double tol_inner;           /* MIXED: relative target of each FP32 inner solve */
+  int max_iter_p, max_iter_h; /* iteration limits */
+  int literal_offdiag;        /* 1: Eq. offdiag with separate W^xy, W^yx (not symmetric) */
+  ccm_alloc_fn alloc;
+  ccm_free_fn free;
+  void* alloc_ctx;
+  void* stream;               /* cudaStream_t for all work of the case, NULL = default */
+} ccm_config;
+
+/* Immersed body given by a level set (Sec. 3.1).  Points on the boundary count as solid. */
+typedef struct {
+  int kind;                   /* CCM_GEOM_* */
+  double cx, cy, r;           /* circle: solid where |x - c| <= r */
+  int naca_tt;                /* NACA 00tt: thickness tt percent of chord */
+  int closed_te;              /* 1: closed trailing edge (-0.1036 quartic coefficient) */
+  double chord, aoa_deg, le_x, le_y;
+  double hp_nx, hp_ny, hp_off;/* half plane: fluid where hp_nx*x + hp_ny*y > hp_off */
+} ccm_geometry;
+
+typedef struct {
+  int iters;                  /* PCG iterations (MIXED: total inner FP32 iterations) */
+  int outer;                  /* MIXED: FP64 refinement sweeps; FP64: 1 */
+  double rel_res;             /* final ||b - K x|| / ||b|| in FP64 */
+  int converged;
+} ccm_solve_stats;
+
+typedef struct {
+  int steps;                  /* steps completed by the call */
+  long long iters_p, iters_h; /* PCG iterations summed over the steps */
+  int last_iters_p, last_iters_h;
+  double last_res_p, last_res_h;
+  double max_div;             /* max |cont(U^{n+1}, D)| over active cells after the last step */
+  double kinetic;             /* sum over velocity positions of V U^2 / 2 after the last step */
+  int converged;              /* every solve of every step converged */
+} ccm_step_stats;
+
+/* Field identifiers for ccm_set_field / ccm_get_field (padded layout, float64). */
+enum {
+  CCM_F_U = 0,                /* x-velocity at u-faces (ghosts and Dirichlet faces included) */
+  CCM_F_V = 1,                /* y-velocity at v-faces */
+  CCM_F_P = 2,                /* pressure P^{n-1/2} at cells */
+  CCM_F_PHI = 3,              /* pressure increment Phi^n at cells (warm start of the Poisson PCG) */
+  CCM_F_CONV_U = 4,           /* conv^{n-1} at u-faces (Adams-Bashforth history) */
+  CCM_F_CONV_V = 5,
+  CCM_F_USTAR = 6,            /* predicted velocity U* of the last step (read only) */
+  CCM_F_VSTAR = 7,
+  CCM_F_DIV = 8,              /* cont(U*, D) of the last step (read only) */
+  CCM_F_STEP = 9,             /* first element: number of steps taken (as a double) */
+  CCM_F_CAP = 16              /* + 9*g + k: capacity k of grid g (read only), g: 0 p, 1 u,
+                                 2 v; k: 0 V, 1 X, 2 Y, 3 Ax, 4 Ay, 5 Wx, 6 Wy, 7 Bx, 8 By
+                                 (Ax/Wx at the cell's left face, Ay/Wy at its bottom face) */
+};
+
+/* Operators for ccm_apply_op.  Inputs/outputs are padded float64 arrays. */
+enum {
+  CCM_OP_CONT = 0,            /* in0=u, in1=v -> out0 = cont(U, 0) at cells (Eq. divergence) */
+  CCM_OP_PRES = 1,            /* in0=P -> out0,out1 = pres(P) on velocity unknowns (Sec. 4.1),
+                                 ghost cells of P read as 0 */
+  CCM_OP_CONV = 2,            /* in0=u, in1=v -> conv(U,U,0,0) on unknowns (Eq. convective),
+                                 Dirichlet faces and ghosts filled from the box data */
+  CCM_OP_VISC = 3,            /* in0=u, in1=v -> visc(S(U)) on unknowns (Sec. 4.2-4.3), box data
+                                 filled as for CONV, outflow rules applied */
+  CCM_OP_HELMHOLTZ = 4,       /* in0=u, in1=v -> (rho/dt) M U - mu visc(S_hom(U)) on unknowns,
+                                 identity on inactive faces (Eq. pm_prediction) */
+  CCM_OP_POISSON = 5,         /* in0=Phi -> -cont(M^-1 pres Phi, 0) on active cells, identity on
+                                 inactive cells (Eq. pm_poisson) */
+  CCM_OP_POISSON_DIAG = 6,    /* -> out0 = diagonal of the POISSON operator */
+  CCM_OP_HELMHOLTZ_DIAG = 7   /* -> out0,out1 = diagonal of the HELMHOLTZ operator */
+};
+
+/* Create a case: validates the configuration and allocates its device memory.  *out is
+ * set only on CCM_OK.  Errors: CCM_E_INVALID, CCM_E_OOM, CCM_E_CUDA. */
+ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out);
+
+/* Release every resource of the case (NULL is accepted). */
+ccm_status ccm_destroy_case(ccm_case c);
+
+/* Compute the capacities of Sec. 3 (Eqs. volumefirstkind to surfacesecondkindy, staggered
+ * per Sec. 3.4) in FP64 on the device for the p-, u- and v-grids from the body's level set
+ * (marching squares with exact edge crossings), derive the operator coefficients, discard
+ * the level set, and initialise the velocity to bc_un[W] (x) and 0 (y) on every velocity
+ * position whose control volume holds fluid.  CCM_E_INVALID if the body comes within two
+ * cells of a box side. */
+ccm_status ccm_set_geometry(ccm_case c, const ccm_geometry* g);
+
+/* Copy a host field into the case (U, V, P, PHI, CONV_U, CONV_V, STEP).  count must be
+ * (nx+3)*(ny+3) (STEP: >= 1).  Setting U or V refills the Dirichlet faces and ghosts.
+ * Errors: CCM_E_INVALID, CCM_E_STATE (before set_geometry), CCM_E_CUDA. */
+ccm_status ccm_set_field(ccm_case c, int field, const double* host, size_t count);
+
+/* Copy a field of the case to host memory (padded layout, count = (nx+3)*(ny+3); STEP:
+ * count >= 1). */
+ccm_status ccm_get_field(ccm_case c, int field, double* host, size_t count);
+
+/* Device address of a field in the case's own pitched layout (row pitch in elements in
+ * *pitch, origin at index (-1, -1)); valid until ccm_destroy_case. */
+ccm_status ccm_field_device_ptr(ccm_case c, int field, void** dptr, int* pitch);
+
+/* Apply one discrete operator (CCM_OP_*) to host arrays; unused pointers may be NULL. */
+ccm_status ccm_apply_op(ccm_case c, int op, const double* in0, const double* in1, double* out0,
+                        double* out1);
+
+/* Advance nsteps projection steps (PmII, Sec. 4.6, Eqs. pm_prediction, pm_poisson,
+ * pm_projection, pm_update) on the device-resident state.  stats may be NULL.  Returns
+ * CCM_E_NOT_CONVERGED if a solve hit its iteration limit (the step is still completed),
+ * CCM_E_TIMEOUT if a device barrier gave up, CCM_E_NONFINITE on NaN/Inf. */
+ccm_status ccm_step(ccm_case c, int nsteps, ccm_step_stats* stats);
+
+/* Enqueue nsteps projection steps on the case's stream and return without waiting; the
+ * statistics accumulate on the device until ccm_read_stats.  Same state rules as
+ * ccm_step.  Errors detected on the host only (CCM_E_STATE, CCM_E_INVALID, CCM_E_CUDA). */
+ccm_status ccm_step_async(ccm_case c, int nsteps);
+
+/* Wait for the case's stream and report the statistics accumulated since the previous
+ * ccm_step, ccm_read_stats or ccm_set_geometry call (same meaning and return codes as
+ * ccm_step). */
+ccm_status ccm_read_stats(ccm_case c, ccm_step_stats* stats);
+
+/* Per-launch timing of the dominant kernel (the Poisson PCG): when enabled, CUDA events are
+ * recorded on the case's stream around every Poisson PCG launch.  ccm_kernel_timing
+ * returns (and resets) the summed event time in ms, the number of PCG launches, the PCG
+ * iterations those launches ran, and the number of library kernel launches enqueued by the
+ * steps since the last reset.  Waits for the case's stream. */
+ccm_status ccm_enable_kernel_timing(ccm_case c, int enable);
+ccm_status ccm_kernel_timing(ccm_case c, double* poisson_ms, long long* poisson_launches,
+                             long long* poisson_iters, long long* kernel_launches);
+
+/* Solve the pressure Poisson system of Eq. pm_poisson, K Phi = rhs (rhs on active cells,
+ * padded layout, host), starting from the case's PHI field, and store the solution in PHI.
+ * With the MIXED precision setting the inner solves run in FP32 and the FP64 residual is
+ * refined to tol_p. */
+ccm_status ccm_solve_pressure(ccm_case c, const double* rhs_host, ccm_solve_stats* stats);
+
+/* Thread-local message of the last failure ("" if none). */
+const char* ccm_last_error(void);
+
+/* Library version (CCM_VERSION). */
+int ccm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCM_H */

@@ -91,6 +91,7 @@ def _load():
             "orc_step": (c_int, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP,
                                  POINTER(OrcStats)]),
             "orc_roles": (None, [cp, _DP, ip, ip, ip]),
+            "orc_predictor_rhs": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP, _DP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -274,6 +275,17 @@ class Oracle:
         a, b = c_double(0.0), c_double(0.0)
         self.lib.orc_cell_boundary(ctypes.byref(self.s), GRIDS.index(grid), i, j, ctypes.byref(a), ctypes.byref(b))
         return a.value, b.value
+
+    def predictor_rhs(self, u, v, p, cu=None, cv=None, first=True):
+        """Right-hand side of Eq. pm_prediction and conv^n from U^n (ghosts filled here)."""
+        u = np.array(u, dtype=np.float64, order="C")
+        v = np.array(v, dtype=np.float64, order="C")
+        cu = self.z() if cu is None else self._c(cu)
+        cv = self.z() if cv is None else self._c(cv)
+        ru, rv, cnu, cnv = self.z(), self.z(), self.z(), self.z()
+        self.lib.orc_predictor_rhs(ctypes.byref(self.s), _p(self.caps), _p(u), _p(v), _p(self._c(p)), _p(cu),
+                                   _p(cv), 1 if first else 0, _p(ru), _p(rv), _p(cnu), _p(cnv))
+        return ru, rv, cnu, cnv
 
     # -- time stepping ---------------------------------------------------------------------
     def init_state(self, pu=None, pv=None, u0=None, v0=0.0):

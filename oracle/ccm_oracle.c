@@ -1172,6 +1172,46 @@ void orc_init_velocity(const orc_case* c, const double* caps, double u0, double 
  * ustar/vstar and bdiv when not NULL.
  * ---------------------------------------------------------------------------------------- */
 
+/* Right-hand side of Eq. pm_prediction on the velocity unknowns (u, v: U^n, ghosts filled
+ * here; p: P^{n-1/2}; cu, cv: conv^{n-1}, replaced by conv^0 when first is set).  Returns
+ * conv^n in cnu, cnv. */
+void orc_predictor_rhs(const orc_case* c, const double* caps, double* u, double* v, const double* p, const double* cu,
+                       const double* cv, int first, double* ru, double* rv, double* cnu, double* cnv) {
+  size_t S = SIZE(c);
+  double* gu = malloc(S * sizeof(double));
+  double* gv = malloc(S * sizeof(double));
+  double* vu = malloc(S * sizeof(double));
+  double* vv = malloc(S * sizeof(double));
+  double* lu = malloc(S * sizeof(double));
+  double* lv = malloc(S * sizeof(double));
+  const double* Vu = CAP(c, caps, G_U, K_V);
+  const double* Vv = CAP(c, caps, G_V, K_V);
+  double rho = c->rho, dt = c->dt, mu = c->mu;
+  fill_bc(c, u, v, 1.0);
+  orc_conv_bc(c, caps, u, v, cnu, cnv);
+  const double* pu = first ? cnu : cu;
+  const double* pv = first ? cnv : cv;
+  orc_pres_bc(c, caps, p, gu, gv);
+  orc_visc_bc(c, caps, u, v, vu, vv);
+  /* lifting of the implicit half: visc(mu S(0, D^{n+1})) from the box boundary values */
+  {
+    double* zu = calloc(S, sizeof(double));
+    double* zv = calloc(S, sizeof(double));
+    orc_visc_bc(c, caps, zu, zv, lu, lv);
+    free(zu); free(zv);
+  }
+  for (size_t k = 0; k < S; ++k) {
+    ru[k] = (rho / dt) * Vu[k] * u[k] - 1.5 * rho * cnu[k] + 0.5 * rho * pu[k] - gu[k] + mu * vu[k] + mu * lu[k];
+    rv[k] = (rho / dt) * Vv[k] * v[k] - 1.5 * rho * cnv[k] + 0.5 * rho * pv[k] - gv[k] + mu * vv[k] + mu * lv[k];
+  }
+  for (int j = -1; j <= c->ny + 1; ++j)
+    for (int i = -1; i <= c->nx + 1; ++i) {
+      if (role_u(c, caps, i, j) != 3) AT(c, ru, i, j) = 0.0;
+      if (role_v(c, caps, i, j) != 3) AT(c, rv, i, j) = 0.0;
+    }
+  free(gu); free(gv); free(vu); free(vv); free(lu); free(lv);
+}
+
 int orc_step(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
              double* cv, int first, double* ustar, double* vstar, double* bdiv, orc_stats* st) {
   size_t S = SIZE(c);
@@ -1179,10 +1219,6 @@ int orc_step(const orc_case* c, const double* caps, double* u, double* v, double
   double* cnv = malloc(S * sizeof(double));
   double* gu = malloc(S * sizeof(double));
   double* gv = malloc(S * sizeof(double));
-  double* vu = malloc(S * sizeof(double));
-  double* vv = malloc(S * sizeof(double));
-  double* lu = malloc(S * sizeof(double));
-  double* lv = malloc(S * sizeof(double));
   double* ru = malloc(S * sizeof(double));
   double* rv = malloc(S * sizeof(double));
   double* xu = malloc(S * sizeof(double));
@@ -1194,24 +1230,8 @@ int orc_step(const orc_case* c, const double* caps, double* u, double* v, double
   const double* Vp = CAP(c, caps, G_P, K_V);
   double rho = c->rho, dt = c->dt, mu = c->mu;
 
-  fill_bc(c, u, v, 1.0);
-  orc_conv_bc(c, caps, u, v, cnu, cnv);
-  if (first) {
-    memcpy(cu, cnu, S * sizeof(double));
-    memcpy(cv, cnv, S * sizeof(double));
-  }
-  orc_pres_bc(c, caps, p, gu, gv);
-  orc_visc_bc(c, caps, u, v, vu, vv);
-  /* lifting of the implicit half: visc(mu S(0, D^{n+1})) from the box boundary values */
-  {
-    double* zu = calloc(S, sizeof(double));
-    double* zv = calloc(S, sizeof(double));
-    orc_visc_bc(c, caps, zu, zv, lu, lv);
-    free(zu); free(zv);
-  }
+  orc_predictor_rhs(c, caps, u, v, p, cu, cv, first, ru, rv, cnu, cnv);
   for (size_t k = 0; k < S; ++k) {
-    ru[k] = (rho / dt) * Vu[k] * u[k] - 1.5 * rho * cnu[k] + 0.5 * rho * cu[k] - gu[k] + mu * vu[k] + mu * lu[k];
-    rv[k] = (rho / dt) * Vv[k] * v[k] - 1.5 * rho * cnv[k] + 0.5 * rho * cv[k] - gv[k] + mu * vv[k] + mu * lv[k];
     xu[k] = u[k];
     xv[k] = v[k];
   }
@@ -1252,7 +1272,7 @@ int orc_step(const orc_case* c, const double* caps, double* u, double* v, double
   st->conv_p = ok_p;
   st->max_div = orc_max_div(c, caps, u, v);
   st->kinetic = orc_kinetic(c, caps, u, v);
-  free(cnu); free(cnv); free(gu); free(gv); free(vu); free(vv); free(lu); free(lv);
+  free(cnu); free(cnv); free(gu); free(gv);
   free(ru); free(rv); free(xu); free(xv); free(b); free(kp);
   return ok_h && ok_p;
 }

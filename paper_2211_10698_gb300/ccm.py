@@ -1,0 +1,259 @@
+"""ctypes binding of libccm (include/ccm.h).  Argument marshalling only: every step of the
+computation runs in the CUDA library, and importing this module fails loudly when the
+library has not been built.
+
+The functions keep the C names (``ccm_create_case``, ``ccm_step``, ...).  ``Case`` is a
+small owner object that builds a ``ccm_config`` from a ``paper_2211_10698_gb300.inputs.Case``
+and releases the library case when it goes away.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import CFUNCTYPE, POINTER, Structure, c_double, c_int, c_longlong, c_size_t, c_void_p
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libccm.so")
+
+CCM_OK, CCM_E_INVALID, CCM_E_OOM, CCM_E_CUDA, CCM_E_NOT_CONVERGED, CCM_E_NONFINITE, CCM_E_TIMEOUT, CCM_E_STATE = range(8)
+STATUS_NAMES = ["CCM_OK", "CCM_E_INVALID", "CCM_E_OOM", "CCM_E_CUDA", "CCM_E_NOT_CONVERGED", "CCM_E_NONFINITE",
+                "CCM_E_TIMEOUT", "CCM_E_STATE"]
+CCM_FP64, CCM_MIXED = 0, 1
+CCM_JACOBI, CCM_CHEBYSHEV = 0, 1
+CCM_F_U, CCM_F_V, CCM_F_P, CCM_F_PHI, CCM_F_CONV_U, CCM_F_CONV_V, CCM_F_USTAR, CCM_F_VSTAR, CCM_F_DIV, CCM_F_STEP = range(10)
+CCM_F_CAP = 16
+(CCM_OP_CONT, CCM_OP_PRES, CCM_OP_CONV, CCM_OP_VISC, CCM_OP_HELMHOLTZ, CCM_OP_POISSON, CCM_OP_POISSON_DIAG,
+ CCM_OP_HELMHOLTZ_DIAG) = range(8)
+CAP_NAMES = ("V", "X", "Y", "AX", "AY", "WX", "WY", "BX", "BY")
+GRIDS = ("p", "u", "v")
+
+ccm_alloc_fn = CFUNCTYPE(c_void_p, c_size_t, c_void_p)
+ccm_free_fn = CFUNCTYPE(None, c_void_p, c_void_p)
+
+
+class ccm_config(Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int),
+                ("x0", c_double), ("x1", c_double), ("y0", c_double), ("y1", c_double),
+                ("rho", c_double), ("mu", c_double), ("dt", c_double),
+                ("bc_type", c_int * 4), ("bc_un", c_double * 4), ("bc_ut", c_double * 4),
+                ("precision", c_int), ("precond", c_int), ("cheb_degree", c_int),
+                ("tol_p", c_double), ("tol_h", c_double), ("tol_inner", c_double),
+                ("max_iter_p", c_int), ("max_iter_h", c_int), ("literal_offdiag", c_int),
+                ("alloc", ccm_alloc_fn), ("free", ccm_free_fn), ("alloc_ctx", c_void_p),
+                ("stream", c_void_p)]
+
+
+class ccm_geometry(Structure):
+    _fields_ = [("kind", c_int), ("cx", c_double), ("cy", c_double), ("r", c_double),
+                ("naca_tt", c_int), ("closed_te", c_int),
+                ("chord", c_double), ("aoa_deg", c_double), ("le_x", c_double), ("le_y", c_double),
+                ("hp_nx", c_double), ("hp_ny", c_double), ("hp_off", c_double)]
+
+
+class ccm_solve_stats(Structure):
+    _fields_ = [("iters", c_int), ("outer", c_int), ("rel_res", c_double), ("converged", c_int)]
+
+
+class ccm_step_stats(Structure):
+    _fields_ = [("steps", c_int), ("iters_p", c_longlong), ("iters_h", c_longlong),
+                ("last_iters_p", c_int), ("last_iters_h", c_int),
+                ("last_res_p", c_double), ("last_res_h", c_double),
+                ("max_div", c_double), ("kinetic", c_double), ("converged", c_int)]
+
+
+class CcmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_DP = POINTER(c_double)
+
+
+def lib():
+    """Load libccm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libccm.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(_LIB_PATH)
+        cp = c_void_p
+        sigs = {
+            "ccm_version": (c_int, []),
+            "ccm_last_error": (ctypes.c_char_p, []),
+            "ccm_create_case": (c_int, [POINTER(ccm_config), POINTER(c_void_p)]),
+            "ccm_destroy_case": (c_int, [cp]),
+            "ccm_set_geometry": (c_int, [cp, POINTER(ccm_geometry)]),
+            "ccm_set_field": (c_int, [cp, c_int, _DP, c_size_t]),
+            "ccm_get_field": (c_int, [cp, c_int, _DP, c_size_t]),
+            "ccm_field_device_ptr": (c_int, [cp, c_int, POINTER(c_void_p), POINTER(c_int)]),
+            "ccm_apply_op": (c_int, [cp, c_int, _DP, _DP, _DP, _DP]),
+            "ccm_step": (c_int, [cp, c_int, POINTER(ccm_step_stats)]),
+            "ccm_solve_pressure": (c_int, [cp, _DP, POINTER(ccm_solve_stats)]),
+            "ccm_step_async": (c_int, [cp, c_int]),
+            "ccm_read_stats": (c_int, [cp, POINTER(ccm_step_stats)]),
+            "ccm_enable_kernel_timing": (c_int, [cp, c_int]),
+            "ccm_kernel_timing": (c_int, [cp, POINTER(c_double), POINTER(c_longlong), POINTER(c_longlong),
+                                          POINTER(c_longlong)]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, allow=()):
+    if status != CCM_OK and status not in allow:
+        raise CcmError(status, lib().ccm_last_error().decode())
+    return status
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DP)
+
+
+def make_config(case, precision=None, precond=None, stream=None) -> ccm_config:
+    cfg = ccm_config()
+    cfg.nx, cfg.ny = case.nx, case.ny
+    cfg.x0, cfg.x1, cfg.y0, cfg.y1 = case.x0, case.x1, case.y0, case.y1
+    cfg.rho, cfg.mu, cfg.dt = case.rho, case.mu, case.dt
+    for s in range(4):
+        cfg.bc_type[s] = int(case.bc_type[s])
+        cfg.bc_un[s] = float(case.bc_un[s])
+        cfg.bc_ut[s] = float(case.bc_ut[s])
+    prec = precision if precision is not None else case.precision
+    cfg.precision = CCM_MIXED if prec == "mixed" else CCM_FP64
+    pc = precond if precond is not None else case.precond
+    cfg.precond = CCM_CHEBYSHEV if pc == "chebyshev" else CCM_JACOBI
+    cfg.cheb_degree = case.cheb_degree
+    cfg.tol_p, cfg.tol_h, cfg.tol_inner = case.tol_p, case.tol_h, case.tol_inner
+    cfg.max_iter_p, cfg.max_iter_h = case.max_iter_p, case.max_iter_h
+    cfg.literal_offdiag = int(case.literal_offdiag)
+    cfg.stream = stream
+    return cfg
+
+
+def make_geometry(geom) -> ccm_geometry:
+    g = ccm_geometry()
+    g.kind = geom.kind
+    g.cx, g.cy, g.r = geom.cx, geom.cy, geom.r
+    g.naca_tt, g.closed_te = geom.naca_tt, geom.closed_te
+    g.chord, g.aoa_deg, g.le_x, g.le_y = geom.chord, geom.aoa_deg, geom.le_x, geom.le_y
+    g.hp_nx, g.hp_ny, g.hp_off = geom.hp_nx, geom.hp_ny, geom.hp_off
+    return g
+
+
+class TorchAllocator:
+    """Device memory for cases from PyTorch's caching allocator (through the ccm_config
+    allocator hooks)."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+
+        def _alloc(nbytes, ctx):
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+
+        def _free(ptr, ctx):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = ccm_alloc_fn(_alloc)
+        self.free = ccm_free_fn(_free)
+
+
+class Case:
+    """A library case built from an ``inputs.Case``; geometry is set at construction."""
+
+    def __init__(self, case, precision=None, precond=None, stream=None, allocator=None, set_geometry=True):
+        self.spec = case
+        self.shape = case.shape
+        self.n = case.shape[0] * case.shape[1]
+        self.cfg = make_config(case, precision, precond, stream)
+        self._allocator = allocator
+        if allocator is not None:
+            self.cfg.alloc = allocator.alloc
+            self.cfg.free = allocator.free
+        h = c_void_p()
+        _check(lib().ccm_create_case(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self.h = h
+        if set_geometry:
+            self.set_geometry(case.geom)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().ccm_destroy_case(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_geometry(self, geom):
+        g = make_geometry(geom)
+        _check(lib().ccm_set_geometry(self.h, ctypes.byref(g)))
+
+    def set_field(self, field, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64)
+        assert a.shape == self.shape
+        _check(lib().ccm_set_field(self.h, field, _ptr(a), a.size))
+
+    def get_field(self, field, out=None):
+        a = np.empty(self.shape) if out is None else out
+        assert a.shape == self.shape and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        _check(lib().ccm_get_field(self.h, field, _ptr(a), a.size))
+        return a
+
+    def cap(self, grid, name):
+        return self.get_field(CCM_F_CAP + 9 * GRIDS.index(grid) + CAP_NAMES.index(name))
+
+    def apply(self, op, in0=None, in1=None, nout=2):
+        i0 = None if in0 is None else np.ascontiguousarray(in0, dtype=np.float64)
+        i1 = None if in1 is None else np.ascontiguousarray(in1, dtype=np.float64)
+        o0 = np.zeros(self.shape)
+        o1 = np.zeros(self.shape) if nout > 1 else None
+        _check(lib().ccm_apply_op(self.h, op, _ptr(i0), _ptr(i1), _ptr(o0), _ptr(o1)))
+        return (o0, o1) if nout > 1 else o0
+
+    def step(self, n=1, allow_not_converged=False):
+        st = ccm_step_stats()
+        allow = (CCM_E_NOT_CONVERGED,) if allow_not_converged else ()
+        _check(lib().ccm_step(self.h, n, ctypes.byref(st)), allow)
+        return {f: getattr(st, f) for f, _ in ccm_step_stats._fields_}
+
+    def step_async(self, n=1):
+        _check(lib().ccm_step_async(self.h, n))
+
+    def read_stats(self, allow_not_converged=False):
+        st = ccm_step_stats()
+        allow = (CCM_E_NOT_CONVERGED,) if allow_not_converged else ()
+        _check(lib().ccm_read_stats(self.h, ctypes.byref(st)), allow)
+        return {f: getattr(st, f) for f, _ in ccm_step_stats._fields_}
+
+    def enable_kernel_timing(self, on=True):
+        _check(lib().ccm_enable_kernel_timing(self.h, 1 if on else 0))
+
+    def kernel_timing(self):
+        ms, nl, it, kl = c_double(), c_longlong(), c_longlong(), c_longlong()
+        _check(lib().ccm_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(it), ctypes.byref(kl)))
+        return dict(poisson_ms=ms.value, poisson_launches=nl.value, poisson_iters=it.value, kernel_launches=kl.value)
+
+    def solve_pressure(self, rhs):
+        r = np.ascontiguousarray(rhs, dtype=np.float64)
+        st = ccm_solve_stats()
+        _check(lib().ccm_solve_pressure(self.h, _ptr(r), ctypes.byref(st)), (CCM_E_NOT_CONVERGED,))
+        return {f: getattr(st, f) for f, _ in ccm_solve_stats._fields_}
+
+    def device_ptr(self, field):
+        p = c_void_p()
+        pitch = c_int()
+        _check(lib().ccm_field_device_ptr(self.h, field, ctypes.byref(p), ctypes.byref(pitch)))
+        return p.value, pitch.value

@@ -1,0 +1,675 @@
+// C ABI of libccm (include/ccm.h): case lifecycle, set-up from the body geometry, field
+// exchange, single-operator application, the PmII step (Sec. 4.6) and the pressure solve.
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "ccm_host.h"
+
+using namespace ccm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ccm_status fail(ccm_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) return fail(CCM_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DevStats {
+  long long total_p, total_h;
+  int iters_p, iters_h;
+  double rr_p, bb_p, rr_h, bb_h;
+  int conv_p, conv_h;
+  int nconv;
+  int pad;
+  double diag[3];  // max |cont|, kinetic, non-finite flag
+};
+
+}  // namespace
+
+struct ccm_case_s {
+  ccm_config cfg;
+  Geom g;
+  Bc bc;
+  Phys ph;
+  cudaStream_t st;
+  void* slab = nullptr;
+  size_t slab_bytes = 0;
+  CapPtrs caps;
+  CoefPtrs co;
+  Coefs cv;
+  // state
+  double *u, *v, *p, *phi, *cnu[2], *cnv[2];
+  int cur = 0;
+  long long nstep = 0;
+  // step work
+  double *ustar, *vstar, *div, *rhs_u, *rhs_v, *rhs_p;
+  double *pr, *pz, *pp0, *pp1, *pq;
+  double *hr_u, *hr_v, *hz_u, *hz_v, *hp_u, *hp_v, *hq_u, *hq_v;
+  float *fx, *fb, *fr, *fz, *fp0, *fp1, *fq;
+  double *t0, *t1, *t2, *t3, *t4, *t5;
+  double* partials;
+  double* dpart;
+  unsigned int* bar_count;
+  int* bar_err;
+  DevStats* ds;
+  bool geometry = false;
+  double n_act = 0.0;
+  int zero_mean = 0;
+  // timing of the Poisson PCG launches (events recorded on the case's stream)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  long long launches = 0, poisson_launches = 0;
+  long long poisson_iters_timed = 0;
+  double poisson_ms = 0.0;
+  long long steps_pending = 0;
+};
+
+namespace {
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+void carve(ccm_case c, Carver& cv) {
+  const size_t N = c->g.count();
+  for (int s = 0; s < 27; ++s) c->caps.a[s] = cv.take<double>(N);
+  CoefPtrs& o = c->co;
+  o.role_u = cv.take<int8_t>(N);
+  o.role_v = cv.take<int8_t>(N);
+  o.act = cv.take<int8_t>(N);
+  double** dd[] = {&o.cu, &o.cv, &o.invdk, &o.diagk, &o.gfu, &o.gfv, &o.pfac, &o.massu, &o.massv, &o.wxx, &o.wyy,
+                   &o.wxa, &o.wxb, &o.invdhu, &o.invdhv, &o.liftu, &o.liftv};
+  for (double** p : dd) *p = cv.take<double>(N);
+  o.cu32 = cv.take<float>(N);
+  o.cv32 = cv.take<float>(N);
+  o.invdk32 = cv.take<float>(N);
+  double** st[] = {&c->u, &c->v, &c->p, &c->phi, &c->cnu[0], &c->cnu[1], &c->cnv[0], &c->cnv[1],
+                   &c->ustar, &c->vstar, &c->div, &c->rhs_u, &c->rhs_v, &c->rhs_p,
+                   &c->pr, &c->pz, &c->pp0, &c->pp1, &c->pq,
+                   &c->hr_u, &c->hr_v, &c->hz_u, &c->hz_v, &c->hp_u, &c->hp_v, &c->hq_u, &c->hq_v,
+                   &c->t0, &c->t1, &c->t2, &c->t3, &c->t4, &c->t5};
+  for (double** p : st) *p = cv.take<double>(N);
+  float** fl[] = {&c->fx, &c->fb, &c->fr, &c->fz, &c->fp0, &c->fp1, &c->fq};
+  for (float** p : fl) *p = cv.take<float>(N);
+  c->partials = cv.take<double>((size_t)pcg_partials_needed());
+  c->dpart = cv.take<double>((size_t)3 * diagnostics_partials(c->g) + 8);
+  c->bar_count = cv.take<unsigned int>(4);
+  c->bar_err = cv.take<int>(4);
+  c->ds = cv.take<DevStats>(1);
+}
+
+void make_view(ccm_case c) {
+  const CoefPtrs& o = c->co;
+  Coefs& v = c->cv;
+  v.role_u = o.role_u; v.role_v = o.role_v; v.act = o.act;
+  v.ax = c->caps.a[cap_slot(0, CK_AX)];
+  v.ay = c->caps.a[cap_slot(0, CK_AY)];
+  v.bxx = c->caps.a[cap_slot(1, CK_BX)];
+  v.bxy = c->caps.a[cap_slot(1, CK_BY)];
+  v.byx = c->caps.a[cap_slot(2, CK_BX)];
+  v.byy = c->caps.a[cap_slot(2, CK_BY)];
+  v.wxx = o.wxx; v.wyy = o.wyy; v.wxa = o.wxa; v.wxb = o.wxb;
+  v.cu = o.cu; v.cv = o.cv; v.invdk = o.invdk;
+  v.gfu = o.gfu; v.gfv = o.gfv; v.pfac = o.pfac;
+  v.massu = o.massu; v.massv = o.massv;
+  v.invdhu = o.invdhu; v.invdhv = o.invdhv;
+  v.liftu = o.liftu; v.liftv = o.liftv;
+  v.cu32 = o.cu32; v.cv32 = o.cv32; v.invdk32 = o.invdk32;
+}
+
+size_t host_count(ccm_case c) { return (size_t)(c->g.nx + 3) * (size_t)(c->g.ny + 3); }
+
+ccm_status upload(ccm_case c, double* dst, const double* host) {
+  CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)c->g.pitch * sizeof(double), host, (size_t)(c->g.nx + 3) * sizeof(double),
+                             (size_t)(c->g.nx + 3) * sizeof(double), (size_t)(c->g.ny + 3), cudaMemcpyHostToDevice,
+                             c->st));
+  return CCM_OK;
+}
+
+ccm_status download(ccm_case c, double* host, const double* src) {
+  CUDA_TRY(cudaMemcpy2DAsync(host, (size_t)(c->g.nx + 3) * sizeof(double), src, (size_t)c->g.pitch * sizeof(double),
+                             (size_t)(c->g.nx + 3) * sizeof(double), (size_t)(c->g.ny + 3), cudaMemcpyDeviceToHost,
+                             c->st));
+  return CCM_OK;
+}
+
+__global__ void k_init_velocity(Geom g, const int8_t* ru, double u0, double* u, double* v) {
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
+  const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
+  if (i > g.nx + 1 || j > g.ny + 1) return;
+  const size_t k = g.idx(i, j);
+  u[k] = ru[k] == R_UNKNOWN ? u0 : 0.0;
+  v[k] = 0.0;
+}
+
+// Zero the velocity positions that are not unknowns or Dirichlet faces' neighbours of the
+// fill (inactive faces hold zero).
+__global__ void k_mask_inactive(Geom g, const int8_t* ru, const int8_t* rv, double* u, double* v) {
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
+  const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
+  if (i > g.nx + 1 || j > g.ny + 1) return;
+  const size_t k = g.idx(i, j);
+  if (ru[k] == R_INACTIVE) u[k] = 0.0;
+  if (rv[k] == R_INACTIVE) v[k] = 0.0;
+}
+
+__global__ void k_mask_cells(Geom g, const int8_t* act, double* x) {
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
+  const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
+  if (i > g.nx + 1 || j > g.ny + 1) return;
+  const size_t k = g.idx(i, j);
+  if (!act[k]) x[k] = 0.0;
+}
+
+dim3 grid_of(const Geom& g, dim3 b) { return dim3((g.nx + 3 + b.x - 1) / b.x, (g.ny + 3 + b.y - 1) / b.y); }
+
+// Conservative bounding box of the body, to check the two-cell margin to the box sides.
+void body_bbox(const ccm_geometry& geo, double& xa, double& xb, double& ya, double& yb) {
+  if (geo.kind == CCM_GEOM_CIRCLE) {
+    xa = geo.cx - geo.r; xb = geo.cx + geo.r; ya = geo.cy - geo.r; yb = geo.cy + geo.r;
+    return;
+  }
+  double a = geo.aoa_deg * (M_PI / 180.0), ca = cos(a), sa = sin(a);
+  double t = geo.naca_tt / 100.0;
+  xa = ya = 1e300; xb = yb = -1e300;
+  for (int s = 0; s <= 2000; ++s) {
+    double xi = s / 2000.0;
+    double yt = 5.0 * t * (0.2969 * sqrt(xi) - 0.1260 * xi - 0.3516 * xi * xi + 0.2843 * xi * xi * xi - 0.1036 * xi * xi * xi * xi);
+    for (int sg = -1; sg <= 1; sg += 2) {
+      double eta = sg * (yt + 1e-3);
+      // inverse rotation of (xi, eta) * chord
+      double px = geo.chord * (xi * ca + eta * sa), py = geo.chord * (-xi * sa + eta * ca);
+      double X = geo.le_x + px, Y = geo.le_y + py;
+      xa = fmin(xa, X); xb = fmax(xb, X); ya = fmin(ya, Y); yb = fmax(yb, Y);
+    }
+  }
+}
+
+ccm_status check_cuda_errors(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CCM_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return CCM_OK;
+}
+
+ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
+  PoissonSolve<double> a{};
+  a.g = c->g;
+  a.cu = c->co.cu; a.cv = c->co.cv; a.invd = c->co.invdk; a.act = c->co.act;
+  a.x = x; a.b = b; a.r = c->pr; a.z = c->pz; a.p0 = c->pp0; a.p1 = c->pp1; a.q = c->pq;
+  a.tol = c->cfg.tol_p; a.max_iter = c->cfg.max_iter_p;
+  a.zero_mean = c->zero_mean; a.n_act = c->n_act;
+  a.partials = c->partials;
+  a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+  a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
+  CUDA_TRY(run_poisson_pcg<double>(a, c->st));
+  return CCM_OK;
+}
+
+ccm_status solve_helmholtz(ccm_case c) {
+  HelmholtzSolve a{};
+  a.c = c->cv; a.g = c->g; a.bc = c->bc; a.ph = c->ph;
+  a.xu = c->u; a.xv = c->v; a.bu = c->rhs_u; a.bv = c->rhs_v;
+  a.ru = c->hr_u; a.rv = c->hr_v; a.zu = c->hz_u; a.zv = c->hz_v;
+  a.pu = c->hp_u; a.pv = c->hp_v; a.qu = c->hq_u; a.qv = c->hq_v;
+  a.tol = c->cfg.tol_h; a.max_iter = c->cfg.max_iter_h;
+  a.partials = c->partials;
+  a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+  a.out = PcgOut{&c->ds->iters_h, &c->ds->rr_h, &c->ds->bb_h, &c->ds->conv_h, &c->ds->total_h, &c->ds->nconv};
+  CUDA_TRY(run_helmholtz_pcg(a, c->st));
+  return CCM_OK;
+}
+
+cudaEvent_t next_event(ccm_case c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+ccm_status poisson_solve(ccm_case c, double* x, double* b) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    e0 = next_event(c);
+    e1 = next_event(c);
+    if (e0) cudaEventRecord(e0, c->st);
+  }
+  ccm_status s = solve_poisson_fp64(c, x, b);
+  if (c->timing && e1) cudaEventRecord(e1, c->st);
+  c->poisson_launches++;
+  c->launches += c->zero_mean ? 5 : 1;
+  return s;
+}
+
+// Sum the recorded Poisson PCG event pairs (after the stream has drained).
+void collect_timing(ccm_case c) {
+  for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[k], c->ev_pool[k + 1]) == cudaSuccess) c->poisson_ms += ms;
+  }
+  c->ev_used = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccm_version(void) { return CCM_VERSION; }
+
+const char* ccm_last_error(void) { return g_last_error.c_str(); }
+
+ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
+  g_last_error.clear();
+  if (!cfg || !out) return fail(CCM_E_INVALID, "null argument");
+  if (cfg->nx < 4 || cfg->ny < 4) return fail(CCM_E_INVALID, "nx and ny must be >= 4");
+  if ((long long)(cfg->nx + 3) * (cfg->ny + 3) > (1LL << 31) - 1024) return fail(CCM_E_INVALID, "grid too large");
+  if (!(cfg->x1 > cfg->x0) || !(cfg->y1 > cfg->y0)) return fail(CCM_E_INVALID, "empty box");
+  if (!(cfg->rho > 0) || !(cfg->mu >= 0) || !(cfg->dt > 0)) return fail(CCM_E_INVALID, "rho, dt must be > 0, mu >= 0");
+  for (int s = 0; s < 4; ++s)
+    if (cfg->bc_type[s] != CCM_BC_DIRICHLET && cfg->bc_type[s] != CCM_BC_OUTFLOW)
+      return fail(CCM_E_INVALID, "unknown boundary type");
+  if (cfg->precision != CCM_FP64 && cfg->precision != CCM_MIXED) return fail(CCM_E_INVALID, "unknown precision");
+  if (cfg->precond != CCM_JACOBI && cfg->precond != CCM_CHEBYSHEV) return fail(CCM_E_INVALID, "unknown preconditioner");
+  if (!(cfg->tol_p > 0) || !(cfg->tol_h > 0) || cfg->max_iter_p < 1 || cfg->max_iter_h < 1)
+    return fail(CCM_E_INVALID, "solver tolerances and limits must be positive");
+  ccm_case c = new ccm_case_s();
+  c->cfg = *cfg;
+  c->g.nx = cfg->nx;
+  c->g.ny = cfg->ny;
+  c->g.pitch = ((cfg->nx + 3) + 31) / 32 * 32;
+  c->g.x0 = cfg->x0;
+  c->g.y0 = cfg->y0;
+  c->g.hx = (cfg->x1 - cfg->x0) / cfg->nx;
+  c->g.hy = (cfg->y1 - cfg->y0) / cfg->ny;
+  for (int s = 0; s < 4; ++s) {
+    c->bc.type[s] = cfg->bc_type[s];
+    c->bc.un[s] = cfg->bc_un[s];
+    c->bc.ut[s] = cfg->bc_ut[s];
+  }
+  c->ph = Phys{cfg->rho, cfg->mu, cfg->dt};
+  c->st = (cudaStream_t)cfg->stream;
+  Carver dry{nullptr};
+  carve(c, dry);
+  c->slab_bytes = dry.off + 256;
+  void* mem = nullptr;
+  if (cfg->alloc) {
+    mem = cfg->alloc(c->slab_bytes, cfg->alloc_ctx);
+    if (!mem) { delete c; return fail(CCM_E_OOM, "allocator hook returned NULL"); }
+  } else {
+    cudaError_t e = cudaMalloc(&mem, c->slab_bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); delete c; return fail(CCM_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+  }
+  c->slab = mem;
+  Carver real{(char*)(((uintptr_t)mem + 255) & ~(uintptr_t)255)};
+  carve(c, real);
+  make_view(c);
+  cudaError_t e = cudaMemsetAsync(mem, 0, c->slab_bytes, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) {
+    if (cfg->free) cfg->free(mem, cfg->alloc_ctx); else cudaFree(mem);
+    delete c;
+    return fail(CCM_E_CUDA, std::string("initialising case memory: ") + cudaGetErrorString(e));
+  }
+  *out = c;
+  return CCM_OK;
+}
+
+ccm_status ccm_destroy_case(ccm_case c) {
+  if (!c) return CCM_OK;
+  cudaStreamSynchronize(c->st);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->slab) {
+    if (c->cfg.free) c->cfg.free(c->slab, c->cfg.alloc_ctx);
+    else cudaFree(c->slab);
+  }
+  delete c;
+  return CCM_OK;
+}
+
+ccm_status ccm_set_geometry(ccm_case c, const ccm_geometry* geo) {
+  g_last_error.clear();
+  if (!c || !geo) return fail(CCM_E_INVALID, "null argument");
+  if (geo->kind < CCM_GEOM_NONE || geo->kind > CCM_GEOM_HALFPLANE) return fail(CCM_E_INVALID, "unknown geometry kind");
+  if (geo->kind == CCM_GEOM_CIRCLE && !(geo->r > 0)) return fail(CCM_E_INVALID, "circle radius must be > 0");
+  if (geo->kind == CCM_GEOM_NACA && (!(geo->chord > 0) || geo->naca_tt < 1 || geo->naca_tt > 40))
+    return fail(CCM_E_INVALID, "bad NACA parameters");
+  if (geo->kind == CCM_GEOM_HALFPLANE && geo->hp_nx == 0.0 && geo->hp_ny == 0.0)
+    return fail(CCM_E_INVALID, "half plane normal is zero");
+  const Geom& g = c->g;
+  if (geo->kind == CCM_GEOM_CIRCLE || geo->kind == CCM_GEOM_NACA) {
+    double xa, xb, ya, yb;
+    body_bbox(*geo, xa, xb, ya, yb);
+    const double mx = 2.5 * g.hx, my = 2.5 * g.hy;
+    if (xa < c->cfg.x0 + mx || xb > c->cfg.x1 - mx || ya < c->cfg.y0 + my || yb > c->cfg.y1 - my)
+      return fail(CCM_E_INVALID, "the body must stay two cells away from every box side");
+  }
+  cudaStream_t st = c->st;
+  CUDA_TRY(launch_capacities(*geo, g, c->caps.a, st));
+  launch_derive(g, c->bc, c->ph, c->cfg.literal_offdiag, c->caps, c->co, st);
+  // lifting of the box data through the viscous operator: visc(S(0, D))
+  CUDA_TRY(cudaMemsetAsync(c->t0, 0, g.count() * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(c->t1, 0, g.count() * sizeof(double), st));
+  launch_fill_bc(g, c->bc, c->t0, c->t1, 1.0, st);
+  launch_visc(c->cv, g, c->bc, c->t0, c->t1, c->co.liftu, c->co.liftv, st);
+  // Jacobi diagonal of the Helmholtz operator by colour probing
+  launch_helmholtz_diag(c->cv, g, c->bc, c->ph, c->t0, c->t1, c->t2, c->t3, c->t4, c->t5, c->co.invdhu, c->co.invdhv,
+                        st);
+  // state
+  const size_t bytes = g.count() * sizeof(double);
+  for (double* a : {c->p, c->phi, c->cnu[0], c->cnu[1], c->cnv[0], c->cnv[1], c->ustar, c->vstar, c->div})
+    CUDA_TRY(cudaMemsetAsync(a, 0, bytes, st));
+  const dim3 b(64, 4);
+  k_init_velocity<<<grid_of(g, b), b, 0, st>>>(g, c->co.role_u, c->cfg.bc_un[CCM_SIDE_W], c->u, c->v);
+  launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
+  CUDA_TRY(cudaMemsetAsync(c->ds, 0, sizeof(DevStats), st));
+  CUDA_TRY(cudaMemsetAsync(c->bar_err, 0, sizeof(int), st));
+  // number of active cells
+  std::vector<int8_t> act(g.count());
+  CUDA_TRY(cudaMemcpyAsync(act.data(), c->co.act, g.count(), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  ccm_status s = check_cuda_errors("set_geometry");
+  if (s != CCM_OK) return s;
+  long long na = 0;
+  for (int8_t a : act) na += a;
+  if (na == 0) return fail(CCM_E_INVALID, "no fluid cell");
+  c->n_act = (double)na;
+  c->zero_mean = 1;
+  for (int q = 0; q < 4; ++q)
+    if (c->bc.type[q] == CCM_BC_OUTFLOW) c->zero_mean = 0;
+  c->cur = 0;
+  c->nstep = 0;
+  c->geometry = true;
+  return CCM_OK;
+}
+
+static double* field_ptr(ccm_case c, int field) {
+  switch (field) {
+    case CCM_F_U: return c->u;
+    case CCM_F_V: return c->v;
+    case CCM_F_P: return c->p;
+    case CCM_F_PHI: return c->phi;
+    case CCM_F_CONV_U: return c->cnu[c->cur];
+    case CCM_F_CONV_V: return c->cnv[c->cur];
+    case CCM_F_USTAR: return c->ustar;
+    case CCM_F_VSTAR: return c->vstar;
+    case CCM_F_DIV: return c->div;
+    default:
+      if (field >= CCM_F_CAP && field < CCM_F_CAP + 27) return c->caps.a[field - CCM_F_CAP];
+      return nullptr;
+  }
+}
+
+ccm_status ccm_set_field(ccm_case c, int field, const double* host, size_t count) {
+  g_last_error.clear();
+  if (!c || !host) return fail(CCM_E_INVALID, "null argument");
+  if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
+  if (field == CCM_F_STEP) {
+    if (count < 1) return fail(CCM_E_INVALID, "count");
+    c->nstep = (long long)host[0];
+    return CCM_OK;
+  }
+  if (field > CCM_F_CONV_V || field < 0) return fail(CCM_E_INVALID, "field is read-only or unknown");
+  if (count != host_count(c)) return fail(CCM_E_INVALID, "count must be (nx+3)*(ny+3)");
+  ccm_status s = upload(c, field_ptr(c, field), host);
+  if (s != CCM_OK) return s;
+  const dim3 b(64, 4);
+  if (field == CCM_F_U || field == CCM_F_V) {
+    k_mask_inactive<<<grid_of(c->g, b), b, 0, c->st>>>(c->g, c->co.role_u, c->co.role_v, c->u, c->v);
+    launch_fill_bc(c->g, c->bc, c->u, c->v, 1.0, c->st);
+  }
+  if (field == CCM_F_P || field == CCM_F_PHI) {
+    // only active cells carry pressure; the ghost ring stays zero
+    k_mask_cells<<<grid_of(c->g, b), b, 0, c->st>>>(c->g, c->co.act, field_ptr(c, field));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  return check_cuda_errors("set_field");
+}
+
+ccm_status ccm_get_field(ccm_case c, int field, double* host, size_t count) {
+  g_last_error.clear();
+  if (!c || !host) return fail(CCM_E_INVALID, "null argument");
+  if (field == CCM_F_STEP) {
+    if (count < 1) return fail(CCM_E_INVALID, "count");
+    host[0] = (double)c->nstep;
+    return CCM_OK;
+  }
+  double* src = field_ptr(c, field);
+  if (!src) return fail(CCM_E_INVALID, "unknown field");
+  if (count != host_count(c)) return fail(CCM_E_INVALID, "count must be (nx+3)*(ny+3)");
+  ccm_status s = download(c, host, src);
+  if (s != CCM_OK) return s;
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  return CCM_OK;
+}
+
+ccm_status ccm_field_device_ptr(ccm_case c, int field, void** dptr, int* pitch) {
+  if (!c || !dptr) return fail(CCM_E_INVALID, "null argument");
+  double* p = field_ptr(c, field);
+  if (!p) return fail(CCM_E_INVALID, "unknown field");
+  *dptr = p;
+  if (pitch) *pitch = c->g.pitch;
+  return CCM_OK;
+}
+
+ccm_status ccm_apply_op(ccm_case c, int op, const double* in0, const double* in1, double* out0, double* out1) {
+  g_last_error.clear();
+  if (!c) return fail(CCM_E_INVALID, "null case");
+  if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
+  const Geom& g = c->g;
+  cudaStream_t st = c->st;
+  ccm_status s = CCM_OK;
+  auto need = [&](const void* p) { return p != nullptr; };
+  switch (op) {
+    case CCM_OP_CONT:
+      if (!need(in0) || !need(in1) || !need(out0)) return fail(CCM_E_INVALID, "CONT needs in0, in1, out0");
+      if ((s = upload(c, c->t0, in0)) || (s = upload(c, c->t1, in1))) return s;
+      launch_cont(c->cv, g, c->t0, c->t1, c->t2, st);
+      if ((s = download(c, out0, c->t2))) return s;
+      break;
+    case CCM_OP_PRES:
+      if (!need(in0) || !need(out0) || !need(out1)) return fail(CCM_E_INVALID, "PRES needs in0, out0, out1");
+      if ((s = upload(c, c->t0, in0))) return s;
+      launch_pres(c->cv, g, c->t0, c->t2, c->t3, st);
+      if ((s = download(c, out0, c->t2)) || (s = download(c, out1, c->t3))) return s;
+      break;
+    case CCM_OP_CONV:
+    case CCM_OP_VISC:
+      if (!need(in0) || !need(in1) || !need(out0) || !need(out1)) return fail(CCM_E_INVALID, "needs in0, in1, out0, out1");
+      if ((s = upload(c, c->t0, in0)) || (s = upload(c, c->t1, in1))) return s;
+      launch_fill_bc(g, c->bc, c->t0, c->t1, 1.0, st);
+      if (op == CCM_OP_CONV) launch_conv(c->cv, g, c->t0, c->t1, c->t2, c->t3, st);
+      else launch_visc(c->cv, g, c->bc, c->t0, c->t1, c->t2, c->t3, st);
+      if ((s = download(c, out0, c->t2)) || (s = download(c, out1, c->t3))) return s;
+      break;
+    case CCM_OP_HELMHOLTZ:
+      if (!need(in0) || !need(in1) || !need(out0) || !need(out1)) return fail(CCM_E_INVALID, "needs in0, in1, out0, out1");
+      if ((s = upload(c, c->t0, in0)) || (s = upload(c, c->t1, in1))) return s;
+      launch_helmholtz(c->cv, g, c->bc, c->ph, c->t0, c->t1, c->t2, c->t3, st);
+      if ((s = download(c, out0, c->t2)) || (s = download(c, out1, c->t3))) return s;
+      break;
+    case CCM_OP_POISSON:
+      if (!need(in0) || !need(out0)) return fail(CCM_E_INVALID, "POISSON needs in0, out0");
+      if ((s = upload(c, c->t0, in0))) return s;
+      launch_poisson(c->cv, g, c->t0, c->t2, c->t1, st);
+      if ((s = download(c, out0, c->t2))) return s;
+      break;
+    case CCM_OP_POISSON_DIAG:
+      if (!need(out0)) return fail(CCM_E_INVALID, "needs out0");
+      if ((s = download(c, out0, c->co.diagk))) return s;
+      break;
+    case CCM_OP_HELMHOLTZ_DIAG:
+      if (!need(out0) || !need(out1)) return fail(CCM_E_INVALID, "needs out0, out1");
+      launch_helmholtz_diag(c->cv, g, c->bc, c->ph, c->t0, c->t1, c->t2, c->t3, c->t4, c->t5, nullptr, nullptr, st);
+      if ((s = download(c, out0, c->t4)) || (s = download(c, out1, c->t5))) return s;
+      break;
+    default:
+      return fail(CCM_E_INVALID, "unknown operator");
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return check_cuda_errors("apply_op");
+}
+
+static ccm_status read_stats(ccm_case c, DevStats& h) {
+  CUDA_TRY(cudaMemcpyAsync(&h, c->ds, sizeof(DevStats), cudaMemcpyDeviceToHost, c->st));
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, c->bar_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  if (err) {
+    cudaMemsetAsync(c->bar_err, 0, sizeof(int), c->st);
+    cudaStreamSynchronize(c->st);
+    return fail(CCM_E_TIMEOUT, "a device-wide barrier gave up waiting");
+  }
+  return check_cuda_errors("solver");
+}
+
+static ccm_status enqueue_steps(ccm_case c, int nsteps) {
+  const Geom& g = c->g;
+  cudaStream_t st = c->st;
+  ccm_status s;
+  for (int n = 0; n < nsteps; ++n) {
+    const int prev = c->cur, next = 1 - c->cur;
+    launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
+    launch_predictor_rhs(c->cv, g, c->bc, c->ph, c->u, c->v, c->p, c->cnu[prev], c->cnv[prev], c->cnu[next],
+                         c->cnv[next], c->rhs_u, c->rhs_v, c->nstep == 0 ? 1 : 0, st);
+    if ((s = solve_helmholtz(c)) != CCM_OK) return s;
+    launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
+    CUDA_TRY(cudaMemcpyAsync(c->ustar, c->u, g.count() * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(c->vstar, c->v, g.count() * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_divergence(c->cv, g, c->ph, c->u, c->v, c->div, c->rhs_p, st);
+    if ((s = poisson_solve(c, c->phi, c->rhs_p)) != CCM_OK) return s;
+    launch_project(c->cv, g, c->phi, c->u, c->v, c->p, st);
+    launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
+    c->launches += 7;  // fill_bc x3, predictor, Helmholtz PCG, divergence, projection
+    c->cur = next;
+    c->nstep++;
+    c->steps_pending++;
+  }
+  return check_cuda_errors("step");
+}
+
+static ccm_status finish_stats(ccm_case c, ccm_step_stats* stats) {
+  const Geom& g = c->g;
+  launch_diagnostics(c->cv, g, c->caps.a[cap_slot(1, CK_V)], c->caps.a[cap_slot(2, CK_V)], c->u, c->v, c->dpart,
+                     c->ds->diag, c->st);
+  DevStats h{};
+  ccm_status s;
+  if ((s = read_stats(c, h)) != CCM_OK) return s;
+  if (c->timing) collect_timing(c);
+  if (stats) {
+    stats->steps = (int)c->steps_pending;
+    stats->iters_p = h.total_p;
+    stats->iters_h = h.total_h;
+    stats->last_iters_p = h.iters_p;
+    stats->last_iters_h = h.iters_h;
+    stats->last_res_p = h.bb_p > 0 ? sqrt(h.rr_p / h.bb_p) : 0.0;
+    stats->last_res_h = h.bb_h > 0 ? sqrt(h.rr_h / h.bb_h) : 0.0;
+    stats->max_div = h.diag[0];
+    stats->kinetic = h.diag[1];
+    stats->converged = h.nconv == 0;
+  }
+  if (c->timing) c->poisson_iters_timed += h.total_p;
+  c->steps_pending = 0;
+  CUDA_TRY(cudaMemsetAsync(c->ds, 0, sizeof(DevStats), c->st));
+  if (h.diag[2] != 0.0) return fail(CCM_E_NONFINITE, "non-finite velocity");
+  if (h.nconv) return fail(CCM_E_NOT_CONVERGED, "a PCG reached its iteration limit");
+  return CCM_OK;
+}
+
+ccm_status ccm_step(ccm_case c, int nsteps, ccm_step_stats* stats) {
+  g_last_error.clear();
+  if (!c) return fail(CCM_E_INVALID, "null case");
+  if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
+  if (nsteps < 0) return fail(CCM_E_INVALID, "nsteps < 0");
+  ccm_status s = enqueue_steps(c, nsteps);
+  if (s != CCM_OK) return s;
+  return finish_stats(c, stats);
+}
+
+ccm_status ccm_step_async(ccm_case c, int nsteps) {
+  g_last_error.clear();
+  if (!c) return fail(CCM_E_INVALID, "null case");
+  if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
+  if (nsteps < 0) return fail(CCM_E_INVALID, "nsteps < 0");
+  return enqueue_steps(c, nsteps);
+}
+
+ccm_status ccm_read_stats(ccm_case c, ccm_step_stats* stats) {
+  g_last_error.clear();
+  if (!c) return fail(CCM_E_INVALID, "null case");
+  if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
+  return finish_stats(c, stats);
+}
+
+ccm_status ccm_enable_kernel_timing(ccm_case c, int enable) {
+  if (!c) return fail(CCM_E_INVALID, "null case");
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  collect_timing(c);
+  c->timing = enable != 0;
+  c->poisson_ms = 0.0;
+  c->poisson_launches = 0;
+  c->poisson_iters_timed = 0;
+  c->launches = 0;
+  return CCM_OK;
+}
+
+ccm_status ccm_kernel_timing(ccm_case c, double* poisson_ms, long long* poisson_launches, long long* poisson_iters,
+                             long long* kernel_launches) {
+  if (!c) return fail(CCM_E_INVALID, "null case");
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  collect_timing(c);
+  if (poisson_ms) *poisson_ms = c->poisson_ms;
+  if (poisson_launches) *poisson_launches = c->poisson_launches;
+  if (poisson_iters) *poisson_iters = c->poisson_iters_timed;
+  if (kernel_launches) *kernel_launches = c->launches;
+  c->poisson_ms = 0.0;
+  c->poisson_launches = 0;
+  c->poisson_iters_timed = 0;
+  c->launches = 0;
+  return CCM_OK;
+}
+
+ccm_status ccm_solve_pressure(ccm_case c, const double* rhs_host, ccm_solve_stats* stats) {
+  g_last_error.clear();
+  if (!c || !rhs_host) return fail(CCM_E_INVALID, "null argument");
+  if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
+  ccm_status s = upload(c, c->rhs_p, rhs_host);
+  if (s != CCM_OK) return s;
+  const dim3 b(64, 4);
+  k_mask_cells<<<grid_of(c->g, b), b, 0, c->st>>>(c->g, c->co.act, c->rhs_p);
+  k_mask_cells<<<grid_of(c->g, b), b, 0, c->st>>>(c->g, c->co.act, c->phi);
+  CUDA_TRY(cudaMemsetAsync(c->ds, 0, sizeof(DevStats), c->st));
+  if ((s = poisson_solve(c, c->phi, c->rhs_p)) != CCM_OK) return s;
+  DevStats h{};
+  if ((s = read_stats(c, h)) != CCM_OK) return s;
+  if (stats) {
+    stats->iters = h.iters_p;
+    stats->outer = 1;
+    stats->rel_res = h.bb_p > 0 ? sqrt(h.rr_p / h.bb_p) : 0.0;
+    stats->converged = h.conv_p;
+  }
+  if (!h.conv_p) return fail(CCM_E_NOT_CONVERGED, "Poisson PCG reached its iteration limit");
+  return CCM_OK;
+}
+
+}  // extern "C"

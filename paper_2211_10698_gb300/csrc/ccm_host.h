@@ -1,0 +1,109 @@
+// Host-side declarations shared by the libccm translation units: argument bundles of the
+// solver kernels and the launchers each .cu file provides.
+#pragma once
+
+#include "ccm_internal.cuh"
+
+namespace ccm {
+
+struct CapPtrs {
+  double* a[27];
+};
+
+// Writable view of the derived coefficients (Coefs is the read-only kernel view).
+struct CoefPtrs {
+  int8_t* role_u;
+  int8_t* role_v;
+  int8_t* act;
+  double *cu, *cv, *invdk, *diagk, *gfu, *gfv, *pfac, *massu, *massv;
+  double *wxx, *wyy, *wxa, *wxb;
+  double *invdhu, *invdhv, *liftu, *liftv;
+  float *cu32, *cv32, *invdk32;
+};
+
+// Where a solver kernel reports: iterations, final squared residual and right-hand side
+// norms, convergence flag; `total` and `nconv` accumulate over calls (may be null).
+struct PcgOut {
+  int* iters;
+  double* rr;
+  double* bb;
+  int* converged;
+  long long* total;
+  int* nconv;
+};
+
+template <class T>
+struct PoissonSolve {
+  Geom g;
+  const T* cu;
+  const T* cv;
+  const T* invd;
+  const int8_t* act;
+  T* x;
+  T* b;
+  T* r;
+  T* z;
+  T* p0;
+  T* p1;
+  T* q;
+  double tol;
+  int max_iter;
+  int zero_mean;
+  double n_act;
+  double* partials;
+  Barrier bar;
+  PcgOut out;
+};
+
+struct HelmholtzSolve {
+  Coefs c;
+  Geom g;
+  Bc bc;
+  Phys ph;
+  double* xu;
+  double* xv;
+  const double* bu;
+  const double* bv;
+  double *ru, *rv, *zu, *zv, *pu, *pv, *qu, *qv;
+  double tol;
+  int max_iter;
+  double* partials;
+  Barrier bar;
+  PcgOut out;
+};
+
+// geometry.cu
+cudaError_t launch_capacities(const ccm_geometry& geo, const Geom& g, double* const* caps_dev, cudaStream_t st);
+
+// operators.cu
+void launch_derive(const Geom& g, const Bc& bc, const Phys& ph, int literal, const CapPtrs& cp, const CoefPtrs& o,
+                   cudaStream_t st);
+void launch_fill_bc(const Geom& g, const Bc& bc, double* u, double* v, double scale, cudaStream_t st);
+void launch_cont(const Coefs& c, const Geom& g, const double* u, const double* v, double* out, cudaStream_t st);
+void launch_pres(const Coefs& c, const Geom& g, const double* p, double* ou, double* ov, cudaStream_t st);
+void launch_conv(const Coefs& c, const Geom& g, const double* u, const double* v, double* ou, double* ov,
+                 cudaStream_t st);
+void launch_visc(const Coefs& c, const Geom& g, const Bc& bc, const double* u, const double* v, double* ou, double* ov,
+                 cudaStream_t st);
+void launch_helmholtz(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, const double* u, const double* v,
+                      double* ou, double* ov, cudaStream_t st);
+void launch_poisson(const Coefs& c, const Geom& g, const double* x, double* out, double* tmp, cudaStream_t st);
+void launch_helmholtz_diag(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, double* eu, double* ev,
+                           double* ou, double* ov, double* du, double* dv, double* iu, double* iv, cudaStream_t st);
+void launch_predictor_rhs(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, const double* u, const double* v,
+                          const double* p, const double* cpu, const double* cpv, double* cnu, double* cnv, double* ru,
+                          double* rv, int first, cudaStream_t st);
+void launch_divergence(const Coefs& c, const Geom& g, const Phys& ph, const double* u, const double* v, double* b,
+                       double* rhs, cudaStream_t st);
+void launch_project(const Coefs& c, const Geom& g, const double* phi, double* u, double* v, double* p, cudaStream_t st);
+int diagnostics_partials(const Geom& g);
+void launch_diagnostics(const Coefs& c, const Geom& g, const double* Vu, const double* Vv, const double* u,
+                        const double* v, double* partials, double* out, cudaStream_t st);
+
+// pcg.cu
+int pcg_partials_needed();
+template <class T>
+cudaError_t run_poisson_pcg(PoissonSolve<T> a, cudaStream_t st);
+cudaError_t run_helmholtz_pcg(HelmholtzSolve a, cudaStream_t st);
+
+}  // namespace ccm

@@ -1,0 +1,289 @@
+// Internal definitions of libccm: device layout of a case, the bounded grid barrier, the
+// deterministic block/grid reductions and the stencil device functions shared by the
+// operator, step and PCG kernels.
+//
+// Layout: every array of a case is (ny + 3) rows of `pitch` elements (pitch >= nx + 3,
+// rounded up to 32 elements); index (i, j), i in [-1, nx+1], j in [-1, ny+1], lives at
+// (j + 1) * pitch + (i + 1).  Index (i, j) names the p-cell (i, j), the u-face at
+// x0 + i*hx, the v-face at y0 + j*hy or the node (x0 + i*hx, y0 + j*hy).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ccm.h"
+
+namespace ccm {
+
+enum Role : int8_t { R_GHOST = 0, R_DIRICHLET = 1, R_INACTIVE = 2, R_UNKNOWN = 3 };
+
+// Capacity slots: grid g in {0 p, 1 u, 2 v} times {V, X, Y, Ax, Ay, Wx, Wy, Bx, By}.
+enum { CK_V = 0, CK_X, CK_Y, CK_AX, CK_AY, CK_WX, CK_WY, CK_BX, CK_BY };
+__host__ __device__ inline int cap_slot(int g, int k) { return 9 * g + k; }
+
+struct Geom {
+  int nx, ny, pitch;
+  double x0, y0, hx, hy;
+  __host__ __device__ size_t idx(int i, int j) const { return (size_t)(j + 1) * pitch + (size_t)(i + 1); }
+  __host__ __device__ size_t count() const { return (size_t)(ny + 3) * pitch; }
+};
+
+struct Bc {
+  int type[4];        // W E S N
+  double un[4], ut[4];
+};
+
+// Coefficients derived from the capacities, all in the padded layout.
+struct Coefs {
+  const int8_t* role_u;
+  const int8_t* role_v;
+  const int8_t* act;        // active pressure cell
+  const double* ax;         // p-grid A^x at u-faces (cont, pres, conv)
+  const double* ay;         // p-grid A^y at v-faces
+  const double* bxx;        // B^xx at u-faces (u-grid Bx)
+  const double* bxy;        // B^xy at u-faces (u-grid By)
+  const double* byx;        // B^yx at v-faces (v-grid Bx)
+  const double* byy;        // B^yy at v-faces (v-grid By)
+  const double* wxx;        // 1/W^xx at p-cells
+  const double* wyy;        // 1/W^yy at p-cells
+  const double* wxa;        // node weight of the u part of S_xy
+  const double* wxb;        // node weight of the v part of S_xy
+  const double* cu;         // Poisson face coefficient A^2/V at u unknowns
+  const double* cv;
+  const double* invdk;      // 1 / diag(K) at active cells
+  const double* gfu;        // (dt/rho) A / V at u unknowns (projection)
+  const double* gfv;
+  const double* pfac;       // (dt mu / 2 rho) / V_p at active cells
+  const double* massu;      // (rho/dt) V at u unknowns
+  const double* massv;
+  const double* invdhu;     // 1 / diag(H) at u unknowns and inactive faces
+  const double* invdhv;
+  const double* liftu;      // visc(S(0, box data)) at u unknowns
+  const double* liftv;
+  const float* cu32;
+  const float* cv32;
+  const float* invdk32;
+};
+
+struct Phys {
+  double rho, mu, dt;
+};
+
+// ---------------------------------------------------------------------------------------
+// Bounded device-wide barrier for cooperative (co-resident) launches.  Thread 0 of each
+// block arrives on a monotonically increasing counter and waits until all blocks of this
+// round have arrived, giving up after `budget` clock cycles; on give-up it raises *err and
+// the caller leaves the kernel.
+// ---------------------------------------------------------------------------------------
+struct Barrier {
+  unsigned int* count;  // zeroed before the launch
+  int* err;
+  long long budget;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool grid_sync(const Barrier& b, unsigned int& target) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    target += gridDim.x;
+    __threadfence();
+    atomicAdd(b.count, 1u);
+    long long t0 = clock64();
+    while (ld_acquire_u32(b.count) < target) {
+      if (clock64() - t0 > b.budget) {
+        atomicExch(b.err, 1);
+        ok = 0;
+        break;
+      }
+    }
+    if (ok && *((volatile int*)b.err) != 0) ok = 0;
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Deterministic block sum of NV values (fixed shuffle tree, fixed warp order); the result
+// is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* >= 32*NV */) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) smem[k * 32 + w] = v[k];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = lane < nw ? smem[k * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      v[k] = s;
+    }
+  }
+}
+
+// Sum of the per-block partials (layout partials[k * nblocks + b]) in a fixed order; every
+// block computes the identical value.  Result broadcast to all threads through smem.
+template <int NV>
+__device__ __forceinline__ void grid_sum(const double* partials, int nblocks, double (&out)[NV], double* smem) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int b = lane; b < nblocks; b += 32) s += __ldcg(&partials[(size_t)k * nblocks + b]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) smem[k] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = smem[k];
+}
+
+// ---------------------------------------------------------------------------------------
+// Stencils.  Arrays are read with explicit (i, j) indices in the padded layout.
+// ---------------------------------------------------------------------------------------
+
+// Homogeneous view of a velocity-like vector: value on unknowns, zero on Dirichlet and
+// inactive faces, and on ghost positions the zero-gradient copy or the reflection of the
+// adjacent position according to the side's boundary type.
+struct HomView {
+  const double* u;
+  const double* v;
+  const int8_t* ru;
+  const int8_t* rv;
+  Geom g;
+  Bc bc;
+  __device__ __forceinline__ double at_u(int i, int j) const {
+    double s = 1.0;
+    if (i < 0) i = 0;
+    else if (i > g.nx) i = g.nx;
+    if (j < 0) { j = 0; if (bc.type[CCM_SIDE_S] == CCM_BC_DIRICHLET) s = -1.0; }
+    else if (j >= g.ny) { j = g.ny - 1; if (bc.type[CCM_SIDE_N] == CCM_BC_DIRICHLET) s = -1.0; }
+    size_t k = g.idx(i, j);
+    return ru[k] == R_UNKNOWN ? s * u[k] : 0.0;
+  }
+  __device__ __forceinline__ double at_v(int i, int j) const {
+    double s = 1.0;
+    if (j < 0) j = 0;
+    else if (j > g.ny) j = g.ny;
+    if (i < 0) { i = 0; if (bc.type[CCM_SIDE_W] == CCM_BC_DIRICHLET) s = -1.0; }
+    else if (i >= g.nx) { i = g.nx - 1; if (bc.type[CCM_SIDE_E] == CCM_BC_DIRICHLET) s = -1.0; }
+    size_t k = g.idx(i, j);
+    return rv[k] == R_UNKNOWN ? s * v[k] : 0.0;
+  }
+};
+
+// Full view: the arrays already hold Dirichlet faces and ghosts (filled by fill_bc).
+struct FullView {
+  const double* u;
+  const double* v;
+  Geom g;
+  __device__ __forceinline__ double at_u(int i, int j) const { return u[g.idx(i, j)]; }
+  __device__ __forceinline__ double at_v(int i, int j) const { return v[g.idx(i, j)]; }
+};
+
+// Strain components (Eqs. diag, offdiag with D = 0).
+template <class View>
+__device__ __forceinline__ double strain_xx(const Coefs& c, const Geom& g, const View& w, int i, int j) {
+  // p-cell (i, j): u-faces i and i+1
+  return (c.bxx[g.idx(i + 1, j)] * w.at_u(i + 1, j) - c.bxx[g.idx(i, j)] * w.at_u(i, j)) * c.wxx[g.idx(i, j)];
+}
+template <class View>
+__device__ __forceinline__ double strain_yy(const Coefs& c, const Geom& g, const View& w, int i, int j) {
+  return (c.byy[g.idx(i, j + 1)] * w.at_v(i, j + 1) - c.byy[g.idx(i, j)] * w.at_v(i, j)) * c.wyy[g.idx(i, j)];
+}
+template <class View>
+__device__ __forceinline__ double strain_xy(const Coefs& c, const Geom& g, const View& w, int i, int j) {
+  // node (i, j): u-faces (i, j-1), (i, j); v-faces (i-1, j), (i, j)
+  const size_t k = g.idx(i, j);
+  double gu = c.bxy[k] * w.at_u(i, j) - c.bxy[g.idx(i, j - 1)] * w.at_u(i, j - 1);
+  double gv = c.byx[k] * w.at_v(i, j) - c.byx[g.idx(i - 1, j)] * w.at_v(i - 1, j);
+  return gu * c.wxa[k] + gv * c.wxb[k];
+}
+
+// visc_x(S) at u-face (i, j) and visc_y(S) at v-face (i, j) (Sec. 4.3), with the outflow
+// rule: the tangential velocity next to an outflow side takes no shear from the nodes on
+// that side.
+template <class View>
+__device__ __forceinline__ double visc_u(const Coefs& c, const Geom& g, const Bc& bc, const View& w, int i, int j) {
+  const size_t k = g.idx(i, j);
+  double sx = strain_xx(c, g, w, i, j) - strain_xx(c, g, w, i - 1, j);
+  double top = (j == g.ny - 1 && bc.type[CCM_SIDE_N] == CCM_BC_OUTFLOW) ? 0.0 : strain_xy(c, g, w, i, j + 1);
+  double bot = (j == 0 && bc.type[CCM_SIDE_S] == CCM_BC_OUTFLOW) ? 0.0 : strain_xy(c, g, w, i, j);
+  return c.bxx[k] * sx + c.bxy[k] * (top - bot);
+}
+template <class View>
+__device__ __forceinline__ double visc_v(const Coefs& c, const Geom& g, const Bc& bc, const View& w, int i, int j) {
+  const size_t k = g.idx(i, j);
+  double sy = strain_yy(c, g, w, i, j) - strain_yy(c, g, w, i, j - 1);
+  double rgt = (i == g.nx - 1 && bc.type[CCM_SIDE_E] == CCM_BC_OUTFLOW) ? 0.0 : strain_xy(c, g, w, i + 1, j);
+  double lft = (i == 0 && bc.type[CCM_SIDE_W] == CCM_BC_OUTFLOW) ? 0.0 : strain_xy(c, g, w, i, j);
+  return c.byy[k] * sy + c.byx[k] * (rgt - lft);
+}
+
+// conv_x(U, U, 0, 0) at u-face (i, j) and conv_y at v-face (i, j) (Eq. convective, D = 0):
+// divergence of the face-interpolated mass fluxes times the interpolated velocity.
+__device__ __forceinline__ double conv_u(const Coefs& c, const Geom& g, const FullView& w, int i, int j) {
+  const double* A = c.ax;
+  const double* B = c.ay;
+  double fe = 0.5 * (A[g.idx(i + 1, j)] * w.at_u(i + 1, j) + A[g.idx(i, j)] * w.at_u(i, j));
+  double fw = 0.5 * (A[g.idx(i, j)] * w.at_u(i, j) + A[g.idx(i - 1, j)] * w.at_u(i - 1, j));
+  double ue = 0.5 * (w.at_u(i + 1, j) + w.at_u(i, j));
+  double uw = 0.5 * (w.at_u(i, j) + w.at_u(i - 1, j));
+  double fn = 0.5 * (B[g.idx(i, j + 1)] * w.at_v(i, j + 1) + B[g.idx(i - 1, j + 1)] * w.at_v(i - 1, j + 1));
+  double fs = 0.5 * (B[g.idx(i, j)] * w.at_v(i, j) + B[g.idx(i - 1, j)] * w.at_v(i - 1, j));
+  double un = 0.5 * (w.at_u(i, j + 1) + w.at_u(i, j));
+  double us = 0.5 * (w.at_u(i, j) + w.at_u(i, j - 1));
+  return (fe * ue - fw * uw) + (fn * un - fs * us);
+}
+__device__ __forceinline__ double conv_v(const Coefs& c, const Geom& g, const FullView& w, int i, int j) {
+  const double* A = c.ax;
+  const double* B = c.ay;
+  double fn = 0.5 * (B[g.idx(i, j + 1)] * w.at_v(i, j + 1) + B[g.idx(i, j)] * w.at_v(i, j));
+  double fs = 0.5 * (B[g.idx(i, j)] * w.at_v(i, j) + B[g.idx(i, j - 1)] * w.at_v(i, j - 1));
+  double vn = 0.5 * (w.at_v(i, j + 1) + w.at_v(i, j));
+  double vs = 0.5 * (w.at_v(i, j) + w.at_v(i, j - 1));
+  double fe = 0.5 * (A[g.idx(i + 1, j)] * w.at_u(i + 1, j) + A[g.idx(i + 1, j - 1)] * w.at_u(i + 1, j - 1));
+  double fw = 0.5 * (A[g.idx(i, j)] * w.at_u(i, j) + A[g.idx(i, j - 1)] * w.at_u(i, j - 1));
+  double ve = 0.5 * (w.at_v(i + 1, j) + w.at_v(i, j));
+  double vw = 0.5 * (w.at_v(i, j) + w.at_v(i - 1, j));
+  return (fn * vn - fs * vs) + (fe * ve - fw * vw);
+}
+
+// cont(U, 0) at p-cell (i, j) (Eq. divergence, D = 0).
+template <class T>
+__device__ __forceinline__ double cont_cell(const Coefs& c, const Geom& g, const T* u, const T* v, int i, int j) {
+  return c.ax[g.idx(i + 1, j)] * (double)u[g.idx(i + 1, j)] - c.ax[g.idx(i, j)] * (double)u[g.idx(i, j)] +
+         c.ay[g.idx(i, j + 1)] * (double)v[g.idx(i, j + 1)] - c.ay[g.idx(i, j)] * (double)v[g.idx(i, j)];
+}
+
+// K x at cell (i, j): sum over faces of c_f (x_c - x_nbr); identity on inactive cells.
+// The ghost ring of x holds zeros (Dirichlet pressure on outflow sides).
+template <class T, class C>
+__device__ __forceinline__ T poisson_row(const C* cu, const C* cv, const int8_t* act, const Geom& g, const T* x,
+                                         size_t k) {
+  T xc = x[k];
+  if (!act[k]) return xc;
+  T cw = (T)cu[k], ce = (T)cu[k + 1], cs = (T)cv[k], cn = (T)cv[k + g.pitch];
+  return cw * (xc - x[k - 1]) + ce * (xc - x[k + 1]) + cs * (xc - x[k - g.pitch]) + cn * (xc - x[k + g.pitch]);
+}
+
+}  // namespace ccm

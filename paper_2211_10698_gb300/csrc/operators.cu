@@ -1,0 +1,373 @@
+// Operator kernels of libccm: coefficient derivation, box boundary fill, the discrete
+// operators of Sec. 4 (cont, pres, conv, visc, the Helmholtz and Poisson operators of the
+// projection step) and the explicit stages of one PmII step (Sec. 4.6).
+//
+// Kernels that touch staggered data run one thread per padded index (i, j) and handle
+// the u-face, v-face and p-cell that carry that index.
+#include "ccm_host.h"
+
+namespace ccm {
+
+#define PAD_IJ(g)                                                        \
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;       \
+  const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;       \
+  if (i > (g).nx + 1 || j > (g).ny + 1) return;                         \
+  const size_t k = (g).idx(i, j);
+
+dim3 pad_grid(const Geom& g, dim3 blk) { return dim3((g.nx + 3 + blk.x - 1) / blk.x, (g.ny + 3 + blk.y - 1) / blk.y); }
+static const dim3 kBlk(64, 4);
+
+__device__ __forceinline__ double inv_or_zero(double w, double eps) { return w > eps ? 1.0 / w : 0.0; }
+
+// ---------------------------------------------------------------------------------------
+// Coefficients derived from the capacities.
+// ---------------------------------------------------------------------------------------
+__global__ void k_derive1(Geom g, Bc bc, Phys ph, int literal, CapPtrs cp, CoefPtrs o) {
+  PAD_IJ(g)
+  const double eps = 1e-12 * g.hx * g.hy;
+  const bool udom = i >= 0 && i <= g.nx && j >= 0 && j < g.ny;
+  const bool vdom = i >= 0 && i < g.nx && j >= 0 && j <= g.ny;
+  const bool udir = udom && ((i == 0 && bc.type[CCM_SIDE_W] == CCM_BC_DIRICHLET) ||
+                             (i == g.nx && bc.type[CCM_SIDE_E] == CCM_BC_DIRICHLET));
+  const bool vdir = vdom && ((j == 0 && bc.type[CCM_SIDE_S] == CCM_BC_DIRICHLET) ||
+                             (j == g.ny && bc.type[CCM_SIDE_N] == CCM_BC_DIRICHLET));
+  const double Vu = cp.a[cap_slot(1, CK_V)][k], Vv = cp.a[cap_slot(2, CK_V)][k];
+  const int8_t ru = !udom ? R_GHOST : udir ? R_DIRICHLET : (Vu > eps ? R_UNKNOWN : R_INACTIVE);
+  const int8_t rv = !vdom ? R_GHOST : vdir ? R_DIRICHLET : (Vv > eps ? R_UNKNOWN : R_INACTIVE);
+  o.role_u[k] = ru;
+  o.role_v[k] = rv;
+  const double Ax = cp.a[cap_slot(0, CK_AX)][k], Ay = cp.a[cap_slot(0, CK_AY)][k];
+  const double ivu = inv_or_zero(Vu, eps), ivv = inv_or_zero(Vv, eps);
+  o.cu[k] = ru == R_UNKNOWN ? Ax * Ax * ivu : 0.0;
+  o.cv[k] = rv == R_UNKNOWN ? Ay * Ay * ivv : 0.0;
+  o.gfu[k] = ru == R_UNKNOWN ? (ph.dt / ph.rho) * Ax * ivu : 0.0;
+  o.gfv[k] = rv == R_UNKNOWN ? (ph.dt / ph.rho) * Ay * ivv : 0.0;
+  o.massu[k] = ru == R_UNKNOWN ? (ph.rho / ph.dt) * Vu : 0.0;
+  o.massv[k] = rv == R_UNKNOWN ? (ph.rho / ph.dt) * Vv : 0.0;
+  // 1/W^xx at p-cell (i, j) is the u-grid Wx at u-cell i+1; 1/W^yy likewise
+  o.wxx[k] = (i + 1 <= g.nx + 1) ? inv_or_zero(cp.a[cap_slot(1, CK_WX)][g.idx(i + 1, j)], eps) : 0.0;
+  o.wyy[k] = (j + 1 <= g.ny + 1) ? inv_or_zero(cp.a[cap_slot(2, CK_WY)][g.idx(i, j + 1)], eps) : 0.0;
+  const double wxy = cp.a[cap_slot(1, CK_WY)][k], wyx = cp.a[cap_slot(2, CK_WX)][k];
+  if (literal) {
+    o.wxa[k] = 0.5 * inv_or_zero(wxy, eps);
+    o.wxb[k] = 0.5 * inv_or_zero(wyx, eps);
+  } else {
+    const double wb = 0.5 * inv_or_zero(0.5 * (wxy + wyx), eps);
+    o.wxa[k] = wb;
+    o.wxb[k] = wb;
+  }
+}
+
+__global__ void k_derive2(Geom g, Phys ph, CapPtrs cp, CoefPtrs o) {
+  PAD_IJ(g)
+  const bool dom = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+  double s = 0.0;
+  if (dom) s = o.cu[k] + o.cu[k + 1] + o.cv[k] + o.cv[k + g.pitch];
+  const bool a = dom && s > 0.0;
+  o.act[k] = a ? 1 : 0;
+  o.invdk[k] = a ? 1.0 / s : (dom ? 1.0 : 0.0);
+  o.diagk[k] = a ? s : (dom ? 1.0 : 0.0);
+  const double eps = 1e-12 * g.hx * g.hy;
+  const double Vp = cp.a[cap_slot(0, CK_V)][k];
+  o.pfac[k] = a ? (ph.dt * ph.mu / (2.0 * ph.rho)) * inv_or_zero(Vp, eps) : 0.0;
+  o.cu32[k] = (float)o.cu[k];
+  o.cv32[k] = (float)o.cv[k];
+  o.invdk32[k] = (float)o.invdk[k];
+}
+
+// ---------------------------------------------------------------------------------------
+// Box boundary data: Dirichlet faces get scale * bc_un, ghosts the zero-gradient copy
+// (outflow and normal components) or the reflection 2 scale bc_ut - interior (tangential
+// components on Dirichlet sides).
+// ---------------------------------------------------------------------------------------
+__global__ void k_fill_bc(Geom g, Bc bc, double* u, double* v, double scale) {
+  PAD_IJ(g)
+  const int nx = g.nx, ny = g.ny;
+  const bool wd = bc.type[CCM_SIDE_W] == CCM_BC_DIRICHLET, ed = bc.type[CCM_SIDE_E] == CCM_BC_DIRICHLET;
+  const bool sd = bc.type[CCM_SIDE_S] == CCM_BC_DIRICHLET, nd = bc.type[CCM_SIDE_N] == CCM_BC_DIRICHLET;
+  auto uval = [&](int a, int b) {
+    if (a == 0 && wd) return scale * bc.un[CCM_SIDE_W];
+    if (a == nx && ed) return scale * bc.un[CCM_SIDE_E];
+    return u[g.idx(a, b)];
+  };
+  auto vval = [&](int a, int b) {
+    if (b == 0 && sd) return scale * bc.un[CCM_SIDE_S];
+    if (b == ny && nd) return scale * bc.un[CCM_SIDE_N];
+    return v[g.idx(a, b)];
+  };
+  // u
+  if (j >= 0 && j < ny) {
+    if ((i == 0 && wd) || (i == nx && ed)) u[k] = uval(i, j);
+    else if (i == -1) u[k] = uval(0, j);
+    else if (i == nx + 1) u[k] = uval(nx, j);
+  } else if (i >= 0 && i <= nx) {
+    if (j == -1) u[k] = sd ? 2.0 * scale * bc.ut[CCM_SIDE_S] - uval(i, 0) : uval(i, 0);
+    else if (j == ny) u[k] = nd ? 2.0 * scale * bc.ut[CCM_SIDE_N] - uval(i, ny - 1) : uval(i, ny - 1);
+  }
+  // v
+  if (i >= 0 && i < nx) {
+    if ((j == 0 && sd) || (j == ny && nd)) v[k] = vval(i, j);
+    else if (j == -1) v[k] = vval(i, 0);
+    else if (j == ny + 1) v[k] = vval(i, ny);
+  } else if (j >= 0 && j <= ny) {
+    if (i == -1) v[k] = wd ? 2.0 * scale * bc.ut[CCM_SIDE_W] - vval(0, j) : vval(0, j);
+    else if (i == nx) v[k] = ed ? 2.0 * scale * bc.ut[CCM_SIDE_E] - vval(nx - 1, j) : vval(nx - 1, j);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Operators (used by ccm_apply_op and by set-up).
+// ---------------------------------------------------------------------------------------
+__global__ void k_cont(Coefs c, Geom g, const double* u, const double* v, double* out) {
+  PAD_IJ(g)
+  const bool dom = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+  out[k] = dom ? cont_cell(c, g, u, v, i, j) : 0.0;
+}
+
+// pres(P) on velocity unknowns; cells outside the box read as zero.
+__global__ void k_pres(Coefs c, Geom g, const double* p, double* ou, double* ov) {
+  PAD_IJ(g)
+  auto P = [&](int a, int b) { return (a >= 0 && a < g.nx && b >= 0 && b < g.ny) ? p[g.idx(a, b)] : 0.0; };
+  ou[k] = c.role_u[k] == R_UNKNOWN ? c.ax[k] * (P(i, j) - P(i - 1, j)) : 0.0;
+  ov[k] = c.role_v[k] == R_UNKNOWN ? c.ay[k] * (P(i, j) - P(i, j - 1)) : 0.0;
+}
+
+__global__ void k_conv(Coefs c, Geom g, FullView w, double* ou, double* ov) {
+  PAD_IJ(g)
+  ou[k] = c.role_u[k] == R_UNKNOWN ? conv_u(c, g, w, i, j) : 0.0;
+  ov[k] = c.role_v[k] == R_UNKNOWN ? conv_v(c, g, w, i, j) : 0.0;
+}
+
+__global__ void k_visc(Coefs c, Geom g, Bc bc, FullView w, double* ou, double* ov) {
+  PAD_IJ(g)
+  ou[k] = c.role_u[k] == R_UNKNOWN ? visc_u(c, g, bc, w, i, j) : 0.0;
+  ov[k] = c.role_v[k] == R_UNKNOWN ? visc_v(c, g, bc, w, i, j) : 0.0;
+}
+
+// Helmholtz operator (rho/dt) M U - mu visc(S_hom(U)); identity on inactive faces.
+__global__ void k_helmholtz(Coefs c, Geom g, Bc bc, Phys ph, HomView w, double* ou, double* ov) {
+  PAD_IJ(g)
+  const int8_t ru = c.role_u[k], rv = c.role_v[k];
+  ou[k] = ru == R_UNKNOWN ? c.massu[k] * w.u[k] - ph.mu * visc_u(c, g, bc, w, i, j) : (ru == R_INACTIVE ? w.u[k] : 0.0);
+  ov[k] = rv == R_UNKNOWN ? c.massv[k] * w.v[k] - ph.mu * visc_v(c, g, bc, w, i, j) : (rv == R_INACTIVE ? w.v[k] : 0.0);
+}
+
+// Poisson operator K = -cont(M^-1 pres(.), 0); identity on inactive cells.  The input is
+// read through a copy whose ghost ring is zero.
+__global__ void k_poisson(Coefs c, Geom g, const double* x, double* out) {
+  PAD_IJ(g)
+  const bool dom = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+  out[k] = dom ? poisson_row(c.cu, c.cv, c.act, g, x, k) : 0.0;
+}
+
+__global__ void k_copy_interior_cells(Geom g, const double* in, double* out) {
+  PAD_IJ(g)
+  const bool dom = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+  out[k] = dom ? in[k] : 0.0;
+}
+
+// Probe vectors for diag(H): ones on the unknown and inactive positions of one component
+// whose indices are congruent to (a, b) mod 3 (H couples positions at distance <= 1).
+__global__ void k_probe_set(Coefs c, Geom g, int comp, int a, int b, double* eu, double* ev) {
+  PAD_IJ(g)
+  const bool col = ((i + 3) % 3 == a) && ((j + 3) % 3 == b);
+  eu[k] = (comp == 0 && col && c.role_u[k] >= R_INACTIVE) ? 1.0 : 0.0;
+  ev[k] = (comp == 1 && col && c.role_v[k] >= R_INACTIVE) ? 1.0 : 0.0;
+}
+__global__ void k_probe_get(Coefs c, Geom g, int comp, int a, int b, const double* ou, const double* ov, double* du,
+                            double* dv) {
+  PAD_IJ(g)
+  const bool col = ((i + 3) % 3 == a) && ((j + 3) % 3 == b);
+  if (comp == 0 && col && c.role_u[k] >= R_INACTIVE) du[k] = ou[k];
+  if (comp == 1 && col && c.role_v[k] >= R_INACTIVE) dv[k] = ov[k];
+}
+__global__ void k_invert_diag(Geom g, const double* du, const double* dv, double* iu, double* iv) {
+  PAD_IJ(g)
+  iu[k] = du[k] != 0.0 ? 1.0 / du[k] : 0.0;
+  iv[k] = dv[k] != 0.0 ? 1.0 / dv[k] : 0.0;
+}
+
+// ---------------------------------------------------------------------------------------
+// Explicit stages of the PmII step (Eq. pm_prediction right-hand side, Eq. pm_poisson
+// right-hand side, Eqs. pm_projection and pm_update).
+// ---------------------------------------------------------------------------------------
+__global__ void k_predictor_rhs(Coefs c, Geom g, Bc bc, Phys ph, FullView w, const double* p, const double* cpu,
+                                const double* cpv, double* cnu, double* cnv, double* ru_, double* rv_, int first) {
+  PAD_IJ(g)
+  auto P = [&](int a, int b) { return (a >= 0 && a < g.nx && b >= 0 && b < g.ny) ? p[g.idx(a, b)] : 0.0; };
+  if (c.role_u[k] == R_UNKNOWN) {
+    const double cn = conv_u(c, g, w, i, j);
+    const double cp = first ? cn : cpu[k];
+    const double gp = c.ax[k] * (P(i, j) - P(i - 1, j));
+    const double vs = visc_u(c, g, bc, w, i, j);
+    ru_[k] = c.massu[k] * w.u[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftu[k];
+    cnu[k] = cn;
+  } else {
+    ru_[k] = 0.0;
+    cnu[k] = 0.0;
+  }
+  if (c.role_v[k] == R_UNKNOWN) {
+    const double cn = conv_v(c, g, w, i, j);
+    const double cp = first ? cn : cpv[k];
+    const double gp = c.ay[k] * (P(i, j) - P(i, j - 1));
+    const double vs = visc_v(c, g, bc, w, i, j);
+    rv_[k] = c.massv[k] * w.v[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftv[k];
+    cnv[k] = cn;
+  } else {
+    rv_[k] = 0.0;
+    cnv[k] = 0.0;
+  }
+}
+
+// b = cont(U*, D) on cells; Poisson right-hand side -(rho/dt) b on active cells.
+__global__ void k_divergence(Coefs c, Geom g, Phys ph, const double* u, const double* v, double* b, double* rhs) {
+  PAD_IJ(g)
+  const bool dom = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+  const double d = dom ? cont_cell(c, g, u, v, i, j) : 0.0;
+  b[k] = d;
+  rhs[k] = c.act[k] ? -(ph.rho / ph.dt) * d : 0.0;
+}
+
+// U^{n+1} = U* - (dt/rho) M^-1 pres(Phi); P^{n+1/2} = P^{n-1/2} + Phi + (dt mu / 2 rho)
+// V_p^-1 K Phi.  Phi's ghost ring is zero.
+__global__ void k_project(Coefs c, Geom g, const double* phi, double* u, double* v, double* p) {
+  PAD_IJ(g)
+  if (c.role_u[k] == R_UNKNOWN) u[k] -= c.gfu[k] * (phi[k] - phi[k - 1]);
+  if (c.role_v[k] == R_UNKNOWN) v[k] -= c.gfv[k] * (phi[k] - phi[k - g.pitch]);
+  if (c.act[k]) p[k] += phi[k] + c.pfac[k] * poisson_row(c.cu, c.cv, c.act, g, phi, k);
+}
+
+// Diagnostics: per-block max |cont(U)| over active cells, sum of V U^2 / 2 over velocity
+// positions inside the box, and a non-finite flag.
+__global__ void k_diagnostics(Coefs c, Geom g, const double* Vu, const double* Vv, const double* u, const double* v,
+                              double* partials) {
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
+  const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
+  double dmax = 0.0, ke = 0.0, bad = 0.0;
+  if (i <= g.nx + 1 && j <= g.ny + 1) {
+    const size_t k = g.idx(i, j);
+    if (c.act[k]) dmax = fabs(cont_cell(c, g, u, v, i, j));
+    if (i >= 0 && i <= g.nx && j >= 0 && j < g.ny) {
+      ke += 0.5 * Vu[k] * u[k] * u[k];
+      if (!isfinite(u[k])) bad = 1.0;
+    }
+    if (i >= 0 && i < g.nx && j >= 0 && j <= g.ny) {
+      ke += 0.5 * Vv[k] * v[k] * v[k];
+      if (!isfinite(v[k])) bad = 1.0;
+    }
+  }
+  __shared__ double sm[3][256];
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  sm[0][t] = dmax; sm[1][t] = ke; sm[2][t] = bad;
+  __syncthreads();
+  for (int s = (blockDim.x * blockDim.y) / 2; s > 0; s >>= 1) {
+    if (t < s) {
+      sm[0][t] = fmax(sm[0][t], sm[0][t + s]);
+      sm[1][t] += sm[1][t + s];
+      sm[2][t] = fmax(sm[2][t], sm[2][t + s]);
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    const size_t nb = (size_t)gridDim.x * gridDim.y;
+    partials[b] = sm[0][0];
+    partials[nb + b] = sm[1][0];
+    partials[2 * nb + b] = sm[2][0];
+  }
+}
+
+__global__ void k_diagnostics_final(const double* partials, int nb, double* out) {
+  __shared__ double sm[3][256];
+  const int t = threadIdx.x;
+  double m = 0.0, s = 0.0, bad = 0.0;
+  for (int b = t; b < nb; b += blockDim.x) {
+    m = fmax(m, partials[b]);
+    s += partials[nb + b];
+    bad = fmax(bad, partials[2 * nb + b]);
+  }
+  sm[0][t] = m; sm[1][t] = s; sm[2][t] = bad;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (t < st) {
+      sm[0][t] = fmax(sm[0][t], sm[0][t + st]);
+      sm[1][t] += sm[1][t + st];
+      sm[2][t] = fmax(sm[2][t], sm[2][t + st]);
+    }
+    __syncthreads();
+  }
+  if (t == 0) { out[0] = sm[0][0]; out[1] = sm[1][0]; out[2] = sm[2][0]; }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------------------
+void launch_derive(const Geom& g, const Bc& bc, const Phys& ph, int literal, const CapPtrs& cp, const CoefPtrs& o,
+                   cudaStream_t st) {
+  k_derive1<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, bc, ph, literal, cp, o);
+  k_derive2<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, ph, cp, o);
+}
+void launch_fill_bc(const Geom& g, const Bc& bc, double* u, double* v, double scale, cudaStream_t st) {
+  k_fill_bc<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, bc, u, v, scale);
+}
+void launch_cont(const Coefs& c, const Geom& g, const double* u, const double* v, double* out, cudaStream_t st) {
+  k_cont<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, u, v, out);
+}
+void launch_pres(const Coefs& c, const Geom& g, const double* p, double* ou, double* ov, cudaStream_t st) {
+  k_pres<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, p, ou, ov);
+}
+void launch_conv(const Coefs& c, const Geom& g, const double* u, const double* v, double* ou, double* ov,
+                 cudaStream_t st) {
+  k_conv<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, FullView{u, v, g}, ou, ov);
+}
+void launch_visc(const Coefs& c, const Geom& g, const Bc& bc, const double* u, const double* v, double* ou, double* ov,
+                 cudaStream_t st) {
+  k_visc<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, bc, FullView{u, v, g}, ou, ov);
+}
+void launch_helmholtz(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, const double* u, const double* v,
+                      double* ou, double* ov, cudaStream_t st) {
+  HomView w{u, v, c.role_u, c.role_v, g, bc};
+  k_helmholtz<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, bc, ph, w, ou, ov);
+}
+void launch_poisson(const Coefs& c, const Geom& g, const double* x, double* out, double* tmp, cudaStream_t st) {
+  k_copy_interior_cells<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, x, tmp);
+  k_poisson<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, tmp, out);
+}
+void launch_helmholtz_diag(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, double* eu, double* ev,
+                           double* ou, double* ov, double* du, double* dv, double* iu, double* iv, cudaStream_t st) {
+  cudaMemsetAsync(du, 0, g.count() * sizeof(double), st);
+  cudaMemsetAsync(dv, 0, g.count() * sizeof(double), st);
+  for (int comp = 0; comp < 2; ++comp)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        k_probe_set<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, comp, a, b, eu, ev);
+        launch_helmholtz(c, g, bc, ph, eu, ev, ou, ov, st);
+        k_probe_get<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, comp, a, b, ou, ov, du, dv);
+      }
+  if (iu) k_invert_diag<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, du, dv, iu, iv);
+}
+void launch_predictor_rhs(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, const double* u, const double* v,
+                          const double* p, const double* cpu, const double* cpv, double* cnu, double* cnv, double* ru,
+                          double* rv, int first, cudaStream_t st) {
+  k_predictor_rhs<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, bc, ph, FullView{u, v, g}, p, cpu, cpv, cnu, cnv, ru, rv,
+                                                       first);
+}
+void launch_divergence(const Coefs& c, const Geom& g, const Phys& ph, const double* u, const double* v, double* b,
+                       double* rhs, cudaStream_t st) {
+  k_divergence<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, ph, u, v, b, rhs);
+}
+void launch_project(const Coefs& c, const Geom& g, const double* phi, double* u, double* v, double* p, cudaStream_t st) {
+  k_project<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, phi, u, v, p);
+}
+int diagnostics_partials(const Geom& g) {
+  dim3 gr = pad_grid(g, kBlk);
+  return (int)(gr.x * gr.y);
+}
+void launch_diagnostics(const Coefs& c, const Geom& g, const double* Vu, const double* Vv, const double* u,
+                        const double* v, double* partials, double* out, cudaStream_t st) {
+  dim3 gr = pad_grid(g, kBlk);
+  k_diagnostics<<<gr, kBlk, 0, st>>>(c, g, Vu, Vv, u, v, partials);
+  k_diagnostics_final<<<1, 256, 0, st>>>(partials, (int)(gr.x * gr.y), out);
+}
+
+}  // namespace ccm
