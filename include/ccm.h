@@ -73,6 +73,10 @@ typedef struct {
   double tol_inner;           /* MIXED: relative target of each FP32 inner solve */
   int max_iter_p, max_iter_h; /* iteration limits */
   int literal_offdiag;        /* 1: Eq. offdiag with separate W^xy, W^yx (not symmetric) */
+  int pressure_update;        /* volume V in the correction of Eq. pm_update,
+                                 P += Phi - (dt mu / 2 rho) V^-1 cont(M^-1 pres Phi, 0):
+                                 0 the full cell hx*hy (bounded in small cut cells; the
+                                 default), 1 the cell's fluid volume V_p, 2 no correction */
   ccm_alloc_fn alloc;
   ccm_free_fn free;
   void* alloc_ctx;

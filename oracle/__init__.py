@@ -46,7 +46,7 @@ class OrcCase(ctypes.Structure):
                 ("naca_tt", c_int), ("closed_te", c_int),
                 ("chord", c_double), ("aoa_deg", c_double), ("le_x", c_double), ("le_y", c_double),
                 ("hp_nx", c_double), ("hp_ny", c_double), ("hp_off", c_double),
-                ("literal_offdiag", c_int), ("precond", c_int), ("cheb_degree", c_int),
+                ("literal_offdiag", c_int), ("pressure_update", c_int), ("precond", c_int), ("cheb_degree", c_int),
                 ("tol_p", c_double), ("tol_h", c_double),
                 ("max_iter_p", c_int), ("max_iter_h", c_int)]
 
@@ -125,6 +125,7 @@ def case_struct(case, precond=None) -> OrcCase:
     s.chord, s.aoa_deg, s.le_x, s.le_y = g.chord, g.aoa_deg, g.le_x, g.le_y
     s.hp_nx, s.hp_ny, s.hp_off = g.hp_nx, g.hp_ny, g.hp_off
     s.literal_offdiag = int(case.literal_offdiag)
+    s.pressure_update = int(case.pressure_update)
     pc = precond if precond is not None else case.precond
     s.precond = 1 if pc == "chebyshev" else 0
     s.cheb_degree = case.cheb_degree

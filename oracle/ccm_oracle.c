@@ -45,6 +45,8 @@ typedef struct {
   double chord, aoa_deg, le_x, le_y;
   double hp_nx, hp_ny, hp_off;
   int literal_offdiag;     /* 1: Eq. offdiag with separate W^xy, W^yx */
+  int pressure_update;     /* volume dividing the viscous correction of Eq. pm_update:
+                              0 the full cell hx*hy, 1 the cell's fluid volume V_p, 2 none */
   int precond;             /* 0 Jacobi, 1 Chebyshev */
   int cheb_degree;
   double tol_p, tol_h;
@@ -1164,7 +1166,11 @@ void orc_init_velocity(const orc_case* c, const double* caps, double u0, double 
  *                                        - pres(P^{n-1/2}) + visc(mu S(U^n)) + visc(mu S_D)
  *   (dt/rho) cont(M^-1 pres Phi, 0) = cont(U*, D)      i.e.  K Phi = -(rho/dt) cont(U*, D)
  *   U^{n+1} = U* - (dt/rho) M^-1 pres(Phi)
- *   P^{n+1/2} = P^{n-1/2} + Phi - (dt mu / 2 rho) V_p^-1 cont(M^-1 pres Phi, 0)
+ *   P^{n+1/2} = P^{n-1/2} + Phi - (dt mu / 2 rho) V^-1 cont(M^-1 pres Phi, 0)
+ * where V, the volume that turns the volume-integrated Laplacian into a point value, is the
+ * full cell hx*hy by default (pressure_update = 0): dividing by the fluid volume V_p of a
+ * small cut cell (pressure_update = 1) makes the correction an unbounded gain there and the
+ * step unstable (the paper does not say which volume).
  * The first step uses conv^{-1} = conv^0; P^{-1/2} = 0; the body is fixed and no-slip
  * (D = 0), the box boundary data are steady, gravity is zero.
  * State arrays: u, v, p (P^{n-1/2}), phi (Phi^n, the warm start), cu, cv (conv^{n-1}).
@@ -1264,8 +1270,11 @@ int orc_step(const orc_case* c, const double* caps, double* u, double* v, double
   orc_poisson(c, caps, phi, kp);
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i < c->nx; ++i)
-      if (cell_active(c, caps, i, j))
-        AT(c, p, i, j) += AT(c, phi, i, j) + (dt * mu / (2.0 * rho)) * winv(c, AT(c, Vp, i, j)) * AT(c, kp, i, j);
+      if (cell_active(c, caps, i, j)) {
+        double iv = c->pressure_update == 0 ? 1.0 / (c->hx * c->hy)
+                    : c->pressure_update == 1 ? winv(c, AT(c, Vp, i, j)) : 0.0;
+        AT(c, p, i, j) += AT(c, phi, i, j) + (dt * mu / (2.0 * rho)) * iv * AT(c, kp, i, j);
+      }
   memcpy(cu, cnu, S * sizeof(double));
   memcpy(cv, cnv, S * sizeof(double));
   st->conv_h = ok_h;

@@ -39,7 +39,7 @@ class ccm_config(Structure):
                 ("bc_type", c_int * 4), ("bc_un", c_double * 4), ("bc_ut", c_double * 4),
                 ("precision", c_int), ("precond", c_int), ("cheb_degree", c_int),
                 ("tol_p", c_double), ("tol_h", c_double), ("tol_inner", c_double),
-                ("max_iter_p", c_int), ("max_iter_h", c_int), ("literal_offdiag", c_int),
+                ("max_iter_p", c_int), ("max_iter_h", c_int), ("literal_offdiag", c_int), ("pressure_update", c_int),
                 ("alloc", ccm_alloc_fn), ("free", ccm_free_fn), ("alloc_ctx", c_void_p),
                 ("stream", c_void_p)]
 
@@ -136,6 +136,7 @@ def make_config(case, precision=None, precond=None, stream=None) -> ccm_config:
     cfg.tol_p, cfg.tol_h, cfg.tol_inner = case.tol_p, case.tol_h, case.tol_inner
     cfg.max_iter_p, cfg.max_iter_h = case.max_iter_p, case.max_iter_h
     cfg.literal_offdiag = int(case.literal_offdiag)
+    cfg.pressure_update = int(getattr(case, "pressure_update", 0))
     cfg.stream = stream
     return cfg
 

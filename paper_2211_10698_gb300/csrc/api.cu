@@ -291,6 +291,7 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
       return fail(CCM_E_INVALID, "unknown boundary type");
   if (cfg->precision != CCM_FP64 && cfg->precision != CCM_MIXED) return fail(CCM_E_INVALID, "unknown precision");
   if (cfg->precond != CCM_JACOBI && cfg->precond != CCM_CHEBYSHEV) return fail(CCM_E_INVALID, "unknown preconditioner");
+  if (cfg->pressure_update < 0 || cfg->pressure_update > 2) return fail(CCM_E_INVALID, "pressure_update must be 0, 1 or 2");
   if (!(cfg->tol_p > 0) || !(cfg->tol_h > 0) || cfg->max_iter_p < 1 || cfg->max_iter_h < 1)
     return fail(CCM_E_INVALID, "solver tolerances and limits must be positive");
   ccm_case c = new ccm_case_s();
@@ -366,7 +367,7 @@ ccm_status ccm_set_geometry(ccm_case c, const ccm_geometry* geo) {
   }
   cudaStream_t st = c->st;
   CUDA_TRY(launch_capacities(*geo, g, c->caps.a, st));
-  launch_derive(g, c->bc, c->ph, c->cfg.literal_offdiag, c->caps, c->co, st);
+  launch_derive(g, c->bc, c->ph, c->cfg.literal_offdiag, c->cfg.pressure_update, c->caps, c->co, st);
   // lifting of the box data through the viscous operator: visc(S(0, D))
   CUDA_TRY(cudaMemsetAsync(c->t0, 0, g.count() * sizeof(double), st));
   CUDA_TRY(cudaMemsetAsync(c->t1, 0, g.count() * sizeof(double), st));

@@ -76,8 +76,8 @@ struct HelmholtzSolve {
 cudaError_t launch_capacities(const ccm_geometry& geo, const Geom& g, double* const* caps_dev, cudaStream_t st);
 
 // operators.cu
-void launch_derive(const Geom& g, const Bc& bc, const Phys& ph, int literal, const CapPtrs& cp, const CoefPtrs& o,
-                   cudaStream_t st);
+void launch_derive(const Geom& g, const Bc& bc, const Phys& ph, int literal, int pupdate, const CapPtrs& cp,
+                   const CoefPtrs& o, cudaStream_t st);
 void launch_fill_bc(const Geom& g, const Bc& bc, double* u, double* v, double scale, cudaStream_t st);
 void launch_cont(const Coefs& c, const Geom& g, const double* u, const double* v, double* out, cudaStream_t st);
 void launch_pres(const Coefs& c, const Geom& g, const double* p, double* ou, double* ov, cudaStream_t st);

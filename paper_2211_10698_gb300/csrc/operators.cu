@@ -58,7 +58,7 @@ __global__ void k_derive1(Geom g, Bc bc, Phys ph, int literal, CapPtrs cp, CoefP
   }
 }
 
-__global__ void k_derive2(Geom g, Phys ph, CapPtrs cp, CoefPtrs o) {
+__global__ void k_derive2(Geom g, Phys ph, int pupdate, CapPtrs cp, CoefPtrs o) {
   PAD_IJ(g)
   const bool dom = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
   double s = 0.0;
@@ -69,7 +69,9 @@ __global__ void k_derive2(Geom g, Phys ph, CapPtrs cp, CoefPtrs o) {
   o.diagk[k] = a ? s : (dom ? 1.0 : 0.0);
   const double eps = 1e-12 * g.hx * g.hy;
   const double Vp = cp.a[cap_slot(0, CK_V)][k];
-  o.pfac[k] = a ? (ph.dt * ph.mu / (2.0 * ph.rho)) * inv_or_zero(Vp, eps) : 0.0;
+  // volume that turns the volume-integrated Laplacian of Eq. pm_update into a point value
+  const double iv = pupdate == 0 ? 1.0 / (g.hx * g.hy) : (pupdate == 1 ? inv_or_zero(Vp, eps) : 0.0);
+  o.pfac[k] = a ? (ph.dt * ph.mu / (2.0 * ph.rho)) * iv : 0.0;
   o.cu32[k] = (float)o.cu[k];
   o.cv32[k] = (float)o.cv[k];
   o.invdk32[k] = (float)o.invdk[k];
@@ -302,10 +304,10 @@ __global__ void k_diagnostics_final(const double* partials, int nb, double* out)
 // ---------------------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------------------
-void launch_derive(const Geom& g, const Bc& bc, const Phys& ph, int literal, const CapPtrs& cp, const CoefPtrs& o,
-                   cudaStream_t st) {
+void launch_derive(const Geom& g, const Bc& bc, const Phys& ph, int literal, int pupdate, const CapPtrs& cp,
+                   const CoefPtrs& o, cudaStream_t st) {
   k_derive1<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, bc, ph, literal, cp, o);
-  k_derive2<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, ph, cp, o);
+  k_derive2<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, ph, pupdate, cp, o);
 }
 void launch_fill_bc(const Geom& g, const Bc& bc, double* u, double* v, double scale, cudaStream_t st) {
   k_fill_bc<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, bc, u, v, scale);

@@ -27,15 +27,63 @@ __device__ __forceinline__ void publish(double* partials, int nb, const double* 
     for (int q = 0; q < nv; ++q) partials[(size_t)q * nb + blockIdx.x] = v[q];
 }
 
-template <class T>
-__global__ void __launch_bounds__(kPcgThreads) k_pcg_poisson(PoissonSolve<T> a) {
-  __shared__ double sm[32 * 5];
+// Sum NV per-thread values over the block through shared memory; only warp 0 adds (in a
+// fixed order), so the FP64 cost is per block, not per thread.  Result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum_smem(double (&v)[NV], double (*red)[kPcgThreads]) {
+#pragma unroll
+  for (int q = 0; q < NV; ++q) red[q][threadIdx.x] = v[q];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int m = lane; m < (int)blockDim.x; m += 32) s += red[q][m];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      v[q] = s;
+    }
+  }
+}
+
+// Cells of this block: one contiguous chunk of the row-major interior, balanced to +-1 cell
+// across blocks (the FP64 pipe of each SM is the bottleneck, so per-SM work must be even).
+struct Chunk {
+  int t0, t1;
+  __device__ Chunk(int ncell) {
+    t0 = (int)((long long)ncell * blockIdx.x / gridDim.x);
+    t1 = (int)((long long)ncell * (blockIdx.x + 1) / gridDim.x);
+  }
+};
+
+// Walks t = first, first + stride, ... < end, keeping (i, j) of the interior cell t.
+struct CellWalk {
+  int t, i, j;
+  const int nx, stride, end;
+  __device__ CellWalk(int first, int stride_, int end_, int nx_) : t(first), nx(nx_), stride(stride_), end(end_) {
+    j = first / nx;
+    i = first - j * nx;
+  }
+  __device__ bool ok() const { return t < end; }
+  __device__ void next() {
+    t += stride;
+    i += stride;
+    while (i >= nx) { i -= nx; ++j; }
+  }
+};
+
+template <class T, bool ZM>
+__global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson(PoissonSolve<T> a) {
+  __shared__ double red[5][kPcgThreads];
+  __shared__ double sm[8];
   unsigned int target = 0;
   const int nb = gridDim.x;
   const Geom g = a.g;
   const int nx = g.nx;
-  const int ncell = g.nx * g.ny;
-  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, ts = gridDim.x * blockDim.x;
+  const Chunk ch(g.nx * g.ny);
+  const int first = ch.t0 + threadIdx.x, stride = blockDim.x;
+  const size_t P_ = (size_t)g.pitch;
   const T* __restrict__ cu = a.cu;
   const T* __restrict__ cv = a.cv;
   const T* __restrict__ invd = a.invd;
@@ -47,9 +95,8 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_poisson(PoissonSolve<T> a) 
 
   // r = b - K x, z = D^-1 r
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int t = t0; t < ncell; t += ts) {
-    const int j = t / nx, i = t - j * nx;
-    const size_t k = g.idx(i, j);
+  for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) {
+    const size_t k = g.idx(w.i, w.j);
     const T bk = a.b[k];
     const T rk = bk - poisson_row(cu, cv, act, g, x, k);
     const T zk = invd[k] * rk;
@@ -59,14 +106,14 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_poisson(PoissonSolve<T> a) 
     v[0] += (double)rk * (double)zk;
     v[1] += (double)rk * (double)rk;
     v[2] += (double)bk * (double)bk;
-    if (act[k]) { v[3] += (double)zk; v[4] += (double)rk; }
+    if (ZM && act[k]) { v[3] += (double)zk; v[4] += (double)rk; }
   }
-  block_sum<5>(v, sm);
+  block_sum_smem<5>(v, red);
   publish(a.partials, nb, v, 5);
   bool ok = grid_sync(a.bar, target);
   double s[5];
   if (ok) grid_sum<5>(a.partials, nb, s, sm);
-  double zmean = (ok && a.zero_mean) ? s[3] / a.n_act : 0.0;
+  double zmean = (ok && ZM) ? s[3] / a.n_act : 0.0;
   double rz = ok ? s[0] - zmean * s[4] : 0.0, rr = ok ? s[1] : 0.0, bb = ok ? s[2] : 0.0;
   const double tol2 = a.tol * a.tol;
   double beta = 0.0;
@@ -75,26 +122,24 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_poisson(PoissonSolve<T> a) 
   T* pold = a.p0;
   T* pnew = a.p1;
   if (ok && bb == 0.0) {
-    for (int t = t0; t < ncell; t += ts) {
-      const int j = t / nx, i = t - j * nx;
-      x[g.idx(i, j)] = (T)0;
-    }
+    for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) x[g.idx(w.i, w.j)] = (T)0;
     conv = true;
   }
   while (ok && !conv) {
     if (rr <= tol2 * bb) { conv = true; break; }
     if (it >= a.max_iter) break;
     const T tb = (T)beta, tzm = (T)zmean;
-    // phase A
+    // phase A: p = z + beta p_old (recomputed at the four neighbours), q = K p, p.q
     double pq[1] = {0.0};
-    for (int t = t0; t < ncell; t += ts) {
-      const int j = t / nx, i = t - j * nx;
-      const size_t k = g.idx(i, j);
-      auto P = [&](size_t m) -> T { return (z[m] - (act[m] ? tzm : (T)0)) + tb * pold[m]; };
+    for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) {
+      const size_t k = g.idx(w.i, w.j);
+      auto P = [&](size_t m) -> T {
+        if (ZM) return (z[m] - (act[m] ? tzm : (T)0)) + tb * pold[m];
+        return z[m] + tb * pold[m];
+      };
       const T pc = P(k);
       T qk;
       if (act[k]) {
-        const size_t P_ = (size_t)g.pitch;
         qk = cu[k] * (pc - P(k - 1)) + cu[k + 1] * (pc - P(k + 1)) + cv[k] * (pc - P(k - P_)) +
              cv[k + P_] * (pc - P(k + P_));
       } else {
@@ -104,33 +149,44 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_poisson(PoissonSolve<T> a) 
       q[k] = qk;
       pq[0] += (double)pc * (double)qk;
     }
-    block_sum<1>(pq, sm);
+    block_sum_smem<1>(pq, red);
     publish(a.partials, nb, pq, 1);
     if (!grid_sync(a.bar, target)) { ok = false; break; }
     double spq[1];
     grid_sum<1>(a.partials, nb, spq, sm);
     const double alpha = rz / spq[0];
     const T ta = (T)alpha;
-    // phase B
-    double w[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int t = t0; t < ncell; t += ts) {
-      const int j = t / nx, i = t - j * nx;
-      const size_t k = g.idx(i, j);
+    // phase B: x += alpha p, r -= alpha q, z = D^-1 r, r.z, r.r
+    double wv[4] = {0.0, 0.0, 0.0, 0.0};
+    for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) {
+      const size_t k = g.idx(w.i, w.j);
       x[k] += ta * pnew[k];
       const T rk = r[k] - ta * q[k];
       const T zk = invd[k] * rk;
       r[k] = rk;
       z[k] = zk;
-      w[0] += (double)rk * (double)zk;
-      w[1] += (double)rk * (double)rk;
-      if (act[k]) { w[2] += (double)zk; w[3] += (double)rk; }
+      wv[0] += (double)rk * (double)zk;
+      wv[1] += (double)rk * (double)rk;
+      if (ZM && act[k]) { wv[2] += (double)zk; wv[3] += (double)rk; }
     }
-    block_sum<4>(w, sm);
-    publish(a.partials, nb, w, 4);
-    if (!grid_sync(a.bar, target)) { ok = false; break; }
     double sw[4];
-    grid_sum<4>(a.partials, nb, sw, sm);
-    zmean = a.zero_mean ? sw[2] / a.n_act : 0.0;
+    if (ZM) {
+      block_sum_smem<4>(wv, red);
+      publish(a.partials, nb, wv, 4);
+    } else {
+      double w2[2] = {wv[0], wv[1]};
+      block_sum_smem<2>(w2, red);
+      publish(a.partials, nb, w2, 2);
+    }
+    if (!grid_sync(a.bar, target)) { ok = false; break; }
+    if (ZM) {
+      grid_sum<4>(a.partials, nb, sw, sm);
+    } else {
+      double s2[2];
+      grid_sum<2>(a.partials, nb, s2, sm);
+      sw[0] = s2[0]; sw[1] = s2[1]; sw[2] = 0.0; sw[3] = 0.0;
+    }
+    zmean = ZM ? sw[2] / a.n_act : 0.0;
     const double rz_new = sw[0] - zmean * sw[3];
     beta = rz_new / rz;
     rz = rz_new;
@@ -316,7 +372,7 @@ int pcg_partials_needed() {
 
 template <class T>
 cudaError_t run_poisson_pcg(PoissonSolve<T> a, cudaStream_t st) {
-  const void* fn = (const void*)k_pcg_poisson<T>;
+  const void* fn = a.zero_mean ? (const void*)k_pcg_poisson<T, true> : (const void*)k_pcg_poisson<T, false>;
   const int blocks = coop_blocks(fn, kPcgThreads, 2);
   if (a.zero_mean) {
     // singular system: warm start and right-hand side projected onto zero-mean fields

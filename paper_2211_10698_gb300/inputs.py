@@ -85,6 +85,7 @@ class Case:
     perturb_sigma: float = 0.0
     seed: int = SEED
     literal_offdiag: int = 0
+    pressure_update: int = 0       # volume in the pressure-update correction: 0 hx*hy, 1 V_p, 2 none
 
     @property
     def hx(self) -> float:

@@ -176,6 +176,22 @@ def test_steps(name, nsteps):
     assert gs["max_div"] < 1e-10 * max(1.0, np.abs(extra["b"]).max())
 
 
+@pytest.mark.parametrize("pupdate", [0, 1, 2])
+def test_pressure_update_volume_options(pupdate):
+    """The three readings of the volume in the correction of Eq. pm_update agree with the
+    oracle (0: full cell, the default, 1: fluid volume V_p, 2: no correction)."""
+    case = CASES["ragged"]()
+    case.tol_p = case.tol_h = 1e-13
+    case.pressure_update = pupdate
+    o = O.Oracle(case)
+    g = ccm.Case(case)
+    s = o.init_state()
+    o.step(s, 3)
+    g.step(3)
+    for f, ref in ((ccm.CCM_F_U, s["u"]), (ccm.CCM_F_P, s["p"])):
+        assert rel(g.get_field(f), ref) < STEP_TOL, f
+
+
 def test_c1_cylinder_re40_100_steps():
     """The 128x64 Re 40 cylinder configuration, 100 steps; CG tolerances tightened to 1e-13
     on both sides so that the comparison measures the discretisation, not the stopping
