@@ -54,9 +54,10 @@ struct ccm_case_s {
   long long nstep = 0;
   // step work
   double *ustar, *vstar, *div, *rhs_u, *rhs_v, *rhs_p;
-  double *pr, *pz, *pp0, *pp1, *pq;
+  double *pr, *pz, *pp0, *pp1, *pq, *pz2, *pw1;
   double *hr_u, *hr_v, *hz_u, *hz_v, *hp_u, *hp_v, *hq_u, *hq_v;
-  float *fx, *fb, *fr, *fz, *fp0, *fp1, *fq;
+  float *fx, *fb, *fr, *fz, *fp0, *fp1, *fq, *fz2, *fw1;
+  double* mixed_sums;
   double *t0, *t1, *t2, *t3, *t4, *t5;
   double* partials;
   double* dpart;
@@ -74,6 +75,10 @@ struct ccm_case_s {
   long long poisson_iters_timed = 0;
   double poisson_ms = 0.0;
   long long steps_pending = 0;
+  // statistics of mixed-precision solves (accumulated on the host)
+  long long mixed_total = 0;
+  int mixed_last = 0, mixed_outer = 0, mixed_nconv = 0;
+  double mixed_rr = 0.0, mixed_bb = 0.0;
 };
 
 namespace {
@@ -97,20 +102,23 @@ void carve(ccm_case c, Carver& cv) {
   o.role_u = cv.take<int8_t>(N);
   o.role_v = cv.take<int8_t>(N);
   o.act = cv.take<int8_t>(N);
+  o.kind = cv.take<int8_t>(N);
   double** dd[] = {&o.cu, &o.cv, &o.invdk, &o.diagk, &o.gfu, &o.gfv, &o.pfac, &o.massu, &o.massv, &o.wxx, &o.wyy,
                    &o.wxa, &o.wxb, &o.invdhu, &o.invdhv, &o.liftu, &o.liftv};
   for (double** p : dd) *p = cv.take<double>(N);
   o.cu32 = cv.take<float>(N);
   o.cv32 = cv.take<float>(N);
   o.invdk32 = cv.take<float>(N);
+  o.diagk32 = cv.take<float>(N);
   double** st[] = {&c->u, &c->v, &c->p, &c->phi, &c->cnu[0], &c->cnu[1], &c->cnv[0], &c->cnv[1],
                    &c->ustar, &c->vstar, &c->div, &c->rhs_u, &c->rhs_v, &c->rhs_p,
-                   &c->pr, &c->pz, &c->pp0, &c->pp1, &c->pq,
+                   &c->pr, &c->pz, &c->pp0, &c->pp1, &c->pq, &c->pz2, &c->pw1,
                    &c->hr_u, &c->hr_v, &c->hz_u, &c->hz_v, &c->hp_u, &c->hp_v, &c->hq_u, &c->hq_v,
                    &c->t0, &c->t1, &c->t2, &c->t3, &c->t4, &c->t5};
   for (double** p : st) *p = cv.take<double>(N);
-  float** fl[] = {&c->fx, &c->fb, &c->fr, &c->fz, &c->fp0, &c->fp1, &c->fq};
+  float** fl[] = {&c->fx, &c->fb, &c->fr, &c->fz, &c->fp0, &c->fp1, &c->fq, &c->fz2, &c->fw1};
   for (float** p : fl) *p = cv.take<float>(N);
+  c->mixed_sums = cv.take<double>(4);
   c->partials = cv.take<double>((size_t)pcg_partials_needed());
   c->dpart = cv.take<double>((size_t)3 * diagnostics_partials(c->g) + 8);
   c->bar_count = cv.take<unsigned int>(4);
@@ -211,11 +219,23 @@ ccm_status check_cuda_errors(const char* where) {
   return CCM_OK;
 }
 
+// Face coefficients of an uncut cell, A^2/V = hy/hx (x faces) and hx/hy (y faces).
+template <class T>
+void set_uniform_coefficients(ccm_case c, PoissonSolve<T>& a) {
+  a.creg_x = c->g.hy / c->g.hx;
+  a.creg_y = c->g.hx / c->g.hy;
+  a.dreg = 2.0 * (a.creg_x + a.creg_y);
+  a.invd_reg = 1.0 / a.dreg;
+}
+
 ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
   PoissonSolve<double> a{};
   a.g = c->g;
-  a.cu = c->co.cu; a.cv = c->co.cv; a.invd = c->co.invdk; a.act = c->co.act;
+  a.cu = c->co.cu; a.cv = c->co.cv; a.dk = c->co.diagk; a.invd = c->co.invdk; a.kind = c->co.kind;
+  set_uniform_coefficients(c, a);
   a.x = x; a.b = b; a.r = c->pr; a.z = c->pz; a.p0 = c->pp0; a.p1 = c->pp1; a.q = c->pq;
+  a.z2 = c->pz2; a.w1 = c->pw1;
+  a.cheb = c->cfg.precond == CCM_CHEBYSHEV ? c->cfg.cheb_degree : 1;
   a.tol = c->cfg.tol_p; a.max_iter = c->cfg.max_iter_p;
   a.zero_mean = c->zero_mean; a.n_act = c->n_act;
   a.partials = c->partials;
@@ -248,7 +268,65 @@ cudaEvent_t next_event(ccm_case c) {
   return c->ev_pool[c->ev_used++];
 }
 
+// Mixed precision: FP64 residual, FP32 PCG on the correction equation K d = r to tol_inner,
+// x += d, until the FP64 residual meets tol_p (or 60 refinement sweeps).
+ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
+  const Geom& g = c->g;
+  cudaStream_t st = c->st;
+  int inner_total = 0, outer = 0;
+  double sums[2] = {0.0, 0.0};
+  bool conv = false;
+  for (; outer < 60; ++outer) {
+    launch_residual64(c->cv, g, x, b, c->fb, c->dpart, c->mixed_sums, st);
+    CUDA_TRY(cudaMemcpyAsync(sums, c->mixed_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (sums[1] == 0.0 || sums[0] <= c->cfg.tol_p * c->cfg.tol_p * sums[1]) { conv = true; break; }
+    CUDA_TRY(cudaMemsetAsync(c->fx, 0, g.count() * sizeof(float), st));
+    PoissonSolve<float> a{};
+    a.g = g;
+    a.cu = c->co.cu32; a.cv = c->co.cv32; a.dk = c->co.diagk32; a.invd = c->co.invdk32; a.kind = c->co.kind;
+    set_uniform_coefficients(c, a);
+    a.x = c->fx; a.b = c->fb; a.r = c->fr; a.z = c->fz; a.p0 = c->fp0; a.p1 = c->fp1; a.q = c->fq;
+    a.z2 = c->fz2; a.w1 = c->fw1;
+    a.cheb = c->cfg.precond == CCM_CHEBYSHEV ? c->cfg.cheb_degree : 1;
+    a.tol = c->cfg.tol_inner > 0 ? c->cfg.tol_inner : 1e-5;
+    a.max_iter = c->cfg.max_iter_p;
+    a.zero_mean = c->zero_mean; a.n_act = c->n_act;
+    a.partials = c->partials;
+    a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+    a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, nullptr, nullptr};
+    CUDA_TRY(run_poisson_pcg<float>(a, st));
+    c->launches += 1 + (c->zero_mean ? 4 : 0);
+    int it = 0;
+    CUDA_TRY(cudaMemcpyAsync(&it, &c->ds->iters_p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    inner_total += it;
+    launch_add_correction(g, c->co.act, x, c->fx, st);
+    c->launches += 3;
+  }
+  c->launches += 2;
+  c->mixed_total += inner_total;
+  c->mixed_last = inner_total;
+  c->mixed_outer = outer;
+  c->mixed_rr = sums[0];
+  c->mixed_bb = sums[1];
+  if (!conv) c->mixed_nconv++;
+  return check_cuda_errors("mixed Poisson solve");
+}
+
 ccm_status poisson_solve(ccm_case c, double* x, double* b) {
+  if (c->cfg.precision == CCM_MIXED) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+      e0 = next_event(c);
+      e1 = next_event(c);
+      if (e0) cudaEventRecord(e0, c->st);
+    }
+    ccm_status s = solve_poisson_mixed(c, x, b);
+    if (c->timing && e1) cudaEventRecord(e1, c->st);
+    c->poisson_launches++;
+    return s;
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
     e0 = next_event(c);
@@ -292,6 +370,8 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
   if (cfg->precision != CCM_FP64 && cfg->precision != CCM_MIXED) return fail(CCM_E_INVALID, "unknown precision");
   if (cfg->precond != CCM_JACOBI && cfg->precond != CCM_CHEBYSHEV) return fail(CCM_E_INVALID, "unknown preconditioner");
   if (cfg->pressure_update < 0 || cfg->pressure_update > 2) return fail(CCM_E_INVALID, "pressure_update must be 0, 1 or 2");
+  if (cfg->precond == CCM_CHEBYSHEV && !cheb_degree_supported(cfg->cheb_degree))
+    return fail(CCM_E_INVALID, "cheb_degree must be 1-6 or 8");
   if (!(cfg->tol_p > 0) || !(cfg->tol_h > 0) || cfg->max_iter_p < 1 || cfg->max_iter_h < 1)
     return fail(CCM_E_INVALID, "solver tolerances and limits must be positive");
   ccm_case c = new ccm_case_s();
@@ -577,6 +657,15 @@ static ccm_status finish_stats(ccm_case c, ccm_step_stats* stats) {
   ccm_status s;
   if ((s = read_stats(c, h)) != CCM_OK) return s;
   if (c->timing) collect_timing(c);
+  if (c->cfg.precision == CCM_MIXED) {
+    h.total_p = c->mixed_total;
+    h.iters_p = c->mixed_last;
+    h.rr_p = c->mixed_rr;
+    h.bb_p = c->mixed_bb;
+    h.nconv += c->mixed_nconv;
+    c->mixed_total = 0;
+    c->mixed_nconv = 0;
+  }
   if (stats) {
     stats->steps = (int)c->steps_pending;
     stats->iters_p = h.total_p;
@@ -663,13 +752,23 @@ ccm_status ccm_solve_pressure(ccm_case c, const double* rhs_host, ccm_solve_stat
   if ((s = poisson_solve(c, c->phi, c->rhs_p)) != CCM_OK) return s;
   DevStats h{};
   if ((s = read_stats(c, h)) != CCM_OK) return s;
+  int conv = h.conv_p, outer = 1;
+  if (c->cfg.precision == CCM_MIXED) {
+    h.iters_p = c->mixed_last;
+    h.rr_p = c->mixed_rr;
+    h.bb_p = c->mixed_bb;
+    conv = c->mixed_nconv == 0;
+    outer = c->mixed_outer;
+    c->mixed_total = 0;
+    c->mixed_nconv = 0;
+  }
   if (stats) {
     stats->iters = h.iters_p;
-    stats->outer = 1;
+    stats->outer = outer;
     stats->rel_res = h.bb_p > 0 ? sqrt(h.rr_p / h.bb_p) : 0.0;
-    stats->converged = h.conv_p;
+    stats->converged = conv;
   }
-  if (!h.conv_p) return fail(CCM_E_NOT_CONVERGED, "Poisson PCG reached its iteration limit");
+  if (!conv) return fail(CCM_E_NOT_CONVERGED, "Poisson solve reached its iteration limit");
   return CCM_OK;
 }
 

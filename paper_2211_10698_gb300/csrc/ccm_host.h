@@ -15,10 +15,11 @@ struct CoefPtrs {
   int8_t* role_u;
   int8_t* role_v;
   int8_t* act;
+  int8_t* kind;           // Poisson row kind: 0 inactive, 1 uncut, 2 cut
   double *cu, *cv, *invdk, *diagk, *gfu, *gfv, *pfac, *massu, *massv;
   double *wxx, *wyy, *wxa, *wxb;
   double *invdhu, *invdhv, *liftu, *liftv;
-  float *cu32, *cv32, *invdk32;
+  float *cu32, *cv32, *invdk32, *diagk32;
 };
 
 // Where a solver kernel reports: iterations, final squared residual and right-hand side
@@ -37,8 +38,11 @@ struct PoissonSolve {
   Geom g;
   const T* cu;
   const T* cv;
-  const T* invd;
-  const int8_t* act;
+  const T* dk;            // diagonal of K
+  const T* invd;          // 1 / diagonal
+  const int8_t* kind;     // 0 inactive (identity row), 1 uncut (constant coefficients), 2 cut
+  double creg_x, creg_y;  // face coefficients of an uncut cell: hy/hx and hx/hy
+  double dreg, invd_reg;  // their diagonal 2 (creg_x + creg_y) and its inverse
   T* x;
   T* b;
   T* r;
@@ -46,6 +50,9 @@ struct PoissonSolve {
   T* p0;
   T* p1;
   T* q;
+  T* z2;          // second z buffer (Chebyshev)
+  T* w1;          // Chebyshev increment
+  int cheb;       // 1: Jacobi; k > 1: k-step Chebyshev preconditioner
   double tol;
   int max_iter;
   int zero_mean;
@@ -97,11 +104,15 @@ void launch_divergence(const Coefs& c, const Geom& g, const Phys& ph, const doub
                        double* rhs, cudaStream_t st);
 void launch_project(const Coefs& c, const Geom& g, const double* phi, double* u, double* v, double* p, cudaStream_t st);
 int diagnostics_partials(const Geom& g);
+void launch_residual64(const Coefs& c, const Geom& g, const double* x, const double* b, float* r32, double* partials,
+                       double* out2, cudaStream_t st);
+void launch_add_correction(const Geom& g, const int8_t* act, double* x, const float* d, cudaStream_t st);
 void launch_diagnostics(const Coefs& c, const Geom& g, const double* Vu, const double* Vv, const double* u,
                         const double* v, double* partials, double* out, cudaStream_t st);
 
 // pcg.cu
 int pcg_partials_needed();
+bool cheb_degree_supported(int k);
 template <class T>
 cudaError_t run_poisson_pcg(PoissonSolve<T> a, cudaStream_t st);
 cudaError_t run_helmholtz_pcg(HelmholtzSolve a, cudaStream_t st);

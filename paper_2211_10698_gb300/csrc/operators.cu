@@ -75,6 +75,16 @@ __global__ void k_derive2(Geom g, Phys ph, int pupdate, CapPtrs cp, CoefPtrs o) 
   o.cu32[k] = (float)o.cu[k];
   o.cv32[k] = (float)o.cv[k];
   o.invdk32[k] = (float)o.invdk[k];
+  o.diagk32[k] = (float)o.diagk[k];
+  // row kind for the PCG: uncut rows (all four faces full) use the uniform-grid constants
+  int8_t kind = 0;
+  if (a) {
+    const double cx = g.hy / g.hx, cy = g.hx / g.hy, e = 1e-14;
+    const bool full = fabs(o.cu[k] - cx) <= e * cx && fabs(o.cu[k + 1] - cx) <= e * cx &&
+                      fabs(o.cv[k] - cy) <= e * cy && fabs(o.cv[k + g.pitch] - cy) <= e * cy;
+    kind = full ? 1 : 2;
+  }
+  o.kind[k] = kind;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -302,8 +312,71 @@ __global__ void k_diagnostics_final(const double* partials, int nb, double* out)
 }
 
 // ---------------------------------------------------------------------------------------
+// Mixed-precision refinement of the Poisson solve: FP64 residual r = b - K x (stored to
+// FP32 for the inner solve) with per-block sums of r.r and b.b, and x += d.
+// ---------------------------------------------------------------------------------------
+__global__ void k_residual64(Coefs c, Geom g, const double* x, const double* b, float* r32, double* partials) {
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
+  const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
+  double rr = 0.0, bb = 0.0;
+  if (i <= g.nx + 1 && j <= g.ny + 1) {
+    const size_t k = g.idx(i, j);
+    float rk32 = 0.0f;
+    if (c.act[k]) {
+      const double rk = b[k] - poisson_row(c.cu, c.cv, c.act, g, x, k);
+      rk32 = (float)rk;
+      rr = rk * rk;
+      bb = b[k] * b[k];
+    }
+    r32[k] = rk32;
+  }
+  __shared__ double sm[2][256];
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  sm[0][t] = rr;
+  sm[1][t] = bb;
+  __syncthreads();
+  for (int s = (blockDim.x * blockDim.y) / 2; s > 0; s >>= 1) {
+    if (t < s) { sm[0][t] += sm[0][t + s]; sm[1][t] += sm[1][t + s]; }
+    __syncthreads();
+  }
+  if (t == 0) {
+    const size_t bi = (size_t)blockIdx.y * gridDim.x + blockIdx.x, nb = (size_t)gridDim.x * gridDim.y;
+    partials[bi] = sm[0][0];
+    partials[nb + bi] = sm[1][0];
+  }
+}
+
+__global__ void k_sum2(const double* partials, int nb, double* out) {
+  __shared__ double sm[2][256];
+  const int t = threadIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int k = t; k < nb; k += blockDim.x) { a += partials[k]; b += partials[nb + k]; }
+  sm[0][t] = a; sm[1][t] = b;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) { sm[0][t] += sm[0][t + s]; sm[1][t] += sm[1][t + s]; }
+    __syncthreads();
+  }
+  if (t == 0) { out[0] = sm[0][0]; out[1] = sm[1][0]; }
+}
+
+__global__ void k_add_correction(Geom g, const int8_t* act, double* x, const float* d) {
+  PAD_IJ(g)
+  if (act[k]) x[k] += (double)d[k];
+}
+
+// ---------------------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------------------
+void launch_residual64(const Coefs& c, const Geom& g, const double* x, const double* b, float* r32, double* partials,
+                       double* out2, cudaStream_t st) {
+  dim3 gr = pad_grid(g, kBlk);
+  k_residual64<<<gr, kBlk, 0, st>>>(c, g, x, b, r32, partials);
+  k_sum2<<<1, 256, 0, st>>>(partials, (int)(gr.x * gr.y), out2);
+}
+void launch_add_correction(const Geom& g, const int8_t* act, double* x, const float* d, cudaStream_t st) {
+  k_add_correction<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, act, x, d);
+}
 void launch_derive(const Geom& g, const Bc& bc, const Phys& ph, int literal, int pupdate, const CapPtrs& cp,
                    const CoefPtrs& o, cudaStream_t st) {
   k_derive1<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, bc, ph, literal, cp, o);

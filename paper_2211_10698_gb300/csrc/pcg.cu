@@ -73,103 +73,198 @@ struct CellWalk {
   }
 };
 
-template <class T, bool ZM>
+// Chebyshev iteration for K z = r from zero on the Jacobi-scaled operator, eigenvalue
+// interval [lmax/30, lmax] with lmax = 2 (Gershgorin bound for a diagonally dominant
+// M-matrix scaled by its diagonal), CHEB steps in all (Saad, Chebyshev acceleration).  On
+// entry z = w1 = D^-1 r / theta (the first step, written by the caller); each further step
+// needs z at the stencil neighbours, so steps are separated by grid barriers and z
+// alternates between two buffers.  Returns the buffer that holds the result.
+struct ChebCoef {
+  static constexpr double lmax = 2.0, lmin = 2.0 / 30.0;
+  static constexpr double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+};
+
+// K x at one cell in diagonal form, d x_c - sum_f c_f x_nbr.  Cells whose four faces and
+// volume are uncut (kind 1) use the constant coefficients of the uniform grid, so their
+// coefficient arrays are not read; cut cells (kind 2) read them; other cells (kind 0:
+// inactive, identity row) return x_c.
+template <class T>
+struct KRow {
+  const T* cu;
+  const T* cv;
+  const T* dk;
+  const int8_t* kind;
+  T cx, cy, dreg;
+  size_t P;
+  __device__ __forceinline__ T operator()(const T* x, size_t k) const {
+    const int8_t t = kind[k];
+    const T xc = x[k];
+    if (t == 1) return dreg * xc - cx * (x[k - 1] + x[k + 1]) - cy * (x[k - P] + x[k + P]);
+    if (t == 2)
+      return dk[k] * xc - cu[k] * x[k - 1] - cu[k + 1] * x[k + 1] - cv[k] * x[k - P] - cv[k + P] * x[k + P];
+    return xc;
+  }
+};
+
+// Per-block scalar state of the PCG recurrences, computed by thread 0 only (FP64 division
+// is a software sequence on this part) and read by every thread from shared memory.
+struct PcgScalars {
+  double rz, rr, bb, beta, alpha, zmean;
+  int it, stop;  // stop: 0 continue, 1 converged, 2 iteration limit
+};
+
+template <class T, bool ZM, int CHEB>
 __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson(PoissonSolve<T> a) {
   __shared__ double red[5][kPcgThreads];
   __shared__ double sm[8];
+  __shared__ PcgScalars S;
   unsigned int target = 0;
   const int nb = gridDim.x;
   const Geom g = a.g;
   const int nx = g.nx;
   const Chunk ch(g.nx * g.ny);
   const int first = ch.t0 + threadIdx.x, stride = blockDim.x;
-  const size_t P_ = (size_t)g.pitch;
-  const T* __restrict__ cu = a.cu;
-  const T* __restrict__ cv = a.cv;
+  const KRow<T> K{a.cu, a.cv, a.dk, a.kind, (T)a.creg_x, (T)a.creg_y, (T)a.dreg, (size_t)g.pitch};
   const T* __restrict__ invd = a.invd;
-  const int8_t* __restrict__ act = a.act;
+  const int8_t* __restrict__ kind = a.kind;
   T* __restrict__ x = a.x;
   T* __restrict__ r = a.r;
-  T* __restrict__ z = a.z;
   T* __restrict__ q = a.q;
+  T* __restrict__ p = a.p0;
+  T* zc = a.z;    // preconditioned residual
+  T* zo = a.z2;   // Chebyshev: the other z buffer
+  const T inv_theta = (T)(1.0 / ChebCoef::theta);
+  const T ireg = (T)a.invd_reg;
+  auto Dinv = [&](size_t k) -> T { return kind[k] == 1 ? ireg : invd[k]; };
 
-  // r = b - K x, z = D^-1 r
+  // Chebyshev steps 1..CHEB-1 after z = w1 = D^-1 r / theta; accumulates r.z and, for
+  // singular systems, the sums of z and r over active cells.
+  auto cheb_rest = [&](double* acc) -> bool {
+    double rho_prev = ChebCoef::delta / ChebCoef::theta;
+    for (int st = 1; st < CHEB; ++st) {
+      if (!grid_sync(a.bar, target)) return false;
+      const double rho = 1.0 / (2.0 * ChebCoef::theta / ChebCoef::delta - rho_prev);
+      const T c1 = (T)(rho * rho_prev), c2 = (T)(2.0 * rho / ChebCoef::delta);
+      const bool last = st == CHEB - 1;
+      for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) {
+        const size_t k = g.idx(w.i, w.j);
+        const T sk = Dinv(k) * (r[k] - K((const T*)zc, k));
+        const T w1 = c1 * a.w1[k] + c2 * sk;
+        a.w1[k] = w1;
+        const T zk = zc[k] + w1;
+        zo[k] = zk;
+        if (last) {
+          acc[0] += (double)r[k] * (double)zk;
+          if (ZM && kind[k]) { acc[2] += (double)zk; acc[3] += (double)r[k]; }
+        }
+      }
+      T* t = zc; zc = zo; zo = t;
+      rho_prev = rho;
+    }
+    return true;
+  };
+
+  // r = b - K x, z = M^-1 r, p = 0
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) {
     const size_t k = g.idx(w.i, w.j);
     const T bk = a.b[k];
-    const T rk = bk - poisson_row(cu, cv, act, g, x, k);
-    const T zk = invd[k] * rk;
+    const T rk = bk - K(x, k);
     r[k] = rk;
-    z[k] = zk;
-    a.p0[k] = (T)0;
-    v[0] += (double)rk * (double)zk;
+    p[k] = (T)0;
     v[1] += (double)rk * (double)rk;
     v[2] += (double)bk * (double)bk;
-    if (ZM && act[k]) { v[3] += (double)zk; v[4] += (double)rk; }
+    if (CHEB > 1) {
+      const T w1 = Dinv(k) * rk * inv_theta;
+      a.w1[k] = w1;
+      zc[k] = w1;
+    } else {
+      const T zk = Dinv(k) * rk;
+      zc[k] = zk;
+      v[0] += (double)rk * (double)zk;
+      if (ZM && kind[k]) { v[3] += (double)zk; v[4] += (double)rk; }
+    }
+  }
+  bool ok = true;
+  if (CHEB > 1) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    ok = cheb_rest(acc);
+    v[0] = acc[0]; v[3] = acc[2]; v[4] = acc[3];
   }
   block_sum_smem<5>(v, red);
   publish(a.partials, nb, v, 5);
-  bool ok = grid_sync(a.bar, target);
-  double s[5];
-  if (ok) grid_sum<5>(a.partials, nb, s, sm);
-  double zmean = (ok && ZM) ? s[3] / a.n_act : 0.0;
-  double rz = ok ? s[0] - zmean * s[4] : 0.0, rr = ok ? s[1] : 0.0, bb = ok ? s[2] : 0.0;
-  const double tol2 = a.tol * a.tol;
-  double beta = 0.0;
-  int it = 0;
-  bool conv = false;
-  T* pold = a.p0;
-  T* pnew = a.p1;
-  if (ok && bb == 0.0) {
-    for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) x[g.idx(w.i, w.j)] = (T)0;
-    conv = true;
+  ok = ok && grid_sync(a.bar, target);
+  if (ok) {
+    double s5[5];
+    grid_sum<5>(a.partials, nb, s5, sm);
+    if (threadIdx.x == 0) {
+      S.zmean = ZM ? s5[3] / a.n_act : 0.0;
+      S.rz = s5[0] - S.zmean * s5[4];
+      S.rr = s5[1];
+      S.bb = s5[2];
+      S.beta = 0.0;
+      S.it = 0;
+      S.stop = (S.bb == 0.0 || S.rr <= a.tol * a.tol * S.bb) ? 1 : (a.max_iter <= 0 ? 2 : 0);
+    }
+    __syncthreads();
   }
-  while (ok && !conv) {
-    if (rr <= tol2 * bb) { conv = true; break; }
-    if (it >= a.max_iter) break;
-    const T tb = (T)beta, tzm = (T)zmean;
-    // phase A: p = z + beta p_old (recomputed at the four neighbours), q = K p, p.q
+  if (ok && S.bb == 0.0)
+    for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) x[g.idx(w.i, w.j)] = (T)0;
+  while (ok && S.stop == 0) {
+    // phase A: p = z + beta p
+    {
+      const T tb = (T)S.beta, tzm = (T)S.zmean;
+      const T* __restrict__ z = zc;
+      for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) {
+        const size_t k = g.idx(w.i, w.j);
+        const T zk = ZM ? z[k] - (kind[k] ? tzm : (T)0) : z[k];
+        p[k] = zk + tb * p[k];
+      }
+    }
+    if (!grid_sync(a.bar, target)) { ok = false; break; }
+    // phase B: q = K p, p.q
     double pq[1] = {0.0};
     for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) {
       const size_t k = g.idx(w.i, w.j);
-      auto P = [&](size_t m) -> T {
-        if (ZM) return (z[m] - (act[m] ? tzm : (T)0)) + tb * pold[m];
-        return z[m] + tb * pold[m];
-      };
-      const T pc = P(k);
-      T qk;
-      if (act[k]) {
-        qk = cu[k] * (pc - P(k - 1)) + cu[k + 1] * (pc - P(k + 1)) + cv[k] * (pc - P(k - P_)) +
-             cv[k + P_] * (pc - P(k + P_));
-      } else {
-        qk = pc;
-      }
-      pnew[k] = pc;
+      const T qk = K(p, k);
       q[k] = qk;
-      pq[0] += (double)pc * (double)qk;
+      pq[0] += (double)p[k] * (double)qk;
     }
     block_sum_smem<1>(pq, red);
     publish(a.partials, nb, pq, 1);
     if (!grid_sync(a.bar, target)) { ok = false; break; }
-    double spq[1];
-    grid_sum<1>(a.partials, nb, spq, sm);
-    const double alpha = rz / spq[0];
-    const T ta = (T)alpha;
-    // phase B: x += alpha p, r -= alpha q, z = D^-1 r, r.z, r.r
+    {
+      double spq[1];
+      grid_sum<1>(a.partials, nb, spq, sm);
+      if (threadIdx.x == 0) S.alpha = S.rz / spq[0];
+      __syncthreads();
+    }
+    // phase C: x += alpha p, r -= alpha q, z = M^-1 r, r.z, r.r
+    const T ta = (T)S.alpha;
     double wv[4] = {0.0, 0.0, 0.0, 0.0};
     for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) {
       const size_t k = g.idx(w.i, w.j);
-      x[k] += ta * pnew[k];
+      x[k] += ta * p[k];
       const T rk = r[k] - ta * q[k];
-      const T zk = invd[k] * rk;
       r[k] = rk;
-      z[k] = zk;
-      wv[0] += (double)rk * (double)zk;
       wv[1] += (double)rk * (double)rk;
-      if (ZM && act[k]) { wv[2] += (double)zk; wv[3] += (double)rk; }
+      if (CHEB > 1) {
+        const T w1 = Dinv(k) * rk * inv_theta;
+        a.w1[k] = w1;
+        zc[k] = w1;
+      } else {
+        const T zk = Dinv(k) * rk;
+        zc[k] = zk;
+        wv[0] += (double)rk * (double)zk;
+        if (ZM && kind[k]) { wv[2] += (double)zk; wv[3] += (double)rk; }
+      }
     }
-    double sw[4];
+    if (CHEB > 1) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      if (!cheb_rest(acc)) { ok = false; break; }
+      wv[0] = acc[0]; wv[2] = acc[2]; wv[3] = acc[3];
+    }
+    double sw[4] = {0.0, 0.0, 0.0, 0.0};
     if (ZM) {
       block_sum_smem<4>(wv, red);
       publish(a.partials, nb, wv, 4);
@@ -184,22 +279,179 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson(PoissonSolve<T> 
     } else {
       double s2[2];
       grid_sum<2>(a.partials, nb, s2, sm);
-      sw[0] = s2[0]; sw[1] = s2[1]; sw[2] = 0.0; sw[3] = 0.0;
+      sw[0] = s2[0]; sw[1] = s2[1];
     }
-    zmean = ZM ? sw[2] / a.n_act : 0.0;
-    const double rz_new = sw[0] - zmean * sw[3];
-    beta = rz_new / rz;
-    rz = rz_new;
-    rr = sw[1];
-    T* tmp = pold; pold = pnew; pnew = tmp;
-    ++it;
+    if (threadIdx.x == 0) {
+      S.zmean = ZM ? sw[2] / a.n_act : 0.0;
+      const double rz_new = sw[0] - S.zmean * sw[3];
+      S.beta = rz_new / S.rz;
+      S.rz = rz_new;
+      S.rr = sw[1];
+      S.it += 1;
+      S.stop = S.rr <= a.tol * a.tol * S.bb ? 1 : (S.it >= a.max_iter ? 2 : 0);
+    }
+    __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.out.iters[0] = it;
-    a.out.rr[0] = rr;
-    a.out.bb[0] = bb;
+    const bool conv = ok && S.stop == 1;
+    a.out.iters[0] = ok ? S.it : 0;
+    a.out.rr[0] = ok ? S.rr : 0.0;
+    a.out.bb[0] = ok ? S.bb : 0.0;
     a.out.converged[0] = conv ? 1 : 0;
-    if (a.out.total) a.out.total[0] += it;
+    if (a.out.total && ok) a.out.total[0] += S.it;
+    if (!conv && a.out.nconv) a.out.nconv[0] += 1;
+  }
+}
+
+// Jacobi-preconditioned CG in the single-reduction (Chronopoulos-Gear) arrangement: the
+// same Krylov iterates as Hestenes-Stiefel PCG in exact arithmetic, with s = K p carried by
+// recurrence so that one iteration needs one SpMV, one reduction and two barriers:
+//   phase 1 (own cells): p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r
+//   phase 2:             w = K u, and the sums r.u, w.u, r.r
+// Singular systems (no outflow side): u is projected onto zero mean over the active cells
+// lazily; since K applied to a constant vanishes on active cells, w = K u is unchanged and
+// only the sums need the correction.
+template <class T, bool ZM>
+__global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_cg(PoissonSolve<T> a) {
+  __shared__ double red[6][kPcgThreads];
+  __shared__ double sm[8];
+  __shared__ PcgScalars S;
+  __shared__ double S_alpha_prev, S_gamma;
+  unsigned int target = 0;
+  const int nb = gridDim.x;
+  const Geom g = a.g;
+  const int nx = g.nx;
+  const Chunk ch(g.nx * g.ny);
+  const int first = ch.t0 + threadIdx.x, stride = blockDim.x;
+  const KRow<T> K{a.cu, a.cv, a.dk, a.kind, (T)a.creg_x, (T)a.creg_y, (T)a.dreg, (size_t)g.pitch};
+  const T* __restrict__ invd = a.invd;
+  const int8_t* __restrict__ kind = a.kind;
+  T* __restrict__ x = a.x;
+  T* __restrict__ r = a.r;
+  T* __restrict__ u = a.z;
+  T* __restrict__ w = a.q;
+  T* __restrict__ p = a.p0;
+  T* __restrict__ sv = a.p1;
+  const T ireg = (T)a.invd_reg;
+
+  // phase 0a: r = b - K x, u = D^-1 r, p = s = 0
+  double bb_part = 0.0;
+  for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
+    const size_t k = g.idx(cw.i, cw.j);
+    const T bk = a.b[k];
+    const T rk = bk - K(x, k);
+    r[k] = rk;
+    u[k] = (kind[k] == 1 ? ireg : invd[k]) * rk;
+    p[k] = (T)0;
+    sv[k] = (T)0;
+    bb_part += (double)bk * (double)bk;
+  }
+  bool ok = grid_sync(a.bar, target);
+  // phase 0b / phase 2: w = K u and the sums
+  auto phase2 = [&](double bbp) {
+    double v[6] = {0.0, 0.0, 0.0, bbp, 0.0, 0.0};
+    for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
+      const size_t k = g.idx(cw.i, cw.j);
+      const T wk = K((const T*)u, k);
+      w[k] = wk;
+      const double rk = (double)r[k], uk = (double)u[k];
+      v[0] += rk * uk;
+      v[1] += (double)wk * uk;
+      v[2] += rk * rk;
+      if (ZM && kind[k]) { v[4] += uk; v[5] += rk; }
+    }
+    // singular systems also need sum(w) over active cells: K 1 = 0 makes it zero in exact
+    // arithmetic, so the correction of w.u uses sum(w) = 0 and only r.u needs sum(r)
+    if (ZM) {
+      block_sum_smem<6>(v, red);
+      publish(a.partials, nb, v, 6);
+    } else {
+      double v4[4] = {v[0], v[1], v[2], v[3]};
+      block_sum_smem<4>(v4, red);
+      publish(a.partials, nb, v4, 4);
+    }
+  };
+  auto finish = [&](double (&s6)[6]) {
+    if (ZM) {
+      grid_sum<6>(a.partials, nb, s6, sm);
+    } else {
+      double s4[4];
+      grid_sum<4>(a.partials, nb, s4, sm);
+      s6[0] = s4[0]; s6[1] = s4[1]; s6[2] = s4[2]; s6[3] = s4[3]; s6[4] = 0.0; s6[5] = 0.0;
+    }
+  };
+  if (ok) {
+    phase2(bb_part);
+    ok = grid_sync(a.bar, target);
+  }
+  if (ok) {
+    double s6[6];
+    finish(s6);
+    if (threadIdx.x == 0) {
+      const double m = ZM ? s6[4] / a.n_act : 0.0;
+      const double gamma = s6[0] - m * s6[5];
+      const double delta = s6[1];  // (K u, u - m) = (K u, u) since sum over active of K u is zero
+      S.zmean = m;
+      S.rr = s6[2];
+      S.bb = s6[3];
+      S_gamma = gamma;
+      S.alpha = delta != 0.0 ? gamma / delta : 0.0;
+      S_alpha_prev = S.alpha;
+      S.beta = 0.0;
+      S.it = 0;
+      S.stop = (S.bb == 0.0 || S.rr <= a.tol * a.tol * S.bb) ? 1 : (a.max_iter <= 0 ? 2 : 0);
+    }
+    __syncthreads();
+  }
+  if (ok && S.bb == 0.0)
+    for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) x[g.idx(cw.i, cw.j)] = (T)0;
+  while (ok && S.stop == 0) {
+    // phase 1
+    {
+      const T ta = (T)S.alpha, tb = (T)S.beta, tm = (T)S.zmean;
+      for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
+        const size_t k = g.idx(cw.i, cw.j);
+        const int8_t kk = kind[k];
+        const T uk = ZM ? u[k] - (kk ? tm : (T)0) : u[k];
+        const T pk = uk + tb * p[k];
+        const T sk = w[k] + tb * sv[k];
+        p[k] = pk;
+        sv[k] = sk;
+        x[k] += ta * pk;
+        const T rk = r[k] - ta * sk;
+        r[k] = rk;
+        u[k] = (kk == 1 ? ireg : invd[k]) * rk;
+      }
+    }
+    if (!grid_sync(a.bar, target)) { ok = false; break; }
+    phase2(0.0);
+    if (!grid_sync(a.bar, target)) { ok = false; break; }
+    double s6[6];
+    finish(s6);
+    if (threadIdx.x == 0) {
+      const double m = ZM ? s6[4] / a.n_act : 0.0;
+      const double gamma = s6[0] - m * s6[5];
+      const double delta = s6[1];
+      const double beta = gamma / S_gamma;
+      const double alpha = gamma / (delta - beta * gamma / S_alpha_prev);
+      S.zmean = m;
+      S.beta = beta;
+      S.alpha = alpha;
+      S_alpha_prev = alpha;
+      S_gamma = gamma;
+      S.rr = s6[2];
+      S.it += 1;
+      S.stop = S.rr <= a.tol * a.tol * S.bb ? 1 : (S.it >= a.max_iter ? 2 : 0);
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool conv = ok && S.stop == 1;
+    a.out.iters[0] = ok ? S.it : 0;
+    a.out.rr[0] = ok ? S.rr : 0.0;
+    a.out.bb[0] = ok ? S.bb : 0.0;
+    a.out.converged[0] = conv ? 1 : 0;
+    if (a.out.total && ok) a.out.total[0] += S.it;
     if (!conv && a.out.nconv) a.out.nconv[0] += 1;
   }
 }
@@ -370,16 +622,32 @@ int pcg_partials_needed() {
   return sms * 4 * 8;  // blocks (at most 4 per SM) times values per reduction
 }
 
+template <class T, bool ZM>
+static const void* poisson_kernel(int cheb) {
+  switch (cheb) {
+    case 2: return (const void*)k_pcg_poisson<T, ZM, 2>;
+    case 3: return (const void*)k_pcg_poisson<T, ZM, 3>;
+    case 4: return (const void*)k_pcg_poisson<T, ZM, 4>;
+    case 5: return (const void*)k_pcg_poisson<T, ZM, 5>;
+    case 6: return (const void*)k_pcg_poisson<T, ZM, 6>;
+    case 8: return (const void*)k_pcg_poisson<T, ZM, 8>;
+    default: return (const void*)k_pcg_poisson_cg<T, ZM>;
+  }
+}
+
+bool cheb_degree_supported(int k) { return k == 1 || (k >= 2 && k <= 6) || k == 8; }
+
 template <class T>
 cudaError_t run_poisson_pcg(PoissonSolve<T> a, cudaStream_t st) {
-  const void* fn = a.zero_mean ? (const void*)k_pcg_poisson<T, true> : (const void*)k_pcg_poisson<T, false>;
+  const int cheb = a.cheb > 1 ? a.cheb : 1;
+  const void* fn = a.zero_mean ? poisson_kernel<T, true>(cheb) : poisson_kernel<T, false>(cheb);
   const int blocks = coop_blocks(fn, kPcgThreads, 2);
   if (a.zero_mean) {
     // singular system: warm start and right-hand side projected onto zero-mean fields
-    k_zero_mean_partials<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.act, a.x, a.partials);
-    k_zero_mean_apply<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.act, a.x, a.partials, blocks, a.n_act);
-    k_zero_mean_partials<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.act, a.b, a.partials);
-    k_zero_mean_apply<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.act, a.b, a.partials, blocks, a.n_act);
+    k_zero_mean_partials<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.x, a.partials);
+    k_zero_mean_apply<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.x, a.partials, blocks, a.n_act);
+    k_zero_mean_partials<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.b, a.partials);
+    k_zero_mean_apply<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.b, a.partials, blocks, a.n_act);
   }
   cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned int), st);
   void* params[] = {&a};
