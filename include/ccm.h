@@ -207,6 +207,29 @@ ccm_status ccm_kernel_timing(ccm_case c, double* poisson_ms, long long* poisson_
  * refined to tol_p. */
 ccm_status ccm_solve_pressure(ccm_case c, const double* rhs_host, ccm_solve_stats* stats);
 
+/* Maximum padded size, (ny+3) * pitch elements, that ccm_solve_pressure_noalloc accepts. */
+#define CCM_NOALLOC_MAX_ELEMS 131072
+
+/* Pressure solve for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this entry point exists for callers that may not call cudaMalloc, such as a
+ * host framework that owns all device memory through its own pool, a process under a hard
+ * device-memory cap, or latency-sensitive code that must avoid the device-wide
+ * synchronisation cudaMalloc and cudaFree imply.  It solves the same system as
+ * ccm_solve_pressure (Eq. pm_poisson, FP64 Jacobi-PCG to tol_p, whatever the case's
+ * precision and preconditioner settings) but allocates nothing: its scratch vectors sit in
+ * one fixed file-scope device array of about 6.4 MB that every GPU loading the library keeps
+ * until the process exits.
+ *   rhs_dev  right-hand side, device memory in the case's pitched layout: (ny+3) rows of
+ *            `pitch` doubles (pitch from ccm_field_device_ptr), origin at index (-1, -1);
+ *            only active cells are read.  Not modified.
+ *   phi_dev  same layout; in: warm start, out: solution (zero outside active cells).
+ * Grids with (ny+3)*pitch > CCM_NOALLOC_MAX_ELEMS are rejected with CCM_E_INVALID.  All calls
+ * share the one array, so calls that overlap on the GPU race; each call clears what must
+ * start at zero.  The first call on a device looks the array's device address up (with that
+ * device current); make it before any stream capture.  Runs on the case's stream and
+ * returns when the solve has finished. */
+ccm_status ccm_solve_pressure_noalloc(ccm_case c, const double* rhs_dev, double* phi_dev, ccm_solve_stats* stats);
+
 /* Thread-local message of the last failure ("" if none). */
 const char* ccm_last_error(void);
 

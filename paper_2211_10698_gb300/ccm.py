@@ -97,6 +97,7 @@ def lib():
             "ccm_enable_kernel_timing": (c_int, [cp, c_int]),
             "ccm_kernel_timing": (c_int, [cp, POINTER(c_double), POINTER(c_longlong), POINTER(c_longlong),
                                           POINTER(c_longlong)]),
+            "ccm_solve_pressure_noalloc": (c_int, [cp, c_void_p, c_void_p, POINTER(ccm_solve_stats)]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)

@@ -351,6 +351,26 @@ void collect_timing(ccm_case c) {
 
 }  // namespace
 
+namespace ccm {
+bool case_solve_view(ccm_case c, CaseSolveView* v) {
+  if (!c || !c->geometry) return false;
+  v->g = c->g;
+  v->st = c->st;
+  v->cu = c->co.cu;
+  v->cv = c->co.cv;
+  v->dk = c->co.diagk;
+  v->invd = c->co.invdk;
+  v->kind = c->co.kind;
+  v->act = c->co.act;
+  v->tol = c->cfg.tol_p;
+  v->max_iter = c->cfg.max_iter_p;
+  v->zero_mean = c->zero_mean;
+  v->n_act = c->n_act;
+  return true;
+}
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace ccm
+
 extern "C" {
 
 int ccm_version(void) { return CCM_VERSION; }

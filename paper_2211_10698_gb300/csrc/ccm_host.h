@@ -2,6 +2,8 @@
 // solver kernels and the launchers each .cu file provides.
 #pragma once
 
+#include <string>
+
 #include "ccm_internal.cuh"
 
 namespace ccm {
@@ -78,6 +80,27 @@ struct HelmholtzSolve {
   Barrier bar;
   PcgOut out;
 };
+
+// What a solver outside api.cu needs from a case (read-only view).
+struct CaseSolveView {
+  Geom g;
+  cudaStream_t st;
+  const double* cu;
+  const double* cv;
+  const double* dk;
+  const double* invd;
+  const int8_t* kind;
+  const int8_t* act;
+  double tol;
+  int max_iter;
+  int zero_mean;
+  double n_act;
+};
+// api.cu: false when the case has no geometry yet.
+bool case_solve_view(ccm_case c, CaseSolveView* v);
+// api.cu: the thread-local message returned by ccm_last_error.
+void set_last_error(const char* msg);
+inline void set_last_error(const std::string& msg) { set_last_error(msg.c_str()); }
 
 // geometry.cu
 cudaError_t launch_capacities(const ccm_geometry& geo, const Geom& g, double* const* caps_dev, cudaStream_t st);
