@@ -137,20 +137,29 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* >= 32
 }
 
 // Sum of the per-block partials (layout partials[k * nblocks + b]) in a fixed order; every
-// block computes the identical value.  Result broadcast to all threads through smem.
+// block computes the identical value.  Warp k reduces quantity k: each lane first issues all
+// of its loads (one L2 round trip for up to 32 * kGridSumPerLane blocks), then adds them in
+// a fixed order, then the warp's shuffle tree finishes.  Result broadcast through smem.
+constexpr int kGridSumPerLane = 10;
 template <int NV>
 __device__ __forceinline__ void grid_sum(const double* partials, int nblocks, double (&out)[NV], double* smem) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __syncthreads();
-  if (w == 0) {
+  if (w < NV) {
+    const double* src = partials + (size_t)w * nblocks;
+    double buf[kGridSumPerLane];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
-      for (int b = lane; b < nblocks; b += 32) s += __ldcg(&partials[(size_t)k * nblocks + b]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) smem[k] = s;
+    for (int m = 0; m < kGridSumPerLane; ++m) {
+      const int b = lane + 32 * m;
+      buf[m] = b < nblocks ? __ldcg(&src[b]) : 0.0;
     }
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < kGridSumPerLane; ++m) s += buf[m];
+    for (int b = lane + 32 * kGridSumPerLane; b < nblocks; b += 32) s += __ldcg(&src[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) smem[w] = s;
   }
   __syncthreads();
 #pragma unroll
