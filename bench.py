@@ -54,6 +54,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed-precision and batched measurements that follow the headline")
     return ap.parse_args()
 
 
@@ -228,6 +230,66 @@ def run_reference(args):
     return 0
 
 
+def _timed_steps(torch, stream, step_fn, steps, flush):
+    """CUDA-event time of `steps` calls of step_fn, L2 flushed between calls (untimed)."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        step_fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def measure_mixed(torch, stream, flush, steps=6, warmup=2):
+    """The headline workload with the mixed-precision Poisson solve (FP32 inner Jacobi-PCG,
+    FP64 residual refined to the same 1e-10): same accuracy target, different arithmetic."""
+    from paper_2211_10698_gb300 import ccm, inputs
+
+    case = inputs.cylinder_re100_1024x512()
+    case.precision = "mixed"
+    g = ccm.Case(case, stream=stream.cuda_stream, allocator=ccm.TorchAllocator())
+    pu, pv = inputs.perturbation(case)
+    g.set_field(ccm.CCM_F_U, g.get_field(ccm.CCM_F_U) + pu)
+    g.set_field(ccm.CCM_F_V, g.get_field(ccm.CCM_F_V) + pv)
+    g.step(warmup)
+    g.enable_kernel_timing(True)
+    ms = _timed_steps(torch, stream, lambda: g.step_async(1), steps, flush)
+    st = g.read_stats()
+    kt = g.kernel_timing()
+    g.close()
+    t = sum(ms)
+    return dict(workload=WORKLOAD, precision="mixed (FP32 inner Jacobi-PCG, FP64 residual refined to 1e-10)",
+                value=case.cells * steps / (t * 1e-3), unit=UNIT, ms_per_step=t / steps, steps=steps,
+                inner_iters_per_step=st["iters_p"] / steps, final_rel_res=st["last_res_p"],
+                poisson_ms_per_step=kt["poisson_ms"] / steps, max_div=st["max_div"], converged=bool(st["converged"]))
+
+
+def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=1):
+    """The 64-case batch (cylinders and NACA00tt sections, 256..1024 cells wide, mixed
+    precision): all cases advance together, one batched Poisson solve per step."""
+    from paper_2211_10698_gb300 import ccm, inputs
+
+    specs = inputs.batch_cases(ncases)
+    alloc = ccm.TorchAllocator()
+    cases = [ccm.Case(c, stream=stream.cuda_stream, allocator=alloc) for c in specs]
+    b = ccm.Batch(ncases, stream=stream.cuda_stream)
+    for c in cases:
+        b.add(c)
+    b.step(warmup)
+    ms = _timed_steps(torch, stream, lambda: b.step(1), steps, flush)
+    stats = b.step(0)
+    cells = sum(c.cells for c in specs)
+    t = sum(ms)
+    b.close()
+    for c in cases:
+        c.close()
+    return dict(workload=f"batch of {ncases} cases ({cells} cells)", precision="mixed", cells=cells,
+                value=cells * steps / (t * 1e-3), unit=UNIT, ms_per_step=t / steps, steps=steps,
+                note="Poisson solves batched (Jacobi inner PCG); explicit stages and Helmholtz solves per case")
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -321,6 +383,17 @@ def run_ours(args):
                     avg_launch_ms=avg_ms, iters_per_launch=iters_per_launch,
                     us_per_iteration=1e3 * avg_ms / max(iters_per_launch, 1), peak_kind=peak_kind)
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        try:
+            extras["mixed_same_accuracy"] = measure_mixed(torch, stream, flush)
+        except Exception as e:  # report, do not lose the headline line
+            extras["mixed_same_accuracy"] = {"error": str(e)}
+        try:
+            extras["batched"] = measure_batch(torch, stream, flush)
+        except Exception as e:
+            extras["batched"] = {"error": str(e)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -343,6 +416,7 @@ def run_ours(args):
                     gpu_launches=int(kt["kernel_launches"]), clocks=clocks,
                     wall_s=wall, step_ms_min=min(step_ms), step_ms_max=max(step_ms),
                     max_div=st["max_div"], kinetic=st["kinetic"], converged=bool(st["converged"]))
+        line.update(extras)
         print(json.dumps(line), flush=True)
     g.close()
     if world > 1:

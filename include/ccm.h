@@ -148,6 +148,9 @@ enum {
  * set only on CCM_OK.  Errors: CCM_E_INVALID, CCM_E_OOM, CCM_E_CUDA. */
 ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out);
 
+/* Device memory a case with this configuration will hold (for admission control). */
+ccm_status ccm_case_bytes(const ccm_config* cfg, size_t* bytes);
+
 /* Release every resource of the case (NULL is accepted). */
 ccm_status ccm_destroy_case(ccm_case c);
 
@@ -229,6 +232,48 @@ ccm_status ccm_solve_pressure(ccm_case c, const double* rhs_host, ccm_solve_stat
  * device current); make it before any stream capture.  Runs on the case's stream and
  * returns when the solve has finished. */
 ccm_status ccm_solve_pressure_noalloc(ccm_case c, const double* rhs_dev, double* phi_dev, ccm_solve_stats* stats);
+
+/* ---- Batches: independent cases advanced together -------------------------------------
+ * Serving form of the step (the paper has one case at a time).  Every case of a batch must
+ * use the batch's stream and the same precision setting.  Per step, each case's explicit
+ * stages and Helmholtz solve run case by case; one cooperative launch then solves the Poisson
+ * systems of all cases (FP64 Jacobi-PCG, or for MIXED the FP64 refinement with batched FP32
+ * inner solves), each case on a range of blocks sized to its expected work; then each case's
+ * projection runs.  A batch holds at most as many cases as the GPU holds PCG blocks (2 per
+ * SM).  Cases keep their own state and can leave and join a batch between steps. */
+typedef struct ccm_batch_s* ccm_batch;
+ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out);
+ccm_status ccm_batch_destroy(ccm_batch b);
+ccm_status ccm_batch_add(ccm_batch b, ccm_case c);
+ccm_status ccm_batch_remove(ccm_batch b, ccm_case c);
+int ccm_batch_size(ccm_batch b);
+/* Advance every case of the batch nsteps steps; stats (may be NULL) receives one entry per
+ * case, in the order the cases were added.  Returns the first non-OK status of any case. */
+ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats);
+
+/* ---- Request loop (serving) ------------------------------------------------------------
+ * Flow-past-body requests wait in a FIFO queue; each round of ccm_server_run admits queued
+ * requests in arrival order while their device footprint (ccm_case_bytes) fits the HBM budget
+ * and a batch slot is free, advances all resident requests by one chunk of steps through a
+ * batch (FP64 and mixed-precision requests in separate batches), and retires the requests
+ * that reached their step count.  Requests submitted while others run join at the next
+ * round (continuous batching).  Not thread-safe: submit, run and poll from one thread. */
+typedef struct ccm_server_s* ccm_server;
+ccm_status ccm_server_create(size_t hbm_budget_bytes, int max_batch, int chunk_steps, void* stream, ccm_server* out);
+ccm_status ccm_server_destroy(ccm_server s);
+/* Queue a request (the config's stream is replaced by the server's); CCM_E_OOM if it can
+ * never fit the budget. */
+ccm_status ccm_server_submit(ccm_server s, const ccm_config* cfg, const ccm_geometry* geo, int nsteps, long long* id);
+/* Run `rounds` rounds; *active (may be NULL) receives the number of queued or running
+ * requests left.  Returns the first error a batch step reported (requests continue). */
+ccm_status ccm_server_run(ccm_server s, int rounds, int* active);
+/* state: 0 queued, 1 running, 2 done, 3 failed; times3: submit, admit, done (seconds, one
+ * monotonic clock); stats: last step's statistics, iteration counts summed over all steps. */
+ccm_status ccm_server_poll(ccm_server s, long long id, int* state, double* times3, ccm_step_stats* stats);
+ccm_status ccm_server_get_field(ccm_server s, long long id, int field, double* host, size_t count);
+/* Free a finished or queued request (CCM_E_STATE while it runs). */
+ccm_status ccm_server_release(ccm_server s, long long id);
+size_t ccm_server_bytes_in_use(ccm_server s);
 
 /* Thread-local message of the last failure ("" if none). */
 const char* ccm_last_error(void);

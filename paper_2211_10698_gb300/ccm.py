@@ -98,6 +98,21 @@ def lib():
             "ccm_kernel_timing": (c_int, [cp, POINTER(c_double), POINTER(c_longlong), POINTER(c_longlong),
                                           POINTER(c_longlong)]),
             "ccm_solve_pressure_noalloc": (c_int, [cp, c_void_p, c_void_p, POINTER(ccm_solve_stats)]),
+            "ccm_batch_create": (c_int, [c_int, c_void_p, POINTER(c_void_p)]),
+            "ccm_batch_destroy": (c_int, [cp]),
+            "ccm_batch_add": (c_int, [cp, cp]),
+            "ccm_batch_remove": (c_int, [cp, cp]),
+            "ccm_batch_size": (c_int, [cp]),
+            "ccm_batch_step": (c_int, [cp, c_int, POINTER(ccm_step_stats)]),
+            "ccm_case_bytes": (c_int, [POINTER(ccm_config), POINTER(c_size_t)]),
+            "ccm_server_create": (c_int, [c_size_t, c_int, c_int, c_void_p, POINTER(c_void_p)]),
+            "ccm_server_destroy": (c_int, [cp]),
+            "ccm_server_submit": (c_int, [cp, POINTER(ccm_config), POINTER(ccm_geometry), c_int, POINTER(c_longlong)]),
+            "ccm_server_run": (c_int, [cp, c_int, POINTER(c_int)]),
+            "ccm_server_poll": (c_int, [cp, c_longlong, POINTER(c_int), POINTER(c_double), POINTER(ccm_step_stats)]),
+            "ccm_server_get_field": (c_int, [cp, c_longlong, c_int, _DP, c_size_t]),
+            "ccm_server_release": (c_int, [cp, c_longlong]),
+            "ccm_server_bytes_in_use": (c_size_t, [cp]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -259,3 +274,92 @@ class Case:
         pitch = c_int()
         _check(lib().ccm_field_device_ptr(self.h, field, ctypes.byref(p), ctypes.byref(pitch)))
         return p.value, pitch.value
+
+
+class Batch:
+    """Cases advanced together (one batched Poisson solve per step)."""
+
+    def __init__(self, max_cases, stream=None):
+        h = c_void_p()
+        _check(lib().ccm_batch_create(max_cases, stream, ctypes.byref(h)))
+        self.h = h
+        self.cases = []
+
+    def add(self, case):
+        _check(lib().ccm_batch_add(self.h, case.h))
+        self.cases.append(case)
+
+    def remove(self, case):
+        _check(lib().ccm_batch_remove(self.h, case.h))
+        self.cases.remove(case)
+
+    def step(self, n=1, allow_not_converged=False):
+        arr = (ccm_step_stats * max(len(self.cases), 1))()
+        allow = (CCM_E_NOT_CONVERGED,) if allow_not_converged else ()
+        _check(lib().ccm_batch_step(self.h, n, arr), allow)
+        return [{f: getattr(arr[i], f) for f, _ in ccm_step_stats._fields_} for i in range(len(self.cases))]
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().ccm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request loop: submit flow-past-body requests, run rounds, poll for completion."""
+
+    STATES = ("queued", "running", "done", "failed")
+
+    def __init__(self, hbm_budget_bytes, max_batch=64, chunk_steps=10, stream=None):
+        h = c_void_p()
+        _check(lib().ccm_server_create(int(hbm_budget_bytes), max_batch, chunk_steps, stream, ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, case, nsteps=None, precision=None, precond=None):
+        cfg = make_config(case, precision, precond)
+        geo = make_geometry(case.geom)
+        rid = c_longlong()
+        _check(lib().ccm_server_submit(self.h, ctypes.byref(cfg), ctypes.byref(geo),
+                                       case.steps if nsteps is None else nsteps, ctypes.byref(rid)))
+        return rid.value
+
+    def run(self, rounds=1):
+        active = c_int()
+        _check(lib().ccm_server_run(self.h, rounds, ctypes.byref(active)), (CCM_E_NOT_CONVERGED,))
+        return active.value
+
+    def poll(self, rid):
+        state = c_int()
+        times = (c_double * 3)()
+        st = ccm_step_stats()
+        _check(lib().ccm_server_poll(self.h, rid, ctypes.byref(state), times, ctypes.byref(st)))
+        return dict(state=self.STATES[state.value], t_submit=times[0], t_admit=times[1], t_done=times[2],
+                    **{f: getattr(st, f) for f, _ in ccm_step_stats._fields_})
+
+    def get_field(self, rid, field, shape):
+        a = np.empty(shape)
+        _check(lib().ccm_server_get_field(self.h, rid, field, _ptr(a), a.size))
+        return a
+
+    def release(self, rid):
+        _check(lib().ccm_server_release(self.h, rid))
+
+    def bytes_in_use(self):
+        return lib().ccm_server_bytes_in_use(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().ccm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -351,6 +351,12 @@ void collect_timing(ccm_case c) {
 
 }  // namespace
 
+extern "C" {
+static ccm_status stage_predict(ccm_case c);
+static void stage_project(ccm_case c);
+static ccm_status finish_stats(ccm_case c, ccm_step_stats* stats);
+}
+
 namespace ccm {
 bool case_solve_view(ccm_case c, CaseSolveView* v) {
   if (!c || !c->geometry) return false;
@@ -369,6 +375,73 @@ bool case_solve_view(ccm_case c, CaseSolveView* v) {
   return true;
 }
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+// Pieces of the step for the batch driver (csrc/batch.cu).
+ccm_status case_stage_predict(ccm_case c) { return stage_predict(c); }
+void case_stage_project(ccm_case c) { stage_project(c); }
+ccm_status case_finish(ccm_case c, ccm_step_stats* stats) { return finish_stats(c, stats); }
+bool case_is_mixed(ccm_case c) { return c->cfg.precision == CCM_MIXED; }
+cudaStream_t case_stream(ccm_case c) { return c->st; }
+size_t case_cells(ccm_case c) { return (size_t)c->g.nx * c->g.ny; }
+int case_nx(ccm_case c) { return c->g.nx; }
+
+// FP64 Jacobi-PCG descriptor of the case's pressure solve (x = Phi, b = the step's right-hand
+// side); statistics go to the case's device counters as for a single solve.
+void case_poisson_fp64(ccm_case c, PoissonSolve<double>* a) {
+  *a = PoissonSolve<double>{};
+  a->g = c->g;
+  a->cu = c->co.cu; a->cv = c->co.cv; a->dk = c->co.diagk; a->invd = c->co.invdk; a->kind = c->co.kind;
+  a->creg_x = c->g.hy / c->g.hx;
+  a->creg_y = c->g.hx / c->g.hy;
+  a->dreg = 2.0 * (a->creg_x + a->creg_y);
+  a->invd_reg = 1.0 / a->dreg;
+  a->x = c->phi; a->b = c->rhs_p; a->r = c->pr; a->z = c->pz; a->q = c->pq; a->p0 = c->pp0; a->p1 = c->pp1;
+  a->cheb = 1;
+  a->tol = c->cfg.tol_p; a->max_iter = c->cfg.max_iter_p;
+  a->zero_mean = c->zero_mean; a->n_act = c->n_act;
+  a->out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
+}
+
+// FP32 descriptor of one inner solve of the mixed-precision refinement (x = the FP32
+// correction, b = the FP32 residual written by case_mixed_residual).
+void case_poisson_fp32(ccm_case c, PoissonSolve<float>* a) {
+  *a = PoissonSolve<float>{};
+  a->g = c->g;
+  a->cu = c->co.cu32; a->cv = c->co.cv32; a->dk = c->co.diagk32; a->invd = c->co.invdk32; a->kind = c->co.kind;
+  a->creg_x = c->g.hy / c->g.hx;
+  a->creg_y = c->g.hx / c->g.hy;
+  a->dreg = 2.0 * (a->creg_x + a->creg_y);
+  a->invd_reg = 1.0 / a->dreg;
+  a->x = c->fx; a->b = c->fb; a->r = c->fr; a->z = c->fz; a->q = c->fq; a->p0 = c->fp0; a->p1 = c->fp1;
+  a->cheb = 1;
+  a->tol = c->cfg.tol_inner > 0 ? c->cfg.tol_inner : 1e-5;
+  a->max_iter = c->cfg.max_iter_p;
+  a->zero_mean = c->zero_mean; a->n_act = c->n_act;
+  a->out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, nullptr, nullptr};
+}
+
+// Mixed refinement helpers: FP64 residual into the FP32 right-hand side with its sums copied
+// to `host2` (valid after the stream syncs), and x += correction.
+ccm_status case_mixed_residual(ccm_case c, double* host2) {
+  launch_residual64(c->cv, c->g, c->phi, c->rhs_p, c->fb, c->dpart, c->mixed_sums, c->st);
+  CUDA_TRY(cudaMemcpyAsync(host2, c->mixed_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(cudaMemsetAsync(c->fx, 0, c->g.count() * sizeof(float), c->st));
+  c->launches += 2;
+  return CCM_OK;
+}
+void case_mixed_correct(ccm_case c) {
+  launch_add_correction(c->g, c->co.act, c->phi, c->fx, c->st);
+  c->launches += 1;
+}
+void case_mixed_account(ccm_case c, long long inner, int outer, double rr, double bb, bool converged) {
+  c->mixed_total += inner;
+  c->mixed_last = (int)inner;
+  c->mixed_outer = outer;
+  c->mixed_rr = rr;
+  c->mixed_bb = bb;
+  if (!converged) c->mixed_nconv++;
+}
+int* case_inner_iters_dev(ccm_case c) { return &c->ds->iters_p; }
 }  // namespace ccm
 
 extern "C" {
@@ -433,6 +506,18 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
     return fail(CCM_E_CUDA, std::string("initialising case memory: ") + cudaGetErrorString(e));
   }
   *out = c;
+  return CCM_OK;
+}
+
+ccm_status ccm_case_bytes(const ccm_config* cfg, size_t* bytes) {
+  if (!cfg || !bytes || cfg->nx < 4 || cfg->ny < 4) return fail(CCM_E_INVALID, "bad configuration");
+  ccm_case_s tmp;
+  tmp.g.nx = cfg->nx;
+  tmp.g.ny = cfg->ny;
+  tmp.g.pitch = ((cfg->nx + 3) + 31) / 32 * 32;
+  Carver dry{nullptr};
+  carve(&tmp, dry);
+  *bytes = dry.off + 256;
   return CCM_OK;
 }
 
@@ -644,27 +729,43 @@ static ccm_status read_stats(ccm_case c, DevStats& h) {
   return check_cuda_errors("solver");
 }
 
-static ccm_status enqueue_steps(ccm_case c, int nsteps) {
+// Stages of one step around the Poisson solve: box data, predictor right-hand side,
+// Helmholtz solve, U* and its divergence (Eq. pm_prediction, right-hand side of
+// Eq. pm_poisson) ...
+static ccm_status stage_predict(ccm_case c) {
   const Geom& g = c->g;
   cudaStream_t st = c->st;
+  const int prev = c->cur, next = 1 - c->cur;
+  launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
+  launch_predictor_rhs(c->cv, g, c->bc, c->ph, c->u, c->v, c->p, c->cnu[prev], c->cnv[prev], c->cnu[next],
+                       c->cnv[next], c->rhs_u, c->rhs_v, c->nstep == 0 ? 1 : 0, st);
+  ccm_status s;
+  if ((s = solve_helmholtz(c)) != CCM_OK) return s;
+  launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
+  CUDA_TRY(cudaMemcpyAsync(c->ustar, c->u, g.count() * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(c->vstar, c->v, g.count() * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_divergence(c->cv, g, c->ph, c->u, c->v, c->div, c->rhs_p, st);
+  return CCM_OK;
+}
+
+// ... and after it: projection, pressure update, box data (Eqs. pm_projection, pm_update).
+static void stage_project(ccm_case c) {
+  const Geom& g = c->g;
+  cudaStream_t st = c->st;
+  launch_project(c->cv, g, c->phi, c->u, c->v, c->p, st);
+  launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
+  c->launches += 7;  // fill_bc x3, predictor, Helmholtz PCG, divergence, projection
+  c->cur = 1 - c->cur;
+  c->nstep++;
+  c->steps_pending++;
+}
+
+static ccm_status enqueue_steps(ccm_case c, int nsteps) {
   ccm_status s;
   for (int n = 0; n < nsteps; ++n) {
-    const int prev = c->cur, next = 1 - c->cur;
-    launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
-    launch_predictor_rhs(c->cv, g, c->bc, c->ph, c->u, c->v, c->p, c->cnu[prev], c->cnv[prev], c->cnu[next],
-                         c->cnv[next], c->rhs_u, c->rhs_v, c->nstep == 0 ? 1 : 0, st);
-    if ((s = solve_helmholtz(c)) != CCM_OK) return s;
-    launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
-    CUDA_TRY(cudaMemcpyAsync(c->ustar, c->u, g.count() * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(c->vstar, c->v, g.count() * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    launch_divergence(c->cv, g, c->ph, c->u, c->v, c->div, c->rhs_p, st);
+    if ((s = stage_predict(c)) != CCM_OK) return s;
     if ((s = poisson_solve(c, c->phi, c->rhs_p)) != CCM_OK) return s;
-    launch_project(c->cv, g, c->phi, c->u, c->v, c->p, st);
-    launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
-    c->launches += 7;  // fill_bc x3, predictor, Helmholtz PCG, divergence, projection
-    c->cur = next;
-    c->nstep++;
-    c->steps_pending++;
+    stage_project(c);
   }
   return check_cuda_errors("step");
 }

@@ -64,6 +64,19 @@ struct PoissonSolve {
   PcgOut out;
 };
 
+// One case of a batched Poisson solve and the contiguous range of blocks that serves it.
+template <class T>
+struct BatchEntry {
+  PoissonSolve<T> a;  // partials, bar of the entry are unused (the batch has its own)
+  int block0, nblocks;
+};
+
+struct BatchControl {
+  double* partials;  // 6 values x blocks
+  int* running;      // per block: its case is still iterating
+  Barrier bar;
+};
+
 struct HelmholtzSolve {
   Coefs c;
   Geom g;
@@ -138,6 +151,25 @@ int pcg_partials_needed();
 bool cheb_degree_supported(int k);
 template <class T>
 cudaError_t run_poisson_pcg(PoissonSolve<T> a, cudaStream_t st);
+int batch_blocks();
+template <class T>
+cudaError_t run_poisson_batch(const PoissonSolve<T>* host_cases, int ncase, const BatchEntry<T>* dev_cases,
+                              const int* dev_block_case, BatchControl ctl, int blocks, cudaStream_t st);
+
+// api.cu: pieces of one step for the batch driver
+ccm_status case_stage_predict(ccm_case c);
+void case_stage_project(ccm_case c);
+ccm_status case_finish(ccm_case c, ccm_step_stats* stats);
+bool case_is_mixed(ccm_case c);
+cudaStream_t case_stream(ccm_case c);
+size_t case_cells(ccm_case c);
+int case_nx(ccm_case c);
+void case_poisson_fp64(ccm_case c, PoissonSolve<double>* a);
+void case_poisson_fp32(ccm_case c, PoissonSolve<float>* a);
+ccm_status case_mixed_residual(ccm_case c, double* host2);
+void case_mixed_correct(ccm_case c);
+void case_mixed_account(ccm_case c, long long inner, int outer, double rr, double bb, bool converged);
+int* case_inner_iters_dev(ccm_case c);
 cudaError_t run_helmholtz_pcg(HelmholtzSolve a, cudaStream_t st);
 
 }  // namespace ccm

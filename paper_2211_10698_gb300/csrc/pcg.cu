@@ -456,6 +456,187 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_cg(PoissonSolve<
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Batched solve: the single-reduction Jacobi PCG above for many independent systems in one
+// cooperative launch.  Block b serves case block_case[b] (a contiguous range of blocks per
+// case, sized by the host in proportion to the expected work); each case reduces over its own
+// blocks, all cases share the barriers, and a converged case's blocks idle through the
+// remaining barriers.  The loop ends when no block reports a running case (a grid-wide sum
+// read after a barrier, so every block takes the same decision).
+// ---------------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void range_sum(const double* partials, int stride, int base, int count, double (&out)[NV],
+                                          double* smem) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (w < NV) {
+    const double* src = partials + (size_t)w * stride + base;
+    double buf[kGridSumPerLane];
+#pragma unroll
+    for (int m = 0; m < kGridSumPerLane; ++m) {
+      const int b = lane + 32 * m;
+      buf[m] = b < count ? __ldcg(&src[b]) : 0.0;
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < kGridSumPerLane; ++m) s += buf[m];
+    for (int b = lane + 32 * kGridSumPerLane; b < count; b += 32) s += __ldcg(&src[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) smem[w] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = smem[k];
+}
+
+template <class T>
+__global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_cg_batch(const BatchEntry<T>* __restrict__ cases,
+                                                                        const int* __restrict__ block_case,
+                                                                        BatchControl ctl) {
+  __shared__ double red[6][kPcgThreads];
+  __shared__ double sm[8];
+  __shared__ PcgScalars S;
+  __shared__ double S_alpha_prev, S_gamma;
+  unsigned int target = 0;
+  const int NB = gridDim.x;
+  const int ci = block_case[blockIdx.x];
+  const BatchEntry<T>& E = cases[ci];
+  const PoissonSolve<T>& a = E.a;
+  const bool ZM = a.zero_mean != 0;
+  const Geom g = a.g;
+  const int nx = g.nx;
+  const int ncell = g.nx * g.ny;
+  const int lb = blockIdx.x - E.block0, nbc = E.nblocks;
+  const int t0 = (int)((long long)ncell * lb / nbc), t1 = (int)((long long)ncell * (lb + 1) / nbc);
+  const int first = t0 + threadIdx.x, stride = blockDim.x;
+  const KRow<T> K{a.cu, a.cv, a.dk, a.kind, (T)a.creg_x, (T)a.creg_y, (T)a.dreg, (size_t)g.pitch};
+  const T* __restrict__ invd = a.invd;
+  const int8_t* __restrict__ kind = a.kind;
+  T* __restrict__ x = a.x;
+  T* __restrict__ r = a.r;
+  T* __restrict__ u = a.z;
+  T* __restrict__ w = a.q;
+  T* __restrict__ p = a.p0;
+  T* __restrict__ sv = a.p1;
+  const T ireg = (T)a.invd_reg;
+
+  double bb_part = 0.0;
+  for (CellWalk cw(first, stride, t1, nx); cw.ok(); cw.next()) {
+    const size_t k = g.idx(cw.i, cw.j);
+    const T bk = a.b[k];
+    const T rk = bk - K(x, k);
+    r[k] = rk;
+    u[k] = (kind[k] == 1 ? ireg : invd[k]) * rk;
+    p[k] = (T)0;
+    sv[k] = (T)0;
+    bb_part += (double)bk * (double)bk;
+  }
+  bool ok = grid_sync(ctl.bar, target);
+  auto phase2 = [&](bool run, double bbp) {
+    double v[6] = {0.0, 0.0, 0.0, bbp, 0.0, 0.0};
+    if (run) {
+      for (CellWalk cw(first, stride, t1, nx); cw.ok(); cw.next()) {
+        const size_t k = g.idx(cw.i, cw.j);
+        const T wk = K((const T*)u, k);
+        w[k] = wk;
+        const double rk = (double)r[k], uk = (double)u[k];
+        v[0] += rk * uk;
+        v[1] += (double)wk * uk;
+        v[2] += rk * rk;
+        if (ZM && kind[k]) { v[4] += uk; v[5] += rk; }
+      }
+    }
+    block_sum_smem<6>(v, red);
+    publish(ctl.partials, NB, v, 6);
+  };
+  if (ok) {
+    phase2(true, bb_part);
+    ok = grid_sync(ctl.bar, target);
+  }
+  if (ok) {
+    double s6[6];
+    range_sum<6>(ctl.partials, NB, E.block0, nbc, s6, sm);
+    if (threadIdx.x == 0) {
+      const double m = ZM ? s6[4] / a.n_act : 0.0;
+      S.zmean = m;
+      S.rr = s6[2];
+      S.bb = s6[3];
+      S_gamma = s6[0] - m * s6[5];
+      S.alpha = s6[1] != 0.0 ? S_gamma / s6[1] : 0.0;
+      S_alpha_prev = S.alpha;
+      S.beta = 0.0;
+      S.it = 0;
+      S.stop = (S.bb == 0.0 || S.rr <= a.tol * a.tol * S.bb) ? 1 : (a.max_iter <= 0 ? 2 : 0);
+    }
+    __syncthreads();
+  }
+  if (ok && S.bb == 0.0)
+    for (CellWalk cw(first, stride, t1, nx); cw.ok(); cw.next()) x[g.idx(cw.i, cw.j)] = (T)0;
+  while (ok) {
+    const bool run = S.stop == 0;
+    if (run) {
+      const T ta = (T)S.alpha, tb = (T)S.beta, tm = (T)S.zmean;
+      for (CellWalk cw(first, stride, t1, nx); cw.ok(); cw.next()) {
+        const size_t k = g.idx(cw.i, cw.j);
+        const int8_t kk = kind[k];
+        const T uk = ZM ? u[k] - (kk ? tm : (T)0) : u[k];
+        const T pk = uk + tb * p[k];
+        const T sk = w[k] + tb * sv[k];
+        p[k] = pk;
+        sv[k] = sk;
+        x[k] += ta * pk;
+        const T rk = r[k] - ta * sk;
+        r[k] = rk;
+        u[k] = (kk == 1 ? ireg : invd[k]) * rk;
+      }
+    }
+    if (threadIdx.x == 0) ctl.running[blockIdx.x] = run ? 1 : 0;
+    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
+    {
+      // number of blocks whose case is still iterating (identical in every block)
+      __shared__ int s_any;
+      if (threadIdx.x < 32) {
+        int c = 0;
+        for (int b = threadIdx.x; b < NB; b += 32) c += __ldcg(&ctl.running[b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if (threadIdx.x == 0) s_any = c;
+      }
+      __syncthreads();
+      if (s_any == 0) break;
+    }
+    phase2(run, 0.0);
+    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
+    double s6[6];
+    range_sum<6>(ctl.partials, NB, E.block0, nbc, s6, sm);
+    if (threadIdx.x == 0 && run) {
+      const double m = ZM ? s6[4] / a.n_act : 0.0;
+      const double gamma = s6[0] - m * s6[5];
+      const double beta = gamma / S_gamma;
+      const double alpha = gamma / (s6[1] - beta * gamma / S_alpha_prev);
+      S.zmean = m;
+      S.beta = beta;
+      S.alpha = alpha;
+      S_alpha_prev = alpha;
+      S_gamma = gamma;
+      S.rr = s6[2];
+      S.it += 1;
+      S.stop = S.rr <= a.tol * a.tol * S.bb ? 1 : (S.it >= a.max_iter ? 2 : 0);
+    }
+    __syncthreads();
+  }
+  if (lb == 0 && threadIdx.x == 0) {
+    const bool conv = ok && S.stop == 1;
+    a.out.iters[0] = ok ? S.it : 0;
+    a.out.rr[0] = ok ? S.rr : 0.0;
+    a.out.bb[0] = ok ? S.bb : 0.0;
+    a.out.converged[0] = conv ? 1 : 0;
+    if (a.out.total && ok) a.out.total[0] += S.it;
+    if (!conv && a.out.nconv) a.out.nconv[0] += 1;
+  }
+}
+
 // Projection of the warm start onto zero mean over active cells (singular systems only).
 template <class T>
 __global__ void k_zero_mean_partials(Geom g, const int8_t* act, const T* x, double* partials) {
@@ -654,6 +835,31 @@ cudaError_t run_poisson_pcg(PoissonSolve<T> a, cudaStream_t st) {
   return cudaLaunchCooperativeKernel(fn, blocks, kPcgThreads, params, 0, st);
 }
 template cudaError_t run_poisson_pcg<double>(PoissonSolve<double>, cudaStream_t);
+
+int batch_blocks() { return coop_blocks((const void*)k_pcg_poisson_cg_batch<double>, kPcgThreads, 2); }
+
+// Singular systems of a batch: warm start and right-hand side projected onto zero mean
+// (what run_poisson_pcg does for a single solve), then one cooperative launch for all.
+template <class T>
+cudaError_t run_poisson_batch(const PoissonSolve<T>* host_cases, int ncase, const BatchEntry<T>* dev_cases,
+                              const int* dev_block_case, BatchControl ctl, int blocks, cudaStream_t st) {
+  for (int c = 0; c < ncase; ++c) {
+    const PoissonSolve<T>& a = host_cases[c];
+    if (!a.zero_mean) continue;
+    k_zero_mean_partials<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.x, ctl.partials);
+    k_zero_mean_apply<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.x, ctl.partials, blocks, a.n_act);
+    k_zero_mean_partials<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.b, ctl.partials);
+    k_zero_mean_apply<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.b, ctl.partials, blocks, a.n_act);
+  }
+  cudaMemsetAsync(ctl.bar.count, 0, sizeof(unsigned int), st);
+  const void* fn = (const void*)k_pcg_poisson_cg_batch<T>;
+  void* params[] = {(void*)&dev_cases, (void*)&dev_block_case, &ctl};
+  return cudaLaunchCooperativeKernel(fn, blocks, kPcgThreads, params, 0, st);
+}
+template cudaError_t run_poisson_batch<double>(const PoissonSolve<double>*, int, const BatchEntry<double>*, const int*,
+                                               BatchControl, int, cudaStream_t);
+template cudaError_t run_poisson_batch<float>(const PoissonSolve<float>*, int, const BatchEntry<float>*, const int*,
+                                              BatchControl, int, cudaStream_t);
 template cudaError_t run_poisson_pcg<float>(PoissonSolve<float>, cudaStream_t);
 
 cudaError_t run_helmholtz_pcg(HelmholtzSolve a, cudaStream_t st) {

@@ -1,0 +1,97 @@
+"""Batched stepping: cases of different sizes and geometries advanced together (one batched
+Poisson solve per step) give the same fields as each case advanced alone, within the
+solver tolerances, in FP64 and in the mixed-precision setting; bookkeeping and errors."""
+import numpy as np
+import pytest
+
+from paper_2211_10698_gb300 import ccm, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2211_10698_gb300 import build
+
+    build.build()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _mix(precision):
+    cs = [
+        I.small_cylinder(nx=48, ny=24, box=(-2.0, 4.0, -1.5, 1.5), r=0.5, cx=0.0, cy=0.0),
+        I.small_cylinder(nx=96, ny=40, box=(-2.0, 4.0, -1.25, 1.25), r=0.43, cx=0.1, cy=-0.05),
+        I.make_case("naca", 96, 48, (-0.5, 1.5, -0.5, 0.5),
+                    I.Geometry(kind=I.GEOM_NACA, naca_tt=12, aoa_deg=7.0), re=200.0, cfl=0.5, lref=1.0),
+        I.small_cylinder(nx=37, ny=23, box=(-1.5, 1.5, -1.0, 1.0), r=0.41, cx=0.07, cy=-0.05,
+                         bc=I.closed_box_bc(lid=1.0), re=50.0),
+        I.make_case("channel", 64, 16, (0.0, 4.0, 0.0, 1.0), I.Geometry(), re=20.0, cfl=0.5, lref=1.0,
+                    bc=((I.BC_DIRICHLET, I.BC_OUTFLOW, I.BC_DIRICHLET, I.BC_DIRICHLET), (1.0, 0, 0, 0), (0, 0, 0, 0))),
+    ]
+    for c in cs:
+        c.precision = precision
+        c.tol_p = 1e-12 if precision == "mixed" else 1e-13
+        c.tol_h = 1e-13
+    return cs
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-8)])
+def test_batch_equals_alone(precision, tol):
+    specs = _mix(precision)
+    alone = [ccm.Case(c) for c in specs]
+    for a in alone:
+        a.step(4)
+    mixed = [ccm.Case(c) for c in specs]
+    b = ccm.Batch(8)
+    for m in mixed:
+        b.add(m)
+    stats = b.step(4)
+    assert len(stats) == len(specs)
+    for a, m, st in zip(alone, mixed, stats):
+        assert st["converged"] and st["steps"] == 4
+        for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P):
+            assert _rel(m.get_field(f), a.get_field(f)) < tol, (m.spec.name, f)
+    b.close()
+
+
+def test_cases_join_and_leave_between_steps():
+    specs = _mix("fp64")[:3]
+    ref = [ccm.Case(c) for c in specs]
+    for r in ref:
+        r.step(3)
+    cs = [ccm.Case(c) for c in specs]
+    b = ccm.Batch(4)
+    b.add(cs[0])
+    b.add(cs[1])
+    b.step(1)
+    b.add(cs[2])
+    cs[2].step(1)  # the late case catches up alone
+    b.step(1)
+    b.remove(cs[0])
+    cs[0].step(1)
+    b.step(1)
+    for r, c in zip(ref, cs):
+        assert _rel(c.get_field(ccm.CCM_F_U), r.get_field(ccm.CCM_F_U)) < 1e-9
+    b.close()
+
+
+def test_batch_errors():
+    specs = _mix("fp64")
+    a = ccm.Case(specs[0])
+    b = ccm.Batch(1)
+    b.add(a)
+    with pytest.raises(ccm.CcmError):
+        b.add(ccm.Case(specs[1]))  # full
+    with pytest.raises(ccm.CcmError):
+        b.add(a)
+    m = specs[1]
+    m.precision = "mixed"
+    b2 = ccm.Batch(2)
+    b2.add(ccm.Case(specs[2]))
+    with pytest.raises(ccm.CcmError):
+        b2.add(ccm.Case(m))  # precision differs
+    b.close()
+    b2.close()
