@@ -290,6 +290,49 @@ def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=1):
                 note="Poisson solves batched (Jacobi inner PCG); explicit stages and Helmholtz solves per case")
 
 
+def measure_serving(precision, nreq=16, step_div=200, budget_gb=150.0, max_batch=64, chunk=5):
+    """A bounded window of the request stream (exponential arrivals at 20/s; cylinders and
+    NACA00tt sections 128..2048 cells wide; the first ``nreq`` requests, their step counts
+    divided by ``step_div``): requests are submitted when their arrival time has passed and the
+    loop runs rounds until all are done.  Latency runs from arrival to completion."""
+    import numpy as np
+
+    from paper_2211_10698_gb300 import ccm, inputs
+
+    reqs = inputs.serving_requests(nreq)
+    srv = ccm.Server(int(budget_gb * 1e9), max_batch=max_batch, chunk_steps=chunk)
+    pending = list(reqs)
+    ids = []
+    t0 = time.monotonic()
+    active = 0
+    peak_bytes = 0
+    while pending or active:
+        now = time.monotonic() - t0
+        if not active and pending and pending[0][0] > now:
+            time.sleep(pending[0][0] - now)
+            now = time.monotonic() - t0
+        while pending and pending[0][0] <= now:
+            arr, c = pending.pop(0)
+            n = max(1, c.steps // step_div)
+            ids.append((arr, c, n, srv.submit(c, nsteps=n, precision=precision,
+                                              precond="jacobi" if precision == "fp64" else None)))
+        active = srv.run(1)
+        peak_bytes = max(peak_bytes, srv.bytes_in_use())
+    lat, cell_steps, t_end, fails = [], 0, 0.0, 0
+    for arr, c, n, rid in ids:
+        p = srv.poll(rid)
+        fails += p["state"] != "done" or not p["converged"]
+        lat.append(p["t_done"] - (t0 + arr))
+        cell_steps += c.cells * n
+        t_end = max(t_end, p["t_done"] - t0)
+        srv.release(rid)
+    srv.close()
+    lat = np.array(lat)
+    return dict(precision=precision, requests=len(ids), value=cell_steps / t_end, unit=UNIT,
+                p50_latency_s=float(np.percentile(lat, 50)), p99_latency_s=float(np.percentile(lat, 99)),
+                makespan_s=t_end, cell_steps=cell_steps, failed=int(fails), peak_hbm_bytes=int(peak_bytes))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -373,11 +416,11 @@ def run_ours(args):
     traffic = traffic_pc * case.cells * iters_per_launch if traffic_pc is not None else None
     if frac_alu >= frac_hbm:
         roof = dict(bound="alu", achieved=achieved_tf, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=frac_alu,
-                    traffic=traffic, kernel="k_pcg_poisson<double>",
+                    traffic=traffic, kernel="k_pcg_poisson_cg<double, 0>",
                     peak_source="FP64 unit count x clock (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)")
     else:
         roof = dict(bound="hbm", achieved=achieved_gbs, peak=peaks["hbm_gbs"], unit="GB/s", frac=frac_hbm,
-                    traffic=traffic, kernel="k_pcg_poisson<double>", peak_source=f"{peak_kind} hbm_gbs")
+                    traffic=traffic, kernel="k_pcg_poisson_cg<double, 0>", peak_source=f"{peak_kind} hbm_gbs")
     roof_alt = dict(hbm_achieved_gbs=achieved_gbs, hbm_peak_gbs=peaks["hbm_gbs"], hbm_frac=frac_hbm,
                     fp64_achieved_tflops=achieved_tf, fp64_peak_tflops=FP64_PEAK_TFLOPS, fp64_frac=frac_alu,
                     avg_launch_ms=avg_ms, iters_per_launch=iters_per_launch,
@@ -393,6 +436,15 @@ def run_ours(args):
             extras["batched"] = measure_batch(torch, stream, flush)
         except Exception as e:
             extras["batched"] = {"error": str(e)}
+        try:
+            torch.cuda.synchronize()
+            sv = dict(workload=f"request stream window: first 16 requests at 20/s, steps/200, "
+                               f"budget 150 GB, batches of up to 64, chunks of 5 steps")
+            sv["mixed"] = measure_serving("mixed")
+            sv["fp64"] = measure_serving("fp64")
+            extras["serving"] = sv
+        except Exception as e:
+            extras["serving"] = {"error": str(e)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

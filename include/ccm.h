@@ -270,8 +270,11 @@ ccm_status ccm_server_run(ccm_server s, int rounds, int* active);
 /* state: 0 queued, 1 running, 2 done, 3 failed; times3: submit, admit, done (seconds, one
  * monotonic clock); stats: last step's statistics, iteration counts summed over all steps. */
 ccm_status ccm_server_poll(ccm_server s, long long id, int* state, double* times3, ccm_step_stats* stats);
+/* Any field of a running request (as ccm_get_field); CCM_F_U, CCM_F_V or CCM_F_P of a finished
+ * one, whose case was destroyed at completion after these fields were copied to host memory
+ * (a finished request holds no device memory). */
 ccm_status ccm_server_get_field(ccm_server s, long long id, int field, double* host, size_t count);
-/* Free a finished or queued request (CCM_E_STATE while it runs). */
+/* Forget a finished or queued request and free its host copies (CCM_E_STATE while it runs). */
 ccm_status ccm_server_release(ccm_server s, long long id);
 size_t ccm_server_bytes_in_use(ccm_server s);
 

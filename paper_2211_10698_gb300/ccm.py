@@ -311,6 +311,14 @@ class Batch:
             pass
 
 
+def case_bytes(case, precision=None, precond=None):
+    """Device bytes a case of this description holds (ccm_case_bytes; allocates nothing)."""
+    cfg = make_config(case, precision, precond)
+    n = c_size_t()
+    _check(lib().ccm_case_bytes(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
 class Server:
     """Request loop: submit flow-past-body requests, run rounds, poll for completion."""
 

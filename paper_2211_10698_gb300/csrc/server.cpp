@@ -8,8 +8,10 @@
 //      while others are in flight),
 //   2. advances every resident case by one chunk of steps through a batch (one batched
 //      Poisson solve per step; FP64 and mixed-precision cases in separate batches),
-//   3. retires the cases that reached their step count: their statistics and timestamps are
-//      kept, their fields stay readable until ccm_server_release frees the memory.
+//   3. retires the cases that reached their step count: their velocity and pressure fields
+//      are copied to host memory and the case is destroyed, so a finished request holds no
+//      device memory; statistics, timestamps and the host copies stay until
+//      ccm_server_release.
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -41,7 +43,10 @@ struct Request {
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
   long long iters_p = 0, iters_h = 0;
   std::string error;
+  std::vector<double> saved[3];  // U, V, P of a finished request (padded layout)
 };
+
+constexpr int kSavedFields[3] = {CCM_F_U, CCM_F_V, CCM_F_P};
 
 }  // namespace
 
@@ -56,6 +61,25 @@ struct ccm_server_s {
   std::map<long long, Request*> all;
   long long next_id = 1;
 };
+
+// Copy the result fields to the host and free the case's device memory.
+static ccm_status retire(ccm_server_s* s, Request* r, int state, double t) {
+  ccm_status st = CCM_OK;
+  if (r->c) {
+    const size_t n = (size_t)(r->cfg.nx + 3) * (size_t)(r->cfg.ny + 3);
+    for (int f = 0; f < 3; ++f) {
+      r->saved[f].resize(n);
+      ccm_status e = ccm_get_field(r->c, kSavedFields[f], r->saved[f].data(), n);
+      if (e != CCM_OK && st == CCM_OK) st = e;
+    }
+    ccm_destroy_case(r->c);
+    r->c = nullptr;
+    s->used -= r->bytes;
+  }
+  r->state = st == CCM_OK ? state : Q_FAILED;
+  r->t_done = t;
+  return st;
+}
 
 extern "C" {
 
@@ -144,8 +168,7 @@ ccm_status ccm_server_run(ccm_server s, int rounds, int* active) {
       if (r->nsteps == 0) {
         ccm_batch_remove(s->batch[k], r->c);
         s->members[k].pop_back();
-        r->state = Q_DONE;
-        r->t_done = r->t_admit;
+        retire(s, r, Q_DONE, r->t_admit);
       }
     }
     // resident requests of each batch advance by the smallest remaining count, capped at chunk
@@ -169,8 +192,7 @@ ccm_status ccm_server_run(ccm_server s, int rounds, int* active) {
       for (Request* r : order) {
         if (r->done_steps >= r->nsteps) {
           ccm_batch_remove(s->batch[k], r->c);
-          r->state = rc == CCM_OK || rc == CCM_E_NOT_CONVERGED ? Q_DONE : Q_FAILED;
-          r->t_done = t;
+          retire(s, r, rc == CCM_OK || rc == CCM_E_NOT_CONVERGED ? Q_DONE : Q_FAILED, t);
         } else {
           keep.push_back(r);
         }
@@ -209,12 +231,21 @@ ccm_status ccm_server_poll(ccm_server s, long long id, int* state, double* times
   return CCM_OK;
 }
 
-// Copy a field of a finished (or running) request to the host (see ccm_get_field).
+// Copy a field to the host: any field of a running request (see ccm_get_field), U, V or P
+// of a finished one.
 ccm_status ccm_server_get_field(ccm_server s, long long id, int field, double* host, size_t count) {
-  if (!s) return CCM_E_INVALID;
+  if (!s || !host) return CCM_E_INVALID;
   auto it = s->all.find(id);
-  if (it == s->all.end() || !it->second->c) return CCM_E_INVALID;
-  return ccm_get_field(it->second->c, field, host, count);
+  if (it == s->all.end()) return CCM_E_INVALID;
+  Request* r = it->second;
+  if (r->c) return ccm_get_field(r->c, field, host, count);
+  for (int f = 0; f < 3; ++f)
+    if (field == kSavedFields[f] && !r->saved[f].empty()) {
+      if (count != r->saved[f].size()) return CCM_E_INVALID;
+      std::copy(r->saved[f].begin(), r->saved[f].end(), host);
+      return CCM_OK;
+    }
+  return CCM_E_INVALID;
 }
 
 // Free the request's device memory and forget it.
