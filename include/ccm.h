@@ -70,13 +70,17 @@ typedef struct {
   int precond;                /* Poisson preconditioner: CCM_JACOBI or CCM_CHEBYSHEV */
   int cheb_degree;            /* Chebyshev polynomial degree (>= 1) */
   double tol_p, tol_h;        /* relative residual targets, Poisson and Helmholtz */
-  double tol_inner;           /* MIXED: relative target of each FP32 inner solve */
+  double tol_inner;           /* MIXED, Chebyshev or singular: relative target of each FP32
+                                 inner solve of the host-driven refinement */
   int max_iter_p, max_iter_h; /* iteration limits */
   int literal_offdiag;        /* 1: Eq. offdiag with separate W^xy, W^yx (not symmetric) */
   int pressure_update;        /* volume V in the correction of Eq. pm_update,
                                  P += Phi - (dt mu / 2 rho) V^-1 cont(M^-1 pres Phi, 0):
                                  0 the full cell hx*hy (bounded in small cut cells; the
                                  default), 1 the cell's fluid volume V_p, 2 no correction */
+  double replace_drop;        /* MIXED, Jacobi, nonsingular (one-launch solve): reduction of the
+                                 FP32 residual that triggers an FP64 residual replacement
+                                 (0 selects 0.5) */
   ccm_alloc_fn alloc;
   ccm_free_fn free;
   void* alloc_ctx;

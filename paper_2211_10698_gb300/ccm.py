@@ -40,6 +40,7 @@ class ccm_config(Structure):
                 ("precision", c_int), ("precond", c_int), ("cheb_degree", c_int),
                 ("tol_p", c_double), ("tol_h", c_double), ("tol_inner", c_double),
                 ("max_iter_p", c_int), ("max_iter_h", c_int), ("literal_offdiag", c_int), ("pressure_update", c_int),
+                ("replace_drop", c_double),
                 ("alloc", ccm_alloc_fn), ("free", ccm_free_fn), ("alloc_ctx", c_void_p),
                 ("stream", c_void_p)]
 
@@ -153,6 +154,7 @@ def make_config(case, precision=None, precond=None, stream=None) -> ccm_config:
     cfg.max_iter_p, cfg.max_iter_h = case.max_iter_p, case.max_iter_h
     cfg.literal_offdiag = int(case.literal_offdiag)
     cfg.pressure_update = int(getattr(case, "pressure_update", 0))
+    cfg.replace_drop = float(getattr(case, "replace_drop", 0.0))
     cfg.stream = stream
     return cfg
 

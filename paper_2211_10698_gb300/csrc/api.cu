@@ -31,7 +31,7 @@ struct DevStats {
   double rr_p, bb_p, rr_h, bb_h;
   int conv_p, conv_h;
   int nconv;
-  int pad;
+  int nrep;        // FP64 residual replacements of the last mixed solve on the device
   double diag[3];  // max |cont|, kinetic, non-finite flag
 };
 
@@ -79,6 +79,7 @@ struct ccm_case_s {
   long long mixed_total = 0;
   int mixed_last = 0, mixed_outer = 0, mixed_nconv = 0;
   double mixed_rr = 0.0, mixed_bb = 0.0;
+  bool mixed_host = false;  // a host-driven refinement ran since the statistics were last read
 };
 
 namespace {
@@ -110,6 +111,9 @@ void carve(ccm_case c, Carver& cv) {
   o.cv32 = cv.take<float>(N);
   o.invdk32 = cv.take<float>(N);
   o.diagk32 = cv.take<float>(N);
+  for (double** q : {&o.sdk, &o.isdk, &o.cus, &o.cvs}) *q = cv.take<double>(N);
+  for (float** q : {&o.isdk32, &o.cus32, &o.cvs32}) *q = cv.take<float>(N);
+  o.kinds = cv.take<int8_t>(N);
   double** st[] = {&c->u, &c->v, &c->p, &c->phi, &c->cnu[0], &c->cnu[1], &c->cnv[0], &c->cnv[1],
                    &c->ustar, &c->vstar, &c->div, &c->rhs_u, &c->rhs_v, &c->rhs_p,
                    &c->pr, &c->pz, &c->pp0, &c->pp1, &c->pq, &c->pz2, &c->pw1,
@@ -229,6 +233,17 @@ void set_uniform_coefficients(ccm_case c, PoissonSolve<T>& a) {
 }
 
 ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
+  if (!c->zero_mean && c->cfg.precond == CCM_JACOBI) {
+    // Jacobi-PCG as CG on the symmetrically scaled system (nonsingular systems)
+    CaseSolveView v;
+    case_solve_view(c, &v);
+    ScaledSolve a = scaled_solve_of(v, x, b, c->pz, c->pr, c->pq, c->pp0, c->pp1);
+    a.partials = c->partials;
+    a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+    a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
+    CUDA_TRY(run_poisson_scaled(a, c->st));
+    return CCM_OK;
+  }
   PoissonSolve<double> a{};
   a.g = c->g;
   a.cu = c->co.cu; a.cv = c->co.cv; a.dk = c->co.diagk; a.invd = c->co.invdk; a.kind = c->co.kind;
@@ -271,6 +286,25 @@ cudaEvent_t next_event(ccm_case c) {
 // Mixed precision: FP64 residual, FP32 PCG on the correction equation K d = r to tol_inner,
 // x += d, until the FP64 residual meets tol_p (or 60 refinement sweeps).
 ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
+  if (!c->zero_mean && c->cfg.precond == CCM_JACOBI) {
+    // one launch: FP32 CG on the scaled system with FP64 residual replacements
+    CaseSolveView v;
+    case_solve_view(c, &v);
+    MixedSolve a{};
+    a.d = scaled_solve_of(v, x, b, nullptr, c->pr, nullptr, nullptr, nullptr);
+    a.d.partials = c->partials;
+    a.d.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+    a.d.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
+    a.cus32 = c->co.cus32; a.cvs32 = c->co.cvs32;
+    a.r = c->fr; a.w = c->fq; a.p = c->fp0; a.s = c->fp1; a.e = c->fx;
+    a.fpartials = (float*)(c->partials + pcg_float_partials_offset());
+    a.drop = c->cfg.replace_drop > 0 && c->cfg.replace_drop < 1 ? c->cfg.replace_drop : 0.5;
+    a.replacements = &c->ds->nrep;
+    CUDA_TRY(run_poisson_mixed(a, c->st));
+    c->launches += 1;
+    return CCM_OK;
+  }
+  c->mixed_host = true;
   const Geom& g = c->g;
   cudaStream_t st = c->st;
   int inner_total = 0, outer = 0;
@@ -368,6 +402,8 @@ bool case_solve_view(ccm_case c, CaseSolveView* v) {
   v->invd = c->co.invdk;
   v->kind = c->co.kind;
   v->act = c->co.act;
+  v->sd = c->co.sdk; v->isd = c->co.isdk; v->cus = c->co.cus; v->cvs = c->co.cvs; v->kinds = c->co.kinds;
+  v->precond = c->cfg.precond;
   v->tol = c->cfg.tol_p;
   v->max_iter = c->cfg.max_iter_p;
   v->zero_mean = c->zero_mean;
@@ -375,6 +411,23 @@ bool case_solve_view(ccm_case c, CaseSolveView* v) {
   return true;
 }
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+ScaledSolve scaled_solve_of(const CaseSolveView& v, double* x, const double* b, double* xs, double* r, double* w,
+                            double* p, double* s) {
+  ScaledSolve a{};
+  a.g = v.g;
+  a.cu = v.cu; a.cv = v.cv; a.dk = v.dk; a.kind = v.kind;
+  a.sd = v.sd; a.isd = v.isd; a.cus = v.cus; a.cvs = v.cvs; a.kinds = v.kinds;
+  a.creg_x = v.g.hy / v.g.hx;
+  a.creg_y = v.g.hx / v.g.hy;
+  a.dreg = 2.0 * (a.creg_x + a.creg_y);
+  a.ax = a.creg_x / a.dreg;
+  a.ay = a.creg_y / a.dreg;
+  a.x = x; a.b = b;
+  a.xs = xs; a.r = r; a.w = w; a.p = p; a.s = s;
+  a.tol = v.tol; a.max_iter = v.max_iter;
+  return a;
+}
 
 // Pieces of the step for the batch driver (csrc/batch.cu).
 ccm_status case_stage_predict(ccm_case c) { return stage_predict(c); }
@@ -434,6 +487,7 @@ void case_mixed_correct(ccm_case c) {
   c->launches += 1;
 }
 void case_mixed_account(ccm_case c, long long inner, int outer, double rr, double bb, bool converged) {
+  c->mixed_host = true;
   c->mixed_total += inner;
   c->mixed_last = (int)inner;
   c->mixed_outer = outer;
@@ -553,6 +607,7 @@ ccm_status ccm_set_geometry(ccm_case c, const ccm_geometry* geo) {
   cudaStream_t st = c->st;
   CUDA_TRY(launch_capacities(*geo, g, c->caps.a, st));
   launch_derive(g, c->bc, c->ph, c->cfg.literal_offdiag, c->cfg.pressure_update, c->caps, c->co, st);
+  launch_scaling(g, c->co, st);
   // lifting of the box data through the viscous operator: visc(S(0, D))
   CUDA_TRY(cudaMemsetAsync(c->t0, 0, g.count() * sizeof(double), st));
   CUDA_TRY(cudaMemsetAsync(c->t1, 0, g.count() * sizeof(double), st));
@@ -778,14 +833,17 @@ static ccm_status finish_stats(ccm_case c, ccm_step_stats* stats) {
   ccm_status s;
   if ((s = read_stats(c, h)) != CCM_OK) return s;
   if (c->timing) collect_timing(c);
-  if (c->cfg.precision == CCM_MIXED) {
-    h.total_p = c->mixed_total;
+  if (c->mixed_host) {
+    // host-driven refinements report through the case; one-launch mixed solves through the
+    // device counters, like FP64 solves
+    h.total_p += c->mixed_total;
     h.iters_p = c->mixed_last;
     h.rr_p = c->mixed_rr;
     h.bb_p = c->mixed_bb;
     h.nconv += c->mixed_nconv;
     c->mixed_total = 0;
     c->mixed_nconv = 0;
+    c->mixed_host = false;
   }
   if (stats) {
     stats->steps = (int)c->steps_pending;
@@ -873,8 +931,8 @@ ccm_status ccm_solve_pressure(ccm_case c, const double* rhs_host, ccm_solve_stat
   if ((s = poisson_solve(c, c->phi, c->rhs_p)) != CCM_OK) return s;
   DevStats h{};
   if ((s = read_stats(c, h)) != CCM_OK) return s;
-  int conv = h.conv_p, outer = 1;
-  if (c->cfg.precision == CCM_MIXED) {
+  int conv = h.conv_p, outer = c->cfg.precision == CCM_MIXED ? h.nrep : 1;
+  if (c->mixed_host) {
     h.iters_p = c->mixed_last;
     h.rr_p = c->mixed_rr;
     h.bb_p = c->mixed_bb;
@@ -882,6 +940,7 @@ ccm_status ccm_solve_pressure(ccm_case c, const double* rhs_host, ccm_solve_stat
     outer = c->mixed_outer;
     c->mixed_total = 0;
     c->mixed_nconv = 0;
+    c->mixed_host = false;
   }
   if (stats) {
     stats->iters = h.iters_p;

@@ -22,6 +22,12 @@ struct CoefPtrs {
   double *wxx, *wyy, *wxa, *wxb;
   double *invdhu, *invdhv, *liftu, *liftv;
   float *cu32, *cv32, *invdk32, *diagk32;
+  // symmetric Jacobi scaling of the Poisson matrix, D^-1/2 K D^-1/2 (unit diagonal):
+  // sqrt(d), 1/sqrt(d) per cell, the scaled face coefficients, and the scaled row kind
+  // (1: the cell and its four neighbours are uncut, so the scaled row is a constant stencil)
+  double *sdk, *isdk, *cus, *cvs;
+  float *isdk32, *cus32, *cvs32;
+  int8_t* kinds;
 };
 
 // Where a solver kernel reports: iterations, final squared residual and right-hand side
@@ -64,6 +70,40 @@ struct PoissonSolve {
   PcgOut out;
 };
 
+// Poisson solve on the symmetrically scaled system (FP64 Jacobi-PCG in exact arithmetic):
+// x~ = D^1/2 x, b~ = D^-1/2 b, K~ x~ = b~ by CG, then x = D^-1/2 x~.
+struct ScaledSolve {
+  Geom g;
+  const double *cu, *cv, *dk;   // K itself, for the initial residual b - K x
+  const int8_t* kind;
+  const double *sd, *isd, *cus, *cvs;
+  const int8_t* kinds;
+  double creg_x, creg_y, dreg;  // uncut-cell constants of K
+  double ax, ay;                // and of K~: creg / dreg
+  double* x;                    // in: warm start; out: solution
+  const double* b;
+  double *xs, *r, *w, *p, *s;   // scaled iterate, residual, K~ r, direction, K~ p
+  double tol;
+  int max_iter;
+  double* partials;
+  Barrier bar;
+  PcgOut out;
+};
+cudaError_t run_poisson_scaled(const ScaledSolve& a, cudaStream_t st);
+
+// Mixed-precision solve of the same system: FP32 CG on K~ with FP64 residual replacements.
+// d.r serves as the FP64 residual; d.xs, d.w, d.p, d.s are unused.
+struct MixedSolve {
+  ScaledSolve d;
+  const float *cus32, *cvs32;
+  float *r, *w, *p, *s, *e;   // FP32 residual, K~ r, direction, K~ p, correction
+  float* fpartials;           // 2 x blocks
+  double drop;                // FP32 residual reduction that triggers a replacement
+  int* replacements;          // out: FP64 replacements made
+};
+cudaError_t run_poisson_mixed(const MixedSolve& a, cudaStream_t st);
+void launch_scaling(const Geom& g, const CoefPtrs& o, cudaStream_t st);
+
 // One case of a batched Poisson solve and the contiguous range of blocks that serves it.
 template <class T>
 struct BatchEntry {
@@ -104,11 +144,18 @@ struct CaseSolveView {
   const double* invd;
   const int8_t* kind;
   const int8_t* act;
+  const double *sd, *isd, *cus, *cvs;  // symmetric Jacobi scaling (see ScaledSolve)
+  const int8_t* kinds;
+  int precond;
   double tol;
   int max_iter;
   int zero_mean;
   double n_act;
 };
+// The FP64 Poisson solve of a case on the scaled system, x and b in device memory, work
+// vectors xs, r, w, p, s given by the caller (r must be zero on the ghost ring).
+ScaledSolve scaled_solve_of(const CaseSolveView& v, double* x, const double* b, double* xs, double* r, double* w,
+                            double* p, double* s);
 // api.cu: false when the case has no geometry yet.
 bool case_solve_view(ccm_case c, CaseSolveView* v);
 // api.cu: the thread-local message returned by ccm_last_error.
@@ -148,6 +195,7 @@ void launch_diagnostics(const Coefs& c, const Geom& g, const double* Vu, const d
 
 // pcg.cu
 int pcg_partials_needed();
+size_t pcg_float_partials_offset();  // in doubles, within a partials buffer of that size
 bool cheb_degree_supported(int k);
 template <class T>
 cudaError_t run_poisson_pcg(PoissonSolve<T> a, cudaStream_t st);

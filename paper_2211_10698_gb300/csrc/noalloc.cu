@@ -4,7 +4,7 @@
 // through its own pool and forbids other allocations, a process running under a hard
 // device-memory cap, or latency-sensitive code that must not trigger the device-wide
 // synchronisation that cudaMalloc and cudaFree imply.  ccm_solve_pressure_noalloc serves
-// them: it runs the same FP64 Jacobi-PCG kernel as ccm_solve_pressure, but its scratch
+// them: it runs the same FP64 Jacobi-PCG kernels as ccm_solve_pressure, but its scratch
 // vectors live in one file-scope __device__ array of fixed size instead of memory the
 // library allocates.  The caller passes the right-hand side and the solution in device
 // memory of its own.
@@ -105,31 +105,40 @@ extern "C" ccm_status ccm_solve_pressure_noalloc(ccm_case c, const double* rhs_d
   cudaError_t e = scratch_address(&S);
   if (e != cudaSuccess) return fail(CCM_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   cudaStream_t st = v.st;
-  // the previous call's contents: p and s must start at zero (their ghost ring is read by the
-  // stencil), and so must the barrier counter and its error flag
-  if ((e = cudaMemsetAsync(S->p, 0, n * sizeof(double), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(S->s, 0, n * sizeof(double), st)) != cudaSuccess ||
+  // the previous call's contents (possibly of another grid size): every work vector is
+  // cleared, since the stencils read them on the ghost ring, and so are the barrier counter
+  // and its error flag
+  if ((e = cudaMemsetAsync(S->r, 0, 5 * kMaxElems * sizeof(double), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(&S->bar_count, 0, sizeof(unsigned int) + sizeof(int), st)) != cudaSuccess)
     return fail(CCM_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   const dim3 blk(64, 4), grd((v.g.nx + 3 + 63) / 64, (v.g.ny + 3 + 3) / 4);
   k_masked_copy<<<grd, blk, 0, st>>>(v.g, v.act, rhs_dev, S->b);
   k_mask<<<grd, blk, 0, st>>>(v.g, v.act, phi_dev);
-  PoissonSolve<double> a{};
-  a.g = v.g;
-  a.cu = v.cu; a.cv = v.cv; a.dk = v.dk; a.invd = v.invd; a.kind = v.kind;
-  a.creg_x = v.g.hy / v.g.hx;
-  a.creg_y = v.g.hx / v.g.hy;
-  a.dreg = 2.0 * (a.creg_x + a.creg_y);
-  a.invd_reg = 1.0 / a.dreg;
-  a.x = phi_dev; a.b = S->b; a.r = S->r; a.z = S->u; a.q = S->w; a.p0 = S->p; a.p1 = S->s;
-  a.z2 = nullptr; a.w1 = nullptr;
-  a.cheb = 1;
-  a.tol = v.tol; a.max_iter = v.max_iter;
-  a.zero_mean = v.zero_mean; a.n_act = v.n_act;
-  a.partials = S->partials;
-  a.bar = Barrier{&S->bar_count, &S->bar_err, 2000000000LL};
-  a.out = PcgOut{&S->iters, &S->rr, &S->bb, &S->converged, nullptr, nullptr};
-  if ((e = run_poisson_pcg<double>(a, st)) != cudaSuccess)
+  if (!v.zero_mean && v.precond == CCM_JACOBI) {
+    ScaledSolve q = scaled_solve_of(v, phi_dev, S->b, S->u, S->r, S->w, S->p, S->s);
+    q.partials = S->partials;
+    q.bar = Barrier{&S->bar_count, &S->bar_err, 2000000000LL};
+    q.out = PcgOut{&S->iters, &S->rr, &S->bb, &S->converged, nullptr, nullptr};
+    e = run_poisson_scaled(q, st);
+  } else {
+    PoissonSolve<double> a{};
+    a.g = v.g;
+    a.cu = v.cu; a.cv = v.cv; a.dk = v.dk; a.invd = v.invd; a.kind = v.kind;
+    a.creg_x = v.g.hy / v.g.hx;
+    a.creg_y = v.g.hx / v.g.hy;
+    a.dreg = 2.0 * (a.creg_x + a.creg_y);
+    a.invd_reg = 1.0 / a.dreg;
+    a.x = phi_dev; a.b = S->b; a.r = S->r; a.z = S->u; a.q = S->w; a.p0 = S->p; a.p1 = S->s;
+    a.z2 = nullptr; a.w1 = nullptr;
+    a.cheb = 1;
+    a.tol = v.tol; a.max_iter = v.max_iter;
+    a.zero_mean = v.zero_mean; a.n_act = v.n_act;
+    a.partials = S->partials;
+    a.bar = Barrier{&S->bar_count, &S->bar_err, 2000000000LL};
+    a.out = PcgOut{&S->iters, &S->rr, &S->bb, &S->converged, nullptr, nullptr};
+    e = run_poisson_pcg<double>(a, st);
+  }
+  if (e != cudaSuccess)
     return fail(CCM_E_CUDA, std::string("Poisson PCG launch: ") + cudaGetErrorString(e));
   struct { double rr, bb; int iters, converged; unsigned int count; int err; } h{};
   static_assert(sizeof(h) == offsetof(Scratch, bar_err) + sizeof(int) - offsetof(Scratch, rr), "layout");

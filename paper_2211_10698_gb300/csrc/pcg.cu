@@ -16,102 +16,9 @@
 // carried through the reductions, so no extra barrier is needed.
 //
 // Helmholtz, per iteration: A: q = H p, p.q | B: x, r, z updates, r.z, r.r | C: p = z + beta p.
-#include "ccm_host.h"
+#include "pcg_common.cuh"
 
 namespace ccm {
-
-constexpr int kPcgThreads = 512;
-
-__device__ __forceinline__ void publish(double* partials, int nb, const double* v, int nv) {
-  if (threadIdx.x == 0)
-    for (int q = 0; q < nv; ++q) partials[(size_t)q * nb + blockIdx.x] = v[q];
-}
-
-// Sum NV per-thread values over the block through shared memory; only warp 0 adds (in a
-// fixed order), so the FP64 cost is per block, not per thread.  Result valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum_smem(double (&v)[NV], double (*red)[kPcgThreads]) {
-#pragma unroll
-  for (int q = 0; q < NV; ++q) red[q][threadIdx.x] = v[q];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double s = 0.0;
-      for (int m = lane; m < (int)blockDim.x; m += 32) s += red[q][m];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      v[q] = s;
-    }
-  }
-}
-
-// Cells of this block: one contiguous chunk of the row-major interior, balanced to +-1 cell
-// across blocks (the FP64 pipe of each SM is the bottleneck, so per-SM work must be even).
-struct Chunk {
-  int t0, t1;
-  __device__ Chunk(int ncell) {
-    t0 = (int)((long long)ncell * blockIdx.x / gridDim.x);
-    t1 = (int)((long long)ncell * (blockIdx.x + 1) / gridDim.x);
-  }
-};
-
-// Walks t = first, first + stride, ... < end, keeping (i, j) of the interior cell t.
-struct CellWalk {
-  int t, i, j;
-  const int nx, stride, end;
-  __device__ CellWalk(int first, int stride_, int end_, int nx_) : t(first), nx(nx_), stride(stride_), end(end_) {
-    j = first / nx;
-    i = first - j * nx;
-  }
-  __device__ bool ok() const { return t < end; }
-  __device__ void next() {
-    t += stride;
-    i += stride;
-    while (i >= nx) { i -= nx; ++j; }
-  }
-};
-
-// Chebyshev iteration for K z = r from zero on the Jacobi-scaled operator, eigenvalue
-// interval [lmax/30, lmax] with lmax = 2 (Gershgorin bound for a diagonally dominant
-// M-matrix scaled by its diagonal), CHEB steps in all (Saad, Chebyshev acceleration).  On
-// entry z = w1 = D^-1 r / theta (the first step, written by the caller); each further step
-// needs z at the stencil neighbours, so steps are separated by grid barriers and z
-// alternates between two buffers.  Returns the buffer that holds the result.
-struct ChebCoef {
-  static constexpr double lmax = 2.0, lmin = 2.0 / 30.0;
-  static constexpr double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
-};
-
-// K x at one cell in diagonal form, d x_c - sum_f c_f x_nbr.  Cells whose four faces and
-// volume are uncut (kind 1) use the constant coefficients of the uniform grid, so their
-// coefficient arrays are not read; cut cells (kind 2) read them; other cells (kind 0:
-// inactive, identity row) return x_c.
-template <class T>
-struct KRow {
-  const T* cu;
-  const T* cv;
-  const T* dk;
-  const int8_t* kind;
-  T cx, cy, dreg;
-  size_t P;
-  __device__ __forceinline__ T operator()(const T* x, size_t k) const {
-    const int8_t t = kind[k];
-    const T xc = x[k];
-    if (t == 1) return dreg * xc - cx * (x[k - 1] + x[k + 1]) - cy * (x[k - P] + x[k + P]);
-    if (t == 2)
-      return dk[k] * xc - cu[k] * x[k - 1] - cu[k + 1] * x[k + 1] - cv[k] * x[k - P] - cv[k + P] * x[k + P];
-    return xc;
-  }
-};
-
-// Per-block scalar state of the PCG recurrences, computed by thread 0 only (FP64 division
-// is a software sequence on this part) and read by every thread from shared memory.
-struct PcgScalars {
-  double rz, rr, bb, beta, alpha, zmean;
-  int it, stop;  // stop: 0 continue, 1 converged, 2 iteration limit
-};
 
 template <class T, bool ZM, int CHEB>
 __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson(PoissonSolve<T> a) {
@@ -800,7 +707,14 @@ int pcg_partials_needed() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms * 4 * 8;  // blocks (at most 4 per SM) times values per reduction
+  return sms * 4 * 8 + sms * 4;  // blocks (at most 4 per SM) times values per reduction, then
+                                 // the FP32 partials of the mixed solve (2 floats per block)
+}
+size_t pcg_float_partials_offset() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (size_t)sms * 4 * 8;
 }
 
 template <class T, bool ZM>

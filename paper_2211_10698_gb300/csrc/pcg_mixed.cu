@@ -1,0 +1,419 @@
+// Mixed-precision pressure Poisson solve (Eq. pm_poisson): conjugate gradients in FP32 on the
+// symmetrically Jacobi-scaled system, anchored by FP64 residual replacements ("reliable
+// updates": Sleijpen and van der Vorst, Computing 56, 1996; used for mixed-precision GPU
+// solvers by Clark et al., Comput. Phys. Commun. 181, 2010).
+//
+// The iterate x and the right-hand side b stay in FP64.  Between replacements the kernel runs
+// the single-reduction CG of pcg_scaled.cu in FP32 on the correction equation
+//     K~ e~ = r~,   r~ = sigma D^-1/2 (b - K x),
+// normalised by sigma = 1 / ||D^-1/2 (b - K x)|| so the FP32 values stay near unit size
+// whatever the scale of b.  When the FP32 residual has dropped by the factor `drop` since the
+// last replacement (or its estimate says the FP64 test may be met) the kernel
+//   R1: folds the correction into x (x += D^-1/2 e~ / sigma, e~ = 0),
+//   R2: forms the true residual b - K x in FP64 and its norms; stops if ||b - K x|| <= tol ||b||,
+//   R3: restarts the FP32 residual from it with the new normalisation,
+// and continues with the same search direction (rescaled to the new normalisation) instead of
+// restarting the Krylov space, which is what keeps the iteration count close to FP64 CG.
+// The FP32 dot products are summed in FP32 per thread, warp and block, the block partials in
+// FP32 across the grid (fixed order, deterministic); the replacement norms are FP64.
+#include "pcg_common.cuh"
+
+namespace ccm {
+
+namespace {
+
+constexpr int kGroup = 3;
+
+// FP32 block sum of NV values: shuffle tree per warp, then warps 0..NV-1 add the 16 warp
+// partials of one quantity each.  Sums land in out[0..NV-1] (shared).
+template <int NV>
+__device__ __forceinline__ void block_sum_f32(const float (&v)[NV], float (*wred)[kPcgThreads / 32], float* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    float s = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) wred[q][w] = s;
+  }
+  __syncthreads();
+  if (w < NV) {
+    float s = lane < kPcgThreads / 32 ? wred[w][lane] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[w] = s;
+  }
+  __syncthreads();
+}
+
+// FP32 grid sum: warp q adds the nb block partials of quantity q (all loads in flight).
+template <int NV>
+__device__ __forceinline__ void grid_sum_f32(const float* partials, int nb, float (&out)[NV], float* smem) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (w < NV) {
+    const float* src = partials + (size_t)w * nb;
+    float buf[kGridSumPerLane];
+#pragma unroll
+    for (int m = 0; m < kGridSumPerLane; ++m) {
+      const int b = lane + 32 * m;
+      buf[m] = b < nb ? __ldcg(&src[b]) : 0.0f;
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int m = 0; m < kGridSumPerLane; ++m) s += buf[m];
+    for (int b = lane + 32 * kGridSumPerLane; b < nb; b += 32) s += __ldcg(&src[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) smem[w] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = smem[k];
+}
+
+__global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve a) {
+  __shared__ double red[4][kPcgThreads];
+  __shared__ float wred[2][kPcgThreads / 32];
+  __shared__ double dsum[8];
+  __shared__ float fsum[8];
+  __shared__ double sc_sigma, sc_rr, sc_bb, sc_rr_ref;
+  __shared__ float sc_alpha, sc_beta, sc_pscale, sc_igamma, sc_ialpha, sc_gref, sc_gfresh;
+  __shared__ int sc_it, sc_stop, sc_replace, sc_nrep;  // stop: 1 converged, 2 iteration limit
+  __shared__ int sc_keep;     // the next phase A uses the stored p and s (formed by phase P)
+  __shared__ int sc_restart;  // the next replacement also restarts the direction (beta = 0)
+  __shared__ int sc_rep_it;   // iteration of the last replacement
+  unsigned int target = 0;
+  const int nb = gridDim.x;
+  const ScaledSolve& d = a.d;
+  const Geom g = d.g;
+  const int nx = g.nx, P = g.pitch;
+  const Chunk ch(g.nx * g.ny);
+  const int first = ch.t0 + threadIdx.x, stride = blockDim.x;
+  const int kdummy = (int)g.idx(0, 0);
+  const KRow<double> K{d.cu, d.cv, d.dk, d.kind, d.creg_x, d.creg_y, d.dreg, (size_t)P};
+  const int8_t* __restrict__ kinds = d.kinds;
+  const float* __restrict__ cus = a.cus32;
+  const float* __restrict__ cvs = a.cvs32;
+  const float ax = (float)d.ax, ay = (float)d.ay;
+  const double* __restrict__ isd = d.isd;
+  double* __restrict__ x = d.x;
+  double* __restrict__ r64 = d.r;  // scaled FP64 residual D^-1/2 (b - K x) at a replacement
+  float* __restrict__ r = a.r;
+  float* __restrict__ w = a.w;
+  float* __restrict__ p = a.p;
+  float* __restrict__ s = a.s;
+  float* __restrict__ e = a.e;
+  float* fpart = a.fpartials;
+  const double tol2 = d.tol * d.tol;
+
+  // R2 (and the start): r64 = D^-1/2 (b - K x); sums ||r64||^2, ||b - K x||^2 (and ||b||^2).
+  auto residual64 = [&](bool with_b) -> bool {
+    double v[3] = {0.0, 0.0, 0.0};
+    for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
+      const size_t k = g.idx(cw.i, cw.j);
+      const double bk = d.b[k];
+      const double rk = bk - K(x, k);
+      const double rs = isd[k] * rk;
+      r64[k] = rs;
+      v[0] += rs * rs;
+      v[1] += rk * rk;
+      v[2] += bk * bk;
+    }
+    if (with_b) block_sum_warps<3>(v, red, dsum);
+    else {
+      const double v2[2] = {v[0], v[1]};
+      block_sum_warps<2>(v2, red, dsum);
+    }
+    if (threadIdx.x == 0)
+      for (int q = 0; q < (with_b ? 3 : 2); ++q) d.partials[(size_t)q * nb + blockIdx.x] = dsum[q];
+    if (!grid_sync(d.bar, target)) return false;
+    double t[3];
+    grid_sum<3>(d.partials, nb, t, dsum);
+    if (threadIdx.x == 0) {
+      if (with_b) sc_bb = t[2];
+      sc_rr = t[1];
+      sc_rr_ref = t[1];
+      const double old = sc_sigma;
+      sc_sigma = t[0] > 0.0 ? 1.0 / sqrt(t[0]) : 1.0;
+      // directions and K~ p carried over are rescaled to the new normalisation
+      const double c = old > 0.0 ? sc_sigma / old : 0.0;
+      sc_pscale = (float)c;
+      sc_igamma = (float)((double)sc_igamma / (c * c + (c == 0.0)));
+      if (sc_bb == 0.0 || sc_rr <= tol2 * sc_bb) sc_stop = 1;
+    }
+    __syncthreads();
+    return true;
+  };
+  // Phase B: w = K~ r (FP32) and the sums gamma = (r, r), delta = (w, r).  With `fresh`, r is
+  // first set from the FP64 residual: r = sigma r64, read at the neighbours the same way.
+  auto phase_b = [&](bool fresh) -> bool {
+    float v[2] = {0.0f, 0.0f};
+    const double sig = sc_sigma;
+    CellWalk cw(first, stride, ch.t1, nx);
+    Group<kGroup> gr;
+    while (next_group(cw, g, kdummy, gr)) {
+      int8_t km[kGroup];
+      float rc[kGroup], rw[kGroup], re[kGroup], rs[kGroup], rn[kGroup];
+      if (fresh) {
+#pragma unroll
+        for (int m = 0; m < kGroup; ++m) {
+          const int k = gr.k[m];
+          km[m] = kinds[k];
+          rc[m] = (float)(sig * r64[k]);
+          rw[m] = (float)(sig * r64[k - 1]);
+          re[m] = (float)(sig * r64[k + 1]);
+          rs[m] = (float)(sig * r64[k - P]);
+          rn[m] = (float)(sig * r64[k + P]);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < kGroup; ++m) {
+          const int k = gr.k[m];
+          km[m] = kinds[k];
+          rc[m] = r[k];
+          rw[m] = r[k - 1];
+          re[m] = r[k + 1];
+          rs[m] = r[k - P];
+          rn[m] = r[k + P];
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < kGroup; ++m) {
+        const int k = gr.k[m];
+        float wk;
+        if (km[m] == 1) wk = rc[m] - ax * (rw[m] + re[m]) - ay * (rs[m] + rn[m]);
+        else if (km[m] == 2) wk = rc[m] - cus[k] * rw[m] - cus[k + 1] * re[m] - cvs[k] * rs[m] - cvs[k + P] * rn[m];
+        else wk = rc[m];
+        if (gr.v[m]) {
+          if (fresh) r[k] = rc[m];
+          w[k] = wk;
+          v[0] += rc[m] * rc[m];
+          v[1] += wk * rc[m];
+        }
+      }
+    }
+    block_sum_f32<2>(v, wred, fsum);
+    if (threadIdx.x == 0) {
+      fpart[blockIdx.x] = fsum[0];
+      fpart[nb + blockIdx.x] = fsum[1];
+    }
+    if (!grid_sync(d.bar, target)) return false;
+    float t[2];
+    grid_sum_f32<2>(fpart, nb, t, fsum);
+    if (threadIdx.x == 0) {
+      const float gamma = t[0], delta = t[1];
+      if (!fresh) {
+        sc_it += 1;         // one more phase A done
+        sc_pscale = 1.0f;   // its rescaling (after a replacement) is spent
+        sc_keep = 0;
+      }
+      if (fresh) sc_gref = gamma;
+      // replace when the FP32 residual fell by `drop`, or when the estimate of the unscaled
+      // residual norm (scaled by the last FP64 value) meets the tolerance
+      const double ratio = (double)gamma / (double)sc_gref;
+      sc_replace = !fresh && (ratio <= a.drop * a.drop || sc_rr_ref * ratio <= tol2 * sc_bb) ? 1 : 0;
+      // A residual about to be replaced is not used: the scalars are formed from the replacing
+      // residual instead (next call, fresh), against the same previous gamma and alpha.
+      if (!sc_replace) {
+        if (fresh && sc_it == 0 && sc_nrep == 0) {
+          sc_beta = 0.0f;
+          sc_alpha = gamma / delta;  // (p, K~ p) = (r, w) exactly
+          sc_igamma = 1.0f / gamma;
+          sc_ialpha = 1.0f / sc_alpha;
+        } else if (fresh && sc_restart) {
+          // restart after a breakdown or back-to-back replacements: steepest descent step
+          sc_beta = 0.0f;
+          sc_alpha = gamma / delta;
+          sc_igamma = 1.0f / gamma;
+          sc_ialpha = 1.0f / sc_alpha;
+          sc_pscale = 0.0f;
+          sc_restart = 0;
+        } else if (fresh) {
+          // after a replacement the recurrences no longer hold exactly: beta as usual, and
+          // alpha = gamma / (p, K~ p) from the formed direction (phase P)
+          sc_beta = gamma * sc_igamma;
+          sc_gfresh = gamma;
+          sc_keep = 1;
+        } else {
+          // Chronopoulos-Gear: beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old)
+          const float beta = gamma * sc_igamma;
+          const float den = delta - beta * gamma * sc_ialpha;
+          if (den > 0.0f && den < INFINITY) {
+            sc_beta = beta;
+            sc_alpha = gamma / den;
+            sc_igamma = 1.0f / gamma;
+            sc_ialpha = 1.0f / sc_alpha;
+          } else {
+            sc_replace = 1;  // loss of positivity in FP32: replace and restart
+            sc_restart = 1;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    return true;
+  };
+
+  // Phase P (after a replacement): p = r + beta' p, s = w + beta' s stored, and
+  // alpha = gamma / (p, s) from a direct reduction.
+  auto phase_p = [&]() -> bool {
+    const float be = sc_beta * sc_pscale;
+    float v[1] = {0.0f};
+    CellWalk cw(first, stride, ch.t1, nx);
+    Group<kGroup> gr;
+    while (next_group(cw, g, kdummy, gr)) {
+      float pm[kGroup], rm[kGroup], wm[kGroup], sm[kGroup];
+#pragma unroll
+      for (int m = 0; m < kGroup; ++m) {
+        const int k = gr.k[m];
+        pm[m] = p[k];
+        rm[m] = r[k];
+        wm[m] = w[k];
+        sm[m] = s[k];
+      }
+#pragma unroll
+      for (int m = 0; m < kGroup; ++m) {
+        const int k = gr.k[m];
+        const float pk = rm[m] + be * pm[m];
+        const float sk = wm[m] + be * sm[m];
+        if (gr.v[m]) {
+          p[k] = pk;
+          s[k] = sk;
+          v[0] += pk * sk;
+        }
+      }
+    }
+    block_sum_f32<1>(v, wred, fsum);
+    if (threadIdx.x == 0) fpart[blockIdx.x] = fsum[0];
+    if (!grid_sync(d.bar, target)) return false;
+    float t[1];
+    grid_sum_f32<1>(fpart, nb, t, fsum);
+    if (threadIdx.x == 0) {
+      sc_alpha = sc_gfresh / t[0];
+      sc_igamma = 1.0f / sc_gfresh;
+      sc_ialpha = 1.0f / sc_alpha;
+    }
+    __syncthreads();
+    return true;
+  };
+
+  if (threadIdx.x == 0) {
+    sc_keep = 0;
+    sc_restart = 0;
+    sc_rep_it = -1000;
+    sc_sigma = 0.0;
+    sc_igamma = 1.0f;
+    sc_pscale = 1.0f;
+    sc_it = 0;
+    sc_stop = 0;
+    sc_nrep = 0;
+    sc_bb = 0.0;
+  }
+  for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
+    const size_t k = g.idx(cw.i, cw.j);
+    p[k] = 0.0f;
+    s[k] = 0.0f;
+    e[k] = 0.0f;
+  }
+  __syncthreads();
+  bool ok = residual64(true);
+  if (ok && sc_stop == 0) ok = phase_b(true);
+  bool limit = false;
+  while (ok && sc_stop == 0) {
+    if (sc_it >= d.max_iter) {
+      limit = true;
+      break;
+    }
+    // phase A (FP32): p = r + beta' p, s = w + beta' s, e += alpha p, r -= alpha s (p and s as
+    // stored when phase P formed them)
+    {
+      const float al = sc_alpha, be = sc_keep ? 0.0f : sc_beta * sc_pscale;
+      const bool keep = sc_keep != 0;
+      CellWalk cw(first, stride, ch.t1, nx);
+      Group<kGroup> gr;
+      while (next_group(cw, g, kdummy, gr)) {
+        float pm[kGroup], rm[kGroup], wm[kGroup], sm[kGroup], em[kGroup];
+#pragma unroll
+        for (int m = 0; m < kGroup; ++m) {
+          const int k = gr.k[m];
+          pm[m] = p[k];
+          rm[m] = r[k];
+          wm[m] = w[k];
+          sm[m] = s[k];
+          em[m] = e[k];
+        }
+#pragma unroll
+        for (int m = 0; m < kGroup; ++m) {
+          const int k = gr.k[m];
+          const float pk = keep ? pm[m] : rm[m] + be * pm[m];
+          const float sk = keep ? sm[m] : wm[m] + be * sm[m];
+          if (gr.v[m]) {
+            if (!keep) {
+              p[k] = pk;
+              s[k] = sk;
+            }
+            e[k] = em[m] + al * pk;
+            r[k] = rm[m] - al * sk;
+          }
+        }
+      }
+    }
+    if (!grid_sync(d.bar, target)) { ok = false; break; }
+    if (!phase_b(false)) { ok = false; break; }
+    if (sc_replace) {
+      // R1: x += D^-1/2 e / sigma, e = 0 (cell-local), then R2 after a barrier, then R3 + B
+      const double isig = 1.0 / sc_sigma;
+      for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
+        const size_t k = g.idx(cw.i, cw.j);
+        x[k] += isd[k] * (double)e[k] * isig;
+        e[k] = 0.0f;
+      }
+      if (threadIdx.x == 0) {
+        sc_nrep += 1;
+        if (sc_it - sc_rep_it < 3) sc_restart = 1;  // replacements back to back: no progress
+        sc_rep_it = sc_it;
+      }
+      if (!grid_sync(d.bar, target)) { ok = false; break; }
+      if (!residual64(false)) { ok = false; break; }
+      if (sc_stop != 0) break;
+      if (!phase_b(true)) { ok = false; break; }
+      if (sc_keep && !phase_p()) { ok = false; break; }
+    }
+  }
+  if (ok && limit) {
+    // iteration limit: keep the progress of the last segment and report the true residual
+    const double isig = 1.0 / sc_sigma;
+    for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
+      const size_t k = g.idx(cw.i, cw.j);
+      x[k] += isd[k] * (double)e[k] * isig;
+    }
+    if (!grid_sync(d.bar, target) || !residual64(false)) ok = false;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool conv = ok && sc_stop == 1;
+    d.out.iters[0] = ok ? sc_it : 0;
+    d.out.rr[0] = ok ? sc_rr : 0.0;
+    d.out.bb[0] = ok ? sc_bb : 0.0;
+    d.out.converged[0] = conv ? 1 : 0;
+    if (d.out.total && ok) d.out.total[0] += sc_it;
+    if (!conv && d.out.nconv) d.out.nconv[0] += 1;
+    if (a.replacements) a.replacements[0] = sc_nrep;
+  }
+}
+
+}  // namespace
+
+cudaError_t run_poisson_mixed(const MixedSolve& a, cudaStream_t st) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_poisson_mixed, kPcgThreads, 0);
+  per = per > 2 ? 2 : (per < 1 ? 1 : per);
+  cudaMemsetAsync(a.d.bar.count, 0, sizeof(unsigned int), st);
+  MixedSolve arg = a;
+  void* params[] = {&arg};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_poisson_mixed, sms * per, kPcgThreads, params, 0, st);
+}
+
+}  // namespace ccm

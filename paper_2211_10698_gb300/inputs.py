@@ -86,6 +86,7 @@ class Case:
     seed: int = SEED
     literal_offdiag: int = 0
     pressure_update: int = 0       # volume in the pressure-update correction: 0 hx*hy, 1 V_p, 2 none
+    replace_drop: float = 0.5      # mixed one-launch solve: FP32 residual drop per FP64 replacement
 
     @property
     def hx(self) -> float:

@@ -192,13 +192,14 @@ def test_mixed_precision_poisson_solve(name, precond):
 
 
 @pytest.mark.parametrize("name", ["cylinder", "naca"])
-def test_mixed_precision_steps(name):
+@pytest.mark.parametrize("precond", ["jacobi", "chebyshev"])
+def test_mixed_precision_steps(name, precond):
     """Steps with the mixed-precision Poisson solve refined to an FP64 residual of 1e-12
     stay within 1e-8 of the FP64 oracle."""
     case = CASES[name]()
     case.tol_p, case.tol_h = 1e-12, 1e-13
     case.precision = "mixed"
-    case.precond = "chebyshev"
+    case.precond = precond
     o = O.Oracle(case)
     g = ccm.Case(case)
     s = o.init_state()
