@@ -285,21 +285,27 @@ cudaEvent_t next_event(ccm_case c) {
 
 // Mixed precision: FP64 residual, FP32 PCG on the correction equation K d = r to tol_inner,
 // x += d, until the FP64 residual meets tol_p (or 60 refinement sweeps).
+// The one-launch mixed solve of a case (x = solution in/out, b = right-hand side).
+void case_mixed_solve(ccm_case c, double* x, const double* b, MixedSolve* a) {
+  CaseSolveView v;
+  case_solve_view(c, &v);
+  *a = MixedSolve{};
+  a->d = scaled_solve_of(v, x, b, nullptr, c->pr, nullptr, nullptr, nullptr);
+  a->d.partials = c->partials;
+  a->d.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+  a->d.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
+  a->cus32 = c->co.cus32; a->cvs32 = c->co.cvs32;
+  a->r = c->fr; a->w = c->fq; a->p = c->fp0; a->s = c->fp1; a->e = c->fx;
+  a->fpartials = (float*)(c->partials + pcg_float_partials_offset());
+  a->drop = c->cfg.replace_drop > 0 && c->cfg.replace_drop < 1 ? c->cfg.replace_drop : 0.5;
+  a->replacements = &c->ds->nrep;
+}
+
 ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
   if (!c->zero_mean && c->cfg.precond == CCM_JACOBI) {
     // one launch: FP32 CG on the scaled system with FP64 residual replacements
-    CaseSolveView v;
-    case_solve_view(c, &v);
     MixedSolve a{};
-    a.d = scaled_solve_of(v, x, b, nullptr, c->pr, nullptr, nullptr, nullptr);
-    a.d.partials = c->partials;
-    a.d.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
-    a.d.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
-    a.cus32 = c->co.cus32; a.cvs32 = c->co.cvs32;
-    a.r = c->fr; a.w = c->fq; a.p = c->fp0; a.s = c->fp1; a.e = c->fx;
-    a.fpartials = (float*)(c->partials + pcg_float_partials_offset());
-    a.drop = c->cfg.replace_drop > 0 && c->cfg.replace_drop < 1 ? c->cfg.replace_drop : 0.5;
-    a.replacements = &c->ds->nrep;
+    case_mixed_solve(c, x, b, &a);
     CUDA_TRY(run_poisson_mixed(a, c->st));
     c->launches += 1;
     return CCM_OK;
@@ -437,6 +443,17 @@ bool case_is_mixed(ccm_case c) { return c->cfg.precision == CCM_MIXED; }
 cudaStream_t case_stream(ccm_case c) { return c->st; }
 size_t case_cells(ccm_case c) { return (size_t)c->g.nx * c->g.ny; }
 int case_nx(ccm_case c) { return c->g.nx; }
+
+// Descriptors of the case's pressure solve (x = Phi, b = the step's right-hand side) for the
+// batched kernels; statistics go to the case's device counters as for a single solve.
+bool case_scaled_ok(ccm_case c) { return !c->zero_mean && c->geometry; }
+void case_scaled_fp64(ccm_case c, ScaledSolve* a) {
+  CaseSolveView v;
+  case_solve_view(c, &v);
+  *a = scaled_solve_of(v, c->phi, c->rhs_p, c->pz, c->pr, c->pq, c->pp0, c->pp1);
+  a->out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
+}
+void case_mixed_batch(ccm_case c, MixedSolve* a) { case_mixed_solve(c, c->phi, c->rhs_p, a); }
 
 // FP64 Jacobi-PCG descriptor of the case's pressure solve (x = Phi, b = the step's right-hand
 // side); statistics go to the case's device counters as for a single solve.

@@ -2,12 +2,14 @@
 //
 // All cases of a batch run on the batch's stream.  Per step, each case's explicit stages and
 // Helmholtz solve are enqueued case by case, then ONE cooperative launch solves the pressure
-// Poisson systems of all cases (k_pcg_poisson_cg_batch: each case gets a contiguous range of
-// blocks in proportion to its expected work, cells x nx, and reduces over its own blocks),
-// then each case's projection is enqueued.  With the MIXED precision setting the FP64
-// residual refinement runs for the whole batch: residuals of the unconverged cases, one
-// host check, one batched FP32 inner solve for those cases, corrections, until every case
-// meets tol_p.
+// Poisson systems of all cases (each case gets a contiguous range of blocks in proportion to
+// its expected work, cells x nx, and reduces over its own blocks), then each case's
+// projection is enqueued.  When every case has an outflow side (nonsingular systems) the
+// launch is k_sc_batch (FP64 CG on the Jacobi-scaled systems) or k_mixed_batch (FP32 CG with
+// FP64 residual replacements, for the MIXED setting), both in pcg_batch.cu.  Otherwise the
+// unscaled Jacobi-PCG batch of pcg.cu runs, and for MIXED the FP64 residual refinement runs
+// from the host for the whole batch: residuals of the unconverged cases, one host check, one
+// batched FP32 inner solve for those cases, corrections, until every case meets tol_p.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -25,6 +27,8 @@ struct ccm_batch_s {
   void* dev = nullptr;
   BatchEntry<double>* e64 = nullptr;
   BatchEntry<float>* e32 = nullptr;
+  ScaledBatchEntry* esc = nullptr;
+  MixedBatchEntry* emx = nullptr;
   int* block_case = nullptr;
   double* partials = nullptr;
   int* running = nullptr;
@@ -70,6 +74,58 @@ void allocate_blocks(const std::vector<ccm_case>& cs, int blocks, std::vector<in
 }
 
 }  // namespace
+
+// One launch of k_sc_batch (FP64) or k_mixed_batch (MIXED) for all cases.
+static ccm_status batch_solve_scaled(ccm_batch b, bool mixed) {
+  const std::vector<ccm_case>& cs = b->cases;
+  const int n = (int)cs.size();
+  std::vector<int> b0, nb;
+  allocate_blocks(cs, b->blocks, b0, nb);
+  std::vector<int> block_case(b->blocks);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < nb[i]; ++k) block_case[b0[i] + k] = i;
+  BatchControl ctl{b->partials, b->running, Barrier{b->bar_count, b->bar_err, 2000000000LL}};
+  cudaError_t e = cudaMemcpyAsync(b->block_case, block_case.data(), sizeof(int) * b->blocks, cudaMemcpyHostToDevice,
+                                  b->st);
+  std::vector<ScaledBatchEntry> es;
+  std::vector<MixedBatchEntry> em;
+  if (e == cudaSuccess && !mixed) {
+    es.resize(n);
+    for (int i = 0; i < n; ++i) {
+      case_scaled_fp64(cs[i], &es[i].a);
+      es[i].block0 = b0[i];
+      es[i].nblocks = nb[i];
+    }
+    e = cudaMemcpyAsync(b->esc, es.data(), sizeof(ScaledBatchEntry) * n, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = run_scaled_batch(b->esc, b->block_case, ctl, b->blocks, b->st);
+  } else if (e == cudaSuccess) {
+    em.resize(n);
+    for (int i = 0; i < n; ++i) {
+      case_mixed_batch(cs[i], &em[i].a);
+      em[i].block0 = b0[i];
+      em[i].nblocks = nb[i];
+    }
+    e = cudaMemcpyAsync(b->emx, em.data(), sizeof(MixedBatchEntry) * n, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = run_mixed_batch(b->emx, b->block_case, ctl, b->blocks, b->st);
+  }
+  // the host tables must outlive the asynchronous copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched Poisson solve: ") + cudaGetErrorString(e));
+  int err = 0;
+  if ((e = cudaMemcpy(&err, b->bar_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return bfail(CCM_E_CUDA, cudaGetErrorString(e));
+  if (err) {
+    cudaMemset(b->bar_err, 0, sizeof(int));
+    return bfail(CCM_E_TIMEOUT, "a device-wide barrier gave up waiting");
+  }
+  return CCM_OK;
+}
+
+static bool all_scaled(ccm_batch b) {
+  for (ccm_case c : b->cases)
+    if (!case_scaled_ok(c)) return false;
+  return true;
+}
 
 static ccm_status batch_solve(ccm_batch b, const std::vector<ccm_case>& cs, bool fp32) {
   const int n = (int)cs.size();
@@ -175,12 +231,14 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
   ccm_batch b = new ccm_batch_s();
   b->st = (cudaStream_t)stream;
   b->max_cases = max_cases;
-  b->blocks = batch_blocks();
+  b->blocks = std::min(batch_blocks(), batch_scaled_blocks());
   if (max_cases > b->blocks) {
+    const int most = b->blocks;
     delete b;
-    return bfail(CCM_E_INVALID, "a batch holds at most " + std::to_string(batch_blocks()) + " cases on this GPU");
+    return bfail(CCM_E_INVALID, "a batch holds at most " + std::to_string(most) + " cases on this GPU");
   }
-  const size_t pieces[7] = {sizeof(BatchEntry<double>) * max_cases, sizeof(BatchEntry<float>) * max_cases,
+  const size_t pieces[9] = {sizeof(BatchEntry<double>) * max_cases, sizeof(BatchEntry<float>) * max_cases,
+                            sizeof(ScaledBatchEntry) * max_cases, sizeof(MixedBatchEntry) * max_cases,
                             sizeof(int) * b->blocks, sizeof(double) * 6 * b->blocks, sizeof(int) * b->blocks,
                             sizeof(unsigned int) * 4, sizeof(int) * 4};
   size_t bytes = 0;
@@ -195,6 +253,8 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
   auto take = [&](size_t n) { char* q = p; p += (n + 255) & ~(size_t)255; return (void*)q; };
   b->e64 = (BatchEntry<double>*)take(sizeof(BatchEntry<double>) * max_cases);
   b->e32 = (BatchEntry<float>*)take(sizeof(BatchEntry<float>) * max_cases);
+  b->esc = (ScaledBatchEntry*)take(sizeof(ScaledBatchEntry) * max_cases);
+  b->emx = (MixedBatchEntry*)take(sizeof(MixedBatchEntry) * max_cases);
   b->block_case = (int*)take(sizeof(int) * b->blocks);
   b->partials = (double*)take(sizeof(double) * 6 * b->blocks);
   b->running = (int*)take(sizeof(int) * b->blocks);
@@ -254,11 +314,14 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
   if (nsteps < 0) return bfail(CCM_E_INVALID, "nsteps < 0");
   if (b->cases.empty()) return CCM_OK;
   const bool mixed = case_is_mixed(b->cases[0]);
+  const bool scaled = all_scaled(b);
   ccm_status s;
   for (int n = 0; n < nsteps; ++n) {
     for (ccm_case c : b->cases)
       if ((s = case_stage_predict(c)) != CCM_OK) return s;
-    if (mixed) {
+    if (scaled) {
+      if ((s = batch_solve_scaled(b, mixed)) != CCM_OK) return s;
+    } else if (mixed) {
       if ((s = batch_mixed(b)) != CCM_OK) return s;
     } else {
       if ((s = batch_solve(b, b->cases, false)) != CCM_OK) return s;

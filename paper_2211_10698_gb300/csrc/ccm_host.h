@@ -97,11 +97,21 @@ struct MixedSolve {
   ScaledSolve d;
   const float *cus32, *cvs32;
   float *r, *w, *p, *s, *e;   // FP32 residual, K~ r, direction, K~ p, correction
-  float* fpartials;           // 2 x blocks
+  float* fpartials;           // 3 x blocks
   double drop;                // FP32 residual reduction that triggers a replacement
   int* replacements;          // out: FP64 replacements made
 };
 cudaError_t run_poisson_mixed(const MixedSolve& a, cudaStream_t st);
+
+// One case of a batched solve and its contiguous range of blocks (pcg_batch.cu).
+struct ScaledBatchEntry {
+  ScaledSolve a;  // partials and bar unused: the batch has its own
+  int block0, nblocks;
+};
+struct MixedBatchEntry {
+  MixedSolve a;
+  int block0, nblocks;
+};
 void launch_scaling(const Geom& g, const CoefPtrs& o, cudaStream_t st);
 
 // One case of a batched Poisson solve and the contiguous range of blocks that serves it.
@@ -200,6 +210,13 @@ bool cheb_degree_supported(int k);
 template <class T>
 cudaError_t run_poisson_pcg(PoissonSolve<T> a, cudaStream_t st);
 int batch_blocks();
+// pcg_batch.cu: blocks of a batched launch, and the two batched solves (ctl.partials holds
+// 5 rows of blocks)
+int batch_scaled_blocks();
+cudaError_t run_scaled_batch(const ScaledBatchEntry* dev_cases, const int* dev_block_case, BatchControl ctl,
+                             int blocks, cudaStream_t st);
+cudaError_t run_mixed_batch(const MixedBatchEntry* dev_cases, const int* dev_block_case, BatchControl ctl,
+                            int blocks, cudaStream_t st);
 template <class T>
 cudaError_t run_poisson_batch(const PoissonSolve<T>* host_cases, int ncase, const BatchEntry<T>* dev_cases,
                               const int* dev_block_case, BatchControl ctl, int blocks, cudaStream_t st);
@@ -213,6 +230,9 @@ cudaStream_t case_stream(ccm_case c);
 size_t case_cells(ccm_case c);
 int case_nx(ccm_case c);
 void case_poisson_fp64(ccm_case c, PoissonSolve<double>* a);
+bool case_scaled_ok(ccm_case c);  // nonsingular: the scaled and mixed batched kernels apply
+void case_scaled_fp64(ccm_case c, ScaledSolve* a);
+void case_mixed_batch(ccm_case c, MixedSolve* a);
 void case_poisson_fp32(ccm_case c, PoissonSolve<float>* a);
 ccm_status case_mixed_residual(ccm_case c, double* host2);
 void case_mixed_correct(ccm_case c);

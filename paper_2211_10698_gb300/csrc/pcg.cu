@@ -371,32 +371,6 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_cg(PoissonSolve<
 // remaining barriers.  The loop ends when no block reports a running case (a grid-wide sum
 // read after a barrier, so every block takes the same decision).
 // ---------------------------------------------------------------------------------------
-template <int NV>
-__device__ __forceinline__ void range_sum(const double* partials, int stride, int base, int count, double (&out)[NV],
-                                          double* smem) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (w < NV) {
-    const double* src = partials + (size_t)w * stride + base;
-    double buf[kGridSumPerLane];
-#pragma unroll
-    for (int m = 0; m < kGridSumPerLane; ++m) {
-      const int b = lane + 32 * m;
-      buf[m] = b < count ? __ldcg(&src[b]) : 0.0;
-    }
-    double s = 0.0;
-#pragma unroll
-    for (int m = 0; m < kGridSumPerLane; ++m) s += buf[m];
-    for (int b = lane + 32 * kGridSumPerLane; b < count; b += 32) s += __ldcg(&src[b]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) smem[w] = s;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = smem[k];
-}
-
 template <class T>
 __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_cg_batch(const BatchEntry<T>* __restrict__ cases,
                                                                         const int* __restrict__ block_case,

@@ -166,4 +166,54 @@ __device__ __forceinline__ double recip_newton(double y) {
   return x * s;
 }
 
+// Sum of the partials of blocks base .. base+count-1 (one case of a batch), quantity w by
+// warp w, all of a lane's loads in flight; the result in every thread.
+template <int NV>
+__device__ __forceinline__ void range_sum(const double* partials, int stride, int base, int count, double (&out)[NV],
+                                          double* smem) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (w < NV) {
+    const double* src = partials + (size_t)w * stride + base;
+    double buf[kGridSumPerLane];
+#pragma unroll
+    for (int m = 0; m < kGridSumPerLane; ++m) {
+      const int b = lane + 32 * m;
+      buf[m] = b < count ? __ldcg(&src[b]) : 0.0;
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < kGridSumPerLane; ++m) s += buf[m];
+    for (int b = lane + 32 * kGridSumPerLane; b < count; b += 32) s += __ldcg(&src[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) smem[w] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = smem[k];
+}
+
+// FP32 block sum of NV values: shuffle tree per warp, then warps 0..NV-1 add the 16 warp
+// partials of one quantity each.  Sums land in out[0..NV-1] (shared).
+template <int NV>
+__device__ __forceinline__ void block_sum_f32(const float (&v)[NV], float (*wred)[kPcgThreads / 32], float* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    float s = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) wred[q][w] = s;
+  }
+  __syncthreads();
+  if (w < NV) {
+    float s = lane < kPcgThreads / 32 ? wred[w][lane] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[w] = s;
+  }
+  __syncthreads();
+}
+
 }  // namespace ccm

@@ -24,28 +24,6 @@ namespace {
 
 constexpr int kGroup = 3;
 
-// FP32 block sum of NV values: shuffle tree per warp, then warps 0..NV-1 add the 16 warp
-// partials of one quantity each.  Sums land in out[0..NV-1] (shared).
-template <int NV>
-__device__ __forceinline__ void block_sum_f32(const float (&v)[NV], float (*wred)[kPcgThreads / 32], float* out) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    float s = v[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) wred[q][w] = s;
-  }
-  __syncthreads();
-  if (w < NV) {
-    float s = lane < kPcgThreads / 32 ? wred[w][lane] : 0.0f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) out[w] = s;
-  }
-  __syncthreads();
-}
-
 // FP32 grid sum: warp q adds the nb block partials of quantity q (all loads in flight).
 template <int NV>
 __device__ __forceinline__ void grid_sum_f32(const float* partials, int nb, float (&out)[NV], float* smem) {
@@ -284,11 +262,13 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
         }
       }
     }
+    // row 2 of the FP32 partials: rows 0-1 (the sums of phase B) may still be read by other
+    // blocks, since no barrier separates that read from this write
     block_sum_f32<1>(v, wred, fsum);
-    if (threadIdx.x == 0) fpart[blockIdx.x] = fsum[0];
+    if (threadIdx.x == 0) fpart[2 * nb + blockIdx.x] = fsum[0];
     if (!grid_sync(d.bar, target)) return false;
     float t[1];
-    grid_sum_f32<1>(fpart, nb, t, fsum);
+    grid_sum_f32<1>(fpart + 2 * nb, nb, t, fsum);
     if (threadIdx.x == 0) {
       sc_alpha = sc_gfresh / t[0];
       sc_igamma = 1.0f / sc_gfresh;

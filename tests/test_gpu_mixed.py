@@ -46,10 +46,11 @@ def test_mixed_iterations_close_to_fp64(nx, ny):
     assert _rel(gmx.get_field(ccm.CCM_F_PHI), g64.get_field(ccm.CCM_F_PHI)) < 1e-5
 
 
-@pytest.mark.parametrize("scale", [1e-30, 1e30])
-def test_mixed_scale_of_rhs(scale):
-    """FP32 values are normalised at every replacement, so a right-hand side far outside
-    FP32's comfortable range converges the same way."""
+@pytest.mark.parametrize("scale", [2.0 ** -100, 2.0 ** 100])
+def test_mixed_scale_of_rhs_exact(scale):
+    """FP32 values are normalised at every replacement: scaling the right-hand side by a power
+    of two changes no FP32 value, so the iteration is the same and the solution scales
+    exactly, whatever the magnitude."""
     c = _case(128, 64)
     rhs = np.random.default_rng(4).standard_normal(c.shape)
     g1 = ccm.Case(c)
@@ -57,7 +58,22 @@ def test_mixed_scale_of_rhs(scale):
     g2 = ccm.Case(c)
     s2 = g2.solve_pressure(rhs * scale)
     assert s1["converged"] and s2["converged"]
-    assert abs(s1["iters"] - s2["iters"]) <= 3
+    assert s1["iters"] == s2["iters"] and s1["outer"] == s2["outer"]
+    assert np.array_equal(g2.get_field(ccm.CCM_F_PHI), g1.get_field(ccm.CCM_F_PHI) * scale)
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e30])
+def test_mixed_scale_of_rhs(scale):
+    """Far outside FP32's range the solve converges the same way; rounding of the scaled
+    values changes the FP32 trajectory, so the iteration count may differ a little."""
+    c = _case(128, 64)
+    rhs = np.random.default_rng(4).standard_normal(c.shape)
+    g1 = ccm.Case(c)
+    s1 = g1.solve_pressure(rhs)
+    g2 = ccm.Case(c)
+    s2 = g2.solve_pressure(rhs * scale)
+    assert s1["converged"] and s2["converged"] and s2["rel_res"] <= 1e-10
+    assert abs(s1["iters"] - s2["iters"]) <= 0.15 * s1["iters"]
     assert _rel(g2.get_field(ccm.CCM_F_PHI) / scale, g1.get_field(ccm.CCM_F_PHI)) < 1e-8
 
 
