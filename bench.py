@@ -55,7 +55,9 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the mixed-precision and batched measurements that follow the headline")
+                    help="skip the measurements that follow the headline")
+    ap.add_argument("--extras", default="mixed,configs,batched,serving",
+                    help="comma-separated subset of the measurements that follow the headline")
     return ap.parse_args()
 
 
@@ -293,6 +295,41 @@ def measure_mixed(torch, stream, flush, steps=6, warmup=2):
                 rel_l2_vs_fp64_path=err)
 
 
+def _measure_case(torch, stream, flush, case, steps, warmup, precision=None, precond=None):
+    from paper_2211_10698_gb300 import ccm
+
+    g = ccm.Case(case, precision=precision, precond=precond, stream=stream.cuda_stream,
+                 allocator=ccm.TorchAllocator())
+    g.step(warmup)
+    g.read_stats()
+    ms = _timed_steps(torch, stream, lambda: g.step_async(1), steps, flush)
+    st = g.read_stats(allow_not_converged=True)
+    g.close()
+    t = sum(ms)
+    return dict(value=case.cells * steps / (t * 1e-3), unit=UNIT, ms_per_step=t / steps, steps=steps,
+                poisson_iters_per_step=st["iters_p"] / steps, helmholtz_iters_per_step=st["iters_h"] / steps,
+                last_rel_res_p=st["last_res_p"], converged=bool(st["converged"]))
+
+
+def measure_configs(torch, stream, flush):
+    """The other single-case configurations: the 128x64 cylinder at Re 40 (FP64), and the
+    2048x1024 NACA0012 at Re 1000 in the mixed setting, with its configured Chebyshev
+    preconditioner (host-driven refinement) and with the one-launch Jacobi solve."""
+    from paper_2211_10698_gb300 import inputs
+
+    out = {}
+    c1 = inputs.cylinder_re40_128x64()
+    out["cylinder_re40_128x64"] = dict(precision="fp64", **_measure_case(torch, stream, flush, c1, 20, 3))
+    c3 = inputs.naca0012_re1000_2048x1024()
+    out["naca0012_re1000_2048x1024"] = dict(
+        precision="mixed", precond=f"chebyshev degree {c3.cheb_degree}",
+        **_measure_case(torch, stream, flush, c3, 2, 1))
+    out["naca0012_re1000_2048x1024_jacobi"] = dict(
+        precision="mixed", precond="jacobi (one launch, FP64 residual replacements)",
+        **_measure_case(torch, stream, flush, c3, 2, 1, precond="jacobi"))
+    return out
+
+
 def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=1):
     """The 64-case batch (cylinders and NACA00tt sections, 256..1024 cells wide, mixed
     precision): all cases advance together, one batched Poisson solve per step."""
@@ -454,15 +491,23 @@ def run_ours(args):
                     us_per_iteration=1e3 * avg_ms / max(iters_per_launch, 1), peak_kind=peak_kind)
 
     extras = {}
-    if rank == 0 and not args.no_extras:
+    want = set() if args.no_extras else set(args.extras.split(","))
+    if rank == 0 and "mixed" in want:
         try:
             extras["mixed_same_accuracy"] = measure_mixed(torch, stream, flush)
         except Exception as e:  # report, do not lose the headline line
             extras["mixed_same_accuracy"] = {"error": str(e)}
+    if rank == 0 and "configs" in want:
+        try:
+            extras["configs"] = measure_configs(torch, stream, flush)
+        except Exception as e:
+            extras["configs"] = {"error": str(e)}
+    if rank == 0 and "batched" in want:
         try:
             extras["batched"] = measure_batch(torch, stream, flush)
         except Exception as e:
             extras["batched"] = {"error": str(e)}
+    if rank == 0 and "serving" in want:
         try:
             torch.cuda.synchronize()
             sv = dict(workload=f"request stream window: first 16 requests at 20/s, steps/200, "
