@@ -76,8 +76,8 @@ def _peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-KERNEL = "k_pcg_poisson_sc"  # FP64 Poisson CG on the Jacobi-scaled system
-KERNEL_SOURCES = ("pcg_common.cuh", "pcg_scaled.cu")
+KERNEL = "k_pcg_poisson_f1"  # FP64 Poisson CG on the Jacobi-scaled system, one barrier per iteration
+KERNEL_SOURCES = ("pcg_common.cuh", "pcg_fused.cu")
 
 
 def kernel_source_hash():

@@ -125,7 +125,7 @@ void carve(ccm_case c, Carver& cv) {
   c->mixed_sums = cv.take<double>(4);
   c->partials = cv.take<double>((size_t)pcg_partials_needed());
   c->dpart = cv.take<double>((size_t)3 * diagnostics_partials(c->g) + 8);
-  c->bar_count = cv.take<unsigned int>(4);
+  c->bar_count = cv.take<unsigned int>(kBarWords);
   c->bar_err = cv.take<int>(4);
   c->ds = cv.take<DevStats>(1);
 }
@@ -235,13 +235,18 @@ void set_uniform_coefficients(ccm_case c, PoissonSolve<T>& a) {
 ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
   if (!c->zero_mean && c->cfg.precond == CCM_JACOBI) {
     // Jacobi-PCG as CG on the symmetrically scaled system (nonsingular systems)
+    // with one grid barrier per iteration (tiles that recompute their ring)
     CaseSolveView v;
     case_solve_view(c, &v);
-    ScaledSolve a = scaled_solve_of(v, x, b, c->pz, c->pr, c->pq, c->pp0, c->pp1);
-    a.partials = c->partials;
-    a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
-    a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
-    CUDA_TRY(run_poisson_scaled(a, c->st));
+    FusedSolve f{};
+    f.a = scaled_solve_of(v, x, b, c->pz, nullptr, nullptr, c->pp0, nullptr);
+    f.a.partials = c->partials;
+    f.a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+    f.a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
+    f.R[0] = c->pr; f.R[1] = c->pz2;
+    f.W[0] = c->pq; f.W[1] = c->pw1;
+    f.S[0] = c->pp1; f.S[1] = c->t5;
+    CUDA_TRY(run_poisson_fused(f, c->st));
     return CCM_OK;
   }
   PoissonSolve<double> a{};

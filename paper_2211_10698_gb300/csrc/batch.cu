@@ -240,7 +240,7 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
   const size_t pieces[9] = {sizeof(BatchEntry<double>) * max_cases, sizeof(BatchEntry<float>) * max_cases,
                             sizeof(ScaledBatchEntry) * max_cases, sizeof(MixedBatchEntry) * max_cases,
                             sizeof(int) * b->blocks, sizeof(double) * 6 * b->blocks, sizeof(int) * b->blocks,
-                            sizeof(unsigned int) * 4, sizeof(int) * 4};
+                            sizeof(unsigned int) * kBarWords, sizeof(int) * 4};
   size_t bytes = 0;
   for (size_t n : pieces) bytes += (n + 255) & ~(size_t)255;
   cudaError_t e = cudaMalloc(&b->dev, bytes);
@@ -258,7 +258,7 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
   b->block_case = (int*)take(sizeof(int) * b->blocks);
   b->partials = (double*)take(sizeof(double) * 6 * b->blocks);
   b->running = (int*)take(sizeof(int) * b->blocks);
-  b->bar_count = (unsigned int*)take(sizeof(unsigned int) * 4);
+  b->bar_count = (unsigned int*)take(sizeof(unsigned int) * kBarWords);
   b->bar_err = (int*)take(sizeof(int) * 4);
   (void)take;
   if ((e = cudaMallocHost(&b->host_sums, sizeof(double) * 2 * max_cases)) != cudaSuccess ||

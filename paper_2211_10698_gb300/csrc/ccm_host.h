@@ -91,6 +91,20 @@ struct ScaledSolve {
 };
 cudaError_t run_poisson_scaled(const ScaledSolve& a, cudaStream_t st);
 
+// The same solve with one grid barrier per iteration (pcg_fused.cu): 2-D tiles, the ring of
+// each tile recomputed by its block, r, w, s double-buffered.  a.xs and a.p are used, a.r,
+// a.w, a.s are not.
+struct FusedSolve {
+  ScaledSolve a;
+  double* R[2];
+  double* W[2];
+  double* S[2];
+  int TX, TY, nbx, ntiles;  // tile plan; TX = 0 lets the launcher choose
+  int list_cap;             // set by the launcher: entries of the per-tile list of non-uniform cells
+};
+cudaError_t run_poisson_fused(FusedSolve f, cudaStream_t st);
+void fused_tiles(int nx, int ny, int blocks, int* TX, int* TY, int* nbx, int* ntiles);
+
 // Mixed-precision solve of the same system: FP32 CG on K~ with FP64 residual replacements.
 // d.r serves as the FP64 residual; d.xs, d.w, d.p, d.s are unused.
 struct MixedSolve {

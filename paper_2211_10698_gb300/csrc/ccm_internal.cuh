@@ -75,6 +75,8 @@ struct Phys {
 // round have arrived, giving up after `budget` clock cycles; on give-up it raises *err and
 // the caller leaves the kernel.
 // ---------------------------------------------------------------------------------------
+// Device-wide barrier of a cooperative launch: one arrival counter.
+constexpr int kBarWords = 1;  // unsigned ints behind Barrier::count
 struct Barrier {
   unsigned int* count;  // zeroed before the launch
   int* err;

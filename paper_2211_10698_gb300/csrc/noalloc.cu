@@ -4,7 +4,8 @@
 // through its own pool and forbids other allocations, a process running under a hard
 // device-memory cap, or latency-sensitive code that must not trigger the device-wide
 // synchronisation that cudaMalloc and cudaFree imply.  ccm_solve_pressure_noalloc serves
-// them: it runs the same FP64 Jacobi-PCG kernels as ccm_solve_pressure, but its scratch
+// them: it runs the same FP64 method as ccm_solve_pressure (CG on the Jacobi-scaled system, in
+// the two-barrier layout, which needs fewer work vectors than the tiled one), but its scratch
 // vectors live in one file-scope __device__ array of fixed size instead of memory the
 // library allocates.  The caller passes the right-hand side and the solution in device
 // memory of its own.
@@ -41,8 +42,8 @@ struct Scratch {
   double partials[kMaxPartials];
   double rr, bb;
   int iters, converged;
-  unsigned int bar_count;
-  int bar_err;
+  int bar_err, pad;
+  unsigned int bar_count[kBarWords];
 };
 
 static __device__ __align__(256) Scratch g_scratch;
@@ -109,7 +110,7 @@ extern "C" ccm_status ccm_solve_pressure_noalloc(ccm_case c, const double* rhs_d
   // cleared, since the stencils read them on the ghost ring, and so are the barrier counter
   // and its error flag
   if ((e = cudaMemsetAsync(S->r, 0, 5 * kMaxElems * sizeof(double), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(&S->bar_count, 0, sizeof(unsigned int) + sizeof(int), st)) != cudaSuccess)
+      (e = cudaMemsetAsync(&S->bar_err, 0, 2 * sizeof(int) + sizeof(unsigned int) * kBarWords, st)) != cudaSuccess)
     return fail(CCM_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   const dim3 blk(64, 4), grd((v.g.nx + 3 + 63) / 64, (v.g.ny + 3 + 3) / 4);
   k_masked_copy<<<grd, blk, 0, st>>>(v.g, v.act, rhs_dev, S->b);
@@ -117,7 +118,7 @@ extern "C" ccm_status ccm_solve_pressure_noalloc(ccm_case c, const double* rhs_d
   if (!v.zero_mean && v.precond == CCM_JACOBI) {
     ScaledSolve q = scaled_solve_of(v, phi_dev, S->b, S->u, S->r, S->w, S->p, S->s);
     q.partials = S->partials;
-    q.bar = Barrier{&S->bar_count, &S->bar_err, 2000000000LL};
+    q.bar = Barrier{S->bar_count, &S->bar_err, 2000000000LL};
     q.out = PcgOut{&S->iters, &S->rr, &S->bb, &S->converged, nullptr, nullptr};
     e = run_poisson_scaled(q, st);
   } else {
@@ -134,14 +135,14 @@ extern "C" ccm_status ccm_solve_pressure_noalloc(ccm_case c, const double* rhs_d
     a.tol = v.tol; a.max_iter = v.max_iter;
     a.zero_mean = v.zero_mean; a.n_act = v.n_act;
     a.partials = S->partials;
-    a.bar = Barrier{&S->bar_count, &S->bar_err, 2000000000LL};
+    a.bar = Barrier{S->bar_count, &S->bar_err, 2000000000LL};
     a.out = PcgOut{&S->iters, &S->rr, &S->bb, &S->converged, nullptr, nullptr};
     e = run_poisson_pcg<double>(a, st);
   }
   if (e != cudaSuccess)
     return fail(CCM_E_CUDA, std::string("Poisson PCG launch: ") + cudaGetErrorString(e));
-  struct { double rr, bb; int iters, converged; unsigned int count; int err; } h{};
-  static_assert(sizeof(h) == offsetof(Scratch, bar_err) + sizeof(int) - offsetof(Scratch, rr), "layout");
+  struct { double rr, bb; int iters, converged; int err, pad; } h{};
+  static_assert(sizeof(h) == offsetof(Scratch, bar_count) - offsetof(Scratch, rr), "layout");
   if ((e = cudaMemcpyAsync(&h, &S->rr, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return fail(CCM_E_CUDA, std::string("reading the solve statistics: ") + cudaGetErrorString(e));

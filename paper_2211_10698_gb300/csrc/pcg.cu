@@ -718,7 +718,7 @@ cudaError_t run_poisson_pcg(PoissonSolve<T> a, cudaStream_t st) {
     k_zero_mean_partials<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.b, a.partials);
     k_zero_mean_apply<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.b, a.partials, blocks, a.n_act);
   }
-  cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
   void* params[] = {&a};
   return cudaLaunchCooperativeKernel(fn, blocks, kPcgThreads, params, 0, st);
 }
@@ -739,7 +739,7 @@ cudaError_t run_poisson_batch(const PoissonSolve<T>* host_cases, int ncase, cons
     k_zero_mean_partials<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.b, ctl.partials);
     k_zero_mean_apply<T><<<blocks, kPcgThreads, 0, st>>>(a.g, a.kind, a.b, ctl.partials, blocks, a.n_act);
   }
-  cudaMemsetAsync(ctl.bar.count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(ctl.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
   const void* fn = (const void*)k_pcg_poisson_cg_batch<T>;
   void* params[] = {(void*)&dev_cases, (void*)&dev_block_case, &ctl};
   return cudaLaunchCooperativeKernel(fn, blocks, kPcgThreads, params, 0, st);
@@ -753,7 +753,7 @@ template cudaError_t run_poisson_pcg<float>(PoissonSolve<float>, cudaStream_t);
 cudaError_t run_helmholtz_pcg(HelmholtzSolve a, cudaStream_t st) {
   const void* fn = (const void*)k_pcg_helmholtz;
   const int blocks = coop_blocks(fn, kPcgThreads, 2);
-  cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
   void* params[] = {&a};
   return cudaLaunchCooperativeKernel(fn, blocks, kPcgThreads, params, 0, st);
 }

@@ -574,14 +574,14 @@ int batch_scaled_blocks() {
 
 cudaError_t run_scaled_batch(const ScaledBatchEntry* dev_cases, const int* dev_block_case, BatchControl ctl,
                              int blocks, cudaStream_t st) {
-  cudaMemsetAsync(ctl.bar.count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(ctl.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
   void* params[] = {(void*)&dev_cases, (void*)&dev_block_case, &ctl};
   return cudaLaunchCooperativeKernel((const void*)k_sc_batch, blocks, kPcgThreads, params, 0, st);
 }
 
 cudaError_t run_mixed_batch(const MixedBatchEntry* dev_cases, const int* dev_block_case, BatchControl ctl,
                             int blocks, cudaStream_t st) {
-  cudaMemsetAsync(ctl.bar.count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(ctl.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
   void* params[] = {(void*)&dev_cases, (void*)&dev_block_case, &ctl};
   return cudaLaunchCooperativeKernel((const void*)k_mixed_batch, blocks, kPcgThreads, params, 0, st);
 }

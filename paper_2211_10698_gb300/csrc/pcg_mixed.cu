@@ -390,7 +390,7 @@ cudaError_t run_poisson_mixed(const MixedSolve& a, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_poisson_mixed, kPcgThreads, 0);
   per = per > 2 ? 2 : (per < 1 ? 1 : per);
-  cudaMemsetAsync(a.d.bar.count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(a.d.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
   MixedSolve arg = a;
   void* params[] = {&arg};
   return cudaLaunchCooperativeKernel((const void*)k_pcg_poisson_mixed, sms * per, kPcgThreads, params, 0, st);

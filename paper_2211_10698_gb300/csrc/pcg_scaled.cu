@@ -281,7 +281,7 @@ void launch_scaling(const Geom& g, const CoefPtrs& o, cudaStream_t st) {
 
 cudaError_t run_poisson_scaled(const ScaledSolve& a, cudaStream_t st) {
   const int blocks = sc_blocks();
-  cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
   ScaledSolve arg = a;
   void* params[] = {&arg};
   return cudaLaunchCooperativeKernel(kScKernel, blocks, kScThreads, params, 0, st);

@@ -65,7 +65,8 @@ def test_noalloc_matches_allocating_solve(which):
         assert status == ccm.CCM_OK, ccm.lib().ccm_last_error()
         got = phi_d[:, :cols].cpu().numpy()
         assert _rel(got, phi_ref) < TOL, (call, _rel(got, phi_ref))
-        assert st.converged and st.iters == ref_stats["iters"]
+        # same method; the sums run over another block layout, so the count may differ by rounding
+        assert st.converged and abs(st.iters - ref_stats["iters"]) <= 2
     g.close()
 
 
