@@ -77,7 +77,7 @@ def _peaks():
 
 
 KERNEL = "k_pcg_poisson_f1"  # FP64 Poisson CG on the Jacobi-scaled system, one barrier per iteration
-KERNEL_SOURCES = ("pcg_common.cuh", "pcg_fused.cu")
+KERNEL_SOURCES = ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fused.cu")
 
 
 def kernel_source_hash():
