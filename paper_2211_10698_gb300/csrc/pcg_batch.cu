@@ -25,7 +25,7 @@ namespace ccm {
 
 namespace {
 
-constexpr int kGroup = 2;
+constexpr int kGroup = 1;  // cells per thread whose loads k_sc_batch issues together (two would spill)
 
 // Cell range of this block within its case.
 struct CaseRange {
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
   const double* __restrict__ cus = a.cus;
   const double* __restrict__ cvs = a.cvs;
   const double* __restrict__ sd = a.sd;
-  const double ax = a.ax, ay = a.ay, dreg = a.dreg;
+  const double dreg = a.dreg;
   double* __restrict__ xs = a.xs;
   double* __restrict__ r = a.r;
   double* __restrict__ w = a.w;
@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
     while (next_group(cw, g, kdummy, gr)) {
       int8_t km[kGroup];
       double rc[kGroup], rw[kGroup], re[kGroup], rs[kGroup], rn[kGroup];
+      double cw[kGroup], ce[kGroup], cs[kGroup], cn[kGroup];
 #pragma unroll
       for (int m = 0; m < kGroup; ++m) {
         const int k = gr.k[m];
@@ -106,18 +107,21 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
         re[m] = r[k + 1];
         rs[m] = r[k - P];
         rn[m] = r[k + P];
+        cw[m] = cus[k];
+        ce[m] = cus[k + 1];
+        cs[m] = cvs[k];
+        cn[m] = cvs[k + P];
       }
 #pragma unroll
       for (int m = 0; m < kGroup; ++m) {
         if (!gr.v[m]) continue;
         const int k = gr.k[m];
-        double wk;
-        if (km[m] == 1) {
-          wk = rc[m] - ax * (rw[m] + re[m]) - ay * (rs[m] + rn[m]);
-        } else {
+        // the scaled coefficient arrays hold the constant stencil on uniform rows and zeros on
+        // inactive ones, so one branch-free row serves every cell: a warp never runs two FP64
+        // paths (an FP64 warp instruction costs the same however few lanes are active)
+        const double wk = rc[m] - cw[m] * rw[m] - ce[m] * re[m] - cs[m] * rs[m] - cn[m] * rn[m];
+        if (km[m] != 1) {
           const double dk = km[m] == 2 ? sd[k] * sd[k] : 1.0;
-          wk = km[m] == 2 ? rc[m] - cus[k] * rw[m] - cus[k + 1] * re[m] - cvs[k] * rs[m] - cvs[k + P] * rn[m]
-                          : rc[m];
           v[1] += (dk - dreg) * (rc[m] * rc[m]);
         }
         w[k] = wk;
@@ -264,12 +268,11 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
   const int lb = blockIdx.x - E.block0, nbc = E.nblocks;
   const CaseRange ch(g.nx * g.ny, lb, nbc);
   const int first = ch.t0 + threadIdx.x, stride = blockDim.x;
-  const int kdummy = (int)g.idx(0, 0);
+  // the FP32 phases work on aligned quads of the case's arrays (see QuadOpsF32)
+  const Quads Q(g);
+  const int u0 = (int)((long long)Q.nquad * lb / nbc), u1 = (int)((long long)Q.nquad * (lb + 1) / nbc);
+  const QuadOpsF32 ops{d.kinds, A.cus32, A.cvs32, (float)d.ax, (float)d.ay, P};
   const KRow<double> K{d.cu, d.cv, d.dk, d.kind, d.creg_x, d.creg_y, d.dreg, (size_t)P};
-  const int8_t* __restrict__ kinds = d.kinds;
-  const float* __restrict__ cus = A.cus32;
-  const float* __restrict__ cvs = A.cvs32;
-  const float ax = (float)d.ax, ay = (float)d.ay;
   const double* __restrict__ isd = d.isd;
   double* __restrict__ x = d.x;
   double* __restrict__ r64 = d.r;
@@ -298,82 +301,25 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
     if (st == ST_ITERATE) {
       const float al = sc_alpha, be = sc_beta;
       const bool keep = sc_keep != 0;
-      CellWalk cw(first, stride, ch.t1, nx);
-      Group<kGroup> gr;
-      while (next_group(cw, g, kdummy, gr)) {
-        float pm[kGroup], rm[kGroup], wm[kGroup], sm[kGroup], em[kGroup];
-#pragma unroll
-        for (int m = 0; m < kGroup; ++m) {
-          const int k = gr.k[m];
-          pm[m] = p[k];
-          rm[m] = r[k];
-          wm[m] = w[k];
-          sm[m] = s[k];
-          em[m] = e[k];
-        }
-#pragma unroll
-        for (int m = 0; m < kGroup; ++m) {
-          if (!gr.v[m]) continue;
-          const int k = gr.k[m];
-          const float pk = keep ? pm[m] : rm[m] + be * pm[m];
-          const float sk = keep ? sm[m] : wm[m] + be * sm[m];
-          if (!keep) {
-            p[k] = pk;
-            s[k] = sk;
-          }
-          e[k] = em[m] + al * pk;
-          r[k] = rm[m] - al * sk;
-        }
-      }
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.update(p, r, w, s, e, Q.k(u), al, be, keep);
     } else if (st == ST_REPLACE) {
       if (sc_init) {
-        for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
-          const size_t k = g.idx(cw.i, cw.j);
-          p[k] = 0.0f;
-          s[k] = 0.0f;
-          e[k] = 0.0f;
+        const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+          const int k0 = Q.k(u);
+          st4(p, k0, z);
+          st4(s, k0, z);
+          st4(e, k0, z);
         }
       } else {
         const double isig = 1.0 / sc_sigma;
-        for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
-          const size_t k = g.idx(cw.i, cw.j);
-          x[k] += isd[k] * (double)e[k] * isig;
-          e[k] = 0.0f;
-        }
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) quad_fold(x, isd, e, Q.k(u), isig, true);
       }
     } else if (st == ST_FRESH) {
       // r = sigma r64 (FP32), w = K~ r, sums (r, r), (w, r)
       float v[2] = {0.0f, 0.0f};
       const double sig = sc_sigma;
-      CellWalk cw(first, stride, ch.t1, nx);
-      Group<kGroup> gr;
-      while (next_group(cw, g, kdummy, gr)) {
-        int8_t km[kGroup];
-        float rc[kGroup], rw[kGroup], re[kGroup], rs[kGroup], rn[kGroup];
-#pragma unroll
-        for (int m = 0; m < kGroup; ++m) {
-          const int k = gr.k[m];
-          km[m] = kinds[k];
-          rc[m] = (float)(sig * r64[k]);
-          rw[m] = (float)(sig * r64[k - 1]);
-          re[m] = (float)(sig * r64[k + 1]);
-          rs[m] = (float)(sig * r64[k - P]);
-          rn[m] = (float)(sig * r64[k + P]);
-        }
-#pragma unroll
-        for (int m = 0; m < kGroup; ++m) {
-          if (!gr.v[m]) continue;
-          const int k = gr.k[m];
-          float wk;
-          if (km[m] == 1) wk = rc[m] - ax * (rw[m] + re[m]) - ay * (rs[m] + rn[m]);
-          else if (km[m] == 2) wk = rc[m] - cus[k] * rw[m] - cus[k + 1] * re[m] - cvs[k] * rs[m] - cvs[k + P] * rn[m];
-          else wk = rc[m];
-          r[k] = rc[m];
-          w[k] = wk;
-          v[0] += rc[m] * rc[m];
-          v[1] += wk * rc[m];
-        }
-      }
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.stencil(r, w, r64, sig, Q.k(u), v);
       block_sum_f32<2>(v, wred, fsum);
       const double dv[2] = {(double)fsum[0], (double)fsum[1]};
       publish(ctl.partials + kRow1 * NB, NB, dv, 2);
@@ -400,34 +346,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
     // ---- slot 2
     if (st == ST_ITERATE) {
       float v[2] = {0.0f, 0.0f};
-      CellWalk cw(first, stride, ch.t1, nx);
-      Group<kGroup> gr;
-      while (next_group(cw, g, kdummy, gr)) {
-        int8_t km[kGroup];
-        float rc[kGroup], rw[kGroup], re[kGroup], rs[kGroup], rn[kGroup];
-#pragma unroll
-        for (int m = 0; m < kGroup; ++m) {
-          const int k = gr.k[m];
-          km[m] = kinds[k];
-          rc[m] = r[k];
-          rw[m] = r[k - 1];
-          re[m] = r[k + 1];
-          rs[m] = r[k - P];
-          rn[m] = r[k + P];
-        }
-#pragma unroll
-        for (int m = 0; m < kGroup; ++m) {
-          if (!gr.v[m]) continue;
-          const int k = gr.k[m];
-          float wk;
-          if (km[m] == 1) wk = rc[m] - ax * (rw[m] + re[m]) - ay * (rs[m] + rn[m]);
-          else if (km[m] == 2) wk = rc[m] - cus[k] * rw[m] - cus[k + 1] * re[m] - cvs[k] * rs[m] - cvs[k + P] * rn[m];
-          else wk = rc[m];
-          w[k] = wk;
-          v[0] += rc[m] * rc[m];
-          v[1] += wk * rc[m];
-        }
-      }
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.stencil(r, w, nullptr, 0.0, Q.k(u), v);
       block_sum_f32<2>(v, wred, fsum);
       const double dv[2] = {(double)fsum[0], (double)fsum[1]};
       publish(ctl.partials + kRow2 * NB, NB, dv, 2);
@@ -449,29 +368,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
       // p = r + beta' p, s = w + beta' s with beta' = beta sigma_new / sigma_old, and (p, s)
       const float be = sc_beta * sc_pscale;
       float v[1] = {0.0f};
-      CellWalk cw(first, stride, ch.t1, nx);
-      Group<kGroup> gr;
-      while (next_group(cw, g, kdummy, gr)) {
-        float pm[kGroup], rm[kGroup], wm[kGroup], sm[kGroup];
-#pragma unroll
-        for (int m = 0; m < kGroup; ++m) {
-          const int k = gr.k[m];
-          pm[m] = p[k];
-          rm[m] = r[k];
-          wm[m] = w[k];
-          sm[m] = s[k];
-        }
-#pragma unroll
-        for (int m = 0; m < kGroup; ++m) {
-          if (!gr.v[m]) continue;
-          const int k = gr.k[m];
-          const float pk = rm[m] + be * pm[m];
-          const float sk = wm[m] + be * sm[m];
-          p[k] = pk;
-          s[k] = sk;
-          v[0] += pk * sk;
-        }
-      }
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) v[0] += ops.form(p, r, w, s, Q.k(u), be);
       block_sum_f32<1>(v, wred, fsum);
       const double dv[1] = {(double)fsum[0]};
       publish(ctl.partials + kRow2 * NB, NB, dv, 1);

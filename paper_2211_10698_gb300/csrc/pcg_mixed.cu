@@ -30,19 +30,6 @@ namespace ccm {
 
 namespace {
 
-__device__ __forceinline__ float4 ld4(const float* a, int k) { return *reinterpret_cast<const float4*>(a + k); }
-__device__ __forceinline__ void st4(float* a, int k, float4 v) { *reinterpret_cast<float4*>(a + k) = v; }
-// (float) (sig * a[k .. k+3]) for an FP64 array (k even: two 16-byte loads)
-__device__ __forceinline__ float4 ld4_scaled(const double* a, int k, double sig) {
-  const double2 lo = *reinterpret_cast<const double2*>(a + k);
-  const double2 hi = *reinterpret_cast<const double2*>(a + k + 2);
-  return make_float4((float)(sig * lo.x), (float)(sig * lo.y), (float)(sig * hi.x), (float)(sig * hi.y));
-}
-__device__ __forceinline__ float at(const float4& v, int m) { return m == 0 ? v.x : m == 1 ? v.y : m == 2 ? v.z : v.w; }
-__device__ __forceinline__ void put(float4& v, int m, float x) {
-  if (m == 0) v.x = x; else if (m == 1) v.y = x; else if (m == 2) v.z = x; else v.w = x;
-}
-
 // FP32 grid sum: warp q adds the nb block partials of quantity q (all loads in flight).
 template <int NV>
 __device__ __forceinline__ void grid_sum_f32(const float* partials, int nb, float (&out)[NV], float* smem) {
@@ -86,21 +73,12 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
   const Geom g = d.g;
   const int nx = g.nx, P = g.pitch;
   const Chunk ch(g.nx * g.ny);
-  // quads: nq per row (row j starts at padded index (j+1) P, the ghost slot of i = -1)
-  const int nq = nx / 4 + 1;
-  const int nquad = g.ny * nq;
-  const int u0 = (int)((long long)nquad * blockIdx.x / gridDim.x);
-  const int u1 = (int)((long long)nquad * (blockIdx.x + 1) / gridDim.x);
-  auto quad_k = [&](int u) -> int {
-    const int j = u / nq;
-    return (j + 1) * P + 4 * (u - j * nq);
-  };
+  const Quads Q(g);
+  const int u0 = (int)((long long)Q.nquad * blockIdx.x / gridDim.x);
+  const int u1 = (int)((long long)Q.nquad * (blockIdx.x + 1) / gridDim.x);
+  const QuadOpsF32 ops{d.kinds, a.cus32, a.cvs32, (float)d.ax, (float)d.ay, P};
   const int first = ch.t0 + threadIdx.x, stride = blockDim.x;
   const KRow<double> K{d.cu, d.cv, d.dk, d.kind, d.creg_x, d.creg_y, d.dreg, (size_t)P};
-  const int8_t* __restrict__ kinds = d.kinds;
-  const float* __restrict__ cus = a.cus32;
-  const float* __restrict__ cvs = a.cvs32;
-  const float ax = (float)d.ax, ay = (float)d.ay;
   const double* __restrict__ isd = d.isd;
   double* __restrict__ x = d.x;
   double* __restrict__ r64 = d.r;  // scaled FP64 residual D^-1/2 (b - K x) at a replacement
@@ -155,47 +133,8 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
   auto phase_b = [&](bool fresh) -> bool {
     float v[2] = {0.0f, 0.0f};
     const double sig = sc_sigma;
-    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-      const int k0 = quad_k(u);
-      // all loads of the quad first: kinds, r at the quad and its four neighbour quads/cells,
-      // and the scaled coefficients (used only by cut rows)
-      const char4 km = *reinterpret_cast<const char4*>(kinds + k0);
-      float4 rc, rs, rq;
-      float rw, re;
-      if (fresh) {
-        rc = ld4_scaled(r64, k0, sig);
-        rs = ld4_scaled(r64, k0 - P, sig);
-        rq = ld4_scaled(r64, k0 + P, sig);
-        rw = (float)(sig * r64[k0 - 1]);
-        re = (float)(sig * r64[k0 + 4]);
-      } else {
-        rc = ld4(r, k0);
-        rs = ld4(r, k0 - P);
-        rq = ld4(r, k0 + P);
-        rw = r[k0 - 1];
-        re = r[k0 + 4];
-      }
-      const float4 cw = ld4(cus, k0), cs = ld4(cvs, k0), cn = ld4(cvs, k0 + P);
-      const float ce4 = cus[k0 + 4];
-      float4 wq;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int8_t kk = m == 0 ? km.x : m == 1 ? km.y : m == 2 ? km.z : km.w;
-        const float c = at(rc, m);
-        const float l = m == 0 ? rw : at(rc, m - 1);
-        const float rr = m == 3 ? re : at(rc, m + 1);
-        const float sv = at(rs, m), nv = at(rq, m);
-        const float ce = m == 3 ? ce4 : at(cw, m + 1);
-        const float wu = c - ax * (l + rr) - ay * (sv + nv);
-        const float wg = c - at(cw, m) * l - ce * rr - at(cs, m) * sv - at(cn, m) * nv;
-        const float wk = kk == 1 ? wu : (kk == 2 ? wg : c);
-        put(wq, m, wk);
-        v[0] += c * c;
-        v[1] += wk * c;
-      }
-      if (fresh) st4(r, k0, rc);
-      st4(w, k0, wq);
-    }
+    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x)
+      ops.stencil(r, w, fresh ? r64 : nullptr, sig, Q.k(u), v);
     block_sum_f32<2>(v, wred, fsum);
     if (threadIdx.x == 0) {
       fpart[blockIdx.x] = fsum[0];
@@ -263,15 +202,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
   auto phase_p = [&]() -> bool {
     const float be = sc_beta * sc_pscale;
     float v[1] = {0.0f};
-    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-      const int k0 = quad_k(u);
-      const float4 pm = ld4(p, k0), rm = ld4(r, k0), wm = ld4(w, k0), sm = ld4(s, k0);
-      const float4 pk = make_float4(rm.x + be * pm.x, rm.y + be * pm.y, rm.z + be * pm.z, rm.w + be * pm.w);
-      const float4 sk = make_float4(wm.x + be * sm.x, wm.y + be * sm.y, wm.z + be * sm.z, wm.w + be * sm.w);
-      st4(p, k0, pk);
-      st4(s, k0, sk);
-      v[0] += pk.x * sk.x + pk.y * sk.y + pk.z * sk.z + pk.w * sk.w;
-    }
+    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) v[0] += ops.form(p, r, w, s, Q.k(u), be);
     // row 2 of the FP32 partials: rows 0-1 (the sums of phase B) may still be read by other
     // blocks, since no barrier separates that read from this write
     block_sum_f32<1>(v, wred, fsum);
@@ -288,18 +219,9 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
     return true;
   };
 
-  // R1 on this block's quads: x += D^-1/2 e / sigma (1/sqrt(d) is 0 on ghost and padding
-  // slots, so x changes on interior cells only), e = 0 when asked
+  // R1 on this block's quads
   auto fold = [&](double isig, bool clear) {
-    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-      const int k0 = quad_k(u);
-      const float4 em = ld4(e, k0);
-      x[k0] += isd[k0] * (double)em.x * isig;
-      x[k0 + 1] += isd[k0 + 1] * (double)em.y * isig;
-      x[k0 + 2] += isd[k0 + 2] * (double)em.z * isig;
-      x[k0 + 3] += isd[k0 + 3] * (double)em.w * isig;
-      if (clear) st4(e, k0, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
-    }
+    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) quad_fold(x, isd, e, Q.k(u), isig, clear);
   };
 
   if (threadIdx.x == 0) {
@@ -315,7 +237,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
     sc_bb = 0.0;
   }
   for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-    const int k0 = quad_k(u);
+    const int k0 = Q.k(u);
     const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     st4(p, k0, z);
     st4(s, k0, z);
@@ -335,19 +257,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
     {
       const float al = sc_alpha, be = sc_keep ? 0.0f : sc_beta * sc_pscale;
       const bool keep = sc_keep != 0;
-      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-        const int k0 = quad_k(u);
-        const float4 pm = ld4(p, k0), rm = ld4(r, k0), wm = ld4(w, k0), sm = ld4(s, k0), em = ld4(e, k0);
-        float4 pk = pm, sk = sm;
-        if (!keep) {
-          pk = make_float4(rm.x + be * pm.x, rm.y + be * pm.y, rm.z + be * pm.z, rm.w + be * pm.w);
-          sk = make_float4(wm.x + be * sm.x, wm.y + be * sm.y, wm.z + be * sm.z, wm.w + be * sm.w);
-          st4(p, k0, pk);
-          st4(s, k0, sk);
-        }
-        st4(e, k0, make_float4(em.x + al * pk.x, em.y + al * pk.y, em.z + al * pk.z, em.w + al * pk.w));
-        st4(r, k0, make_float4(rm.x - al * sk.x, rm.y - al * sk.y, rm.z - al * sk.z, rm.w - al * sk.w));
-      }
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.update(p, r, w, s, e, Q.k(u), al, be, keep);
     }
     if (!grid_sync(d.bar, target)) { ok = false; break; }
     if (!phase_b(false)) { ok = false; break; }
