@@ -56,6 +56,9 @@ struct ccm_case_s {
   double *ustar, *vstar, *div, *rhs_u, *rhs_v, *rhs_p;
   double *pr, *pz, *pp0, *pp1, *pq, *pz2, *pw1;
   double *hr_u, *hr_v, *hz_u, *hz_v, *hp_u, *hp_v, *hq_u, *hq_v;
+  double *hs_u, *hs_v;     // K p of the Helmholtz CG
+  HelmCoefPtrs hc;         // the Helmholtz operator, nine coefficients per unknown face
+  int* hc_bad;             // set when probing finds a coupling outside that pattern
   float *fx, *fb, *fr, *fz, *fp0, *fp1, *fq, *fz2, *fw1;
   double* mixed_sums;
   double *t0, *t1, *t2, *t3, *t4, *t5;
@@ -128,6 +131,10 @@ void carve(ccm_case c, Carver& cv) {
   c->bar_count = cv.take<unsigned int>(kBarWords);
   c->bar_err = cv.take<int>(4);
   c->ds = cv.take<DevStats>(1);
+  c->hs_u = cv.take<double>(N);
+  c->hs_v = cv.take<double>(N);
+  for (int q = 0; q < 18; ++q) c->hc.a[q] = cv.take<double>(N);
+  c->hc_bad = cv.take<int>(4);
 }
 
 void make_view(ccm_case c) {
@@ -266,16 +273,19 @@ ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
 }
 
 ccm_status solve_helmholtz(ccm_case c) {
-  HelmholtzSolve a{};
-  a.c = c->cv; a.g = c->g; a.bc = c->bc; a.ph = c->ph;
+  HelmCSolve a{};
+  a.g = c->g;
+  a.ru = c->co.role_u; a.rv = c->co.role_v;
+  a.h = c->hc;
+  a.invu = c->co.invdhu; a.invv = c->co.invdhv;
   a.xu = c->u; a.xv = c->v; a.bu = c->rhs_u; a.bv = c->rhs_v;
-  a.ru = c->hr_u; a.rv = c->hr_v; a.zu = c->hz_u; a.zv = c->hz_v;
-  a.pu = c->hp_u; a.pv = c->hp_v; a.qu = c->hq_u; a.qv = c->hq_v;
+  a.rU = c->hr_u; a.rV = c->hr_v; a.zU = c->hz_u; a.zV = c->hz_v; a.wU = c->hq_u; a.wV = c->hq_v;
+  a.pU = c->hp_u; a.pV = c->hp_v; a.sU = c->hs_u; a.sV = c->hs_v;
   a.tol = c->cfg.tol_h; a.max_iter = c->cfg.max_iter_h;
   a.partials = c->partials;
   a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
   a.out = PcgOut{&c->ds->iters_h, &c->ds->rr_h, &c->ds->bb_h, &c->ds->conv_h, &c->ds->total_h, &c->ds->nconv};
-  CUDA_TRY(run_helmholtz_pcg(a, c->st));
+  CUDA_TRY(run_helmholtz_coef(a, c->st));
   return CCM_OK;
 }
 
@@ -638,6 +648,8 @@ ccm_status ccm_set_geometry(ccm_case c, const ccm_geometry* geo) {
   // Jacobi diagonal of the Helmholtz operator by colour probing
   launch_helmholtz_diag(c->cv, g, c->bc, c->ph, c->t0, c->t1, c->t2, c->t3, c->t4, c->t5, c->co.invdhu, c->co.invdhv,
                         st);
+  // its nine coefficients per unknown face, by colour probing
+  launch_helmholtz_coefs(c->cv, g, c->bc, c->ph, c->t0, c->t1, c->t2, c->t3, c->hc, c->hc_bad, st);
   // state
   const size_t bytes = g.count() * sizeof(double);
   for (double* a : {c->p, c->phi, c->cnu[0], c->cnu[1], c->cnv[0], c->cnv[1], c->ustar, c->vstar, c->div})
@@ -650,9 +662,12 @@ ccm_status ccm_set_geometry(ccm_case c, const ccm_geometry* geo) {
   // number of active cells
   std::vector<int8_t> act(g.count());
   CUDA_TRY(cudaMemcpyAsync(act.data(), c->co.act, g.count(), cudaMemcpyDeviceToHost, st));
+  int hc_bad = 0;
+  CUDA_TRY(cudaMemcpyAsync(&hc_bad, c->hc_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   ccm_status s = check_cuda_errors("set_geometry");
   if (s != CCM_OK) return s;
+  if (hc_bad) return fail(CCM_E_INVALID, "the Helmholtz operator couples faces outside its nine-point pattern");
   long long na = 0;
   for (int8_t a : act) na += a;
   if (na == 0) return fail(CCM_E_INVALID, "no fluid cell");

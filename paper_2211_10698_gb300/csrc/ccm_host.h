@@ -141,22 +141,37 @@ struct BatchControl {
   Barrier bar;
 };
 
-struct HelmholtzSolve {
-  Coefs c;
+// The Helmholtz operator of the predictor (Eq. pm_prediction, homogeneous part) as nine
+// coefficients per unknown face, found by colour probing at set-up.  u-row (face (i, j)):
+// 0 u(i,j), 1 u(i-1,j), 2 u(i+1,j), 3 u(i,j-1), 4 u(i,j+1), 5 v(i-1,j), 6 v(i,j), 7 v(i-1,j+1),
+// 8 v(i,j+1).  v-row: 9 v(i,j), 10 v(i-1,j), 11 v(i+1,j), 12 v(i,j-1), 13 v(i,j+1), 14 u(i,j-1),
+// 15 u(i+1,j-1), 16 u(i,j), 17 u(i+1,j).  Ghost reflections are folded into these; faces that
+// are not unknowns get coefficient 0.
+struct HelmCoefPtrs {
+  double* a[18];
+};
+void launch_helmholtz_coefs(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, double* eu, double* ev,
+                            double* ou, double* ov, const HelmCoefPtrs& h, int* bad, cudaStream_t st);
+
+// Helmholtz PCG on the coefficient form (pcg_helm.cu): single-reduction Jacobi CG over the
+// unknown u and v faces.
+struct HelmCSolve {
   Geom g;
-  Bc bc;
-  Phys ph;
-  double* xu;
-  double* xv;
-  const double* bu;
-  const double* bv;
-  double *ru, *rv, *zu, *zv, *pu, *pv, *qu, *qv;
+  const int8_t* ru;
+  const int8_t* rv;
+  HelmCoefPtrs h;
+  const double* invu;  // 1 / diagonal
+  const double* invv;
+  double *xu, *xv;
+  const double *bu, *bv;
+  double *rU, *rV, *zU, *zV, *wU, *wV, *pU, *pV, *sU, *sV;
   double tol;
   int max_iter;
   double* partials;
   Barrier bar;
   PcgOut out;
 };
+cudaError_t run_helmholtz_coef(const HelmCSolve& a, cudaStream_t st);
 
 // What a solver outside api.cu needs from a case (read-only view).
 struct CaseSolveView {
@@ -252,6 +267,5 @@ ccm_status case_mixed_residual(ccm_case c, double* host2);
 void case_mixed_correct(ccm_case c);
 void case_mixed_account(ccm_case c, long long inner, int outer, double rr, double bb, bool converged);
 int* case_inner_iters_dev(ccm_case c);
-cudaError_t run_helmholtz_pcg(HelmholtzSolve a, cudaStream_t st);
 
 }  // namespace ccm

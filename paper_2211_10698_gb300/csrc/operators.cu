@@ -193,6 +193,41 @@ __global__ void k_probe_get(Coefs c, Geom g, int comp, int a, int b, const doubl
   if (comp == 0 && col && c.role_u[k] >= R_INACTIVE) du[k] = ou[k];
   if (comp == 1 && col && c.role_v[k] >= R_INACTIVE) dv[k] = ov[k];
 }
+// Coefficient extraction: after applying the operator to the unit vector of colour (a, b) of
+// component comp, row (i, j) sees exactly one unit inside its 3x3 neighbourhood, at the offset
+// (di, dj) with i + di = a, j + dj = b (mod 3); its response is the coefficient of that
+// neighbour.  A response at an offset outside the row's pattern is flagged in *bad.
+__global__ void k_probe_coef(Coefs c, Geom g, int comp, int a, int b, const double* ou, const double* ov,
+                             HelmCoefPtrs h, int* bad) {
+  PAD_IJ(g)
+  auto off = [](int want, int at) {
+    const int d = ((want - at) % 3 + 3) % 3;
+    return d == 2 ? -1 : d;
+  };
+  const int di = off(a, i), dj = off(b, j);
+  if (c.role_u[k] == R_UNKNOWN) {
+    int slot = -1;
+    if (comp == 0)
+      slot = (di == 0 && dj == 0) ? 0 : (di == -1 && dj == 0) ? 1 : (di == 1 && dj == 0) ? 2
+           : (di == 0 && dj == -1) ? 3 : (di == 0 && dj == 1) ? 4 : -1;
+    else
+      slot = (di == -1 && dj == 0) ? 5 : (di == 0 && dj == 0) ? 6 : (di == -1 && dj == 1) ? 7
+           : (di == 0 && dj == 1) ? 8 : -1;
+    if (slot >= 0) h.a[slot][k] = ou[k];
+    else if (ou[k] != 0.0) atomicOr(bad, 1);
+  }
+  if (c.role_v[k] == R_UNKNOWN) {
+    int slot = -1;
+    if (comp == 1)
+      slot = (di == 0 && dj == 0) ? 9 : (di == -1 && dj == 0) ? 10 : (di == 1 && dj == 0) ? 11
+           : (di == 0 && dj == -1) ? 12 : (di == 0 && dj == 1) ? 13 : -1;
+    else
+      slot = (di == 0 && dj == -1) ? 14 : (di == 1 && dj == -1) ? 15 : (di == 0 && dj == 0) ? 16
+           : (di == 1 && dj == 0) ? 17 : -1;
+    if (slot >= 0) h.a[slot][k] = ov[k];
+    else if (ov[k] != 0.0) atomicOr(bad, 1);
+  }
+}
 __global__ void k_invert_diag(Geom g, const double* du, const double* dv, double* iu, double* iv) {
   PAD_IJ(g)
   iu[k] = du[k] != 0.0 ? 1.0 / du[k] : 0.0;
@@ -420,6 +455,18 @@ void launch_helmholtz_diag(const Coefs& c, const Geom& g, const Bc& bc, const Ph
         k_probe_get<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, comp, a, b, ou, ov, du, dv);
       }
   if (iu) k_invert_diag<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, du, dv, iu, iv);
+}
+void launch_helmholtz_coefs(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, double* eu, double* ev,
+                            double* ou, double* ov, const HelmCoefPtrs& h, int* bad, cudaStream_t st) {
+  for (int q = 0; q < 18; ++q) cudaMemsetAsync(h.a[q], 0, g.count() * sizeof(double), st);
+  cudaMemsetAsync(bad, 0, sizeof(int), st);
+  for (int comp = 0; comp < 2; ++comp)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        k_probe_set<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, comp, a, b, eu, ev);
+        launch_helmholtz(c, g, bc, ph, eu, ev, ou, ov, st);
+        k_probe_coef<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, comp, a, b, ou, ov, h, bad);
+      }
 }
 void launch_predictor_rhs(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, const double* u, const double* v,
                           const double* p, const double* cpu, const double* cpv, double* cnu, double* cnv, double* ru,

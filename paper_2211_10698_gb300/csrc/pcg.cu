@@ -1,12 +1,13 @@
-// Persistent preconditioned conjugate-gradient kernels for the two linear systems of the
-// PmII step (Sec. 4.6): the pressure Poisson system K Phi = rhs (Eq. pm_poisson) and the
-// Crank-Nicolson Helmholtz system H U* = rhs (Eq. pm_prediction).
+// Persistent preconditioned conjugate-gradient kernels for the pressure Poisson system
+// K Phi = rhs of the PmII step (Eq. pm_poisson) on the unscaled system: the three-phase
+// kernel with the Chebyshev preconditioner, the single-reduction Jacobi kernel for singular
+// systems, and their batched form.  (Nonsingular Jacobi solves use the scaled kernels of
+// pcg_scaled.cu, pcg_fused.cu and pcg_mixed.cu; the Helmholtz solve is in pcg_helm.cu.)
 //
 // One cooperative launch runs the whole solve: every block stays resident, device-wide
 // barriers are the bounded spin barrier of ccm_internal.cuh, and the dot products are
 // block partials summed by every block in one fixed order (deterministic, no atomics on
-// floating point).  Standard Hestenes-Stiefel PCG with Jacobi preconditioning; the
-// convergence test ||r|| <= tol ||b|| is made before every iteration.
+// floating point).  The convergence test ||r|| <= tol ||b|| is made before every iteration.
 //
 // Poisson, per iteration:   A: p = z + beta p_old (recomputed for the stencil neighbours
 //                              instead of a third barrier), q = K p, p.q   | barrier
@@ -14,8 +15,6 @@
 // When the Poisson system is singular (no outflow side) the preconditioned residual is
 // projected onto zero-mean fields over the active cells (end of Sec. 4.6); the mean is
 // carried through the reductions, so no extra barrier is needed.
-//
-// Helmholtz, per iteration: A: q = H p, p.q | B: x, r, z updates, r.z, r.r | C: p = z + beta p.
 #include "pcg_common.cuh"
 
 namespace ccm {
@@ -548,123 +547,6 @@ __global__ void k_zero_mean_apply(Geom g, const int8_t* act, T* x, const double*
 }
 
 // ---------------------------------------------------------------------------------------
-// Helmholtz PCG over the velocity unknowns (u and v faces in the padded layout).
-// ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPcgThreads) k_pcg_helmholtz(HelmholtzSolve a) {
-  __shared__ double sm[32 * 3];
-  unsigned int target = 0;
-  const int nb = gridDim.x;
-  const Geom g = a.g;
-  const Coefs& c = a.c;
-  const int total = (int)g.count();
-  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, ts = gridDim.x * blockDim.x;
-  const HomView wx{a.xu, a.xv, c.role_u, c.role_v, g, a.bc};
-  const HomView wp{a.pu, a.pv, c.role_u, c.role_v, g, a.bc};
-  const double mu = a.ph.mu;
-
-  double v[3] = {0.0, 0.0, 0.0};
-  for (int t = t0; t < total; t += ts) {
-    const int j = t / g.pitch - 1, i = t - (j + 1) * g.pitch - 1;
-    if (i > g.nx + 1) continue;
-    const size_t k = (size_t)t;
-    if (c.role_u[k] == R_UNKNOWN) {
-      const double hx = c.massu[k] * wx.u[k] - mu * visc_u(c, g, a.bc, wx, i, j);
-      const double rk = a.bu[k] - hx, zk = c.invdhu[k] * rk;
-      a.ru[k] = rk; a.zu[k] = zk; a.pu[k] = zk;
-      v[0] += rk * zk; v[1] += rk * rk; v[2] += a.bu[k] * a.bu[k];
-    }
-    if (c.role_v[k] == R_UNKNOWN) {
-      const double hv = c.massv[k] * wx.v[k] - mu * visc_v(c, g, a.bc, wx, i, j);
-      const double rk = a.bv[k] - hv, zk = c.invdhv[k] * rk;
-      a.rv[k] = rk; a.zv[k] = zk; a.pv[k] = zk;
-      v[0] += rk * zk; v[1] += rk * rk; v[2] += a.bv[k] * a.bv[k];
-    }
-  }
-  block_sum<3>(v, sm);
-  publish(a.partials, nb, v, 3);
-  bool ok = grid_sync(a.bar, target);
-  double s[3];
-  if (ok) grid_sum<3>(a.partials, nb, s, sm);
-  double rz = ok ? s[0] : 0.0, rr = ok ? s[1] : 0.0, bb = ok ? s[2] : 0.0;
-  const double tol2 = a.tol * a.tol;
-  int it = 0;
-  bool conv = false;
-  if (ok && bb == 0.0) {
-    for (int t = t0; t < total; t += ts) {
-      if (c.role_u[t] == R_UNKNOWN) a.xu[t] = 0.0;
-      if (c.role_v[t] == R_UNKNOWN) a.xv[t] = 0.0;
-    }
-    conv = true;
-  }
-  while (ok && !conv) {
-    if (rr <= tol2 * bb) { conv = true; break; }
-    if (it >= a.max_iter) break;
-    double pq[1] = {0.0};
-    for (int t = t0; t < total; t += ts) {
-      const int j = t / g.pitch - 1, i = t - (j + 1) * g.pitch - 1;
-      if (i > g.nx + 1) continue;
-      const size_t k = (size_t)t;
-      if (c.role_u[k] == R_UNKNOWN) {
-        const double qk = c.massu[k] * wp.u[k] - mu * visc_u(c, g, a.bc, wp, i, j);
-        a.qu[k] = qk;
-        pq[0] += a.pu[k] * qk;
-      }
-      if (c.role_v[k] == R_UNKNOWN) {
-        const double qk = c.massv[k] * wp.v[k] - mu * visc_v(c, g, a.bc, wp, i, j);
-        a.qv[k] = qk;
-        pq[0] += a.pv[k] * qk;
-      }
-    }
-    block_sum<1>(pq, sm);
-    publish(a.partials, nb, pq, 1);
-    if (!grid_sync(a.bar, target)) { ok = false; break; }
-    double spq[1];
-    grid_sum<1>(a.partials, nb, spq, sm);
-    const double alpha = rz / spq[0];
-    double w[2] = {0.0, 0.0};
-    for (int t = t0; t < total; t += ts) {
-      const size_t k = (size_t)t;
-      if (c.role_u[k] == R_UNKNOWN) {
-        a.xu[k] += alpha * a.pu[k];
-        const double rk = a.ru[k] - alpha * a.qu[k], zk = c.invdhu[k] * rk;
-        a.ru[k] = rk; a.zu[k] = zk;
-        w[0] += rk * zk; w[1] += rk * rk;
-      }
-      if (c.role_v[k] == R_UNKNOWN) {
-        a.xv[k] += alpha * a.pv[k];
-        const double rk = a.rv[k] - alpha * a.qv[k], zk = c.invdhv[k] * rk;
-        a.rv[k] = rk; a.zv[k] = zk;
-        w[0] += rk * zk; w[1] += rk * rk;
-      }
-    }
-    block_sum<2>(w, sm);
-    publish(a.partials, nb, w, 2);
-    if (!grid_sync(a.bar, target)) { ok = false; break; }
-    double sw[2];
-    grid_sum<2>(a.partials, nb, sw, sm);
-    const double beta = sw[0] / rz;
-    rz = sw[0];
-    rr = sw[1];
-    ++it;
-    if (rr <= tol2 * bb || it >= a.max_iter) continue;  // p is not needed any more
-    for (int t = t0; t < total; t += ts) {
-      const size_t k = (size_t)t;
-      if (c.role_u[k] == R_UNKNOWN) a.pu[k] = a.zu[k] + beta * a.pu[k];
-      if (c.role_v[k] == R_UNKNOWN) a.pv[k] = a.zv[k] + beta * a.pv[k];
-    }
-    if (!grid_sync(a.bar, target)) { ok = false; break; }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.out.iters[0] = it;
-    a.out.rr[0] = rr;
-    a.out.bb[0] = bb;
-    a.out.converged[0] = conv ? 1 : 0;
-    if (a.out.total) a.out.total[0] += it;
-    if (!conv && a.out.nconv) a.out.nconv[0] += 1;
-  }
-}
-
-// ---------------------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------------------
 static int coop_blocks(const void* fn, int threads, int max_per_sm) {
@@ -750,12 +632,5 @@ template cudaError_t run_poisson_batch<float>(const PoissonSolve<float>*, int, c
                                               BatchControl, int, cudaStream_t);
 template cudaError_t run_poisson_pcg<float>(PoissonSolve<float>, cudaStream_t);
 
-cudaError_t run_helmholtz_pcg(HelmholtzSolve a, cudaStream_t st) {
-  const void* fn = (const void*)k_pcg_helmholtz;
-  const int blocks = coop_blocks(fn, kPcgThreads, 2);
-  cudaMemsetAsync(a.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
-  void* params[] = {&a};
-  return cudaLaunchCooperativeKernel(fn, blocks, kPcgThreads, params, 0, st);
-}
 
 }  // namespace ccm
