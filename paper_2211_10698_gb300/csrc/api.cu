@@ -311,14 +311,17 @@ void case_mixed_solve(ccm_case c, double* x, const double* b, MixedSolve* a) {
   a->d.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
   a->cus32 = c->co.cus32; a->cvs32 = c->co.cvs32;
   a->r = c->fr; a->w = c->fq; a->p = c->fp0; a->s = c->fp1; a->e = c->fx;
+  a->cheb = c->cfg.precond == CCM_CHEBYSHEV ? c->cfg.cheb_degree : 1;
+  a->zA = c->fz2; a->zB = c->fw1; a->dch = c->fb;
   a->fpartials = (float*)(c->partials + pcg_float_partials_offset());
   a->drop = c->cfg.replace_drop > 0 && c->cfg.replace_drop < 1 ? c->cfg.replace_drop : 0.5;
   a->replacements = &c->ds->nrep;
 }
 
 ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
-  if (!c->zero_mean && c->cfg.precond == CCM_JACOBI) {
-    // one launch: FP32 CG on the scaled system with FP64 residual replacements
+  if (!c->zero_mean) {
+    // one launch: FP32 CG on the scaled system with FP64 residual replacements (Jacobi or
+    // Chebyshev preconditioner)
     MixedSolve a{};
     case_mixed_solve(c, x, b, &a);
     CUDA_TRY(run_poisson_mixed(a, c->st));
@@ -468,7 +471,10 @@ void case_scaled_fp64(ccm_case c, ScaledSolve* a) {
   *a = scaled_solve_of(v, c->phi, c->rhs_p, c->pz, c->pr, c->pq, c->pp0, c->pp1);
   a->out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
 }
-void case_mixed_batch(ccm_case c, MixedSolve* a) { case_mixed_solve(c, c->phi, c->rhs_p, a); }
+void case_mixed_batch(ccm_case c, MixedSolve* a) {
+  case_mixed_solve(c, c->phi, c->rhs_p, a);
+  a->cheb = 1;  // the batched kernel preconditions with Jacobi
+}
 
 // FP64 Jacobi-PCG descriptor of the case's pressure solve (x = Phi, b = the step's right-hand
 // side); statistics go to the case's device counters as for a single solve.

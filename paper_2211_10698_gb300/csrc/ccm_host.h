@@ -110,7 +110,9 @@ void fused_tiles(int nx, int ny, int blocks, int* TX, int* TY, int* nbx, int* nt
 struct MixedSolve {
   ScaledSolve d;
   const float *cus32, *cvs32;
-  float *r, *w, *p, *s, *e;   // FP32 residual, K~ r, direction, K~ p, correction
+  float *r, *w, *p, *s, *e;   // FP32 residual, K~ u, direction, K~ p, correction
+  int cheb;                   // 1: Jacobi (u = r); k > 1: k-step Chebyshev preconditioner
+  float *zA, *zB, *dch;       // Chebyshev iterates and direction (cheb > 1)
   float* fpartials;           // 3 x blocks
   double drop;                // FP32 residual reduction that triggers a replacement
   int* replacements;          // out: FP64 replacements made

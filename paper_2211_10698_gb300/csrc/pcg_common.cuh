@@ -311,6 +311,29 @@ struct QuadOpsF32 {
     if (r64) st4(r, k0, rc);
     st4(w, k0, wq);
   }
+  // K~ z on the quad (z at the quad returned in zc), loads issued together as in stencil()
+  __device__ __forceinline__ float4 apply(const float* z, int k0, float4& zc) const {
+    const char4 km = *reinterpret_cast<const char4*>(kinds + k0);
+    zc = ld4(z, k0);
+    const float4 zs = ld4(z, k0 - P), zq = ld4(z, k0 + P);
+    const float zw = z[k0 - 1], ze = z[k0 + 4];
+    const float4 cw = ld4(cus, k0), cs = ld4(cvs, k0), cn = ld4(cvs, k0 + P);
+    const float ce4 = cus[k0 + 4];
+    float4 out;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int8_t kk = m == 0 ? km.x : m == 1 ? km.y : m == 2 ? km.z : km.w;
+      const float c = at(zc, m);
+      const float l = m == 0 ? zw : at(zc, m - 1);
+      const float rr = m == 3 ? ze : at(zc, m + 1);
+      const float sv = at(zs, m), nv = at(zq, m);
+      const float ce = m == 3 ? ce4 : at(cw, m + 1);
+      const float wu = c - ax * (l + rr) - ay * (sv + nv);
+      const float wg = c - at(cw, m) * l - ce * rr - at(cs, m) * sv - at(cn, m) * nv;
+      put(out, m, kk == 1 ? wu : (kk == 2 ? wg : c));
+    }
+    return out;
+  }
   // the direction after a replacement: p = r + be p, s = w + be s stored; returns (p, s) on
   // the quad
   __device__ __forceinline__ float form(float* p, const float* r, const float* w, float* s, int k0,

@@ -58,7 +58,7 @@ __device__ __forceinline__ void grid_sum_f32(const float* partials, int nb, floa
 
 __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve a) {
   __shared__ double red[4][kPcgThreads];
-  __shared__ float wred[2][kPcgThreads / 32];
+  __shared__ float wred[3][kPcgThreads / 32];
   __shared__ double dsum[8];
   __shared__ float fsum[8];
   __shared__ double sc_sigma, sc_rr, sc_bb, sc_rr_ref;
@@ -88,6 +88,12 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
   float* __restrict__ s = a.s;
   float* __restrict__ e = a.e;
   float* fpart = a.fpartials;
+  // Chebyshev preconditioner (cheb > 1): z1 = r / theta, then cheb - 1 steps of the Chebyshev
+  // iteration for K~ z = r, alternating between zA and zB; u = M^-1 r is the last iterate.
+  // With Jacobi (cheb = 1) u is r itself.
+  const int cheb = a.cheb > 1 ? a.cheb : 1;
+  float* __restrict__ uvec = cheb == 1 ? r : ((cheb & 1) ? a.zA : a.zB);
+  const float ith = (float)(1.0 / ChebCoef::theta);
   const double tol2 = d.tol * d.tol;
 
   // R2 (and the start): r64 = D^-1/2 (b - K x); sums ||r64||^2, ||b - K x||^2 (and ||b||^2).
@@ -128,32 +134,89 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
     __syncthreads();
     return true;
   };
-  // Phase B: w = K~ r (FP32) and the sums gamma = (r, r), delta = (w, r).  With `fresh`, r is
-  // first set from the FP64 residual: r = sigma r64, read at the neighbours the same way.
+  // The Chebyshev steps 2 .. cheb (Saad, Chebyshev acceleration; eigenvalue interval of the
+  // scaled operator as in ChebCoef): d = c1 d + c2 (r - K~ z), z_next = z + d, a grid barrier
+  // after each (the next step and phase B read the neighbours).
+  auto cheb_steps = [&]() -> bool {
+    const double sig1 = ChebCoef::theta / ChebCoef::delta;
+    double rho_prev = 1.0 / sig1;
+    for (int j = 1; j < cheb; ++j) {
+      const double rho = 1.0 / (2.0 * sig1 - rho_prev);
+      const float c1 = (float)(rho * rho_prev), c2 = (float)(2.0 * rho / ChebCoef::delta);
+      rho_prev = rho;
+      const float* zin = (j & 1) ? a.zA : a.zB;
+      float* zout = (j & 1) ? a.zB : a.zA;
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+        const int k0 = Q.k(u);
+        float4 zc;
+        const float4 kz = ops.apply(zin, k0, zc);
+        const float4 rq = ld4(r, k0), dq = ld4(a.dch, k0);
+        const float4 dn = make_float4(c1 * dq.x + c2 * (rq.x - kz.x), c1 * dq.y + c2 * (rq.y - kz.y),
+                                      c1 * dq.z + c2 * (rq.z - kz.z), c1 * dq.w + c2 * (rq.w - kz.w));
+        st4(a.dch, k0, dn);
+        st4(zout, k0, make_float4(zc.x + dn.x, zc.y + dn.y, zc.z + dn.z, zc.w + dn.w));
+      }
+      if (!grid_sync(d.bar, target)) return false;
+    }
+    return true;
+  };
+  // Phase B: w = K~ u (FP32) and the sums gamma = (r, u), delta = (w, u), (r, r).  With `fresh`,
+  // r is first set from the FP64 residual, r = sigma r64: with Jacobi it is read at the
+  // neighbours the same way; with Chebyshev z1 = r / theta is formed and the steps run first.
   auto phase_b = [&](bool fresh) -> bool {
-    float v[2] = {0.0f, 0.0f};
+    float v[3] = {0.0f, 0.0f, 0.0f};
     const double sig = sc_sigma;
-    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x)
-      ops.stencil(r, w, fresh ? r64 : nullptr, sig, Q.k(u), v);
-    block_sum_f32<2>(v, wred, fsum);
+    if (cheb == 1) {
+      float v2[2] = {0.0f, 0.0f};
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x)
+        ops.stencil(r, w, fresh ? r64 : nullptr, sig, Q.k(u), v2);
+      v[0] = v2[0];
+      v[1] = v2[1];
+      v[2] = v2[0];
+    } else {
+      if (fresh) {
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+          const int k0 = Q.k(u);
+          const float4 rc = ld4_scaled(r64, k0, sig);
+          const float4 z1 = make_float4(rc.x * ith, rc.y * ith, rc.z * ith, rc.w * ith);
+          st4(r, k0, rc);
+          st4(a.zA, k0, z1);
+          st4(a.dch, k0, z1);
+        }
+        if (!grid_sync(d.bar, target)) return false;
+      }
+      if (!cheb_steps()) return false;
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+        const int k0 = Q.k(u);
+        float4 uc;
+        const float4 wq = ops.apply(uvec, k0, uc);
+        const float4 rq = ld4(r, k0);
+        st4(w, k0, wq);
+        v[0] += rq.x * uc.x + rq.y * uc.y + rq.z * uc.z + rq.w * uc.w;
+        v[1] += wq.x * uc.x + wq.y * uc.y + wq.z * uc.z + wq.w * uc.w;
+        v[2] += rq.x * rq.x + rq.y * rq.y + rq.z * rq.z + rq.w * rq.w;
+      }
+    }
+    block_sum_f32<3>(v, wred, fsum);
     if (threadIdx.x == 0) {
       fpart[blockIdx.x] = fsum[0];
       fpart[nb + blockIdx.x] = fsum[1];
+      fpart[2 * nb + blockIdx.x] = fsum[2];
     }
     if (!grid_sync(d.bar, target)) return false;
-    float t[2];
-    grid_sum_f32<2>(fpart, nb, t, fsum);
+    float t[3];
+    grid_sum_f32<3>(fpart, nb, t, fsum);
     if (threadIdx.x == 0) {
-      const float gamma = t[0], delta = t[1];
+      const float gamma = t[0], delta = t[1], rr32 = t[2];
       if (!fresh) {
         sc_it += 1;         // one more phase A done
         sc_pscale = 1.0f;   // its rescaling (after a replacement) is spent
         sc_keep = 0;
       }
-      if (fresh) sc_gref = gamma;
+      if (fresh) sc_gref = rr32;
       // replace when the FP32 residual fell by `drop`, or when the estimate of the unscaled
       // residual norm (scaled by the last FP64 value) meets the tolerance
-      const double ratio = (double)gamma / (double)sc_gref;
+      const double ratio = (double)rr32 / (double)sc_gref;
       sc_replace = !fresh && (ratio <= a.drop * a.drop || sc_rr_ref * ratio <= tol2 * sc_bb) ? 1 : 0;
       // A residual about to be replaced is not used: the scalars are formed from the replacing
       // residual instead (next call, fresh), against the same previous gamma and alpha.
@@ -202,14 +265,14 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
   auto phase_p = [&]() -> bool {
     const float be = sc_beta * sc_pscale;
     float v[1] = {0.0f};
-    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) v[0] += ops.form(p, r, w, s, Q.k(u), be);
-    // row 2 of the FP32 partials: rows 0-1 (the sums of phase B) may still be read by other
+    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) v[0] += ops.form(p, uvec, w, s, Q.k(u), be);
+    // row 3 of the FP32 partials: rows 0-2 (the sums of phase B) may still be read by other
     // blocks, since no barrier separates that read from this write
     block_sum_f32<1>(v, wred, fsum);
-    if (threadIdx.x == 0) fpart[2 * nb + blockIdx.x] = fsum[0];
+    if (threadIdx.x == 0) fpart[3 * nb + blockIdx.x] = fsum[0];
     if (!grid_sync(d.bar, target)) return false;
     float t[1];
-    grid_sum_f32<1>(fpart + 2 * nb, nb, t, fsum);
+    grid_sum_f32<1>(fpart + 3 * nb, nb, t, fsum);
     if (threadIdx.x == 0) {
       sc_alpha = sc_gfresh / t[0];
       sc_igamma = 1.0f / sc_gfresh;
@@ -257,7 +320,29 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
     {
       const float al = sc_alpha, be = sc_keep ? 0.0f : sc_beta * sc_pscale;
       const bool keep = sc_keep != 0;
-      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.update(p, r, w, s, e, Q.k(u), al, be, keep);
+      if (cheb == 1) {
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.update(p, r, w, s, e, Q.k(u), al, be, keep);
+      } else {
+        // the same update with u = M^-1 r, and the first Chebyshev step z1 = d = r / theta
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+          const int k0 = Q.k(u);
+          const float4 pm = ld4(p, k0), um = ld4(uvec, k0), wm = ld4(w, k0), sm = ld4(s, k0), em = ld4(e, k0);
+          const float4 rm = ld4(r, k0);
+          float4 pk = pm, sk = sm;
+          if (!keep) {
+            pk = make_float4(um.x + be * pm.x, um.y + be * pm.y, um.z + be * pm.z, um.w + be * pm.w);
+            sk = make_float4(wm.x + be * sm.x, wm.y + be * sm.y, wm.z + be * sm.z, wm.w + be * sm.w);
+            st4(p, k0, pk);
+            st4(s, k0, sk);
+          }
+          st4(e, k0, make_float4(em.x + al * pk.x, em.y + al * pk.y, em.z + al * pk.z, em.w + al * pk.w));
+          const float4 rn = make_float4(rm.x - al * sk.x, rm.y - al * sk.y, rm.z - al * sk.z, rm.w - al * sk.w);
+          st4(r, k0, rn);
+          const float4 z1 = make_float4(rn.x * ith, rn.y * ith, rn.z * ith, rn.w * ith);
+          st4(a.zA, k0, z1);
+          st4(a.dch, k0, z1);
+        }
+      }
     }
     if (!grid_sync(d.bar, target)) { ok = false; break; }
     if (!phase_b(false)) { ok = false; break; }
