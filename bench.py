@@ -332,7 +332,8 @@ def measure_configs(torch, stream, flush):
 
 def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=1):
     """The 64-case batch (cylinders and NACA00tt sections, 256..1024 cells wide, mixed
-    precision): all cases advance together, one batched Poisson solve per step."""
+    precision, Chebyshev degree 4 as configured): all cases advance together, one batched
+    Poisson solve per step."""
     from paper_2211_10698_gb300 import ccm, inputs
 
     specs = inputs.batch_cases(ncases)
@@ -342,16 +343,22 @@ def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=1):
     for c in cases:
         b.add(c)
     b.step(warmup)
-    ms = _timed_steps(torch, stream, lambda: b.step(1), steps, flush)
-    stats = b.step(0)
+    last = []
+    ms = _timed_steps(torch, stream, lambda: last.append(b.step(1)), steps, flush)
     cells = sum(c.cells for c in specs)
     t = sum(ms)
+    its = [st["last_iters_p"] for st in last[-1]]
+    conv = all(st["converged"] for sts in last for st in sts)
     b.close()
     for c in cases:
         c.close()
+    pcs = sorted({f"{c.precond}" + (f" degree {c.cheb_degree}" if c.precond == "chebyshev" else "") for c in specs})
     return dict(workload=f"batch of {ncases} cases ({cells} cells)", precision="mixed", cells=cells,
                 value=cells * steps / (t * 1e-3), unit=UNIT, ms_per_step=t / steps, steps=steps,
-                note="Poisson solves batched (Jacobi inner PCG); explicit stages and Helmholtz solves per case")
+                precond=", ".join(pcs), poisson_iters_last_step={"max": max(its), "mean": sum(its) / len(its)},
+                converged=conv,
+                note="every stage of a step is one launch for all cases: explicit stages, the Helmholtz "
+                     "solves and the Poisson solves (cooperative)")
 
 
 def measure_serving(precision, nreq=16, step_div=200, budget_gb=150.0, max_batch=64, chunk=5):

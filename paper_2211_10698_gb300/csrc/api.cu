@@ -272,7 +272,8 @@ ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
   return CCM_OK;
 }
 
-ccm_status solve_helmholtz(ccm_case c) {
+// The CN Helmholtz solve of the predictor (Eq. pm_prediction) on the probed coefficients.
+void helm_solve_of(ccm_case c, HelmCSolve* out) {
   HelmCSolve a{};
   a.g = c->g;
   a.ru = c->co.role_u; a.rv = c->co.role_v;
@@ -285,6 +286,12 @@ ccm_status solve_helmholtz(ccm_case c) {
   a.partials = c->partials;
   a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
   a.out = PcgOut{&c->ds->iters_h, &c->ds->rr_h, &c->ds->bb_h, &c->ds->conv_h, &c->ds->total_h, &c->ds->nconv};
+  *out = a;
+}
+
+ccm_status solve_helmholtz(ccm_case c) {
+  HelmCSolve a{};
+  helm_solve_of(c, &a);
   CUDA_TRY(run_helmholtz_coef(a, c->st));
   return CCM_OK;
 }
@@ -334,6 +341,11 @@ ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
   int inner_total = 0, outer = 0;
   double sums[2] = {0.0, 0.0};
   bool conv = false;
+  // singular system: warm start and right-hand side projected onto zero mean in FP64, as
+  // the FP64 solve does (the FP32 corrections are zero-mean only to FP32 rounding, so the
+  // result is projected again at the end)
+  CUDA_TRY(project_zero_mean(g, c->co.act, x, c->partials, (double)c->n_act, st));
+  CUDA_TRY(project_zero_mean(g, c->co.act, b, c->partials, (double)c->n_act, st));
   for (; outer < 60; ++outer) {
     launch_residual64(c->cv, g, x, b, c->fb, c->dpart, c->mixed_sums, st);
     CUDA_TRY(cudaMemcpyAsync(sums, c->mixed_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -362,7 +374,8 @@ ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
     launch_add_correction(g, c->co.act, x, c->fx, st);
     c->launches += 3;
   }
-  c->launches += 2;
+  CUDA_TRY(project_zero_mean(g, c->co.act, x, c->partials, (double)c->n_act, st));
+  c->launches += 8;
   c->mixed_total += inner_total;
   c->mixed_last = inner_total;
   c->mixed_outer = outer;
@@ -453,9 +466,28 @@ ScaledSolve scaled_solve_of(const CaseSolveView& v, double* x, const double* b, 
   return a;
 }
 
+// The case's arrays for the batched explicit stages of its next step (csrc/batch.cu).
+void case_stage_case(ccm_case c, StageCase* e) {
+  const int prev = c->cur, next = 1 - c->cur;
+  StageCase a{};
+  a.c = c->cv; a.g = c->g; a.bc = c->bc; a.ph = c->ph;
+  a.u = c->u; a.v = c->v; a.p = c->p; a.phi = c->phi;
+  a.cpu = c->cnu[prev]; a.cpv = c->cnv[prev]; a.cnu = c->cnu[next]; a.cnv = c->cnv[next];
+  a.ru = c->rhs_u; a.rv = c->rhs_v;
+  a.ustar = c->ustar; a.vstar = c->vstar; a.div = c->div; a.rhs = c->rhs_p;
+  a.first = c->nstep == 0 ? 1 : 0;
+  stage_case_blocks(c->g, &a.gx);
+  *e = a;
+}
+void case_helm_solve(ccm_case c, HelmCSolve* a) { helm_solve_of(c, a); }
+// Host bookkeeping of a step whose stages ran batched (as stage_project does for one case).
+void case_step_done(ccm_case c) {
+  c->cur = 1 - c->cur;
+  c->nstep++;
+  c->steps_pending++;
+}
+
 // Pieces of the step for the batch driver (csrc/batch.cu).
-ccm_status case_stage_predict(ccm_case c) { return stage_predict(c); }
-void case_stage_project(ccm_case c) { stage_project(c); }
 ccm_status case_finish(ccm_case c, ccm_step_stats* stats) { return finish_stats(c, stats); }
 bool case_is_mixed(ccm_case c) { return c->cfg.precision == CCM_MIXED; }
 cudaStream_t case_stream(ccm_case c) { return c->st; }
@@ -471,10 +503,7 @@ void case_scaled_fp64(ccm_case c, ScaledSolve* a) {
   *a = scaled_solve_of(v, c->phi, c->rhs_p, c->pz, c->pr, c->pq, c->pp0, c->pp1);
   a->out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
 }
-void case_mixed_batch(ccm_case c, MixedSolve* a) {
-  case_mixed_solve(c, c->phi, c->rhs_p, a);
-  a->cheb = 1;  // the batched kernel preconditions with Jacobi
-}
+void case_mixed_batch(ccm_case c, MixedSolve* a) { case_mixed_solve(c, c->phi, c->rhs_p, a); }
 
 // FP64 Jacobi-PCG descriptor of the case's pressure solve (x = Phi, b = the step's right-hand
 // side); statistics go to the case's device counters as for a single solve.
@@ -513,6 +542,15 @@ void case_poisson_fp32(ccm_case c, PoissonSolve<float>* a) {
 
 // Mixed refinement helpers: FP64 residual into the FP32 right-hand side with its sums copied
 // to `host2` (valid after the stream syncs), and x += correction.
+// Singular systems: Phi and the right-hand side onto zero mean in FP64 (start and end of the
+// batched refinement, as solve_poisson_mixed does for one case); nothing for other systems.
+ccm_status case_mixed_project(ccm_case c, bool with_rhs) {
+  if (!c->zero_mean) return CCM_OK;
+  CUDA_TRY(project_zero_mean(c->g, c->co.act, c->phi, c->partials, (double)c->n_act, c->st));
+  if (with_rhs) CUDA_TRY(project_zero_mean(c->g, c->co.act, c->rhs_p, c->partials, (double)c->n_act, c->st));
+  c->launches += with_rhs ? 4 : 2;
+  return CCM_OK;
+}
 ccm_status case_mixed_residual(ccm_case c, double* host2) {
   launch_residual64(c->cv, c->g, c->phi, c->rhs_p, c->fb, c->dpart, c->mixed_sums, c->st);
   CUDA_TRY(cudaMemcpyAsync(host2, c->mixed_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));

@@ -1,15 +1,17 @@
 // Batches of independent cases advanced together (the serving form of the projection step).
 //
-// All cases of a batch run on the batch's stream.  Per step, each case's explicit stages and
-// Helmholtz solve are enqueued case by case, then ONE cooperative launch solves the pressure
-// Poisson systems of all cases (each case gets a contiguous range of blocks in proportion to
-// its expected work, cells x nx, and reduces over its own blocks), then each case's
-// projection is enqueued.  When every case has an outflow side (nonsingular systems) the
-// launch is k_sc_batch (FP64 CG on the Jacobi-scaled systems) or k_mixed_batch (FP32 CG with
-// FP64 residual replacements, for the MIXED setting), both in pcg_batch.cu.  Otherwise the
-// unscaled Jacobi-PCG batch of pcg.cu runs, and for MIXED the FP64 residual refinement runs
-// from the host for the whole batch: residuals of the unconverged cases, one host check, one
-// batched FP32 inner solve for those cases, corrections, until every case meets tol_p.
+// All cases of a batch run on the batch's stream, and every stage of a step is one launch for
+// all cases: the explicit stages (box data, predictor right-hand side, U* and the Poisson
+// right-hand side, projection) run the single-case per-point code over a table of cases
+// (operators.cu), the CN Helmholtz solves one cooperative launch (pcg_helm.cu), and the
+// pressure Poisson solves one cooperative launch (each case gets a contiguous range of blocks
+// in proportion to its expected work and reduces over its own blocks).  When every case has
+// an outflow side (nonsingular systems) the Poisson launch is k_sc_batch (FP64 CG on the
+// Jacobi-scaled systems) or k_mixed_batch (FP32 CG with FP64 residual replacements, Jacobi or
+// Chebyshev per case, for the MIXED setting), both in pcg_batch.cu.  Otherwise the unscaled
+// Jacobi-PCG batch of pcg.cu runs, and for MIXED the FP64 residual refinement runs from the
+// host for the whole batch: residuals of the unconverged cases, one host check, one batched
+// FP32 inner solve for those cases, corrections, until every case meets tol_p.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -35,6 +37,17 @@ struct ccm_batch_s {
   unsigned int* bar_count = nullptr;
   int* bar_err = nullptr;
   double* host_sums = nullptr;  // pinned: 2 per case
+  // batched explicit stages and Helmholtz solves: device tables and their pinned staging
+  StageCase* stages = nullptr;
+  int* stage_starts = nullptr;
+  HelmBatchEntry* helm = nullptr;
+  int* helm_block_case = nullptr;
+  void* pinned = nullptr;
+  StageCase* h_stages = nullptr;
+  int* h_starts = nullptr;
+  HelmBatchEntry* h_helm = nullptr;
+  int* h_helm_block_case = nullptr;
+  cudaEvent_t tables_done = nullptr;  // the last upload of the pinned tables has completed
 };
 
 namespace {
@@ -44,14 +57,16 @@ ccm_status bfail(ccm_status s, const std::string& m) {
   return s;
 }
 
-// Contiguous block ranges proportional to the expected PCG work (cells x nx: Jacobi
-// iterations grow like the grid dimension), at least one block per case.
-void allocate_blocks(const std::vector<ccm_case>& cs, int blocks, std::vector<int>& b0, std::vector<int>& nb) {
+// Contiguous block ranges proportional to the expected work, at least one block per case:
+// cells x nx for the Poisson solve (its iteration count grows like the grid dimension), cells
+// for the Helmholtz solve (mass-dominated: about the same iteration count at every size).
+void allocate_blocks(const std::vector<ccm_case>& cs, int blocks, std::vector<int>& b0, std::vector<int>& nb,
+                     bool by_width = true) {
   const int n = (int)cs.size();
   std::vector<double> w(n);
   double tot = 0.0;
   for (int i = 0; i < n; ++i) {
-    w[i] = (double)case_cells(cs[i]) * (double)case_nx(cs[i]);
+    w[i] = (double)case_cells(cs[i]) * (by_width ? (double)case_nx(cs[i]) : 1.0);
     tot += w[i];
   }
   nb.assign(n, 1);
@@ -187,6 +202,12 @@ static ccm_status batch_mixed(ccm_batch b) {
   std::vector<long long> inner(n, 0);
   std::vector<int> outer(n, 0);
   std::vector<double> rr(n, 0.0), bb(n, 0.0);
+  // singular systems: Phi and the right-hand side onto zero mean in FP64 first (and Phi again
+  // at the end), as the single-case refinement does
+  for (ccm_case c : b->cases) {
+    ccm_status s = case_mixed_project(c, true);
+    if (s != CCM_OK) return s;
+  }
   int sweep = 0;
   for (; sweep < 60; ++sweep) {
     std::vector<ccm_case> act;
@@ -219,7 +240,69 @@ static ccm_status batch_mixed(ccm_batch b) {
       case_mixed_correct(act[k]);
     }
   }
+  for (ccm_case c : b->cases) {
+    ccm_status s = case_mixed_project(c, false);
+    if (s != CCM_OK) return s;
+  }
   for (int i = 0; i < n; ++i) case_mixed_account(b->cases[i], inner[i], done[i] ? outer[i] : sweep, rr[i], bb[i], done[i]);
+  return CCM_OK;
+}
+
+// The explicit stages and the Helmholtz solves of one step, batched: one launch per stage for
+// all cases (Eq. pm_prediction: box data, right-hand side, CN Helmholtz solve, box data, then
+// U* and the Poisson right-hand side cont(U*, D)).  The case tables are written to pinned
+// memory and copied to the device on the batch's stream; the previous copy must have
+// completed before the pinned tables are rewritten.
+static ccm_status batch_predict(ccm_batch b) {
+  const std::vector<ccm_case>& cs = b->cases;
+  const int n = (int)cs.size();
+  cudaError_t e = cudaEventSynchronize(b->tables_done);
+  if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched stages: ") + cudaGetErrorString(e));
+  int total = 0;
+  for (int i = 0; i < n; ++i) {
+    case_stage_case(cs[i], &b->h_stages[i]);
+    b->h_starts[i] = total;
+    int gx = 0;
+    total += stage_case_blocks(b->h_stages[i].g, &gx);
+  }
+  b->h_starts[n] = total;
+  std::vector<int> b0, nb;
+  allocate_blocks(cs, b->blocks, b0, nb, false);
+  for (int i = 0; i < n; ++i) {
+    case_helm_solve(cs[i], &b->h_helm[i].a);
+    b->h_helm[i].block0 = b0[i];
+    b->h_helm[i].nblocks = nb[i];
+    for (int k = 0; k < nb[i]; ++k) b->h_helm_block_case[b0[i] + k] = i;
+  }
+  cudaStream_t st = b->st;
+  if ((e = cudaMemcpyAsync(b->stages, b->h_stages, sizeof(StageCase) * n, cudaMemcpyHostToDevice, st)) ==
+          cudaSuccess &&
+      (e = cudaMemcpyAsync(b->stage_starts, b->h_starts, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st)) ==
+          cudaSuccess &&
+      (e = cudaMemcpyAsync(b->helm, b->h_helm, sizeof(HelmBatchEntry) * n, cudaMemcpyHostToDevice, st)) ==
+          cudaSuccess &&
+      (e = cudaMemcpyAsync(b->helm_block_case, b->h_helm_block_case, sizeof(int) * b->blocks,
+                           cudaMemcpyHostToDevice, st)) == cudaSuccess)
+    e = cudaEventRecord(b->tables_done, st);
+  BatchControl ctl{b->partials, b->running, Barrier{b->bar_count, b->bar_err, 2000000000LL}};
+  if (e == cudaSuccess) e = launch_stage_batch(STAGE_FILL_BC, b->stages, b->stage_starts, n, total, st);
+  if (e == cudaSuccess) e = launch_stage_batch(STAGE_PREDICT, b->stages, b->stage_starts, n, total, st);
+  if (e == cudaSuccess) e = run_helm_batch(b->helm, b->helm_block_case, ctl, b->blocks, st);
+  if (e == cudaSuccess) e = launch_stage_batch(STAGE_FILL_BC, b->stages, b->stage_starts, n, total, st);
+  if (e == cudaSuccess) e = launch_stage_batch(STAGE_DIVERGENCE, b->stages, b->stage_starts, n, total, st);
+  if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched stages: ") + cudaGetErrorString(e));
+  return CCM_OK;
+}
+
+// ... and after the Poisson solves: projection and pressure update (Eqs. pm_projection,
+// pm_update), then box data, for all cases (the stage table of the step is still on the device).
+static ccm_status batch_project(ccm_batch b) {
+  const int n = (int)b->cases.size();
+  const int total = b->h_starts[n];
+  cudaError_t e = launch_stage_batch(STAGE_PROJECT, b->stages, b->stage_starts, n, total, b->st);
+  if (e == cudaSuccess) e = launch_stage_batch(STAGE_FILL_BC, b->stages, b->stage_starts, n, total, b->st);
+  if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched stages: ") + cudaGetErrorString(e));
+  for (ccm_case c : b->cases) case_step_done(c);
   return CCM_OK;
 }
 
@@ -237,10 +320,12 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
     delete b;
     return bfail(CCM_E_INVALID, "a batch holds at most " + std::to_string(most) + " cases on this GPU");
   }
-  const size_t pieces[9] = {sizeof(BatchEntry<double>) * max_cases, sizeof(BatchEntry<float>) * max_cases,
-                            sizeof(ScaledBatchEntry) * max_cases, sizeof(MixedBatchEntry) * max_cases,
-                            sizeof(int) * b->blocks, sizeof(double) * 6 * b->blocks, sizeof(int) * b->blocks,
-                            sizeof(unsigned int) * kBarWords, sizeof(int) * 4};
+  const size_t pieces[13] = {sizeof(BatchEntry<double>) * max_cases, sizeof(BatchEntry<float>) * max_cases,
+                             sizeof(ScaledBatchEntry) * max_cases, sizeof(MixedBatchEntry) * max_cases,
+                             sizeof(int) * b->blocks, sizeof(double) * 6 * b->blocks, sizeof(int) * 2 * b->blocks,
+                             sizeof(unsigned int) * kBarWords, sizeof(int) * 4, sizeof(StageCase) * max_cases,
+                             sizeof(int) * (max_cases + 1), sizeof(HelmBatchEntry) * max_cases,
+                             sizeof(int) * b->blocks};
   size_t bytes = 0;
   for (size_t n : pieces) bytes += (n + 255) & ~(size_t)255;
   cudaError_t e = cudaMalloc(&b->dev, bytes);
@@ -257,16 +342,35 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
   b->emx = (MixedBatchEntry*)take(sizeof(MixedBatchEntry) * max_cases);
   b->block_case = (int*)take(sizeof(int) * b->blocks);
   b->partials = (double*)take(sizeof(double) * 6 * b->blocks);
-  b->running = (int*)take(sizeof(int) * b->blocks);
+  b->running = (int*)take(sizeof(int) * 2 * b->blocks);
   b->bar_count = (unsigned int*)take(sizeof(unsigned int) * kBarWords);
   b->bar_err = (int*)take(sizeof(int) * 4);
-  (void)take;
+  b->stages = (StageCase*)take(sizeof(StageCase) * max_cases);
+  b->stage_starts = (int*)take(sizeof(int) * (max_cases + 1));
+  b->helm = (HelmBatchEntry*)take(sizeof(HelmBatchEntry) * max_cases);
+  b->helm_block_case = (int*)take(sizeof(int) * b->blocks);
+  const size_t hbytes = sizeof(StageCase) * max_cases + sizeof(HelmBatchEntry) * max_cases +
+                        sizeof(int) * (max_cases + 1) + sizeof(int) * b->blocks;
   if ((e = cudaMallocHost(&b->host_sums, sizeof(double) * 2 * max_cases)) != cudaSuccess ||
+      (e = cudaMallocHost(&b->pinned, hbytes)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->tables_done, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaMemset(b->dev, 0, bytes)) != cudaSuccess) {
     cudaFree(b->dev);
     if (b->host_sums) cudaFreeHost(b->host_sums);
+    if (b->pinned) cudaFreeHost(b->pinned);
+    if (b->tables_done) cudaEventDestroy(b->tables_done);
     delete b;
     return bfail(CCM_E_CUDA, cudaGetErrorString(e));
+  }
+  {
+    char* h = (char*)b->pinned;
+    b->h_stages = (StageCase*)h;
+    h += sizeof(StageCase) * max_cases;
+    b->h_helm = (HelmBatchEntry*)h;
+    h += sizeof(HelmBatchEntry) * max_cases;
+    b->h_starts = (int*)h;
+    h += sizeof(int) * (max_cases + 1);
+    b->h_helm_block_case = (int*)h;
   }
   *out = b;
   return CCM_OK;
@@ -277,6 +381,8 @@ ccm_status ccm_batch_destroy(ccm_batch b) {
   cudaStreamSynchronize(b->st);
   cudaFree(b->dev);
   cudaFreeHost(b->host_sums);
+  cudaFreeHost(b->pinned);
+  cudaEventDestroy(b->tables_done);
   delete b;
   return CCM_OK;
 }
@@ -317,8 +423,7 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
   const bool scaled = all_scaled(b);
   ccm_status s;
   for (int n = 0; n < nsteps; ++n) {
-    for (ccm_case c : b->cases)
-      if ((s = case_stage_predict(c)) != CCM_OK) return s;
+    if ((s = batch_predict(b)) != CCM_OK) return s;
     if (scaled) {
       if ((s = batch_solve_scaled(b, mixed)) != CCM_OK) return s;
     } else if (mixed) {
@@ -326,7 +431,7 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
     } else {
       if ((s = batch_solve(b, b->cases, false)) != CCM_OK) return s;
     }
-    for (ccm_case c : b->cases) case_stage_project(c);
+    if ((s = batch_project(b)) != CCM_OK) return s;
   }
   ccm_status worst = CCM_OK;
   for (size_t i = 0; i < b->cases.size(); ++i) {

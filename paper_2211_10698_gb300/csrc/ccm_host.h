@@ -139,7 +139,7 @@ struct BatchEntry {
 
 struct BatchControl {
   double* partials;  // 6 values x blocks
-  int* running;      // per block: its case is still iterating
+  int* running;      // per block: its case is still iterating (two halves of gridDim.x)
   Barrier bar;
 };
 
@@ -174,6 +174,32 @@ struct HelmCSolve {
   PcgOut out;
 };
 cudaError_t run_helmholtz_coef(const HelmCSolve& a, cudaStream_t st);
+// One case of a batched explicit stage (operators.cu): its arrays for the step and its range
+// of the launch's blocks (starts[] is the prefix over cases of stage_case_blocks()).
+enum { STAGE_FILL_BC = 0, STAGE_PREDICT = 1, STAGE_DIVERGENCE = 2, STAGE_PROJECT = 3, STAGE_KINDS = 4 };
+struct StageCase {
+  Coefs c;
+  Geom g;
+  Bc bc;
+  Phys ph;
+  double *u, *v, *p;
+  const double* phi;
+  const double *cpu, *cpv;          // conv at the previous step (Adams-Bashforth)
+  double *cnu, *cnv, *ru, *rv;      // conv now, the predictor's right-hand side
+  double *ustar, *vstar, *div, *rhs;
+  int first;                        // first step: conv^{n-1} := conv^n
+  int gx;                           // blocks per padded row (stage_case_blocks)
+};
+int stage_case_blocks(const Geom& g, int* gx);
+cudaError_t launch_stage_batch(int kind, const StageCase* dev_cases, const int* dev_starts, int n, int blocks,
+                               cudaStream_t st);
+struct HelmBatchEntry {
+  HelmCSolve a;  // partials and bar unused: the batch has its own
+  int block0, nblocks;
+};
+int batch_helm_blocks();
+cudaError_t run_helm_batch(const HelmBatchEntry* dev_cases, const int* dev_block_case, BatchControl ctl, int blocks,
+                           cudaStream_t st);
 
 // What a solver outside api.cu needs from a case (read-only view).
 struct CaseSolveView {
@@ -244,6 +270,9 @@ int batch_blocks();
 // pcg_batch.cu: blocks of a batched launch, and the two batched solves (ctl.partials holds
 // 5 rows of blocks)
 int batch_scaled_blocks();
+int poisson_zero_mean_blocks();
+cudaError_t project_zero_mean(const Geom& g, const int8_t* act, double* x, double* partials, double n_act,
+                              cudaStream_t st);
 cudaError_t run_scaled_batch(const ScaledBatchEntry* dev_cases, const int* dev_block_case, BatchControl ctl,
                              int blocks, cudaStream_t st);
 cudaError_t run_mixed_batch(const MixedBatchEntry* dev_cases, const int* dev_block_case, BatchControl ctl,
@@ -253,8 +282,6 @@ cudaError_t run_poisson_batch(const PoissonSolve<T>* host_cases, int ncase, cons
                               const int* dev_block_case, BatchControl ctl, int blocks, cudaStream_t st);
 
 // api.cu: pieces of one step for the batch driver
-ccm_status case_stage_predict(ccm_case c);
-void case_stage_project(ccm_case c);
 ccm_status case_finish(ccm_case c, ccm_step_stats* stats);
 bool case_is_mixed(ccm_case c);
 cudaStream_t case_stream(ccm_case c);
@@ -264,7 +291,11 @@ void case_poisson_fp64(ccm_case c, PoissonSolve<double>* a);
 bool case_scaled_ok(ccm_case c);  // nonsingular: the scaled and mixed batched kernels apply
 void case_scaled_fp64(ccm_case c, ScaledSolve* a);
 void case_mixed_batch(ccm_case c, MixedSolve* a);
+void case_helm_solve(ccm_case c, HelmCSolve* a);
+void case_stage_case(ccm_case c, StageCase* e);
+void case_step_done(ccm_case c);
 void case_poisson_fp32(ccm_case c, PoissonSolve<float>* a);
+ccm_status case_mixed_project(ccm_case c, bool with_rhs);
 ccm_status case_mixed_residual(ccm_case c, double* host2);
 void case_mixed_correct(ccm_case c);
 void case_mixed_account(ccm_case c, long long inner, int outer, double rr, double bb, bool converged);

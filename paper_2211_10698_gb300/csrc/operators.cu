@@ -92,8 +92,8 @@ __global__ void k_derive2(Geom g, Phys ph, int pupdate, CapPtrs cp, CoefPtrs o) 
 // (outflow and normal components) or the reflection 2 scale bc_ut - interior (tangential
 // components on Dirichlet sides).
 // ---------------------------------------------------------------------------------------
-__global__ void k_fill_bc(Geom g, Bc bc, double* u, double* v, double scale) {
-  PAD_IJ(g)
+__device__ __forceinline__ void fill_bc_at(const Geom& g, const Bc& bc, double* u, double* v, double scale, int i,
+                                           int j, size_t k) {
   const int nx = g.nx, ny = g.ny;
   const bool wd = bc.type[CCM_SIDE_W] == CCM_BC_DIRICHLET, ed = bc.type[CCM_SIDE_E] == CCM_BC_DIRICHLET;
   const bool sd = bc.type[CCM_SIDE_S] == CCM_BC_DIRICHLET, nd = bc.type[CCM_SIDE_N] == CCM_BC_DIRICHLET;
@@ -125,6 +125,10 @@ __global__ void k_fill_bc(Geom g, Bc bc, double* u, double* v, double scale) {
     if (i == -1) v[k] = wd ? 2.0 * scale * bc.ut[CCM_SIDE_W] - vval(0, j) : vval(0, j);
     else if (i == nx) v[k] = ed ? 2.0 * scale * bc.ut[CCM_SIDE_E] - vval(nx - 1, j) : vval(nx - 1, j);
   }
+}
+__global__ void k_fill_bc(Geom g, Bc bc, double* u, double* v, double scale) {
+  PAD_IJ(g)
+  fill_bc_at(g, bc, u, v, scale, i, j, k);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -238,9 +242,10 @@ __global__ void k_invert_diag(Geom g, const double* du, const double* dv, double
 // Explicit stages of the PmII step (Eq. pm_prediction right-hand side, Eq. pm_poisson
 // right-hand side, Eqs. pm_projection and pm_update).
 // ---------------------------------------------------------------------------------------
-__global__ void k_predictor_rhs(Coefs c, Geom g, Bc bc, Phys ph, FullView w, const double* p, const double* cpu,
-                                const double* cpv, double* cnu, double* cnv, double* ru_, double* rv_, int first) {
-  PAD_IJ(g)
+__device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph,
+                                                 const FullView& w, const double* p, const double* cpu,
+                                                 const double* cpv, double* cnu, double* cnv, double* ru_, double* rv_,
+                                                 int first, int i, int j, size_t k) {
   auto P = [&](int a, int b) { return (a >= 0 && a < g.nx && b >= 0 && b < g.ny) ? p[g.idx(a, b)] : 0.0; };
   if (c.role_u[k] == R_UNKNOWN) {
     const double cn = conv_u(c, g, w, i, j);
@@ -265,23 +270,73 @@ __global__ void k_predictor_rhs(Coefs c, Geom g, Bc bc, Phys ph, FullView w, con
     cnv[k] = 0.0;
   }
 }
+__global__ void k_predictor_rhs(Coefs c, Geom g, Bc bc, Phys ph, FullView w, const double* p, const double* cpu,
+                                const double* cpv, double* cnu, double* cnv, double* ru_, double* rv_, int first) {
+  PAD_IJ(g)
+  predictor_rhs_at(c, g, bc, ph, w, p, cpu, cpv, cnu, cnv, ru_, rv_, first, i, j, k);
+}
 
 // b = cont(U*, D) on cells; Poisson right-hand side -(rho/dt) b on active cells.
-__global__ void k_divergence(Coefs c, Geom g, Phys ph, const double* u, const double* v, double* b, double* rhs) {
-  PAD_IJ(g)
+__device__ __forceinline__ void divergence_at(const Coefs& c, const Geom& g, const Phys& ph, const double* u,
+                                              const double* v, double* b, double* rhs, int i, int j, size_t k) {
   const bool dom = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
   const double d = dom ? cont_cell(c, g, u, v, i, j) : 0.0;
   b[k] = d;
   rhs[k] = c.act[k] ? -(ph.rho / ph.dt) * d : 0.0;
 }
+__global__ void k_divergence(Coefs c, Geom g, Phys ph, const double* u, const double* v, double* b, double* rhs) {
+  PAD_IJ(g)
+  divergence_at(c, g, ph, u, v, b, rhs, i, j, k);
+}
 
 // U^{n+1} = U* - (dt/rho) M^-1 pres(Phi); P^{n+1/2} = P^{n-1/2} + Phi + (dt mu / 2 rho)
 // V_p^-1 K Phi.  Phi's ghost ring is zero.
-__global__ void k_project(Coefs c, Geom g, const double* phi, double* u, double* v, double* p) {
-  PAD_IJ(g)
+__device__ __forceinline__ void project_at(const Coefs& c, const Geom& g, const double* phi, double* u, double* v,
+                                           double* p, int i, int j, size_t k) {
   if (c.role_u[k] == R_UNKNOWN) u[k] -= c.gfu[k] * (phi[k] - phi[k - 1]);
   if (c.role_v[k] == R_UNKNOWN) v[k] -= c.gfv[k] * (phi[k] - phi[k - g.pitch]);
   if (c.act[k]) p[k] += phi[k] + c.pfac[k] * poisson_row(c.cu, c.cv, c.act, g, phi, k);
+}
+__global__ void k_project(Coefs c, Geom g, const double* phi, double* u, double* v, double* p) {
+  PAD_IJ(g)
+  project_at(c, g, phi, u, v, p, i, j, k);
+}
+
+// ---------------------------------------------------------------------------------------
+// The explicit stages for the cases of a batch, one launch per stage: the blocks of case c
+// are starts[c] .. starts[c+1]-1 and tile its padded rows, pitch included, in rows of gx
+// blocks (kBlk), so each thread runs the same per-point body as the single-case kernel.  The divergence stage
+// also takes the copies U* of the predicted velocity (the whole padded arrays, pitch included,
+// as the single-case step copies them).
+// ---------------------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(256) k_stage_batch(const StageCase* __restrict__ cases,
+                                                     const int* __restrict__ starts, int n) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const StageCase& S = cases[lo];
+  const int lb = (int)blockIdx.x - starts[lo];
+  const int bx = lb % S.gx, by = lb / S.gx;
+  const int i = bx * (int)blockDim.x + (int)threadIdx.x - 1;
+  const int j = by * (int)blockDim.y + (int)threadIdx.y - 1;
+  const Geom& g = S.g;
+  if (j > g.ny + 1) return;
+  const size_t k = g.idx(i, j);
+  if (KIND == STAGE_DIVERGENCE && i <= g.pitch - 2) {
+    S.ustar[k] = S.u[k];
+    S.vstar[k] = S.v[k];
+  }
+  if (i > g.nx + 1) return;
+  if (KIND == STAGE_FILL_BC) fill_bc_at(g, S.bc, S.u, S.v, 1.0, i, j, k);
+  if (KIND == STAGE_PREDICT)
+    predictor_rhs_at(S.c, g, S.bc, S.ph, FullView{S.u, S.v, g}, S.p, S.cpu, S.cpv, S.cnu, S.cnv, S.ru, S.rv, S.first,
+                     i, j, k);
+  if (KIND == STAGE_DIVERGENCE) divergence_at(S.c, g, S.ph, S.u, S.v, S.div, S.rhs, i, j, k);
+  if (KIND == STAGE_PROJECT) project_at(S.c, g, S.phi, S.u, S.v, S.p, i, j, k);
 }
 
 // Diagnostics: per-block max |cont(U)| over active cells, sum of V U^2 / 2 over velocity
@@ -480,6 +535,22 @@ void launch_divergence(const Coefs& c, const Geom& g, const Phys& ph, const doub
 }
 void launch_project(const Coefs& c, const Geom& g, const double* phi, double* u, double* v, double* p, cudaStream_t st) {
   k_project<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, phi, u, v, p);
+}
+int stage_case_blocks(const Geom& g, int* gx) {
+  *gx = (g.pitch + (int)kBlk.x - 1) / (int)kBlk.x;
+  return *gx * (int)((g.ny + 3 + kBlk.y - 1) / kBlk.y);
+}
+cudaError_t launch_stage_batch(int kind, const StageCase* dev_cases, const int* dev_starts, int n, int blocks,
+                               cudaStream_t st) {
+  if (n <= 0 || blocks <= 0) return cudaSuccess;
+  switch (kind) {
+    case STAGE_FILL_BC: k_stage_batch<STAGE_FILL_BC><<<blocks, kBlk, 0, st>>>(dev_cases, dev_starts, n); break;
+    case STAGE_PREDICT: k_stage_batch<STAGE_PREDICT><<<blocks, kBlk, 0, st>>>(dev_cases, dev_starts, n); break;
+    case STAGE_DIVERGENCE: k_stage_batch<STAGE_DIVERGENCE><<<blocks, kBlk, 0, st>>>(dev_cases, dev_starts, n); break;
+    case STAGE_PROJECT: k_stage_batch<STAGE_PROJECT><<<blocks, kBlk, 0, st>>>(dev_cases, dev_starts, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 int diagnostics_partials(const Geom& g) {
   dim3 gr = pad_grid(g, kBlk);

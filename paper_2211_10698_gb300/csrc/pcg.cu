@@ -608,6 +608,17 @@ template cudaError_t run_poisson_pcg<double>(PoissonSolve<double>, cudaStream_t)
 
 int batch_blocks() { return coop_blocks((const void*)k_pcg_poisson_cg_batch<double>, kPcgThreads, 2); }
 
+// x minus its mean over the active cells, in FP64 (the null-space projection of a singular
+// system, end of Sec. 4.6); partials holds at least poisson_zero_mean_blocks() values.
+int poisson_zero_mean_blocks() { return coop_blocks((const void*)k_zero_mean_partials<double>, kPcgThreads, 2); }
+cudaError_t project_zero_mean(const Geom& g, const int8_t* act, double* x, double* partials, double n_act,
+                              cudaStream_t st) {
+  const int blocks = poisson_zero_mean_blocks();
+  k_zero_mean_partials<double><<<blocks, kPcgThreads, 0, st>>>(g, act, x, partials);
+  k_zero_mean_apply<double><<<blocks, kPcgThreads, 0, st>>>(g, act, x, partials, blocks, n_act);
+  return cudaGetLastError();
+}
+
 // Singular systems of a batch: warm start and right-hand side projected onto zero mean
 // (what run_poisson_pcg does for a single solve), then one cooperative launch for all.
 template <class T>

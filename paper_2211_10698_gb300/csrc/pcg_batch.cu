@@ -4,60 +4,33 @@
 //
 // Block b serves case block_case[b]: each case owns a contiguous range of blocks, sized by
 // the host to its expected work, and reduces over its own blocks only, in the same fixed
-// order as a single solve.  Every block passes the same grid barriers: each iteration has
-// two slots separated by barriers, and a case fills them according to where it is.  After
-// the first barrier every block counts the blocks whose case is still working (the same
-// count in every block), and the launch ends when none is.
+// order as a single solve.  Every block passes the same grid barriers, and after each one
+// every block counts the blocks whose case is still working (the same count in every block);
+// the launch ends when none is.
 //
-// Mixed solve, per case:
-//   ITERATE  slot 1: vector update A;   slot 2: w = K~ r and its sums;  then the scalars and
-//            the replacement test (FP32 residual fallen by `drop`, a loss of positivity, or
-//            the iteration limit)
-//   REPLACE  slot 1: x += D^-1/2 e / sigma;  slot 2: the FP64 residual and its norms; then the
-//            convergence test on ||b - K x|| and the new normalisation sigma
-//   FRESH    slot 1: r = sigma D^-1/2 (b - K x), w = K~ r and their sums (reduced after the
-//            first barrier);  slot 2: p, K~ p formed and (p, K~ p) summed; then alpha
-//   DONE     idle
-// The first pass starts in REPLACE with e = 0.
-#include "pcg_common.cuh"
+// FP64 solve: two barriers per CG iteration, as in pcg_scaled.cu.
+//
+// Mixed solve: each case steps through slots, one barrier after each, according to where it
+// is (so cases of different sizes, preconditioners and replacement histories share every
+// barrier):
+//   iteration      UPDATE (vector update A),
+//                  CHEB x (degree - 1) (Chebyshev steps from z1 = r / theta; none with Jacobi),
+//                  APPLY (w = K~ u and its sums), then the scalars and the replacement test
+//                  (FP32 residual fallen by `drop`, a loss of positivity, or the limit)
+//   replacement    FOLD (x += D^-1/2 e / sigma), RESID (FP64 residual and its norms; the
+//                  convergence test and the new normalisation sigma), FRESH (r = sigma r64;
+//                  Jacobi: also w = K~ r and its sums; Chebyshev: then CHEB and APPLY),
+//                  FORM (p, K~ p formed and (p, K~ p) summed; then alpha)
+//   DONE           idle
+// The first pass starts in FOLD with p = s = e = 0.
+#include "batch_common.cuh"
+#include "pcg_quad.cuh"
 
 namespace ccm {
 
 namespace {
 
 constexpr int kGroup = 1;  // cells per thread whose loads k_sc_batch issues together (two would spill)
-
-// Cell range of this block within its case.
-struct CaseRange {
-  int t0, t1;
-  __device__ CaseRange(int ncell, int lb, int nbc) {
-    t0 = (int)((long long)ncell * lb / nbc);
-    t1 = (int)((long long)ncell * (lb + 1) / nbc);
-  }
-};
-
-// Number of blocks whose flag is set (same value in every block; read after a barrier).
-__device__ __forceinline__ int count_running(const int* running, int nb, int* s_count) {
-  if (threadIdx.x < 32) {
-    int c = 0;
-    for (int b = threadIdx.x; b < nb; b += 32) c += __ldcg(&running[b]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if (threadIdx.x == 0) *s_count = c;
-  }
-  __syncthreads();
-  return *s_count;
-}
-
-__device__ __forceinline__ void publish(double* partials, int nb, const double* v, int nv) {
-  if (threadIdx.x == 0)
-    for (int q = 0; q < nv; ++q) partials[(size_t)q * nb + blockIdx.x] = v[q];
-}
-
-// Rows of the partials: sums published before the first barrier of an iteration use rows 0-1,
-// those published before the second use rows 2-4, so a block that runs ahead never writes
-// a row that another block of its case may still be reading.
-constexpr int kRow1 = 0, kRow2 = 2;
 
 // ---------------------------------------------------------------------------------------
 // FP64 CG on the scaled system, batched.
@@ -68,10 +41,11 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
   __shared__ double bsum[8];
   __shared__ double gsum[8];
   __shared__ double sc_alpha, sc_beta, sc_igamma, sc_ialpha, sc_rr, sc_bb;
-  __shared__ int sc_it, sc_stop, s_count;
+  __shared__ int sc_it, sc_stop;
   unsigned int target = 0;
   const int NB = gridDim.x;
-  const ScaledBatchEntry& E = cases[block_case[blockIdx.x]];
+  __shared__ __align__(16) unsigned char s_entry[sizeof(ScaledBatchEntry)];
+  const ScaledBatchEntry& E = stage_entry(cases, block_case, s_entry);
   const ScaledSolve& a = E.a;
   const Geom g = a.g;
   const int nx = g.nx, P = g.pitch;
@@ -199,7 +173,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
     }
     if (threadIdx.x == 0) ctl.running[blockIdx.x] = run ? 1 : 0;
     if (!grid_sync(ctl.bar, target)) { ok = false; break; }
-    if (count_running(ctl.running, NB, &s_count) == 0) break;
+    if (!any_running(ctl.running, NB)) break;
     if (run) {
       v[0] = v[1] = v[2] = 0.0;
       phase_b(v);
@@ -247,62 +221,83 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
 // ---------------------------------------------------------------------------------------
 // Mixed-precision solve, batched.
 // ---------------------------------------------------------------------------------------
-enum { ST_ITERATE = 0, ST_REPLACE = 1, ST_FRESH = 2, ST_DONE = 3 };
+// Slots of the mixed solve; a grid barrier follows each, and the sums a slot publishes are
+// reduced after it.
+enum : int {
+  SL_FOLD = 0,    // x += D^-1/2 e / sigma, e = 0 (first pass: p = s = e = 0)
+  SL_RESID = 1,   // r64 = D^-1/2 (b - K x) and its norms
+  SL_FRESH = 2,   // r = sigma r64; Jacobi: also w = K~ r and the sums
+  SL_CHEB = 3,    // Chebyshev step j (1 .. cheb - 1) for K~ z = r (step 1 from z1 = r / theta)
+  SL_APPLY = 4,   // w = K~ u and the sums (r, u), (w, u), (r, r)
+  SL_FORM = 5,    // p = u + beta' p, s = w + beta' s and (p, s)
+  SL_UPDATE = 6,  // vector update A
+  SL_DONE = 7
+};
 
 __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatchEntry* __restrict__ cases,
                                                                 const int* __restrict__ block_case, BatchControl ctl) {
   __shared__ double red[3][kPcgThreads];
-  __shared__ float wred[2][kPcgThreads / 32];
+  __shared__ float wred[3][kPcgThreads / 32];
   __shared__ double dsum[8];
   __shared__ float fsum[8];
-  __shared__ double sc_sigma, sc_rr, sc_bb, sc_rr_ref;
+  __shared__ double sc_sigma, sc_rr, sc_bb, sc_rr_ref, sc_racc[3];
   __shared__ float sc_alpha, sc_beta, sc_pscale, sc_igamma, sc_ialpha, sc_gref, sc_gfresh;
-  __shared__ int sc_state, sc_it, sc_stop, sc_nrep, sc_rep_it, sc_keep, sc_restart, sc_final, sc_init, s_count;
+  __shared__ int sc_slot, sc_part, sc_j, sc_fresh, sc_it, sc_stop, sc_nrep, sc_rep_it, sc_keep, sc_restart, sc_final,
+      sc_init;
   unsigned int target = 0;
   const int NB = gridDim.x;
-  const MixedBatchEntry& E = cases[block_case[blockIdx.x]];
+  __shared__ __align__(16) unsigned char s_entry[sizeof(MixedBatchEntry)];
+  const MixedBatchEntry& E = stage_entry(cases, block_case, s_entry);
   const MixedSolve& A = E.a;
   const ScaledSolve& d = A.d;
   const Geom g = d.g;
-  const int nx = g.nx, P = g.pitch;
+  const int nx = g.nx;
   const int lb = blockIdx.x - E.block0, nbc = E.nblocks;
   const CaseRange ch(g.nx * g.ny, lb, nbc);
-  const int first = ch.t0 + threadIdx.x, stride = blockDim.x;
+  // The FP64 residual of a replacement costs several times an FP32 slot (its FP64 row and
+  // sums run on the narrow FP64 pipe), and every slot lasts as long as its slowest block, so
+  // while one case replaces, all others would wait.  It is therefore taken in parts of about
+  // 1024 cells per block, one part per slot (the same count in every block of the case).
+  const int nparts = min(16, max(1, (g.nx * g.ny / nbc + 1023) / 1024));
   // the FP32 phases work on aligned quads of the case's arrays (see QuadOpsF32)
   const Quads Q(g);
   const int u0 = (int)((long long)Q.nquad * lb / nbc), u1 = (int)((long long)Q.nquad * (lb + 1) / nbc);
-  const QuadOpsF32 ops{d.kinds, A.cus32, A.cvs32, (float)d.ax, (float)d.ay, P};
-  const KRow<double> K{d.cu, d.cv, d.dk, d.kind, d.creg_x, d.creg_y, d.dreg, (size_t)P};
-  const double* __restrict__ isd = d.isd;
-  double* __restrict__ x = d.x;
-  double* __restrict__ r64 = d.r;
+  const QuadOpsF32 ops{d.kinds, A.cus32, A.cvs32, (float)d.ax, (float)d.ay, g.pitch};
+  const double* __restrict__ r64 = d.r;
   float* __restrict__ r = A.r;
   float* __restrict__ w = A.w;
   float* __restrict__ p = A.p;
   float* __restrict__ s = A.s;
   float* __restrict__ e = A.e;
+  // Chebyshev preconditioner (cheb > 1): z1 = r / theta, then cheb - 1 steps alternating
+  // between zA and zB; u = M^-1 r is the last iterate.  With Jacobi u is r itself.
+  const int cheb = A.cheb > 1 ? A.cheb : 1;
+  constexpr float ith = (float)(1.0 / ChebCoef::theta);
   const double tol2 = d.tol * d.tol;
 
   if (threadIdx.x == 0) {
-    sc_state = ST_REPLACE;
+    sc_slot = SL_FOLD;
+    sc_part = 0;
     sc_init = 1;
     sc_sigma = 0.0;
     sc_bb = 0.0;
     sc_igamma = 1.0f;
     sc_pscale = 1.0f;
-    sc_it = sc_stop = sc_nrep = sc_keep = sc_restart = sc_final = 0;
+    sc_j = sc_fresh = sc_it = sc_stop = sc_nrep = sc_keep = sc_restart = sc_final = 0;
     sc_rep_it = -1000;
   }
   __syncthreads();
   bool ok = true;
-  while (ok) {
-    const int st = sc_state;
-    // ---- slot 1
-    if (st == ST_ITERATE) {
-      const float al = sc_alpha, be = sc_beta;
-      const bool keep = sc_keep != 0;
-      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.update(p, r, w, s, e, Q.k(u), al, be, keep);
-    } else if (st == ST_REPLACE) {
+  // Slot t publishes its sums in rows 3 (t & 1) .. 3 (t & 1) + 2 of the partials and its
+  // running flag in half (t & 1) of `running`: the rows a slot reads after its barrier are
+  // written again two slots later, after a barrier that every block reaches only once it has
+  // read them.
+  for (unsigned int t = 0; ok; ++t) {
+    const int sl = sc_slot, part = sc_part;
+    const bool last_part = part == nparts - 1;
+    double* prow = ctl.partials + (size_t)(3 * (t & 1)) * NB;
+    int* run = ctl.running + (size_t)(t & 1) * NB;
+    if (sl == SL_FOLD) {
       if (sc_init) {
         const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
@@ -313,133 +308,201 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
         }
       } else {
         const double isig = 1.0 / sc_sigma;
-        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) quad_fold(x, isd, e, Q.k(u), isig, true);
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) quad_fold(d.x, d.isd, e, Q.k(u), isig, true);
       }
-    } else if (st == ST_FRESH) {
-      // r = sigma r64 (FP32), w = K~ r, sums (r, r), (w, r)
-      float v[2] = {0.0f, 0.0f};
-      const double sig = sc_sigma;
-      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.stencil(r, w, r64, sig, Q.k(u), v);
-      block_sum_f32<2>(v, wred, fsum);
-      const double dv[2] = {(double)fsum[0], (double)fsum[1]};
-      publish(ctl.partials + kRow1 * NB, NB, dv, 2);
-    }
-    if (threadIdx.x == 0) ctl.running[blockIdx.x] = st != ST_DONE ? 1 : 0;
-    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
-    if (count_running(ctl.running, NB, &s_count) == 0) break;
-    if (st == ST_FRESH) {
-      double t[2];
-      range_sum<2>(ctl.partials + kRow1 * NB, NB, E.block0, nbc, t, dsum);
-      if (threadIdx.x == 0) {
-        const float gamma = (float)t[0];
-        sc_gref = gamma;
-        sc_gfresh = gamma;
-        if ((sc_it == 0 && sc_nrep == 0) || sc_restart) {
-          sc_beta = 0.0f;
-          sc_restart = 0;
-        } else {
-          sc_beta = gamma * sc_igamma;
-        }
-      }
-      __syncthreads();
-    }
-    // ---- slot 2
-    if (st == ST_ITERATE) {
-      float v[2] = {0.0f, 0.0f};
-      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.stencil(r, w, nullptr, 0.0, Q.k(u), v);
-      block_sum_f32<2>(v, wred, fsum);
-      const double dv[2] = {(double)fsum[0], (double)fsum[1]};
-      publish(ctl.partials + kRow2 * NB, NB, dv, 2);
-    } else if (st == ST_REPLACE) {
+    } else if (sl == SL_RESID) {
+      // part `part` of the block's cells: r64 = D^-1/2 (b - K x) and the norms, summed over
+      // the parts in shared memory and published with the last
+      const KRow<double> K{d.cu, d.cv, d.dk, d.kind, d.creg_x, d.creg_y, d.dreg, (size_t)g.pitch};
+      const int len = ch.t1 - ch.t0;
+      const int a0 = ch.t0 + (int)((long long)len * part / nparts);
+      const int a1 = ch.t0 + (int)((long long)len * (part + 1) / nparts);
       double v[3] = {0.0, 0.0, 0.0};
-      for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
+      for (CellWalk cw(a0 + threadIdx.x, blockDim.x, a1, nx); cw.ok(); cw.next()) {
         const size_t k = g.idx(cw.i, cw.j);
         const double bk = d.b[k];
-        const double rk = bk - K(x, k);
-        const double rs = isd[k] * rk;
-        r64[k] = rs;
+        const double rk = bk - K(d.x, k);
+        const double rs = d.isd[k] * rk;
+        d.r[k] = rs;
         v[0] += rs * rs;
         v[1] += rk * rk;
         v[2] += bk * bk;
       }
       block_sum_warps<3>(v, red, dsum);
-      publish(ctl.partials + kRow2 * NB, NB, dsum, 3);
-    } else if (st == ST_FRESH) {
-      // p = r + beta' p, s = w + beta' s with beta' = beta sigma_new / sigma_old, and (p, s)
-      const float be = sc_beta * sc_pscale;
-      float v[1] = {0.0f};
-      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) v[0] += ops.form(p, r, w, s, Q.k(u), be);
-      block_sum_f32<1>(v, wred, fsum);
-      const double dv[1] = {(double)fsum[0]};
-      publish(ctl.partials + kRow2 * NB, NB, dv, 1);
-    }
-    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
-    // ---- after the second barrier: scalars and the next state
-    if (st == ST_ITERATE) {
-      double t[2];
-      range_sum<2>(ctl.partials + kRow2 * NB, NB, E.block0, nbc, t, dsum);
       if (threadIdx.x == 0) {
-        const float gamma = (float)t[0], delta = (float)t[1];
-        sc_it += 1;
-        sc_keep = 0;
-        const double ratio = (double)gamma / (double)sc_gref;
-        int replace = (ratio <= A.drop * A.drop || sc_rr_ref * ratio <= tol2 * sc_bb) ? 1 : 0;
-        if (!replace) {
-          const float beta = gamma * sc_igamma;
-          const float den = delta - beta * gamma * sc_ialpha;
-          if (den > 0.0f && den < INFINITY) {
-            sc_beta = beta;
-            sc_alpha = gamma / den;
-            sc_igamma = 1.0f / gamma;
-            sc_ialpha = 1.0f / sc_alpha;
-          } else {
-            replace = 1;
-            sc_restart = 1;
-          }
-        }
-        if (!replace && sc_it >= d.max_iter) {
-          replace = 1;
-          sc_final = 1;
-        }
-        if (replace) {
-          sc_nrep += 1;
-          if (sc_it - sc_rep_it < 3) sc_restart = 1;
-          sc_rep_it = sc_it;
-          sc_state = ST_REPLACE;
+        for (int q = 0; q < 3; ++q) sc_racc[q] = part == 0 ? dsum[q] : sc_racc[q] + dsum[q];
+        if (last_part) publish(prow, NB, sc_racc, 3);
+      }
+    } else if (sl == SL_FRESH) {
+      const double sig = sc_sigma;
+      if (cheb == 1) {
+        // r = sigma r64 (FP32), w = K~ r, sums (r, r), (w, r)
+        float v[2] = {0.0f, 0.0f};
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.stencil(r, w, r64, sig, Q.k(u), v);
+        block_sum_f32<2>(v, wred, fsum);
+        const double dv[3] = {(double)fsum[0], (double)fsum[1], (double)fsum[0]};
+        publish(prow, NB, dv, 3);
+      } else {
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+          const int k0 = Q.k(u);
+          st4(r, k0, ld4_scaled(r64, k0, sig));
         }
       }
-    } else if (st == ST_REPLACE) {
-      double t[3];
-      range_sum<3>(ctl.partials + kRow2 * NB, NB, E.block0, nbc, t, dsum);
-      if (threadIdx.x == 0) {
-        if (sc_init) sc_bb = t[2];
-        sc_rr = t[1];
-        sc_rr_ref = t[1];
+    } else if (sl == SL_CHEB) {
+      const int j = sc_j;
+      float c1, c2;
+      cheb_step_coef(j, c1, c2);
+      float* zout = (j & 1) ? A.zB : A.zA;
+      if (j == 1) {
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.cheb_first(r, A.dch, zout, Q.k(u), ith, c1, c2);
+      } else {
+        const float* zin = (j & 1) ? A.zA : A.zB;
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.cheb_step(zin, r, A.dch, zout, Q.k(u), c1, c2);
+      }
+    } else if (sl == SL_APPLY) {
+      float v[3] = {0.0f, 0.0f, 0.0f};
+      if (cheb == 1) {
+        float v2[2] = {0.0f, 0.0f};
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.stencil(r, w, nullptr, 0.0, Q.k(u), v2);
+        v[0] = v2[0];
+        v[1] = v2[1];
+        v[2] = v2[0];
+      } else {
+        const float* uvec = (cheb & 1) ? A.zA : A.zB;
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.apply_sums(uvec, r, w, Q.k(u), v);
+      }
+      block_sum_f32<3>(v, wred, fsum);
+      const double dv[3] = {(double)fsum[0], (double)fsum[1], (double)fsum[2]};
+      publish(prow, NB, dv, 3);
+    } else if (sl == SL_FORM) {
+      // p = u + beta' p, s = w + beta' s with beta' = beta sigma_new / sigma_old, and (p, s)
+      const float be = sc_beta * sc_pscale;
+      const float* uvec = cheb == 1 ? r : ((cheb & 1) ? A.zA : A.zB);
+      float v[1] = {0.0f};
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) v[0] += ops.form(p, uvec, w, s, Q.k(u), be);
+      block_sum_f32<1>(v, wred, fsum);
+      const double dv[1] = {(double)fsum[0]};
+      publish(prow, NB, dv, 1);
+    } else if (sl == SL_UPDATE) {
+      const float al = sc_alpha, be = sc_beta;
+      const bool keep = sc_keep != 0;
+      if (cheb == 1) {
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.update(p, r, w, s, e, Q.k(u), al, be, keep);
+      } else {
+        // the same update with u = M^-1 r
+        const float* uvec = (cheb & 1) ? A.zA : A.zB;
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x)
+          ops.update_u(p, uvec, r, w, s, e, Q.k(u), al, be, keep);
+      }
+    }
+    if (threadIdx.x == 0) run[blockIdx.x] = sl != SL_DONE ? 1 : 0;
+    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
+    if (!any_running(run, NB)) break;
+    // ---- after the barrier: the slot's sums, the scalars and the next slot
+    const bool sums3 = (sl == SL_RESID && last_part) || sl == SL_APPLY || (sl == SL_FRESH && cheb == 1);
+    double t3[3] = {0.0, 0.0, 0.0};
+    if (sums3) range_sum<3>(prow, NB, E.block0, nbc, t3, dsum);
+    else if (sl == SL_FORM) {
+      double t1[1];
+      range_sum<1>(prow, NB, E.block0, nbc, t1, dsum);
+      t3[0] = t1[0];
+    }
+    if (threadIdx.x == 0) {
+      if (sl == SL_FOLD) {
+        sc_slot = SL_RESID;
+      } else if (sl == SL_RESID && !last_part) {
+        sc_part = part + 1;
+      } else if (sl == SL_RESID) {
+        sc_part = 0;
+        if (sc_init) sc_bb = t3[2];
+        sc_rr = t3[1];
+        sc_rr_ref = t3[1];
         const double old = sc_init ? 0.0 : sc_sigma;
-        sc_sigma = t[0] > 0.0 ? 1.0 / sqrt(t[0]) : 1.0;
+        sc_sigma = t3[0] > 0.0 ? 1.0 / sqrt(t3[0]) : 1.0;
+        // directions and K~ p carried over are rescaled to the new normalisation
         const double c = old > 0.0 ? sc_sigma / old : 0.0;
         sc_pscale = (float)c;
         sc_igamma = (float)((double)sc_igamma / (c * c + (c == 0.0)));
         sc_init = 0;
         if (sc_bb == 0.0 || sc_rr <= tol2 * sc_bb) {
           sc_stop = 1;
-          sc_state = ST_DONE;
+          sc_slot = SL_DONE;
         } else if (sc_final) {
           sc_stop = 2;
-          sc_state = ST_DONE;
+          sc_slot = SL_DONE;
         } else {
-          sc_state = ST_FRESH;
+          sc_fresh = 1;
+          sc_slot = SL_FRESH;
         }
-      }
-    } else if (st == ST_FRESH) {
-      double t[1];
-      range_sum<1>(ctl.partials + kRow2 * NB, NB, E.block0, nbc, t, dsum);
-      if (threadIdx.x == 0) {
-        sc_alpha = sc_gfresh / (float)t[0];
+      } else if (sl == SL_FRESH && cheb > 1) {
+        sc_j = 1;
+        sc_slot = SL_CHEB;
+      } else if (sl == SL_CHEB) {
+        if (sc_j + 1 < cheb) sc_j += 1;
+        else sc_slot = SL_APPLY;
+      } else if (sl == SL_FORM) {
+        sc_alpha = sc_gfresh / (float)t3[0];
         sc_igamma = 1.0f / sc_gfresh;
         sc_ialpha = 1.0f / sc_alpha;
         sc_keep = 1;
-        sc_state = ST_ITERATE;
+        sc_slot = SL_UPDATE;
+      } else if (sl == SL_UPDATE) {
+        sc_fresh = 0;
+        if (cheb > 1) {
+          sc_j = 1;
+          sc_slot = SL_CHEB;
+        } else {
+          sc_slot = SL_APPLY;
+        }
+      } else if (sums3) {
+        // SL_APPLY, or SL_FRESH with Jacobi: gamma = (r, u), delta = (w, u), (r, r)
+        const float gamma = (float)t3[0], delta = (float)t3[1], rr32 = (float)t3[2];
+        if (sc_fresh) {
+          // after a replacement: beta as usual (none at the start or after a restart), and
+          // alpha = gamma / (p, K~ p) from the formed direction
+          sc_gref = rr32;
+          sc_gfresh = gamma;
+          if ((sc_it == 0 && sc_nrep == 0) || sc_restart) {
+            sc_beta = 0.0f;
+            sc_restart = 0;
+          } else {
+            sc_beta = gamma * sc_igamma;
+          }
+          sc_slot = SL_FORM;
+        } else {
+          sc_it += 1;
+          sc_keep = 0;
+          // replace when the FP32 residual fell by `drop`, or when the estimate of the unscaled
+          // residual norm meets the tolerance
+          const double ratio = (double)rr32 / (double)sc_gref;
+          int replace = (ratio <= A.drop * A.drop || sc_rr_ref * ratio <= tol2 * sc_bb) ? 1 : 0;
+          if (!replace) {
+            // Chronopoulos-Gear: beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old)
+            const float beta = gamma * sc_igamma;
+            const float den = delta - beta * gamma * sc_ialpha;
+            if (den > 0.0f && den < INFINITY) {
+              sc_beta = beta;
+              sc_alpha = gamma / den;
+              sc_igamma = 1.0f / gamma;
+              sc_ialpha = 1.0f / sc_alpha;
+            } else {
+              replace = 1;  // loss of positivity in FP32: replace and restart
+              sc_restart = 1;
+            }
+          }
+          if (!replace && sc_it >= d.max_iter) {
+            replace = 1;
+            sc_final = 1;
+          }
+          if (replace) {
+            sc_nrep += 1;
+            if (sc_it - sc_rep_it < 3) sc_restart = 1;  // replacements back to back: no progress
+            sc_rep_it = sc_it;
+            sc_slot = SL_FOLD;
+          } else {
+            sc_slot = SL_UPDATE;
+          }
+        }
       }
     }
     __syncthreads();

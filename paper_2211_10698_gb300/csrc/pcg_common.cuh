@@ -216,146 +216,4 @@ __device__ __forceinline__ void block_sum_f32(const float (&v)[NV], float (*wred
   __syncthreads();
 }
 
-// ---------------------------------------------------------------------------------------
-// FP32 phases of the mixed solve on aligned quads of the padded arrays (padded indices
-// k0 .. k0+3 with k0 a multiple of 4; the pitch is a multiple of 32, so every row starts a
-// quad).  A row's quads span its interior cells plus the ghost and padding slots beside
-// them; those slots hold zero in every FP32 vector and stay zero (their inputs are zero and
-// their row kind is the identity), so quads are processed whole.
-// ---------------------------------------------------------------------------------------
-__device__ __forceinline__ float4 ld4(const float* a, int k) { return *reinterpret_cast<const float4*>(a + k); }
-__device__ __forceinline__ void st4(float* a, int k, float4 v) { *reinterpret_cast<float4*>(a + k) = v; }
-// (float) (sig * a[k .. k+3]) for an FP64 array (k even: two 16-byte loads)
-__device__ __forceinline__ float4 ld4_scaled(const double* a, int k, double sig) {
-  const double2 lo = *reinterpret_cast<const double2*>(a + k);
-  const double2 hi = *reinterpret_cast<const double2*>(a + k + 2);
-  return make_float4((float)(sig * lo.x), (float)(sig * lo.y), (float)(sig * hi.x), (float)(sig * hi.y));
-}
-__device__ __forceinline__ float at(const float4& v, int m) { return m == 0 ? v.x : m == 1 ? v.y : m == 2 ? v.z : v.w; }
-__device__ __forceinline__ void put(float4& v, int m, float x) {
-  if (m == 0) v.x = x; else if (m == 1) v.y = x; else if (m == 2) v.z = x; else v.w = x;
-}
-
-// Quads of a grid: nq per row, row j starting at padded index (j+1) pitch (the ghost slot of
-// i = -1); quad u of the row-major enumeration starts at k(u).
-struct Quads {
-  int nq, nquad, P;
-  __device__ Quads(const Geom& g) : nq(g.nx / 4 + 1), nquad(g.ny * (g.nx / 4 + 1)), P(g.pitch) {}
-  __device__ int k(int u) const {
-    const int j = u / nq;
-    return (j + 1) * P + 4 * (u - j * nq);
-  }
-};
-
-struct QuadOpsF32 {
-  const int8_t* kinds;
-  const float* cus;
-  const float* cvs;
-  float ax, ay;
-  int P;
-  // vector update: p = r + be p, s = w + be s (or p, s as stored when keep), e += al p,
-  // r -= al s
-  __device__ __forceinline__ void update(float* p, float* r, const float* w, float* s, float* e, int k0, float al,
-                                         float be, bool keep) const {
-    const float4 pm = ld4(p, k0), rm = ld4(r, k0), wm = ld4(w, k0), sm = ld4(s, k0), em = ld4(e, k0);
-    float4 pk = pm, sk = sm;
-    if (!keep) {
-      pk = make_float4(rm.x + be * pm.x, rm.y + be * pm.y, rm.z + be * pm.z, rm.w + be * pm.w);
-      sk = make_float4(wm.x + be * sm.x, wm.y + be * sm.y, wm.z + be * sm.z, wm.w + be * sm.w);
-      st4(p, k0, pk);
-      st4(s, k0, sk);
-    }
-    st4(e, k0, make_float4(em.x + al * pk.x, em.y + al * pk.y, em.z + al * pk.z, em.w + al * pk.w));
-    st4(r, k0, make_float4(rm.x - al * sk.x, rm.y - al * sk.y, rm.z - al * sk.z, rm.w - al * sk.w));
-  }
-  // w = K~ r on the quad and the sums (r, r), (w, r) into v.  With r64 given, r is first set
-  // from sig * r64 (read the same way at the neighbours).  All loads are issued first: kinds,
-  // r at the quad, its W/E cells and S/N quads, and the scaled coefficients (used only by cut
-  // rows).
-  __device__ __forceinline__ void stencil(float* r, float* w, const double* r64, double sig, int k0,
-                                          float (&v)[2]) const {
-    const char4 km = *reinterpret_cast<const char4*>(kinds + k0);
-    float4 rc, rs, rq;
-    float rw, re;
-    if (r64) {
-      rc = ld4_scaled(r64, k0, sig);
-      rs = ld4_scaled(r64, k0 - P, sig);
-      rq = ld4_scaled(r64, k0 + P, sig);
-      rw = (float)(sig * r64[k0 - 1]);
-      re = (float)(sig * r64[k0 + 4]);
-    } else {
-      rc = ld4(r, k0);
-      rs = ld4(r, k0 - P);
-      rq = ld4(r, k0 + P);
-      rw = r[k0 - 1];
-      re = r[k0 + 4];
-    }
-    const float4 cw = ld4(cus, k0), cs = ld4(cvs, k0), cn = ld4(cvs, k0 + P);
-    const float ce4 = cus[k0 + 4];
-    float4 wq;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int8_t kk = m == 0 ? km.x : m == 1 ? km.y : m == 2 ? km.z : km.w;
-      const float c = at(rc, m);
-      const float l = m == 0 ? rw : at(rc, m - 1);
-      const float rr = m == 3 ? re : at(rc, m + 1);
-      const float sv = at(rs, m), nv = at(rq, m);
-      const float ce = m == 3 ? ce4 : at(cw, m + 1);
-      const float wu = c - ax * (l + rr) - ay * (sv + nv);
-      const float wg = c - at(cw, m) * l - ce * rr - at(cs, m) * sv - at(cn, m) * nv;
-      const float wk = kk == 1 ? wu : (kk == 2 ? wg : c);
-      put(wq, m, wk);
-      v[0] += c * c;
-      v[1] += wk * c;
-    }
-    if (r64) st4(r, k0, rc);
-    st4(w, k0, wq);
-  }
-  // K~ z on the quad (z at the quad returned in zc), loads issued together as in stencil()
-  __device__ __forceinline__ float4 apply(const float* z, int k0, float4& zc) const {
-    const char4 km = *reinterpret_cast<const char4*>(kinds + k0);
-    zc = ld4(z, k0);
-    const float4 zs = ld4(z, k0 - P), zq = ld4(z, k0 + P);
-    const float zw = z[k0 - 1], ze = z[k0 + 4];
-    const float4 cw = ld4(cus, k0), cs = ld4(cvs, k0), cn = ld4(cvs, k0 + P);
-    const float ce4 = cus[k0 + 4];
-    float4 out;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int8_t kk = m == 0 ? km.x : m == 1 ? km.y : m == 2 ? km.z : km.w;
-      const float c = at(zc, m);
-      const float l = m == 0 ? zw : at(zc, m - 1);
-      const float rr = m == 3 ? ze : at(zc, m + 1);
-      const float sv = at(zs, m), nv = at(zq, m);
-      const float ce = m == 3 ? ce4 : at(cw, m + 1);
-      const float wu = c - ax * (l + rr) - ay * (sv + nv);
-      const float wg = c - at(cw, m) * l - ce * rr - at(cs, m) * sv - at(cn, m) * nv;
-      put(out, m, kk == 1 ? wu : (kk == 2 ? wg : c));
-    }
-    return out;
-  }
-  // the direction after a replacement: p = r + be p, s = w + be s stored; returns (p, s) on
-  // the quad
-  __device__ __forceinline__ float form(float* p, const float* r, const float* w, float* s, int k0,
-                                        float be) const {
-    const float4 pm = ld4(p, k0), rm = ld4(r, k0), wm = ld4(w, k0), sm = ld4(s, k0);
-    const float4 pk = make_float4(rm.x + be * pm.x, rm.y + be * pm.y, rm.z + be * pm.z, rm.w + be * pm.w);
-    const float4 sk = make_float4(wm.x + be * sm.x, wm.y + be * sm.y, wm.z + be * sm.z, wm.w + be * sm.w);
-    st4(p, k0, pk);
-    st4(s, k0, sk);
-    return pk.x * sk.x + pk.y * sk.y + pk.z * sk.z + pk.w * sk.w;
-  }
-};
-
-// x += D^-1/2 e * isig on the quad (1/sqrt(d) is 0 on ghost and padding slots, so x changes on
-// interior cells only); e = 0 when asked
-__device__ __forceinline__ void quad_fold(double* x, const double* isd, float* e, int k0, double isig, bool clear) {
-  const float4 em = ld4(e, k0);
-  x[k0] += isd[k0] * (double)em.x * isig;
-  x[k0 + 1] += isd[k0 + 1] * (double)em.y * isig;
-  x[k0 + 2] += isd[k0 + 2] * (double)em.z * isig;
-  x[k0 + 3] += isd[k0 + 3] * (double)em.w * isig;
-  if (clear) st4(e, k0, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
-}
-
 }  // namespace ccm

@@ -13,7 +13,11 @@
 // Rows are the unknown faces of both components; a block takes a balanced contiguous range of
 // the padded index, where faces that are not unknowns are skipped (their coefficients in the
 // unknowns' rows are 0).
-#include "pcg_common.cuh"
+//
+// k_helm_batch solves the systems of the cases of a batch in one cooperative launch: each case
+// owns a contiguous range of blocks and reduces over them only, every block passes the same
+// two barriers per iteration, and the launch ends when no case iterates.
+#include "batch_common.cuh"
 
 namespace ccm {
 
@@ -192,6 +196,168 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_helmholtz_c(HelmCSolve a
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// The same solve for the cases of a batch.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPcgThreads, 2) k_helm_batch(const HelmBatchEntry* __restrict__ cases,
+                                                               const int* __restrict__ block_case, BatchControl ctl) {
+  __shared__ double red[4][kPcgThreads];
+  __shared__ double bsum[8];
+  __shared__ double gsum[8];
+  __shared__ double sc_alpha, sc_beta, sc_igamma, sc_ialpha, sc_rr, sc_bb;
+  __shared__ int sc_it, sc_stop;
+  __shared__ __align__(16) unsigned char s_entry[sizeof(HelmBatchEntry)];
+  unsigned int target = 0;
+  const int NB = gridDim.x;
+  const HelmBatchEntry& E = stage_entry(cases, block_case, s_entry);
+  const HelmCSolve& a = E.a;
+  const Geom g = a.g;
+  const HelmRows H{a.h, g.pitch};
+  const int lb = blockIdx.x - E.block0, nbc = E.nblocks;
+  const int T0 = (int)g.idx(0, 0), T1 = (int)g.idx(g.nx, g.ny) + 1;
+  const int t0 = T0 + (int)((long long)(T1 - T0) * lb / nbc);
+  const int t1 = T0 + (int)((long long)(T1 - T0) * (lb + 1) / nbc);
+  const int8_t* __restrict__ ru = a.ru;
+  const int8_t* __restrict__ rv = a.rv;
+
+  auto phase_b = [&](double (&v)[4]) {
+    for (int k = t0 + threadIdx.x; k < t1; k += blockDim.x) {
+      if (ru[k] == R_UNKNOWN) {
+        const double w = H.row_u(a.zU, a.zV, k), r = a.rU[k], z = a.zU[k];
+        a.wU[k] = w;
+        v[0] += r * z;
+        v[1] += w * z;
+        v[2] += r * r;
+      }
+      if (rv[k] == R_UNKNOWN) {
+        const double w = H.row_v(a.zU, a.zV, k), r = a.rV[k], z = a.zV[k];
+        a.wV[k] = w;
+        v[0] += r * z;
+        v[1] += w * z;
+        v[2] += r * r;
+      }
+    }
+  };
+
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = t0 + threadIdx.x; k < t1; k += blockDim.x) {
+    if (ru[k] == R_UNKNOWN) {
+      const double b = a.bu[k], r = b - H.row_u(a.xu, a.xv, k);
+      a.rU[k] = r;
+      a.zU[k] = a.invu[k] * r;
+      a.pU[k] = 0.0;
+      a.sU[k] = 0.0;
+      v[3] += b * b;
+    }
+    if (rv[k] == R_UNKNOWN) {
+      const double b = a.bv[k], r = b - H.row_v(a.xu, a.xv, k);
+      a.rV[k] = r;
+      a.zV[k] = a.invv[k] * r;
+      a.pV[k] = 0.0;
+      a.sV[k] = 0.0;
+      v[3] += b * b;
+    }
+  }
+  bool ok = grid_sync(ctl.bar, target);
+  if (ok) {
+    phase_b(v);
+    block_sum_warps<4>(v, red, bsum);
+    publish(ctl.partials, NB, bsum, 4);
+    ok = grid_sync(ctl.bar, target);
+  }
+  if (ok) {
+    double t[4];
+    range_sum<4>(ctl.partials, NB, E.block0, nbc, t, gsum);
+    if (threadIdx.x == 0) {
+      const double gamma = t[0], delta = t[1];
+      sc_rr = t[2];
+      sc_bb = t[3];
+      sc_it = 0;
+      sc_stop = (sc_bb == 0.0 || sc_rr <= a.tol * a.tol * sc_bb) ? 1 : (a.max_iter <= 0 ? 2 : 0);
+      if (sc_stop == 0) {
+        sc_igamma = recip_newton(gamma);
+        sc_alpha = gamma * recip_newton(delta);
+        sc_ialpha = delta * sc_igamma;
+        sc_beta = 0.0;
+      }
+    }
+    __syncthreads();
+  }
+  if (ok && sc_bb == 0.0)
+    for (int k = t0 + threadIdx.x; k < t1; k += blockDim.x) {
+      if (ru[k] == R_UNKNOWN) a.xu[k] = 0.0;
+      if (rv[k] == R_UNKNOWN) a.xv[k] = 0.0;
+    }
+  while (ok) {
+    const bool run = sc_stop == 0;
+    if (run) {
+      const double al = sc_alpha, be = sc_beta;
+      for (int k = t0 + threadIdx.x; k < t1; k += blockDim.x) {
+        if (ru[k] == R_UNKNOWN) {
+          const double p = a.zU[k] + be * a.pU[k], s = a.wU[k] + be * a.sU[k];
+          a.pU[k] = p;
+          a.sU[k] = s;
+          a.xu[k] += al * p;
+          const double r = a.rU[k] - al * s;
+          a.rU[k] = r;
+          a.zU[k] = a.invu[k] * r;
+        }
+        if (rv[k] == R_UNKNOWN) {
+          const double p = a.zV[k] + be * a.pV[k], s = a.wV[k] + be * a.sV[k];
+          a.pV[k] = p;
+          a.sV[k] = s;
+          a.xv[k] += al * p;
+          const double r = a.rV[k] - al * s;
+          a.rV[k] = r;
+          a.zV[k] = a.invv[k] * r;
+        }
+      }
+    }
+    // running flags are written before the first barrier and read after it; the partials
+    // before the second and after it
+    if (threadIdx.x == 0) ctl.running[blockIdx.x] = run ? 1 : 0;
+    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
+    if (!any_running(ctl.running, NB)) break;
+    if (run) {
+      v[0] = v[1] = v[2] = 0.0;
+      phase_b(v);
+      const double v3[3] = {v[0], v[1], v[2]};
+      block_sum_warps<3>(v3, red, bsum);
+      publish(ctl.partials, NB, bsum, 3);
+    }
+    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
+    if (run) {
+      double t[3];
+      range_sum<3>(ctl.partials, NB, E.block0, nbc, t, gsum);
+      if (threadIdx.x == 0) {
+        const double gamma = t[0], delta = t[1];
+        sc_rr = t[2];
+        sc_it += 1;
+        sc_stop = sc_rr <= a.tol * a.tol * sc_bb ? 1 : (sc_it >= a.max_iter ? 2 : 0);
+        if (sc_stop == 0) {
+          const double beta = gamma * sc_igamma;
+          const double den = delta - beta * gamma * sc_ialpha;
+          const double ig = recip_newton(gamma);
+          sc_beta = beta;
+          sc_alpha = gamma * recip_newton(den);
+          sc_ialpha = den * ig;
+          sc_igamma = ig;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (lb == 0 && threadIdx.x == 0) {
+    const bool conv = ok && sc_stop == 1;
+    a.out.iters[0] = ok ? sc_it : 0;
+    a.out.rr[0] = ok ? sc_rr : 0.0;
+    a.out.bb[0] = ok ? sc_bb : 0.0;
+    a.out.converged[0] = conv ? 1 : 0;
+    if (a.out.total && ok) a.out.total[0] += sc_it;
+    if (!conv && a.out.nconv) a.out.nconv[0] += 1;
+  }
+}
+
 }  // namespace
 
 cudaError_t run_helmholtz_coef(const HelmCSolve& a, cudaStream_t st) {
@@ -204,6 +370,26 @@ cudaError_t run_helmholtz_coef(const HelmCSolve& a, cudaStream_t st) {
   HelmCSolve arg = a;
   void* params[] = {&arg};
   return cudaLaunchCooperativeKernel((const void*)k_pcg_helmholtz_c, sms * per, kPcgThreads, params, 0, st);
+}
+
+}  // namespace ccm
+
+namespace ccm {
+
+int batch_helm_blocks() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_helm_batch, kPcgThreads, 0);
+  per = per > 2 ? 2 : (per < 1 ? 1 : per);
+  return sms * per;
+}
+
+cudaError_t run_helm_batch(const HelmBatchEntry* dev_cases, const int* dev_block_case, BatchControl ctl, int blocks,
+                           cudaStream_t st) {
+  cudaMemsetAsync(ctl.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
+  void* params[] = {(void*)&dev_cases, (void*)&dev_block_case, &ctl};
+  return cudaLaunchCooperativeKernel((const void*)k_helm_batch, blocks, kPcgThreads, params, 0, st);
 }
 
 }  // namespace ccm

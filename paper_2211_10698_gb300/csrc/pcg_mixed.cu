@@ -24,7 +24,7 @@
 // is the identity), so a quad is processed whole, without masks.  Blocks take balanced
 // contiguous ranges of quads; on the 1024x512 grid a thread holds at most one quad, so every
 // FP32 phase needs a single round of loads.  The FP64 residual of a replacement walks cells.
-#include "pcg_common.cuh"
+#include "pcg_quad.cuh"
 
 namespace ccm {
 
@@ -78,7 +78,6 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
   const int u1 = (int)((long long)Q.nquad * (blockIdx.x + 1) / gridDim.x);
   const QuadOpsF32 ops{d.kinds, a.cus32, a.cvs32, (float)d.ax, (float)d.ay, P};
   const int first = ch.t0 + threadIdx.x, stride = blockDim.x;
-  const KRow<double> K{d.cu, d.cv, d.dk, d.kind, d.creg_x, d.creg_y, d.dreg, (size_t)P};
   const double* __restrict__ isd = d.isd;
   double* __restrict__ x = d.x;
   double* __restrict__ r64 = d.r;  // scaled FP64 residual D^-1/2 (b - K x) at a replacement
@@ -92,12 +91,12 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
   // iteration for K~ z = r, alternating between zA and zB; u = M^-1 r is the last iterate.
   // With Jacobi (cheb = 1) u is r itself.
   const int cheb = a.cheb > 1 ? a.cheb : 1;
-  float* __restrict__ uvec = cheb == 1 ? r : ((cheb & 1) ? a.zA : a.zB);
-  const float ith = (float)(1.0 / ChebCoef::theta);
+  constexpr float ith = (float)(1.0 / ChebCoef::theta);
   const double tol2 = d.tol * d.tol;
 
   // R2 (and the start): r64 = D^-1/2 (b - K x); sums ||r64||^2, ||b - K x||^2 (and ||b||^2).
   auto residual64 = [&](bool with_b) -> bool {
+    const KRow<double> K{d.cu, d.cv, d.dk, d.kind, d.creg_x, d.creg_y, d.dreg, (size_t)P};
     double v[3] = {0.0, 0.0, 0.0};
     for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
       const size_t k = g.idx(cw.i, cw.j);
@@ -134,27 +133,19 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
     __syncthreads();
     return true;
   };
-  // The Chebyshev steps 2 .. cheb (Saad, Chebyshev acceleration; eigenvalue interval of the
-  // scaled operator as in ChebCoef): d = c1 d + c2 (r - K~ z), z_next = z + d, a grid barrier
-  // after each (the next step and phase B read the neighbours).
+  // The Chebyshev steps 1 .. cheb - 1 (Saad, Chebyshev acceleration; eigenvalue interval of
+  // the scaled operator as in ChebCoef), a grid barrier after each (the next step and phase
+  // B read the neighbours).  Step 1 starts from z1 = d1 = r / theta, formed from r on the fly.
   auto cheb_steps = [&]() -> bool {
-    const double sig1 = ChebCoef::theta / ChebCoef::delta;
-    double rho_prev = 1.0 / sig1;
     for (int j = 1; j < cheb; ++j) {
-      const double rho = 1.0 / (2.0 * sig1 - rho_prev);
-      const float c1 = (float)(rho * rho_prev), c2 = (float)(2.0 * rho / ChebCoef::delta);
-      rho_prev = rho;
-      const float* zin = (j & 1) ? a.zA : a.zB;
+      float c1, c2;
+      cheb_step_coef(j, c1, c2);
       float* zout = (j & 1) ? a.zB : a.zA;
-      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-        const int k0 = Q.k(u);
-        float4 zc;
-        const float4 kz = ops.apply(zin, k0, zc);
-        const float4 rq = ld4(r, k0), dq = ld4(a.dch, k0);
-        const float4 dn = make_float4(c1 * dq.x + c2 * (rq.x - kz.x), c1 * dq.y + c2 * (rq.y - kz.y),
-                                      c1 * dq.z + c2 * (rq.z - kz.z), c1 * dq.w + c2 * (rq.w - kz.w));
-        st4(a.dch, k0, dn);
-        st4(zout, k0, make_float4(zc.x + dn.x, zc.y + dn.y, zc.z + dn.z, zc.w + dn.w));
+      if (j == 1) {
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.cheb_first(r, a.dch, zout, Q.k(u), ith, c1, c2);
+      } else {
+        const float* zin = (j & 1) ? a.zA : a.zB;
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.cheb_step(zin, r, a.dch, zout, Q.k(u), c1, c2);
       }
       if (!grid_sync(d.bar, target)) return false;
     }
@@ -162,7 +153,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
   };
   // Phase B: w = K~ u (FP32) and the sums gamma = (r, u), delta = (w, u), (r, r).  With `fresh`,
   // r is first set from the FP64 residual, r = sigma r64: with Jacobi it is read at the
-  // neighbours the same way; with Chebyshev z1 = r / theta is formed and the steps run first.
+  // neighbours the same way; with Chebyshev it is stored and the steps run first.
   auto phase_b = [&](bool fresh) -> bool {
     float v[3] = {0.0f, 0.0f, 0.0f};
     const double sig = sc_sigma;
@@ -177,25 +168,13 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
       if (fresh) {
         for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
           const int k0 = Q.k(u);
-          const float4 rc = ld4_scaled(r64, k0, sig);
-          const float4 z1 = make_float4(rc.x * ith, rc.y * ith, rc.z * ith, rc.w * ith);
-          st4(r, k0, rc);
-          st4(a.zA, k0, z1);
-          st4(a.dch, k0, z1);
+          st4(r, k0, ld4_scaled(r64, k0, sig));
         }
         if (!grid_sync(d.bar, target)) return false;
       }
       if (!cheb_steps()) return false;
-      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-        const int k0 = Q.k(u);
-        float4 uc;
-        const float4 wq = ops.apply(uvec, k0, uc);
-        const float4 rq = ld4(r, k0);
-        st4(w, k0, wq);
-        v[0] += rq.x * uc.x + rq.y * uc.y + rq.z * uc.z + rq.w * uc.w;
-        v[1] += wq.x * uc.x + wq.y * uc.y + wq.z * uc.z + wq.w * uc.w;
-        v[2] += rq.x * rq.x + rq.y * rq.y + rq.z * rq.z + rq.w * rq.w;
-      }
+      const float* uvec = (cheb & 1) ? a.zA : a.zB;
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.apply_sums(uvec, r, w, Q.k(u), v);
     }
     block_sum_f32<3>(v, wred, fsum);
     if (threadIdx.x == 0) {
@@ -265,6 +244,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
   auto phase_p = [&]() -> bool {
     const float be = sc_beta * sc_pscale;
     float v[1] = {0.0f};
+    const float* uvec = cheb == 1 ? r : ((cheb & 1) ? a.zA : a.zB);
     for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) v[0] += ops.form(p, uvec, w, s, Q.k(u), be);
     // row 3 of the FP32 partials: rows 0-2 (the sums of phase B) may still be read by other
     // blocks, since no barrier separates that read from this write
@@ -323,25 +303,10 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
       if (cheb == 1) {
         for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.update(p, r, w, s, e, Q.k(u), al, be, keep);
       } else {
-        // the same update with u = M^-1 r, and the first Chebyshev step z1 = d = r / theta
-        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-          const int k0 = Q.k(u);
-          const float4 pm = ld4(p, k0), um = ld4(uvec, k0), wm = ld4(w, k0), sm = ld4(s, k0), em = ld4(e, k0);
-          const float4 rm = ld4(r, k0);
-          float4 pk = pm, sk = sm;
-          if (!keep) {
-            pk = make_float4(um.x + be * pm.x, um.y + be * pm.y, um.z + be * pm.z, um.w + be * pm.w);
-            sk = make_float4(wm.x + be * sm.x, wm.y + be * sm.y, wm.z + be * sm.z, wm.w + be * sm.w);
-            st4(p, k0, pk);
-            st4(s, k0, sk);
-          }
-          st4(e, k0, make_float4(em.x + al * pk.x, em.y + al * pk.y, em.z + al * pk.z, em.w + al * pk.w));
-          const float4 rn = make_float4(rm.x - al * sk.x, rm.y - al * sk.y, rm.z - al * sk.z, rm.w - al * sk.w);
-          st4(r, k0, rn);
-          const float4 z1 = make_float4(rn.x * ith, rn.y * ith, rn.z * ith, rn.w * ith);
-          st4(a.zA, k0, z1);
-          st4(a.dch, k0, z1);
-        }
+        // the same update with u = M^-1 r
+        const float* uvec = (cheb & 1) ? a.zA : a.zB;
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x)
+          ops.update_u(p, uvec, r, w, s, e, Q.k(u), al, be, keep);
       }
     }
     if (!grid_sync(d.bar, target)) { ok = false; break; }
