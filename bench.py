@@ -304,11 +304,22 @@ def _measure_case(torch, stream, flush, case, steps, warmup, precision=None, pre
     g.read_stats()
     ms = _timed_steps(torch, stream, lambda: g.step_async(1), steps, flush)
     st = g.read_stats(allow_not_converged=True)
+    plan = _plan_dict(g)
     g.close()
     t = sum(ms)
     return dict(value=case.cells * steps / (t * 1e-3), unit=UNIT, ms_per_step=t / steps, steps=steps,
                 poisson_iters_per_step=st["iters_p"] / steps, helmholtz_iters_per_step=st["iters_h"] / steps,
-                last_rel_res_p=st["last_res_p"], converged=bool(st["converged"]))
+                last_rel_res_p=st["last_res_p"], converged=bool(st["converged"]), launch_plan=plan)
+
+
+def _plan_dict(g):
+    """The launch shape the set-up autotuner chose for the case's Poisson solve."""
+    tx, ty, nbx, ntiles, mb = g.launch_plan()
+    if tx:
+        return dict(kind="tiles", tile=[tx, ty], tiles=ntiles)
+    if mb:
+        return dict(kind="blocks", blocks=mb)
+    return dict(kind="built-in")
 
 
 def measure_configs(torch, stream, flush):
@@ -423,6 +434,7 @@ def run_ours(args):
     g.set_field(ccm.CCM_F_U, g.get_field(ccm.CCM_F_U) + pu)
     g.set_field(ccm.CCM_F_V, g.get_field(ccm.CCM_F_V) + pv)
     g.step(args.warmup)
+    launch_plan = _plan_dict(g)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     g.enable_kernel_timing(True)
@@ -540,7 +552,8 @@ def run_ours(args):
                     config=dict(workload=WORKLOAD, nx=case.nx, ny=case.ny, cells=case.cells, precision="fp64",
                                 precond="jacobi", tol_p=case.tol_p, tol_h=case.tol_h, parallelism=f"replicas{world}",
                                 l2="flushed between timed steps (256 MiB write, outside the step events)",
-                                poisson_iters_per_step=iters_p, helmholtz_iters_per_step=iters_h),
+                                poisson_iters_per_step=iters_p, helmholtz_iters_per_step=iters_h,
+                                launch_plan=launch_plan),
                     roofline=roof, roofline_detail=roof_alt, cpu_baseline=cpu,
                     e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes,
                              steps=args.e2e_steps),

@@ -81,6 +81,11 @@ typedef struct {
   double replace_drop;        /* MIXED, Jacobi, nonsingular (one-launch solve): reduction of the
                                  FP32 residual that triggers an FP64 residual replacement
                                  (0 selects 0.5) */
+  int autotune;               /* 1: set_geometry times candidate launch shapes of the case's
+                                 one-launch Poisson solve (FP64 Jacobi: the tile plan; MIXED: the
+                                 block count) on a short scratch solve and keeps the fastest,
+                                 cached per grid size for the process; 0: the built-in plan.
+                                 Batched solves (ccm_batch_*) do not use it. */
   ccm_alloc_fn alloc;
   ccm_free_fn free;
   void* alloc_ctx;
@@ -154,6 +159,12 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out);
 
 /* Device memory a case with this configuration will hold (for admission control). */
 ccm_status ccm_case_bytes(const ccm_config* cfg, size_t* bytes);
+
+/* The launch shape of the case's one-launch Poisson solve: plan[0..3] = tile width, tile
+ * height, tiles per row and tiles of the FP64 one-barrier solve (0 where it does not apply or
+ * the built-in plan is used), plan[4] = blocks of the mixed solve (0: built-in).  Valid after
+ * set_geometry. */
+ccm_status ccm_launch_plan(ccm_case c, int plan[5]);
 
 /* Release every resource of the case (NULL is accepted). */
 ccm_status ccm_destroy_case(ccm_case c);

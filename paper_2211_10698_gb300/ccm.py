@@ -40,7 +40,7 @@ class ccm_config(Structure):
                 ("precision", c_int), ("precond", c_int), ("cheb_degree", c_int),
                 ("tol_p", c_double), ("tol_h", c_double), ("tol_inner", c_double),
                 ("max_iter_p", c_int), ("max_iter_h", c_int), ("literal_offdiag", c_int), ("pressure_update", c_int),
-                ("replace_drop", c_double),
+                ("replace_drop", c_double), ("autotune", c_int),
                 ("alloc", ccm_alloc_fn), ("free", ccm_free_fn), ("alloc_ctx", c_void_p),
                 ("stream", c_void_p)]
 
@@ -106,6 +106,7 @@ def lib():
             "ccm_batch_size": (c_int, [cp]),
             "ccm_batch_step": (c_int, [cp, c_int, POINTER(ccm_step_stats)]),
             "ccm_case_bytes": (c_int, [POINTER(ccm_config), POINTER(c_size_t)]),
+            "ccm_launch_plan": (c_int, [c_void_p, POINTER(c_int)]),
             "ccm_server_create": (c_int, [c_size_t, c_int, c_int, c_void_p, POINTER(c_void_p)]),
             "ccm_server_destroy": (c_int, [cp]),
             "ccm_server_submit": (c_int, [cp, POINTER(ccm_config), POINTER(ccm_geometry), c_int, POINTER(c_longlong)]),
@@ -155,6 +156,7 @@ def make_config(case, precision=None, precond=None, stream=None) -> ccm_config:
     cfg.literal_offdiag = int(case.literal_offdiag)
     cfg.pressure_update = int(getattr(case, "pressure_update", 0))
     cfg.replace_drop = float(getattr(case, "replace_drop", 0.0))
+    cfg.autotune = int(getattr(case, "autotune", 0))
     cfg.stream = stream
     return cfg
 
@@ -247,6 +249,13 @@ class Case:
         allow = (CCM_E_NOT_CONVERGED,) if allow_not_converged else ()
         _check(lib().ccm_step(self.h, n, ctypes.byref(st)), allow)
         return {f: getattr(st, f) for f, _ in ccm_step_stats._fields_}
+
+    def launch_plan(self):
+        """(tile width, tile height, tiles per row, tiles, mixed blocks) of the single-case
+        Poisson solve; zeros where the built-in shape is used."""
+        plan = (c_int * 5)()
+        _check(lib().ccm_launch_plan(self.h, plan))
+        return tuple(plan)
 
     def step_async(self, n=1):
         _check(lib().ccm_step_async(self.h, n))

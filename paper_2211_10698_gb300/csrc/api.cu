@@ -83,6 +83,7 @@ struct ccm_case_s {
   int mixed_last = 0, mixed_outer = 0, mixed_nconv = 0;
   double mixed_rr = 0.0, mixed_bb = 0.0;
   bool mixed_host = false;  // a host-driven refinement ran since the statistics were last read
+  TuneResult tune{};        // launch shape of the one-launch Poisson solve (zero: built-in)
 };
 
 namespace {
@@ -253,6 +254,8 @@ ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
     f.R[0] = c->pr; f.R[1] = c->pz2;
     f.W[0] = c->pq; f.W[1] = c->pw1;
     f.S[0] = c->pp1; f.S[1] = c->t5;
+    const TilePlan& tp = c->tune.plan;
+    f.TX = tp.TX; f.TY = tp.TY; f.nbx = tp.nbx; f.ntiles = tp.ntiles;
     CUDA_TRY(run_poisson_fused(f, c->st));
     return CCM_OK;
   }
@@ -323,6 +326,7 @@ void case_mixed_solve(ccm_case c, double* x, const double* b, MixedSolve* a) {
   a->fpartials = (float*)(c->partials + pcg_float_partials_offset());
   a->drop = c->cfg.replace_drop > 0 && c->cfg.replace_drop < 1 ? c->cfg.replace_drop : 0.5;
   a->replacements = &c->ds->nrep;
+  a->blocks = c->tune.mixed_blocks;
 }
 
 ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
@@ -383,6 +387,81 @@ ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
   c->mixed_bb = sums[1];
   if (!conv) c->mixed_nconv++;
   return check_cuda_errors("mixed Poisson solve");
+}
+
+// Launch-shape autotuning of the one-launch Poisson solve, at set-up (see tune.cu): every
+// candidate runs kTuneIters iterations of the case's own solve (tolerance 0, so all do the
+// same work) from x = 0 on a positive constant right-hand side.  x and b are the copies U*
+// and V* of the predicted velocity, outputs of each step and free at set-up; the statistics
+// the runs leave are cleared.
+constexpr int kTuneIters = 24;
+
+ccm_status autotune_poisson(ccm_case c) {
+  if (!c->cfg.autotune || c->zero_mean) return CCM_OK;
+  const bool mixed = c->cfg.precision == CCM_MIXED;
+  if (!mixed && c->cfg.precond != CCM_JACOBI) return CCM_OK;  // FP64 Chebyshev: no plan to choose
+  const Geom& g = c->g;
+  cudaStream_t st = c->st;
+  const int most = mixed ? mixed_blocks() : fused_blocks();
+  const int deg = c->cfg.precond == CCM_CHEBYSHEV ? c->cfg.cheb_degree : 1;
+  TuneResult r{};
+  if (tune_cache_get(g.nx, g.ny, c->cfg.precision, c->cfg.precond, deg, most, &r)) {
+    c->tune = r;
+    return CCM_OK;
+  }
+  double* x = c->ustar;
+  double* b = c->vstar;
+  const size_t bytes = g.count() * sizeof(double);
+  CUDA_TRY(cudaMemsetAsync(b, 0x3f, bytes, st));  // every double 0x3f3f...3f, about 4.8e-4
+  int best = -1;
+  std::vector<float> ms;
+  cudaError_t e = cudaSuccess;
+  if (mixed) {
+    const std::vector<int> cand = mixed_block_candidates(most);
+    MixedSolve a{};
+    case_mixed_solve(c, x, b, &a);
+    a.d.tol = 0.0;
+    a.d.max_iter = kTuneIters;
+    e = time_launches((int)cand.size(), [&](int k) -> cudaError_t {
+      cudaError_t me = cudaMemsetAsync(x, 0, bytes, st);
+      if (me != cudaSuccess) return me;
+      a.blocks = cand[k];
+      return run_poisson_mixed(a, st);
+    }, st, &best, &ms);
+    if (best >= 0) r.mixed_blocks = cand[best];
+  } else {
+    const std::vector<TilePlan> cand = fused_plan_candidates(g.nx, g.ny, most);
+    CaseSolveView v;
+    case_solve_view(c, &v);
+    FusedSolve f{};
+    f.a = scaled_solve_of(v, x, b, c->pz, nullptr, nullptr, c->pp0, nullptr);
+    f.a.partials = c->partials;
+    f.a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+    f.a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, nullptr, nullptr};
+    f.a.tol = 0.0;
+    f.a.max_iter = kTuneIters;
+    f.R[0] = c->pr; f.R[1] = c->pz2;
+    f.W[0] = c->pq; f.W[1] = c->pw1;
+    f.S[0] = c->pp1; f.S[1] = c->t5;
+    e = time_launches((int)cand.size(), [&](int k) -> cudaError_t {
+      cudaError_t me = cudaMemsetAsync(x, 0, bytes, st);
+      if (me != cudaSuccess) return me;
+      f.TX = cand[k].TX; f.TY = cand[k].TY; f.nbx = cand[k].nbx; f.ntiles = cand[k].ntiles;
+      return run_poisson_fused(f, st);
+    }, st, &best, &ms);
+    if (best >= 0) r.plan = cand[best];
+  }
+  if (e != cudaSuccess) return fail(CCM_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  CUDA_TRY(cudaMemsetAsync(x, 0, bytes, st));
+  CUDA_TRY(cudaMemsetAsync(b, 0, bytes, st));
+  CUDA_TRY(cudaMemsetAsync(c->ds, 0, sizeof(DevStats), st));
+  int bar_err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bar_err, c->bar_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (bar_err) return fail(CCM_E_TIMEOUT, "autotune: a device-wide barrier gave up waiting");
+  if (best >= 0) tune_cache_put(g.nx, g.ny, c->cfg.precision, c->cfg.precond, deg, most, r);
+  c->tune = r;
+  return CCM_OK;
 }
 
 ccm_status poisson_solve(ccm_case c, double* x, double* b) {
@@ -639,6 +718,18 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
   return CCM_OK;
 }
 
+ccm_status ccm_launch_plan(ccm_case c, int plan[5]) {
+  g_last_error.clear();
+  if (!c || !plan) return fail(CCM_E_INVALID, "null argument");
+  if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
+  plan[0] = c->tune.plan.TX;
+  plan[1] = c->tune.plan.TY;
+  plan[2] = c->tune.plan.nbx;
+  plan[3] = c->tune.plan.ntiles;
+  plan[4] = c->tune.mixed_blocks;
+  return CCM_OK;
+}
+
 ccm_status ccm_case_bytes(const ccm_config* cfg, size_t* bytes) {
   if (!cfg || !bytes || cfg->nx < 4 || cfg->ny < 4) return fail(CCM_E_INVALID, "bad configuration");
   ccm_case_s tmp;
@@ -722,7 +813,7 @@ ccm_status ccm_set_geometry(ccm_case c, const ccm_geometry* geo) {
   c->cur = 0;
   c->nstep = 0;
   c->geometry = true;
-  return CCM_OK;
+  return autotune_poisson(c);
 }
 
 static double* field_ptr(ccm_case c, int field) {

@@ -2,7 +2,9 @@
 // solver kernels and the launchers each .cu file provides.
 #pragma once
 
+#include <functional>
 #include <string>
+#include <vector>
 
 #include "ccm_internal.cuh"
 
@@ -104,6 +106,25 @@ struct FusedSolve {
 };
 cudaError_t run_poisson_fused(FusedSolve f, cudaStream_t st);
 void fused_tiles(int nx, int ny, int blocks, int* TX, int* TY, int* nbx, int* ntiles);
+int fused_blocks();
+
+// Launch-shape autotuner (tune.cu).
+struct TilePlan {
+  int TX, TY, nbx, ntiles;
+};
+struct TuneResult {
+  TilePlan plan;   // FP64 one-barrier solve (TX = 0: not tuned)
+  int mixed_blocks;  // mixed one-launch solve (0: not tuned)
+};
+std::vector<TilePlan> fused_plan_candidates(int nx, int ny, int blocks);
+std::vector<int> mixed_block_candidates(int blocks);
+bool tune_cache_get(int nx, int ny, int precision, int precond, int degree, int blocks, TuneResult* r);
+void tune_cache_put(int nx, int ny, int precision, int precond, int degree, int blocks, const TuneResult& r);
+// Times launch(k) for k = 0 .. n-1 with CUDA events on st (after one untimed launch(0));
+// candidates whose launch returns cudaErrorInvalidConfiguration are skipped.  best = the
+// fastest index, ms = the times (-1 where skipped).
+cudaError_t time_launches(int n, const std::function<cudaError_t(int)>& launch, cudaStream_t st, int* best,
+                          std::vector<float>* ms);
 
 // Mixed-precision solve of the same system: FP32 CG on K~ with FP64 residual replacements.
 // d.r serves as the FP64 residual; d.xs, d.w, d.p, d.s are unused.
@@ -113,10 +134,12 @@ struct MixedSolve {
   float *r, *w, *p, *s, *e;   // FP32 residual, K~ u, direction, K~ p, correction
   int cheb;                   // 1: Jacobi (u = r); k > 1: k-step Chebyshev preconditioner
   float *zA, *zB, *dch;       // Chebyshev iterates and direction (cheb > 1)
-  float* fpartials;           // 3 x blocks
+  float* fpartials;           // 4 x blocks
   double drop;                // FP32 residual reduction that triggers a replacement
   int* replacements;          // out: FP64 replacements made
+  int blocks;                 // single-case launch size (0: two blocks per SM)
 };
+int mixed_blocks();
 cudaError_t run_poisson_mixed(const MixedSolve& a, cudaStream_t st);
 
 // One case of a batched solve and its contiguous range of blocks (pcg_batch.cu).

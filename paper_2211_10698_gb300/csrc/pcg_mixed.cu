@@ -347,16 +347,22 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
 
 }  // namespace
 
-cudaError_t run_poisson_mixed(const MixedSolve& a, cudaStream_t st) {
+int mixed_blocks() {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_poisson_mixed, kPcgThreads, 0);
   per = per > 2 ? 2 : (per < 1 ? 1 : per);
+  return sms * per;
+}
+
+cudaError_t run_poisson_mixed(const MixedSolve& a, cudaStream_t st) {
+  const int most = mixed_blocks();
+  const int blocks = a.blocks > 0 && a.blocks <= most ? a.blocks : most;
   cudaMemsetAsync(a.d.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
   MixedSolve arg = a;
   void* params[] = {&arg};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg_poisson_mixed, sms * per, kPcgThreads, params, 0, st);
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_poisson_mixed, blocks, kPcgThreads, params, 0, st);
 }
 
 }  // namespace ccm

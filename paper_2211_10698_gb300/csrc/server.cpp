@@ -120,6 +120,7 @@ ccm_status ccm_server_submit(ccm_server s, const ccm_config* cfg, const ccm_geom
   r->id = s->next_id++;
   r->cfg = *cfg;
   r->cfg.stream = s->stream;
+  r->cfg.autotune = 0;  // requests advance in batches, which do not use the single-case launch plan
   r->geo = *geo;
   r->nsteps = nsteps;
   r->t_submit = now_s();

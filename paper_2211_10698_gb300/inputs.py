@@ -87,6 +87,7 @@ class Case:
     literal_offdiag: int = 0
     pressure_update: int = 0       # volume in the pressure-update correction: 0 hx*hy, 1 V_p, 2 none
     replace_drop: float = 0.5      # mixed one-launch solve: FP32 residual drop per FP64 replacement
+    autotune: int = 1              # time launch shapes of the single-case Poisson solve at set-up
 
     @property
     def hx(self) -> float:
@@ -177,7 +178,7 @@ def batch_cases(n: int = 64, seed: int = SEED, steps: int = 500,
             lref = 1.0
         out.append(make_case(f"batch{k:03d}", nx, ny, (-2.0, 6.0, -2.0, 2.0), geom, re=re,
                              cfl=0.5, lref=lref, steps=steps, precision="mixed",
-                             precond="chebyshev", seed=seed + k))
+                             precond="chebyshev", seed=seed + k, autotune=0))
     return out
 
 

@@ -1,0 +1,68 @@
+"""Launch-shape autotuner of the single-case Poisson solve: the chosen tile plan (FP64) or
+block count (mixed) is a valid shape, the solve with it gives the fields of the built-in
+shape within the solver tolerances, and the choice is cached per grid size."""
+import numpy as np
+import pytest
+
+from paper_2211_10698_gb300 import ccm, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2211_10698_gb300 import build
+
+    build.build()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _case(nx, ny, precision, autotune, precond="jacobi"):
+    c = I.small_cylinder(nx=nx, ny=ny, box=(-2.0, 6.0, -2.0, 2.0), r=0.5, cx=0.0, cy=0.0)
+    c.precision, c.precond, c.autotune = precision, precond, autotune
+    c.tol_p = 1e-12
+    c.tol_h = 1e-13
+    return c
+
+
+@pytest.mark.parametrize("nx,ny", [(128, 64), (61, 20), (300, 36)])
+def test_fp64_tile_plan(nx, ny):
+    tuned = ccm.Case(_case(nx, ny, "fp64", 1))
+    plain = ccm.Case(_case(nx, ny, "fp64", 0))
+    tx, ty, nbx, ntiles, mb = tuned.launch_plan()
+    assert tx in (32, 64, 128, 256, 512) and ty >= 1 and mb == 0
+    assert nbx == -(-nx // tx) and ntiles == nbx * -(-ny // ty)
+    assert plain.launch_plan() == (0, 0, 0, 0, 0)
+    # the same size again: the cached plan
+    assert ccm.Case(_case(nx, ny, "fp64", 1)).launch_plan() == (tx, ty, nbx, ntiles, mb)
+    st_t = tuned.step(3)
+    st_p = plain.step(3)
+    assert st_t["converged"] and st_p["converged"]
+    for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P):
+        assert _rel(tuned.get_field(f), plain.get_field(f)) < 1e-9, f
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "chebyshev"])
+def test_mixed_block_count(precond):
+    tuned = ccm.Case(_case(160, 64, "mixed", 1, precond))
+    plain = ccm.Case(_case(160, 64, "mixed", 0, precond))
+    plan = tuned.launch_plan()
+    assert plan[:4] == (0, 0, 0, 0)
+    most = plan[4]
+    assert most >= 1
+    st_t = tuned.step(3)
+    st_p = plain.step(3)
+    assert st_t["converged"] and st_p["converged"]
+    for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P):
+        assert _rel(tuned.get_field(f), plain.get_field(f)) < 1e-8, f
+
+
+def test_singular_and_fp64_chebyshev_keep_builtin_shape():
+    closed = I.small_cylinder(nx=37, ny=23, box=(-1.5, 1.5, -1.0, 1.0), r=0.41, cx=0.07, cy=-0.05,
+                              bc=I.closed_box_bc(lid=1.0), re=50.0)
+    closed.autotune = 1
+    assert ccm.Case(closed).launch_plan() == (0, 0, 0, 0, 0)
+    assert ccm.Case(_case(64, 32, "fp64", 1, "chebyshev")).launch_plan() == (0, 0, 0, 0, 0)
