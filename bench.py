@@ -360,6 +360,7 @@ def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=1):
     t = sum(ms)
     its = [st["last_iters_p"] for st in last[-1]]
     conv = all(st["converged"] for sts in last for st in sts)
+    graph_steps = b.graph_steps()
     b.close()
     for c in cases:
         c.close()
@@ -367,9 +368,10 @@ def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=1):
     return dict(workload=f"batch of {ncases} cases ({cells} cells)", precision="mixed", cells=cells,
                 value=cells * steps / (t * 1e-3), unit=UNIT, ms_per_step=t / steps, steps=steps,
                 precond=", ".join(pcs), poisson_iters_last_step={"max": max(its), "mean": sum(its) / len(its)},
-                converged=conv,
+                converged=conv, graph_steps=graph_steps,
                 note="every stage of a step is one launch for all cases: explicit stages, the Helmholtz "
-                     "solves and the Poisson solves (cooperative)")
+                     "solves and the Poisson solves (cooperative); steps after the first replay captured "
+                     "CUDA graphs")
 
 
 def measure_serving(precision, nreq=16, step_div=200, budget_gb=150.0, max_batch=64, chunk=5):

@@ -250,12 +250,16 @@ ccm_status ccm_solve_pressure_noalloc(ccm_case c, const double* rhs_dev, double*
 
 /* ---- Batches: independent cases advanced together -------------------------------------
  * Serving form of the step (the paper has one case at a time).  Every case of a batch must
- * use the batch's stream and the same precision setting.  Per step, each case's explicit
- * stages and Helmholtz solve run case by case; one cooperative launch then solves the Poisson
- * systems of all cases (FP64 Jacobi-PCG, or for MIXED the FP64 refinement with batched FP32
- * inner solves), each case on a range of blocks sized to its expected work; then each case's
- * projection runs.  A batch holds at most as many cases as the GPU holds PCG blocks (2 per
- * SM).  Cases keep their own state and can leave and join a batch between steps. */
+ * use the batch's stream and the same precision setting.  Every stage of a step is one launch
+ * for all cases: the explicit stages (box data, predictor right-hand side, U* and the Poisson
+ * right-hand side, projection), one cooperative launch for the CN Helmholtz solves, and one
+ * for the Poisson solves (FP64 CG or the mixed solve with each case's preconditioner; with a
+ * singular case, FP64 Jacobi-PCG or the FP64 refinement with batched FP32 inner solves),
+ * each case on a range of blocks sized to its expected work.  When every case has an outflow
+ * side, steps after each case's first replay two captured CUDA graphs (one per time-level
+ * parity), recaptured when the cases change.  A batch holds at most as many cases as the GPU
+ * holds PCG blocks (2 per SM).  Cases keep their own state and can leave and join a batch
+ * between steps. */
 typedef struct ccm_batch_s* ccm_batch;
 ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out);
 ccm_status ccm_batch_destroy(ccm_batch b);
@@ -265,6 +269,11 @@ int ccm_batch_size(ccm_batch b);
 /* Advance every case of the batch nsteps steps; stats (may be NULL) receives one entry per
  * case, in the order the cases were added.  Returns the first non-OK status of any case. */
 ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats);
+/* Whether steps replay captured graphs (1, the default) or issue every launch (0).  Both give
+ * the same fields bit for bit. */
+ccm_status ccm_batch_set_graphs(ccm_batch b, int enable);
+/* Steps this batch has replayed from captured graphs. */
+ccm_status ccm_batch_graph_steps(ccm_batch b, long long* steps);
 
 /* ---- Request loop (serving) ------------------------------------------------------------
  * Flow-past-body requests wait in a FIFO queue; each round of ccm_server_run admits queued

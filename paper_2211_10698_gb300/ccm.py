@@ -105,6 +105,8 @@ def lib():
             "ccm_batch_remove": (c_int, [cp, cp]),
             "ccm_batch_size": (c_int, [cp]),
             "ccm_batch_step": (c_int, [cp, c_int, POINTER(ccm_step_stats)]),
+            "ccm_batch_set_graphs": (c_int, [cp, c_int]),
+            "ccm_batch_graph_steps": (c_int, [cp, POINTER(c_longlong)]),
             "ccm_case_bytes": (c_int, [POINTER(ccm_config), POINTER(c_size_t)]),
             "ccm_launch_plan": (c_int, [c_void_p, POINTER(c_int)]),
             "ccm_server_create": (c_int, [c_size_t, c_int, c_int, c_void_p, POINTER(c_void_p)]),
@@ -309,6 +311,14 @@ class Batch:
         allow = (CCM_E_NOT_CONVERGED,) if allow_not_converged else ()
         _check(lib().ccm_batch_step(self.h, n, arr), allow)
         return [{f: getattr(arr[i], f) for f, _ in ccm_step_stats._fields_} for i in range(len(self.cases))]
+
+    def set_graphs(self, enable=True):
+        _check(lib().ccm_batch_set_graphs(self.h, 1 if enable else 0))
+
+    def graph_steps(self):
+        n = c_longlong()
+        _check(lib().ccm_batch_graph_steps(self.h, ctypes.byref(n)))
+        return n.value
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -84,6 +85,7 @@ struct ccm_case_s {
   double mixed_rr = 0.0, mixed_bb = 0.0;
   bool mixed_host = false;  // a host-driven refinement ran since the statistics were last read
   TuneResult tune{};        // launch shape of the one-launch Poisson solve (zero: built-in)
+  unsigned long long serial = 0;  // unique per case for the life of the process
 };
 
 namespace {
@@ -545,19 +547,24 @@ ScaledSolve scaled_solve_of(const CaseSolveView& v, double* x, const double* b, 
   return a;
 }
 
-// The case's arrays for the batched explicit stages of its next step (csrc/batch.cu).
-void case_stage_case(ccm_case c, StageCase* e) {
-  const int prev = c->cur, next = 1 - c->cur;
+// The case's arrays for the batched explicit stages of its next step (ahead = 0) or of the
+// step after it (ahead = 1: the two time levels of conv swapped) (csrc/batch.cu).
+void case_stage_case(ccm_case c, StageCase* e, int ahead) {
+  const int cur = c->cur ^ (ahead & 1);
+  const int prev = cur, next = 1 - cur;
   StageCase a{};
   a.c = c->cv; a.g = c->g; a.bc = c->bc; a.ph = c->ph;
   a.u = c->u; a.v = c->v; a.p = c->p; a.phi = c->phi;
   a.cpu = c->cnu[prev]; a.cpv = c->cnv[prev]; a.cnu = c->cnu[next]; a.cnv = c->cnv[next];
   a.ru = c->rhs_u; a.rv = c->rhs_v;
   a.ustar = c->ustar; a.vstar = c->vstar; a.div = c->div; a.rhs = c->rhs_p;
-  a.first = c->nstep == 0 ? 1 : 0;
+  a.first = c->nstep + ahead == 0 ? 1 : 0;
   stage_case_blocks(c->g, &a.gx);
   *e = a;
 }
+int case_cur(ccm_case c) { return c->cur; }
+unsigned long long case_serial(ccm_case c) { return c->serial; }
+long long case_nstep(ccm_case c) { return c->nstep; }
 void case_helm_solve(ccm_case c, HelmCSolve* a) { helm_solve_of(c, a); }
 // Host bookkeeping of a step whose stages ran batched (as stage_project does for one case).
 void case_step_done(ccm_case c) {
@@ -677,6 +684,8 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
   if (!(cfg->tol_p > 0) || !(cfg->tol_h > 0) || cfg->max_iter_p < 1 || cfg->max_iter_h < 1)
     return fail(CCM_E_INVALID, "solver tolerances and limits must be positive");
   ccm_case c = new ccm_case_s();
+  static std::atomic<unsigned long long> next_serial{1};
+  c->serial = next_serial++;
   c->cfg = *cfg;
   c->g.nx = cfg->nx;
   c->g.ny = cfg->ny;

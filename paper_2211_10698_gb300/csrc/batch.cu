@@ -48,6 +48,16 @@ struct ccm_batch_s {
   HelmBatchEntry* h_helm = nullptr;
   int* h_helm_block_case = nullptr;
   cudaEvent_t tables_done = nullptr;  // the last upload of the pinned tables has completed
+  // captured steps: graph k runs a step with stage table k (k = 1: one step ahead)
+  StageCase* stages2 = nullptr;
+  bool use_graphs = true;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  std::vector<unsigned long long> gcases;  // serials of the cases the graphs were captured for
+  std::vector<int> gcur;         // their time-level parity when graph 0 is next
+  int gphase = 0;                // the graph the next step replays
+  bool gmixed = false;
+  long long graph_steps = 0;     // steps replayed from graphs
+  cudaStream_t cap_st = nullptr; // capture runs here (the legacy default stream cannot capture)
 };
 
 namespace {
@@ -90,8 +100,24 @@ void allocate_blocks(const std::vector<ccm_case>& cs, int blocks, std::vector<in
 
 }  // namespace
 
-// One launch of k_sc_batch (FP64) or k_mixed_batch (MIXED) for all cases.
-static ccm_status batch_solve_scaled(ccm_batch b, bool mixed) {
+// Waits for the stream and turns a barrier give-up of any launch since the last check into
+// CCM_E_TIMEOUT.
+static ccm_status check_barrier(ccm_batch b, const char* what) {
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  int err = 0;
+  if ((e = cudaMemcpy(&err, b->bar_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return bfail(CCM_E_CUDA, cudaGetErrorString(e));
+  if (err) {
+    cudaMemset(b->bar_err, 0, sizeof(int));
+    return bfail(CCM_E_TIMEOUT, "a device-wide barrier gave up waiting");
+  }
+  return CCM_OK;
+}
+
+// Entries and block map of the scaled Poisson launch (k_sc_batch for FP64, k_mixed_batch for
+// MIXED), copied to the device; returns once the copies have completed.
+static ccm_status upload_poisson_tables(ccm_batch b, bool mixed) {
   const std::vector<ccm_case>& cs = b->cases;
   const int n = (int)cs.size();
   std::vector<int> b0, nb;
@@ -99,7 +125,6 @@ static ccm_status batch_solve_scaled(ccm_batch b, bool mixed) {
   std::vector<int> block_case(b->blocks);
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < nb[i]; ++k) block_case[b0[i] + k] = i;
-  BatchControl ctl{b->partials, b->running, Barrier{b->bar_count, b->bar_err, 2000000000LL}};
   cudaError_t e = cudaMemcpyAsync(b->block_case, block_case.data(), sizeof(int) * b->blocks, cudaMemcpyHostToDevice,
                                   b->st);
   std::vector<ScaledBatchEntry> es;
@@ -112,7 +137,6 @@ static ccm_status batch_solve_scaled(ccm_batch b, bool mixed) {
       es[i].nblocks = nb[i];
     }
     e = cudaMemcpyAsync(b->esc, es.data(), sizeof(ScaledBatchEntry) * n, cudaMemcpyHostToDevice, b->st);
-    if (e == cudaSuccess) e = run_scaled_batch(b->esc, b->block_case, ctl, b->blocks, b->st);
   } else if (e == cudaSuccess) {
     em.resize(n);
     for (int i = 0; i < n; ++i) {
@@ -121,19 +145,18 @@ static ccm_status batch_solve_scaled(ccm_batch b, bool mixed) {
       em[i].nblocks = nb[i];
     }
     e = cudaMemcpyAsync(b->emx, em.data(), sizeof(MixedBatchEntry) * n, cudaMemcpyHostToDevice, b->st);
-    if (e == cudaSuccess) e = run_mixed_batch(b->emx, b->block_case, ctl, b->blocks, b->st);
   }
   // the host tables must outlive the asynchronous copies
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
-  if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched Poisson solve: ") + cudaGetErrorString(e));
-  int err = 0;
-  if ((e = cudaMemcpy(&err, b->bar_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return bfail(CCM_E_CUDA, cudaGetErrorString(e));
-  if (err) {
-    cudaMemset(b->bar_err, 0, sizeof(int));
-    return bfail(CCM_E_TIMEOUT, "a device-wide barrier gave up waiting");
-  }
+  if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched Poisson tables: ") + cudaGetErrorString(e));
   return CCM_OK;
+}
+
+// One cooperative launch solves every case's Poisson system (tables already on the device).
+static cudaError_t launch_poisson_scaled(ccm_batch b, bool mixed) {
+  BatchControl ctl{b->partials, b->running, Barrier{b->bar_count, b->bar_err, 2000000000LL}};
+  return mixed ? run_mixed_batch(b->emx, b->block_case, ctl, b->blocks, b->st)
+               : run_scaled_batch(b->esc, b->block_case, ctl, b->blocks, b->st);
 }
 
 static bool all_scaled(ccm_batch b) {
@@ -248,60 +271,177 @@ static ccm_status batch_mixed(ccm_batch b) {
   return CCM_OK;
 }
 
-// The explicit stages and the Helmholtz solves of one step, batched: one launch per stage for
-// all cases (Eq. pm_prediction: box data, right-hand side, CN Helmholtz solve, box data, then
-// U* and the Poisson right-hand side cont(U*, D)).  The case tables are written to pinned
-// memory and copied to the device on the batch's stream; the previous copy must have
-// completed before the pinned tables are rewritten.
-static ccm_status batch_predict(ccm_batch b) {
+// Tables of the batched explicit stages (ahead = 0: the next step; 1: the step after it) and,
+// with `helm`, of the Helmholtz launch.  They are written to pinned memory and copied to the
+// device on the batch's stream; the previous copy must have completed before the pinned
+// tables are rewritten.
+static ccm_status upload_stage_tables(ccm_batch b, StageCase* dst, int ahead, bool helm) {
   const std::vector<ccm_case>& cs = b->cases;
   const int n = (int)cs.size();
   cudaError_t e = cudaEventSynchronize(b->tables_done);
   if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched stages: ") + cudaGetErrorString(e));
   int total = 0;
   for (int i = 0; i < n; ++i) {
-    case_stage_case(cs[i], &b->h_stages[i]);
+    case_stage_case(cs[i], &b->h_stages[i], ahead);
     b->h_starts[i] = total;
     int gx = 0;
     total += stage_case_blocks(b->h_stages[i].g, &gx);
   }
   b->h_starts[n] = total;
-  std::vector<int> b0, nb;
-  allocate_blocks(cs, b->blocks, b0, nb, false);
-  for (int i = 0; i < n; ++i) {
-    case_helm_solve(cs[i], &b->h_helm[i].a);
-    b->h_helm[i].block0 = b0[i];
-    b->h_helm[i].nblocks = nb[i];
-    for (int k = 0; k < nb[i]; ++k) b->h_helm_block_case[b0[i] + k] = i;
-  }
   cudaStream_t st = b->st;
-  if ((e = cudaMemcpyAsync(b->stages, b->h_stages, sizeof(StageCase) * n, cudaMemcpyHostToDevice, st)) ==
-          cudaSuccess &&
-      (e = cudaMemcpyAsync(b->stage_starts, b->h_starts, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st)) ==
-          cudaSuccess &&
-      (e = cudaMemcpyAsync(b->helm, b->h_helm, sizeof(HelmBatchEntry) * n, cudaMemcpyHostToDevice, st)) ==
-          cudaSuccess &&
-      (e = cudaMemcpyAsync(b->helm_block_case, b->h_helm_block_case, sizeof(int) * b->blocks,
-                           cudaMemcpyHostToDevice, st)) == cudaSuccess)
-    e = cudaEventRecord(b->tables_done, st);
-  BatchControl ctl{b->partials, b->running, Barrier{b->bar_count, b->bar_err, 2000000000LL}};
-  if (e == cudaSuccess) e = launch_stage_batch(STAGE_FILL_BC, b->stages, b->stage_starts, n, total, st);
-  if (e == cudaSuccess) e = launch_stage_batch(STAGE_PREDICT, b->stages, b->stage_starts, n, total, st);
-  if (e == cudaSuccess) e = run_helm_batch(b->helm, b->helm_block_case, ctl, b->blocks, st);
-  if (e == cudaSuccess) e = launch_stage_batch(STAGE_FILL_BC, b->stages, b->stage_starts, n, total, st);
-  if (e == cudaSuccess) e = launch_stage_batch(STAGE_DIVERGENCE, b->stages, b->stage_starts, n, total, st);
-  if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched stages: ") + cudaGetErrorString(e));
+  e = cudaMemcpyAsync(dst, b->h_stages, sizeof(StageCase) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->stage_starts, b->h_starts, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
+  if (helm && e == cudaSuccess) {
+    std::vector<int> b0, nb;
+    allocate_blocks(cs, b->blocks, b0, nb, false);
+    for (int i = 0; i < n; ++i) {
+      case_helm_solve(cs[i], &b->h_helm[i].a);
+      b->h_helm[i].block0 = b0[i];
+      b->h_helm[i].nblocks = nb[i];
+      for (int k = 0; k < nb[i]; ++k) b->h_helm_block_case[b0[i] + k] = i;
+    }
+    e = cudaMemcpyAsync(b->helm, b->h_helm, sizeof(HelmBatchEntry) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->helm_block_case, b->h_helm_block_case, sizeof(int) * b->blocks, cudaMemcpyHostToDevice,
+                          st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->tables_done, st);
+  if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched stage tables: ") + cudaGetErrorString(e));
   return CCM_OK;
 }
 
-// ... and after the Poisson solves: projection and pressure update (Eqs. pm_projection,
-// pm_update), then box data, for all cases (the stage table of the step is still on the device).
-static ccm_status batch_project(ccm_batch b) {
+// The explicit stages and the Helmholtz solves of one step, one launch per stage for all
+// cases (Eq. pm_prediction: box data, right-hand side, CN Helmholtz solve, box data, then U*
+// and the Poisson right-hand side cont(U*, D)).
+static cudaError_t launch_predict(ccm_batch b, const StageCase* tab) {
   const int n = (int)b->cases.size();
   const int total = b->h_starts[n];
-  cudaError_t e = launch_stage_batch(STAGE_PROJECT, b->stages, b->stage_starts, n, total, b->st);
-  if (e == cudaSuccess) e = launch_stage_batch(STAGE_FILL_BC, b->stages, b->stage_starts, n, total, b->st);
+  cudaStream_t st = b->st;
+  BatchControl ctl{b->partials, b->running, Barrier{b->bar_count, b->bar_err, 2000000000LL}};
+  cudaError_t e = launch_stage_batch(STAGE_FILL_BC, tab, b->stage_starts, n, total, st);
+  if (e == cudaSuccess) e = launch_stage_batch(STAGE_PREDICT, tab, b->stage_starts, n, total, st);
+  if (e == cudaSuccess) e = run_helm_batch(b->helm, b->helm_block_case, ctl, b->blocks, st);
+  if (e == cudaSuccess) e = launch_stage_batch(STAGE_FILL_BC, tab, b->stage_starts, n, total, st);
+  if (e == cudaSuccess) e = launch_stage_batch(STAGE_DIVERGENCE, tab, b->stage_starts, n, total, st);
+  return e;
+}
+
+// ... and after the Poisson solves: projection and pressure update (Eqs. pm_projection,
+// pm_update), then box data.
+static cudaError_t launch_project(ccm_batch b, const StageCase* tab) {
+  const int n = (int)b->cases.size();
+  const int total = b->h_starts[n];
+  cudaError_t e = launch_stage_batch(STAGE_PROJECT, tab, b->stage_starts, n, total, b->st);
+  if (e == cudaSuccess) e = launch_stage_batch(STAGE_FILL_BC, tab, b->stage_starts, n, total, b->st);
+  return e;
+}
+
+static void drop_graphs(ccm_batch b) {
+  for (cudaGraphExec_t& g : b->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  b->gcases.clear();
+  b->gcur.clear();
+}
+
+// Whether the captured graphs still describe the batch: the same cases (by serial number: a
+// new case can take a destroyed one's address), each at the time level the graph about to run
+// expects (a case stepped on its own in between invalidates).
+static bool graphs_valid(ccm_batch b, bool mixed) {
+  if (!b->gexec[0] || !b->gexec[1] || b->gcases.size() != b->cases.size() || b->gmixed != mixed) return false;
+  for (size_t i = 0; i < b->cases.size(); ++i)
+    if (case_serial(b->cases[i]) != b->gcases[i] || case_cur(b->cases[i]) != (b->gcur[i] ^ b->gphase)) return false;
+  return true;
+}
+
+// Captures one step with each stage table (the next step and the one after it): explicit
+// stages, Helmholtz launch, Poisson launch, projection.  The tables are uploaded once, before
+// capture; a step replays with no host work but the bookkeeping of the time levels.  If the
+// capture fails, *ok stays false, the batch stops trying (its steps issue every launch) and
+// ccm_last_error says why.
+static ccm_status capture_graphs(ccm_batch b, bool mixed, bool* ok) {
+  *ok = false;
+  drop_graphs(b);
+  ccm_status s;
+  if ((s = upload_stage_tables(b, b->stages, 0, true)) != CCM_OK) return s;
+  if ((s = upload_stage_tables(b, b->stages2, 1, false)) != CCM_OK) return s;
+  if ((s = upload_poisson_tables(b, mixed)) != CCM_OK) return s;
+  const StageCase* tab[2] = {b->stages, b->stages2};
+  if (!b->cap_st && cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    b->cap_st = nullptr;
+    cudaGetLastError();
+    return CCM_OK;
+  }
+  const cudaStream_t run_st = b->st;
+  for (int k = 0; k < 2; ++k) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      set_last_error(std::string("graph capture (steps run without graphs): ") + cudaGetErrorString(e));
+      cudaGetLastError();
+      drop_graphs(b);
+      b->use_graphs = false;  // not again for this batch
+      return CCM_OK;
+    }
+    b->st = b->cap_st;  // the launch helpers issue on b->st
+    cudaError_t le = launch_predict(b, tab[k]);
+    if (le == cudaSuccess) le = launch_poisson_scaled(b, mixed);
+    if (le == cudaSuccess) le = launch_project(b, tab[k]);
+    b->st = run_st;
+    e = cudaStreamEndCapture(b->cap_st, &graph);
+    if (le != cudaSuccess || e != cudaSuccess || !graph) {
+      set_last_error(std::string("graph capture (steps run without graphs): ") +
+                     cudaGetErrorString(le != cudaSuccess ? le : e));
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      drop_graphs(b);
+      b->use_graphs = false;  // not again for this batch
+      return CCM_OK;
+    }
+    e = cudaGraphInstantiate(&b->gexec[k], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      set_last_error(std::string("graph instantiation (steps run without graphs): ") + cudaGetErrorString(e));
+      b->gexec[k] = nullptr;
+      cudaGetLastError();
+      drop_graphs(b);
+      b->use_graphs = false;  // not again for this batch
+      return CCM_OK;
+    }
+  }
+  b->gcases.clear();
+  b->gcur.clear();
+  for (ccm_case c : b->cases) {
+    b->gcases.push_back(case_serial(c));
+    b->gcur.push_back(case_cur(c));
+  }
+  b->gphase = 0;
+  b->gmixed = mixed;
+  *ok = true;
+  return CCM_OK;
+}
+
+// One step without graphs: tables uploaded, every launch issued, the stream waited for.
+static ccm_status eager_step(ccm_batch b, bool mixed, bool scaled) {
+  ccm_status s;
+  if ((s = upload_stage_tables(b, b->stages, 0, true)) != CCM_OK) return s;
+  if (scaled && (s = upload_poisson_tables(b, mixed)) != CCM_OK) return s;
+  cudaError_t e = launch_predict(b, b->stages);
   if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched stages: ") + cudaGetErrorString(e));
+  if (scaled) {
+    if ((e = launch_poisson_scaled(b, mixed)) != cudaSuccess)
+      return bfail(CCM_E_CUDA, std::string("batched Poisson solve: ") + cudaGetErrorString(e));
+  } else if (mixed) {
+    if ((s = batch_mixed(b)) != CCM_OK) return s;
+  } else {
+    if ((s = batch_solve(b, b->cases, false)) != CCM_OK) return s;
+  }
+  if ((e = launch_project(b, b->stages)) != cudaSuccess)
+    return bfail(CCM_E_CUDA, std::string("batched stages: ") + cudaGetErrorString(e));
+  if ((s = check_barrier(b, "batched step")) != CCM_OK) return s;
   for (ccm_case c : b->cases) case_step_done(c);
   return CCM_OK;
 }
@@ -320,12 +460,12 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
     delete b;
     return bfail(CCM_E_INVALID, "a batch holds at most " + std::to_string(most) + " cases on this GPU");
   }
-  const size_t pieces[13] = {sizeof(BatchEntry<double>) * max_cases, sizeof(BatchEntry<float>) * max_cases,
+  const size_t pieces[14] = {sizeof(BatchEntry<double>) * max_cases, sizeof(BatchEntry<float>) * max_cases,
                              sizeof(ScaledBatchEntry) * max_cases, sizeof(MixedBatchEntry) * max_cases,
                              sizeof(int) * b->blocks, sizeof(double) * 6 * b->blocks, sizeof(int) * 2 * b->blocks,
                              sizeof(unsigned int) * kBarWords, sizeof(int) * 4, sizeof(StageCase) * max_cases,
                              sizeof(int) * (max_cases + 1), sizeof(HelmBatchEntry) * max_cases,
-                             sizeof(int) * b->blocks};
+                             sizeof(int) * b->blocks, sizeof(StageCase) * max_cases};
   size_t bytes = 0;
   for (size_t n : pieces) bytes += (n + 255) & ~(size_t)255;
   cudaError_t e = cudaMalloc(&b->dev, bytes);
@@ -349,6 +489,7 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
   b->stage_starts = (int*)take(sizeof(int) * (max_cases + 1));
   b->helm = (HelmBatchEntry*)take(sizeof(HelmBatchEntry) * max_cases);
   b->helm_block_case = (int*)take(sizeof(int) * b->blocks);
+  b->stages2 = (StageCase*)take(sizeof(StageCase) * max_cases);
   const size_t hbytes = sizeof(StageCase) * max_cases + sizeof(HelmBatchEntry) * max_cases +
                         sizeof(int) * (max_cases + 1) + sizeof(int) * b->blocks;
   if ((e = cudaMallocHost(&b->host_sums, sizeof(double) * 2 * max_cases)) != cudaSuccess ||
@@ -379,6 +520,8 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
 ccm_status ccm_batch_destroy(ccm_batch b) {
   if (!b) return CCM_OK;
   cudaStreamSynchronize(b->st);
+  drop_graphs(b);
+  if (b->cap_st) cudaStreamDestroy(b->cap_st);
   cudaFree(b->dev);
   cudaFreeHost(b->host_sums);
   cudaFreeHost(b->pinned);
@@ -422,23 +565,52 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
   const bool mixed = case_is_mixed(b->cases[0]);
   const bool scaled = all_scaled(b);
   ccm_status s;
-  for (int n = 0; n < nsteps; ++n) {
-    if ((s = batch_predict(b)) != CCM_OK) return s;
-    if (scaled) {
-      if ((s = batch_solve_scaled(b, mixed)) != CCM_OK) return s;
-    } else if (mixed) {
-      if ((s = batch_mixed(b)) != CCM_OK) return s;
-    } else {
-      if ((s = batch_solve(b, b->cases, false)) != CCM_OK) return s;
-    }
-    if ((s = batch_project(b)) != CCM_OK) return s;
+  int n = 0;
+  // a case's first step starts Adams-Bashforth and runs eagerly
+  bool first = false;
+  for (ccm_case c : b->cases) first = first || case_nstep(c) == 0;
+  if (nsteps > 0 && first) {
+    if ((s = eager_step(b, mixed, scaled)) != CCM_OK) return s;
+    n = 1;
   }
+  if (n < nsteps && scaled && b->use_graphs) {
+    bool ok = graphs_valid(b, mixed);
+    if (!ok && (s = capture_graphs(b, mixed, &ok)) != CCM_OK) return s;
+    if (ok) {
+      for (; n < nsteps; ++n) {
+        const cudaError_t e = cudaGraphLaunch(b->gexec[b->gphase], b->st);
+        if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+        b->gphase ^= 1;
+        b->graph_steps++;
+        for (ccm_case c : b->cases) case_step_done(c);
+      }
+      if ((s = check_barrier(b, "batch graph")) != CCM_OK) return s;
+    }
+  }
+  for (; n < nsteps; ++n)
+    if ((s = eager_step(b, mixed, scaled)) != CCM_OK) return s;
   ccm_status worst = CCM_OK;
   for (size_t i = 0; i < b->cases.size(); ++i) {
     s = case_finish(b->cases[i], stats ? &stats[i] : nullptr);
     if (s != CCM_OK && worst == CCM_OK) worst = s;
   }
   return worst;
+}
+
+ccm_status ccm_batch_set_graphs(ccm_batch b, int enable) {
+  set_last_error("");
+  if (!b) return bfail(CCM_E_INVALID, "null batch");
+  cudaStreamSynchronize(b->st);
+  b->use_graphs = enable != 0;
+  if (!b->use_graphs) drop_graphs(b);
+  return CCM_OK;
+}
+
+ccm_status ccm_batch_graph_steps(ccm_batch b, long long* steps) {
+  set_last_error("");
+  if (!b || !steps) return bfail(CCM_E_INVALID, "null argument");
+  *steps = b->graph_steps;
+  return CCM_OK;
 }
 
 }  // extern "C"

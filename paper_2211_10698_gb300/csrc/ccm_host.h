@@ -315,7 +315,10 @@ bool case_scaled_ok(ccm_case c);  // nonsingular: the scaled and mixed batched k
 void case_scaled_fp64(ccm_case c, ScaledSolve* a);
 void case_mixed_batch(ccm_case c, MixedSolve* a);
 void case_helm_solve(ccm_case c, HelmCSolve* a);
-void case_stage_case(ccm_case c, StageCase* e);
+void case_stage_case(ccm_case c, StageCase* e, int ahead);
+int case_cur(ccm_case c);
+unsigned long long case_serial(ccm_case c);  // unique per case (addresses can be reused)
+long long case_nstep(ccm_case c);
 void case_step_done(ccm_case c);
 void case_poisson_fp32(ccm_case c, PoissonSolve<float>* a);
 ccm_status case_mixed_project(ccm_case c, bool with_rhs);
