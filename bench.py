@@ -58,6 +58,8 @@ def _args():
                     help="skip the measurements that follow the headline")
     ap.add_argument("--extras", default="mixed,configs,batched,serving",
                     help="comma-separated subset of the measurements that follow the headline")
+    ap.add_argument("--batch-cases", type=int, default=64,
+                    help="cases of the batched measurement (the first N of the seeded 64-case mix)")
     return ap.parse_args()
 
 
@@ -525,7 +527,7 @@ def run_ours(args):
             extras["configs"] = {"error": str(e)}
     if rank == 0 and "batched" in want:
         try:
-            extras["batched"] = measure_batch(torch, stream, flush)
+            extras["batched"] = measure_batch(torch, stream, flush, ncases=args.batch_cases)
         except Exception as e:
             extras["batched"] = {"error": str(e)}
     if rank == 0 and "serving" in want:

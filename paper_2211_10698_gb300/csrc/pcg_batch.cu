@@ -20,7 +20,8 @@
 //   replacement    FOLD (x += D^-1/2 e / sigma), RESID (FP64 residual and its norms; the
 //                  convergence test and the new normalisation sigma), FRESH (r = sigma r64;
 //                  Jacobi: also w = K~ r and its sums; Chebyshev: then CHEB and APPLY),
-//                  FORM (p, K~ p formed and (p, K~ p) summed; then alpha)
+//                  FORM (p, K~ p formed and (p, K~ p) summed; then alpha), WAIT (idle until
+//                  the next slot where iterations start: t = 0 mod the iteration's length)
 //   DONE           idle
 // The first pass starts in FOLD with p = s = e = 0.
 #include "batch_common.cuh"
@@ -116,12 +117,12 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
     s[k] = 0.0;
     v[3] += bk * bk;
   }
-  bool ok = grid_sync(ctl.bar, target);
+  bool ok = grid_sync_lean(ctl.bar, target);
   if (ok) {
     phase_b(v);
     block_sum_warps<4>(v, red, bsum);
     publish(ctl.partials, NB, bsum, 4);
-    ok = grid_sync(ctl.bar, target);
+    ok = grid_sync_lean(ctl.bar, target);
   }
   if (ok) {
     double t[4];
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
       }
     }
     if (threadIdx.x == 0) ctl.running[blockIdx.x] = run ? 1 : 0;
-    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
+    if (!grid_sync_lean(ctl.bar, target)) { ok = false; break; }
     if (!any_running(ctl.running, NB)) break;
     if (run) {
       v[0] = v[1] = v[2] = 0.0;
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
       block_sum_warps<3>(v3, red, bsum);
       publish(ctl.partials, NB, bsum, 3);
     }
-    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
+    if (!grid_sync_lean(ctl.bar, target)) { ok = false; break; }
     if (run) {
       double t[3];
       range_sum<3>(ctl.partials, NB, E.block0, nbc, t, gsum);
@@ -231,7 +232,8 @@ enum : int {
   SL_APPLY = 4,   // w = K~ u and the sums (r, u), (w, u), (r, r)
   SL_FORM = 5,    // p = u + beta' p, s = w + beta' s and (p, s)
   SL_UPDATE = 6,  // vector update A
-  SL_DONE = 7
+  SL_DONE = 7,
+  SL_WAIT = 8     // idle until the slot where this case's iterations start (see below)
 };
 
 __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatchEntry* __restrict__ cases,
@@ -273,6 +275,13 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
   // between zA and zB; u = M^-1 r is the last iterate.  With Jacobi u is r itself.
   const int cheb = A.cheb > 1 ? A.cheb : 1;
   constexpr float ith = (float)(1.0 / ChebCoef::theta);
+  // An iteration takes `period` slots (UPDATE, the Chebyshev steps, APPLY) and starts only at
+  // slots t = 0 mod period, so the iterations of cases with the same preconditioner run in
+  // phase: their updates (the costliest slot, about 40 B per cell) share slots, and so do
+  // their cheaper Chebyshev and APPLY slots.  Out of phase, nearly every slot would hold some
+  // case's update and last as long as one.  A case that ends a replacement waits for the next
+  // start; a replacement begins right after an APPLY, so its FOLD falls on an update slot.
+  const unsigned int period = cheb > 1 ? (unsigned int)cheb + 1u : 2u;
   const double tol2 = d.tol * d.tol;
 
   if (threadIdx.x == 0) {
@@ -288,10 +297,9 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
   }
   __syncthreads();
   bool ok = true;
-  // Slot t publishes its sums in rows 3 (t & 1) .. 3 (t & 1) + 2 of the partials and its
-  // running flag in half (t & 1) of `running`: the rows a slot reads after its barrier are
-  // written again two slots later, after a barrier that every block reaches only once it has
-  // read them.
+  // Slot t publishes its sums in rows 3 (t & 1) .. 3 (t & 1) + 2 of the partials: the rows a
+  // slot reads after its barrier are written again two slots later, after a barrier that every
+  // block reaches only once it has read them.
   for (unsigned int t = 0; ok; ++t) {
     const int sl = sc_slot, part = sc_part;
     const bool last_part = part == nparts - 1;
@@ -395,9 +403,12 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
           ops.update_u(p, uvec, r, w, s, e, Q.k(u), al, be, keep);
       }
     }
-    if (threadIdx.x == 0) run[blockIdx.x] = sl != SL_DONE ? 1 : 0;
-    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
-    if (!any_running(run, NB)) break;
+    // whether any case still works is checked every fourth slot (the flags of slot t are read
+    // after its barrier and written again four slots later); a finished case idles meanwhile
+    const bool check = (t & 3u) == 3u;
+    if (check && threadIdx.x == 0) run[blockIdx.x] = sl != SL_DONE ? 1 : 0;
+    if (!grid_sync_lean(ctl.bar, target)) { ok = false; break; }
+    if (check && !any_running(run, NB)) break;
     // ---- after the barrier: the slot's sums, the scalars and the next slot
     const bool sums3 = (sl == SL_RESID && last_part) || sl == SL_APPLY || (sl == SL_FRESH && cheb == 1);
     double t3[3] = {0.0, 0.0, 0.0};
@@ -445,7 +456,9 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
         sc_igamma = 1.0f / sc_gfresh;
         sc_ialpha = 1.0f / sc_alpha;
         sc_keep = 1;
-        sc_slot = SL_UPDATE;
+        sc_slot = (t + 1) % period == 0 ? SL_UPDATE : SL_WAIT;
+      } else if (sl == SL_WAIT) {
+        if ((t + 1) % period == 0) sc_slot = SL_UPDATE;
       } else if (sl == SL_UPDATE) {
         sc_fresh = 0;
         if (cheb > 1) {
