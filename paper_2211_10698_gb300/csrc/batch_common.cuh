@@ -27,32 +27,6 @@ __device__ __forceinline__ const Entry& stage_entry(const Entry* cases, const in
   return *reinterpret_cast<const Entry*>(smem);
 }
 
-// Device-wide barrier of the batched launches: thread 0 arrives with one release add and
-// polls the counter with acquire loads (the block barriers on either side order the other
-// threads' memory accesses through thread 0), giving up after `budget` clock cycles with
-// *err raised, like grid_sync; it leaves out grid_sync's separate fences and its re-read of
-// the error flag, which cost about a microsecond per barrier.
-__device__ __forceinline__ bool grid_sync_lean(const Barrier& b, unsigned int& target) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    target += gridDim.x;
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(b.count), "r"(1u) : "memory");
-    const long long t0 = clock64();
-    while (ld_acquire_u32(b.count) < target) {
-      if (clock64() - t0 > b.budget) {
-        atomicExch(b.err, 1);
-        ok = 0;
-        break;
-      }
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // Whether any block's flag is set (the same answer in every block; read after a barrier):
 // every thread loads at most a few flags, all in flight at once, and the block ORs them.
 __device__ __forceinline__ bool any_running(const int* running, int nb) {

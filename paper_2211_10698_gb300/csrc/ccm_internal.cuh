@@ -71,9 +71,10 @@ struct Phys {
 
 // ---------------------------------------------------------------------------------------
 // Bounded device-wide barrier for cooperative (co-resident) launches.  Thread 0 of each
-// block arrives on a monotonically increasing counter and waits until all blocks of this
-// round have arrived, giving up after `budget` clock cycles; on give-up it raises *err and
-// the caller leaves the kernel.
+// block arrives on a monotonically increasing counter (one release add) and polls it with
+// acquire loads until all blocks of this round have arrived, giving up after `budget` clock
+// cycles; on give-up it raises *err and the caller leaves the kernel (the other blocks give
+// up at their own next barrier).
 // ---------------------------------------------------------------------------------------
 // Device-wide barrier of a cooperative launch: one arrival counter.
 constexpr int kBarWords = 1;  // unsigned ints behind Barrier::count
@@ -95,9 +96,11 @@ __device__ __forceinline__ bool grid_sync(const Barrier& b, unsigned int& target
   if (threadIdx.x == 0) {
     int ok = 1;
     target += gridDim.x;
-    __threadfence();
-    atomicAdd(b.count, 1u);
-    long long t0 = clock64();
+    // release: the block's writes before the block barrier above become visible with the
+    // arrival; the acquire loads below order what follows after every block's arrival (the
+    // block barrier below carries both to the other threads of the block)
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(b.count), "r"(1u) : "memory");
+    const long long t0 = clock64();
     while (ld_acquire_u32(b.count) < target) {
       if (clock64() - t0 > b.budget) {
         atomicExch(b.err, 1);
@@ -105,8 +108,6 @@ __device__ __forceinline__ bool grid_sync(const Barrier& b, unsigned int& target
         break;
       }
     }
-    if (ok && *((volatile int*)b.err) != 0) ok = 0;
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

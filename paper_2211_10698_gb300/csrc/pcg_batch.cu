@@ -117,12 +117,12 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
     s[k] = 0.0;
     v[3] += bk * bk;
   }
-  bool ok = grid_sync_lean(ctl.bar, target);
+  bool ok = grid_sync(ctl.bar, target);
   if (ok) {
     phase_b(v);
     block_sum_warps<4>(v, red, bsum);
     publish(ctl.partials, NB, bsum, 4);
-    ok = grid_sync_lean(ctl.bar, target);
+    ok = grid_sync(ctl.bar, target);
   }
   if (ok) {
     double t[4];
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
       }
     }
     if (threadIdx.x == 0) ctl.running[blockIdx.x] = run ? 1 : 0;
-    if (!grid_sync_lean(ctl.bar, target)) { ok = false; break; }
+    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
     if (!any_running(ctl.running, NB)) break;
     if (run) {
       v[0] = v[1] = v[2] = 0.0;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
       block_sum_warps<3>(v3, red, bsum);
       publish(ctl.partials, NB, bsum, 3);
     }
-    if (!grid_sync_lean(ctl.bar, target)) { ok = false; break; }
+    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
     if (run) {
       double t[3];
       range_sum<3>(ctl.partials, NB, E.block0, nbc, t, gsum);
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
     // after its barrier and written again four slots later); a finished case idles meanwhile
     const bool check = (t & 3u) == 3u;
     if (check && threadIdx.x == 0) run[blockIdx.x] = sl != SL_DONE ? 1 : 0;
-    if (!grid_sync_lean(ctl.bar, target)) { ok = false; break; }
+    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
     if (check && !any_running(run, NB)) break;
     // ---- after the barrier: the slot's sums, the scalars and the next slot
     const bool sums3 = (sl == SL_RESID && last_part) || sl == SL_APPLY || (sl == SL_FRESH && cheb == 1);

@@ -258,12 +258,12 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_helm_batch(const HelmBatchEn
       v[3] += b * b;
     }
   }
-  bool ok = grid_sync_lean(ctl.bar, target);
+  bool ok = grid_sync(ctl.bar, target);
   if (ok) {
     phase_b(v);
     block_sum_warps<4>(v, red, bsum);
     publish(ctl.partials, NB, bsum, 4);
-    ok = grid_sync_lean(ctl.bar, target);
+    ok = grid_sync(ctl.bar, target);
   }
   if (ok) {
     double t[4];
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_helm_batch(const HelmBatchEn
     // running flags are written before the first barrier and read after it; the partials
     // before the second and after it
     if (threadIdx.x == 0) ctl.running[blockIdx.x] = run ? 1 : 0;
-    if (!grid_sync_lean(ctl.bar, target)) { ok = false; break; }
+    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
     if (!any_running(ctl.running, NB)) break;
     if (run) {
       v[0] = v[1] = v[2] = 0.0;
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_helm_batch(const HelmBatchEn
       block_sum_warps<3>(v3, red, bsum);
       publish(ctl.partials, NB, bsum, 3);
     }
-    if (!grid_sync_lean(ctl.bar, target)) { ok = false; break; }
+    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
     if (run) {
       double t[3];
       range_sum<3>(ctl.partials, NB, E.block0, nbc, t, gsum);
