@@ -58,6 +58,8 @@ def _args():
                     help="skip the measurements that follow the headline")
     ap.add_argument("--extras", default="mixed,configs,batched,serving",
                     help="comma-separated subset of the measurements that follow the headline")
+    ap.add_argument("--configs", default="",
+                    help="comma-separated names of the single-case configurations to run (default: all)")
     ap.add_argument("--batch-cases", type=int, default=64,
                     help="cases of the batched measurement (the first N of the seeded 64-case mix)")
     return ap.parse_args()
@@ -324,22 +326,28 @@ def _plan_dict(g):
     return dict(kind="built-in")
 
 
-def measure_configs(torch, stream, flush):
+def measure_configs(torch, stream, flush, only=None):
     """The other single-case configurations: the 128x64 cylinder at Re 40 (FP64), and the
     2048x1024 NACA0012 at Re 1000 in the mixed setting, with its configured Chebyshev
-    preconditioner (host-driven refinement) and with the one-launch Jacobi solve."""
+    preconditioner and with Jacobi (both one-launch solves).  `only`: names to run."""
     from paper_2211_10698_gb300 import inputs
 
+    def want(name):
+        return not only or name in only
+
     out = {}
-    c1 = inputs.cylinder_re40_128x64()
-    out["cylinder_re40_128x64"] = dict(precision="fp64", **_measure_case(torch, stream, flush, c1, 20, 3))
+    if want("cylinder_re40_128x64"):
+        c1 = inputs.cylinder_re40_128x64()
+        out["cylinder_re40_128x64"] = dict(precision="fp64", **_measure_case(torch, stream, flush, c1, 20, 3))
     c3 = inputs.naca0012_re1000_2048x1024()
-    out["naca0012_re1000_2048x1024"] = dict(
-        precision="mixed", precond=f"chebyshev degree {c3.cheb_degree}",
-        **_measure_case(torch, stream, flush, c3, 2, 1))
-    out["naca0012_re1000_2048x1024_jacobi"] = dict(
-        precision="mixed", precond="jacobi (one launch, FP64 residual replacements)",
-        **_measure_case(torch, stream, flush, c3, 2, 1, precond="jacobi"))
+    if want("naca0012_re1000_2048x1024"):
+        out["naca0012_re1000_2048x1024"] = dict(
+            precision="mixed", precond=f"chebyshev degree {c3.cheb_degree}",
+            **_measure_case(torch, stream, flush, c3, 2, 1))
+    if want("naca0012_re1000_2048x1024_jacobi"):
+        out["naca0012_re1000_2048x1024_jacobi"] = dict(
+            precision="mixed", precond="jacobi (one launch, FP64 residual replacements)",
+            **_measure_case(torch, stream, flush, c3, 2, 1, precond="jacobi"))
     return out
 
 
@@ -522,7 +530,8 @@ def run_ours(args):
             extras["mixed_same_accuracy"] = {"error": str(e)}
     if rank == 0 and "configs" in want:
         try:
-            extras["configs"] = measure_configs(torch, stream, flush)
+            extras["configs"] = measure_configs(torch, stream, flush,
+                                                set(filter(None, args.configs.split(","))))
         except Exception as e:
             extras["configs"] = {"error": str(e)}
     if rank == 0 and "batched" in want:
