@@ -318,7 +318,9 @@ def _measure_case(torch, stream, flush, case, steps, warmup, precision=None, pre
 
 def _plan_dict(g):
     """The launch shape the set-up autotuner chose for the case's Poisson solve."""
-    tx, ty, nbx, ntiles, mb = g.launch_plan()
+    tx, ty, nbx, ntiles, mb, cl = g.launch_plan()
+    if cl:
+        return dict(kind="cluster", ctas=cl)
     if tx:
         return dict(kind="tiles", tile=[tx, ty], tiles=ntiles)
     if mb:

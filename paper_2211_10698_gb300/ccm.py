@@ -109,6 +109,7 @@ def lib():
             "ccm_batch_graph_steps": (c_int, [cp, POINTER(c_longlong)]),
             "ccm_case_bytes": (c_int, [POINTER(ccm_config), POINTER(c_size_t)]),
             "ccm_launch_plan": (c_int, [c_void_p, POINTER(c_int)]),
+            "ccm_set_launch_plan": (c_int, [c_void_p, POINTER(c_int)]),
             "ccm_server_create": (c_int, [c_size_t, c_int, c_int, c_void_p, POINTER(c_void_p)]),
             "ccm_server_destroy": (c_int, [cp]),
             "ccm_server_submit": (c_int, [cp, POINTER(ccm_config), POINTER(ccm_geometry), c_int, POINTER(c_longlong)]),
@@ -253,11 +254,15 @@ class Case:
         return {f: getattr(st, f) for f, _ in ccm_step_stats._fields_}
 
     def launch_plan(self):
-        """(tile width, tile height, tiles per row, tiles, mixed blocks) of the single-case
-        Poisson solve; zeros where the built-in shape is used."""
-        plan = (c_int * 5)()
+        """(tile width, tile height, tiles per row, tiles, mixed blocks, cluster CTAs) of the
+        single-case Poisson solve; zeros where the built-in shape is used."""
+        plan = (c_int * 6)()
         _check(lib().ccm_launch_plan(self.h, plan))
         return tuple(plan)
+
+    def set_launch_plan(self, plan):
+        arr = (c_int * 6)(*plan)
+        _check(lib().ccm_set_launch_plan(self.h, arr))
 
     def step_async(self, n=1):
         _check(lib().ccm_step_async(self.h, n))

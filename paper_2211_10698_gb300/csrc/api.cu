@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <string>
 #include <vector>
@@ -256,6 +257,13 @@ ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
     f.R[0] = c->pr; f.R[1] = c->pz2;
     f.W[0] = c->pq; f.W[1] = c->pw1;
     f.S[0] = c->pp1; f.S[1] = c->t5;
+    if (c->tune.cluster > 0) {
+      // small grid: the whole solve inside one thread-block cluster
+      ClusterSolve cs{};
+      cs.a = f.a;
+      CUDA_TRY(run_poisson_cluster(cs, c->tune.cluster, c->st));
+      return CCM_OK;
+    }
     const TilePlan& tp = c->tune.plan;
     f.TX = tp.TX; f.TY = tp.TY; f.nbx = tp.nbx; f.ntiles = tp.ntiles;
     CUDA_TRY(run_poisson_fused(f, c->st));
@@ -433,6 +441,8 @@ ccm_status autotune_poisson(ccm_case c) {
     if (best >= 0) r.mixed_blocks = cand[best];
   } else {
     const std::vector<TilePlan> cand = fused_plan_candidates(g.nx, g.ny, most);
+    const std::vector<int> ccand = cluster_candidates(g.nx, g.ny);
+    const int nf = (int)cand.size();
     CaseSolveView v;
     case_solve_view(c, &v);
     FusedSolve f{};
@@ -445,13 +455,19 @@ ccm_status autotune_poisson(ccm_case c) {
     f.R[0] = c->pr; f.R[1] = c->pz2;
     f.W[0] = c->pq; f.W[1] = c->pw1;
     f.S[0] = c->pp1; f.S[1] = c->t5;
-    e = time_launches((int)cand.size(), [&](int k) -> cudaError_t {
+    e = time_launches(nf + (int)ccand.size(), [&](int k) -> cudaError_t {
       cudaError_t me = cudaMemsetAsync(x, 0, bytes, st);
       if (me != cudaSuccess) return me;
+      if (k >= nf) {
+        ClusterSolve cs{};
+        cs.a = f.a;
+        return run_poisson_cluster(cs, ccand[k - nf], st);
+      }
       f.TX = cand[k].TX; f.TY = cand[k].TY; f.nbx = cand[k].nbx; f.ntiles = cand[k].ntiles;
       return run_poisson_fused(f, st);
     }, st, &best, &ms);
-    if (best >= 0) r.plan = cand[best];
+    if (best >= nf) r.cluster = ccand[best - nf];
+    else if (best >= 0) r.plan = cand[best];
   }
   if (e != cudaSuccess) return fail(CCM_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
   CUDA_TRY(cudaMemsetAsync(x, 0, bytes, st));
@@ -727,7 +743,7 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
   return CCM_OK;
 }
 
-ccm_status ccm_launch_plan(ccm_case c, int plan[5]) {
+ccm_status ccm_launch_plan(ccm_case c, int plan[6]) {
   g_last_error.clear();
   if (!c || !plan) return fail(CCM_E_INVALID, "null argument");
   if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
@@ -736,6 +752,34 @@ ccm_status ccm_launch_plan(ccm_case c, int plan[5]) {
   plan[2] = c->tune.plan.nbx;
   plan[3] = c->tune.plan.ntiles;
   plan[4] = c->tune.mixed_blocks;
+  plan[5] = c->tune.cluster;
+  return CCM_OK;
+}
+
+ccm_status ccm_set_launch_plan(ccm_case c, const int plan[6]) {
+  g_last_error.clear();
+  if (!c || !plan) return fail(CCM_E_INVALID, "null argument");
+  if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
+  TuneResult r{};
+  const Geom& g = c->g;
+  if (plan[0] != 0) {
+    const int tx = plan[0], ty = plan[1];
+    const bool pow2 = tx >= 32 && tx <= 512 && (tx & (tx - 1)) == 0;
+    const int nbx = (g.nx + tx - 1) / std::max(tx, 1);
+    if (!pow2 || ty < 1 || plan[2] != nbx || plan[3] != nbx * ((g.ny + ty - 1) / ty) || plan[3] > fused_blocks())
+      return fail(CCM_E_INVALID, "tile plan: width a power of two in 32..512, tiles = ceil(nx/w) ceil(ny/h)");
+    r.plan = TilePlan{tx, ty, plan[2], plan[3]};
+  }
+  if (plan[4] < 0 || plan[4] > mixed_blocks()) return fail(CCM_E_INVALID, "mixed blocks out of range");
+  r.mixed_blocks = plan[4];
+  if (plan[5] != 0) {
+    bool ok = false;
+    for (int C : cluster_candidates(g.nx, g.ny)) ok = ok || C == plan[5];
+    if (!ok) return fail(CCM_E_INVALID, "cluster size: 2, 4, 8 or 16 CTAs, at most ny, band in shared memory");
+    if (plan[0] != 0) return fail(CCM_E_INVALID, "a tile plan and a cluster exclude each other");
+    r.cluster = plan[5];
+  }
+  c->tune = r;
   return CCM_OK;
 }
 

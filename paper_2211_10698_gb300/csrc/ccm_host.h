@@ -108,16 +108,27 @@ cudaError_t run_poisson_fused(FusedSolve f, cudaStream_t st);
 void fused_tiles(int nx, int ny, int blocks, int* TX, int* TY, int* nbx, int* ntiles);
 int fused_blocks();
 
+// The same solve for small grids inside one thread-block cluster (pcg_cluster.cu).
+struct ClusterSolve {
+  ScaledSolve a;  // partials and bar unused
+  int nmax;       // set by the launcher: cells of the largest band
+};
+size_t cluster_smem_bytes(int nx, int ny, int C);
+// C CTAs (1..16); cudaErrorInvalidConfiguration if the grid or the GPU does not allow it
+cudaError_t run_poisson_cluster(ClusterSolve f, int C, cudaStream_t st);
+
 // Launch-shape autotuner (tune.cu).
 struct TilePlan {
   int TX, TY, nbx, ntiles;
 };
 struct TuneResult {
-  TilePlan plan;   // FP64 one-barrier solve (TX = 0: not tuned)
+  TilePlan plan;     // FP64 one-barrier solve (TX = 0: not tuned)
   int mixed_blocks;  // mixed one-launch solve (0: not tuned)
+  int cluster;       // FP64 solve inside one cluster of this many CTAs (0: not chosen)
 };
 std::vector<TilePlan> fused_plan_candidates(int nx, int ny, int blocks);
 std::vector<int> mixed_block_candidates(int blocks);
+std::vector<int> cluster_candidates(int nx, int ny);
 bool tune_cache_get(int nx, int ny, int precision, int precond, int degree, int blocks, TuneResult* r);
 void tune_cache_put(int nx, int ny, int precision, int precond, int degree, int blocks, const TuneResult& r);
 // Times launch(k) for k = 0 .. n-1 with CUDA events on st (after one untimed launch(0));

@@ -1,10 +1,11 @@
 // Launch-shape autotuner for the one-launch Poisson solves: the tile plan of the FP64 CG with
-// one barrier per iteration (pcg_fused.cu) and the block count of the mixed-precision solve
-// (pcg_mixed.cu).  Which shape is fastest depends on the grid: a large grid wants every SM
-// busy, a small one loses more to the grid barrier across many blocks than it gains from
-// them.  The caller times each candidate on a short solve of the case's own operator
-// (a fixed number of iterations on a scratch right-hand side) and keeps the fastest; results
-// are cached per grid size and solver setting for the life of the process.
+// one barrier per iteration (pcg_fused.cu) or, on small grids, the size of the one cluster
+// that holds the whole FP64 solve (pcg_cluster.cu), and the block count of the
+// mixed-precision solve (pcg_mixed.cu).  Which shape is fastest depends on the grid: a large
+// grid wants every SM busy, a small one loses more to the grid barrier across many blocks
+// than it gains from them.  The caller times each candidate on a short solve of the case's
+// own operator (a fixed number of iterations on a scratch right-hand side) and keeps the
+// fastest; results are cached per grid size and solver setting for the life of the process.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -40,6 +41,13 @@ std::vector<TilePlan> fused_plan_candidates(int nx, int ny, int blocks) {
 std::vector<int> mixed_block_candidates(int blocks) {
   std::vector<int> out;
   for (int b = blocks; b >= 1 && out.size() < 6; b /= 2) out.push_back(b);
+  return out;
+}
+
+std::vector<int> cluster_candidates(int nx, int ny) {
+  std::vector<int> out;
+  for (int C = 16; C >= 2; C /= 2)
+    if (C <= ny && cluster_smem_bytes(nx, ny, C) <= 200 * 1024) out.push_back(C);
   return out;
 }
 

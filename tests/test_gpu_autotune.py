@@ -32,12 +32,16 @@ def _case(nx, ny, precision, autotune, precond="jacobi"):
 def test_fp64_tile_plan(nx, ny):
     tuned = ccm.Case(_case(nx, ny, "fp64", 1))
     plain = ccm.Case(_case(nx, ny, "fp64", 0))
-    tx, ty, nbx, ntiles, mb = tuned.launch_plan()
-    assert tx in (32, 64, 128, 256, 512) and ty >= 1 and mb == 0
-    assert nbx == -(-nx // tx) and ntiles == nbx * -(-ny // ty)
-    assert plain.launch_plan() == (0, 0, 0, 0, 0)
+    tx, ty, nbx, ntiles, mb, cl = tuned.launch_plan()
+    assert mb == 0
+    if cl:
+        assert cl in (2, 4, 8, 16) and cl <= ny and (tx, ty, nbx, ntiles) == (0, 0, 0, 0)
+    else:
+        assert tx in (32, 64, 128, 256, 512) and ty >= 1
+        assert nbx == -(-nx // tx) and ntiles == nbx * -(-ny // ty)
+    assert plain.launch_plan() == (0, 0, 0, 0, 0, 0)
     # the same size again: the cached plan
-    assert ccm.Case(_case(nx, ny, "fp64", 1)).launch_plan() == (tx, ty, nbx, ntiles, mb)
+    assert ccm.Case(_case(nx, ny, "fp64", 1)).launch_plan() == (tx, ty, nbx, ntiles, mb, cl)
     st_t = tuned.step(3)
     st_p = plain.step(3)
     assert st_t["converged"] and st_p["converged"]
@@ -50,7 +54,7 @@ def test_mixed_block_count(precond):
     tuned = ccm.Case(_case(160, 64, "mixed", 1, precond))
     plain = ccm.Case(_case(160, 64, "mixed", 0, precond))
     plan = tuned.launch_plan()
-    assert plan[:4] == (0, 0, 0, 0)
+    assert plan[:4] == (0, 0, 0, 0) and plan[5] == 0
     most = plan[4]
     assert most >= 1
     st_t = tuned.step(3)
@@ -64,5 +68,34 @@ def test_singular_and_fp64_chebyshev_keep_builtin_shape():
     closed = I.small_cylinder(nx=37, ny=23, box=(-1.5, 1.5, -1.0, 1.0), r=0.41, cx=0.07, cy=-0.05,
                               bc=I.closed_box_bc(lid=1.0), re=50.0)
     closed.autotune = 1
-    assert ccm.Case(closed).launch_plan() == (0, 0, 0, 0, 0)
-    assert ccm.Case(_case(64, 32, "fp64", 1, "chebyshev")).launch_plan() == (0, 0, 0, 0, 0)
+    assert ccm.Case(closed).launch_plan() == (0, 0, 0, 0, 0, 0)
+    assert ccm.Case(_case(64, 32, "fp64", 1, "chebyshev")).launch_plan() == (0, 0, 0, 0, 0, 0)
+
+
+@pytest.mark.parametrize("nx,ny,ctas", [(128, 64, 16), (128, 64, 2), (61, 20, 16), (96, 40, 8), (300, 36, 4)])
+def test_cluster_solve_matches_tiled_solve(nx, ny, ctas):
+    """The FP64 solve held in one thread-block cluster (bands of rows, neighbour rows through
+    distributed shared memory) gives the fields of the tiled one-barrier solve."""
+    clus = ccm.Case(_case(nx, ny, "fp64", 0))
+    clus.set_launch_plan((0, 0, 0, 0, 0, ctas))
+    assert clus.launch_plan()[5] == ctas
+    tiled = ccm.Case(_case(nx, ny, "fp64", 0))
+    st_c = clus.step(3)
+    st_t = tiled.step(3)
+    assert st_c["converged"] and st_t["converged"]
+    assert abs(st_c["iters_p"] - st_t["iters_p"]) <= 3
+    for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P):
+        assert _rel(clus.get_field(f), tiled.get_field(f)) < 1e-9, f
+
+
+def test_launch_plan_validation():
+    c = ccm.Case(_case(128, 64, "fp64", 0))
+    for bad in [(48, 8, 3, 24, 0, 0), (64, 8, 2, 15, 0, 0), (0, 0, 0, 0, 0, 3), (0, 0, 0, 0, 0, 128),
+                (64, 8, 2, 16, 0, 8)]:
+        with pytest.raises(ccm.CcmError):
+            c.set_launch_plan(bad)
+    big = ccm.Case(_case(1024, 512, "fp64", 0))
+    with pytest.raises(ccm.CcmError):
+        big.set_launch_plan((0, 0, 0, 0, 0, 16))  # a band of 32 rows does not fit shared memory
+    c.set_launch_plan((64, 8, 2, 16, 0, 0))
+    assert c.launch_plan() == (64, 8, 2, 16, 0, 0)
