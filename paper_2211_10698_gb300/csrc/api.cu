@@ -217,7 +217,8 @@ void body_bbox(const ccm_geometry& geo, double& xa, double& xb, double& ya, doub
   xa = ya = 1e300; xb = yb = -1e300;
   for (int s = 0; s <= 2000; ++s) {
     double xi = s / 2000.0;
-    double yt = 5.0 * t * (0.2969 * sqrt(xi) - 0.1260 * xi - 0.3516 * xi * xi + 0.2843 * xi * xi * xi - 0.1036 * xi * xi * xi * xi);
+    const double x2 = xi * xi;
+    double yt = 5.0 * t * (0.2969 * sqrt(xi) - 0.1260 * xi - 0.3516 * x2 + 0.2843 * x2 * xi - 0.1036 * x2 * x2);
     for (int sg = -1; sg <= 1; sg += 2) {
       double eta = sg * (yt + 1e-3);
       // inverse rotation of (xi, eta) * chord
@@ -694,7 +695,8 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
       return fail(CCM_E_INVALID, "unknown boundary type");
   if (cfg->precision != CCM_FP64 && cfg->precision != CCM_MIXED) return fail(CCM_E_INVALID, "unknown precision");
   if (cfg->precond != CCM_JACOBI && cfg->precond != CCM_CHEBYSHEV) return fail(CCM_E_INVALID, "unknown preconditioner");
-  if (cfg->pressure_update < 0 || cfg->pressure_update > 2) return fail(CCM_E_INVALID, "pressure_update must be 0, 1 or 2");
+  if (cfg->pressure_update < 0 || cfg->pressure_update > 2)
+    return fail(CCM_E_INVALID, "pressure_update must be 0, 1 or 2");
   if (cfg->precond == CCM_CHEBYSHEV && !cheb_degree_supported(cfg->cheb_degree))
     return fail(CCM_E_INVALID, "cheb_degree must be 1-6 or 8");
   if (!(cfg->tol_p > 0) || !(cfg->tol_h > 0) || cfg->max_iter_p < 1 || cfg->max_iter_h < 1)
@@ -726,7 +728,11 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
     if (!mem) { delete c; return fail(CCM_E_OOM, "allocator hook returned NULL"); }
   } else {
     cudaError_t e = cudaMalloc(&mem, c->slab_bytes);
-    if (e != cudaSuccess) { cudaGetLastError(); delete c; return fail(CCM_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return fail(CCM_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
   }
   c->slab = mem;
   Carver real{(char*)(((uintptr_t)mem + 255) & ~(uintptr_t)255)};
@@ -961,7 +967,8 @@ ccm_status ccm_apply_op(ccm_case c, int op, const double* in0, const double* in1
       break;
     case CCM_OP_CONV:
     case CCM_OP_VISC:
-      if (!need(in0) || !need(in1) || !need(out0) || !need(out1)) return fail(CCM_E_INVALID, "needs in0, in1, out0, out1");
+      if (!need(in0) || !need(in1) || !need(out0) || !need(out1))
+        return fail(CCM_E_INVALID, "needs in0, in1, out0, out1");
       if ((s = upload(c, c->t0, in0)) || (s = upload(c, c->t1, in1))) return s;
       launch_fill_bc(g, c->bc, c->t0, c->t1, 1.0, st);
       if (op == CCM_OP_CONV) launch_conv(c->cv, g, c->t0, c->t1, c->t2, c->t3, st);
@@ -969,7 +976,8 @@ ccm_status ccm_apply_op(ccm_case c, int op, const double* in0, const double* in1
       if ((s = download(c, out0, c->t2)) || (s = download(c, out1, c->t3))) return s;
       break;
     case CCM_OP_HELMHOLTZ:
-      if (!need(in0) || !need(in1) || !need(out0) || !need(out1)) return fail(CCM_E_INVALID, "needs in0, in1, out0, out1");
+      if (!need(in0) || !need(in1) || !need(out0) || !need(out1))
+        return fail(CCM_E_INVALID, "needs in0, in1, out0, out1");
       if ((s = upload(c, c->t0, in0)) || (s = upload(c, c->t1, in1))) return s;
       launch_helmholtz(c->cv, g, c->bc, c->ph, c->t0, c->t1, c->t2, c->t3, st);
       if ((s = download(c, out0, c->t2)) || (s = download(c, out1, c->t3))) return s;

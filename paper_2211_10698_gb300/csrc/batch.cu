@@ -266,7 +266,8 @@ static ccm_status batch_mixed(ccm_batch b) {
     ccm_status s = case_mixed_project(c, false);
     if (s != CCM_OK) return s;
   }
-  for (int i = 0; i < n; ++i) case_mixed_account(b->cases[i], inner[i], done[i] ? outer[i] : sweep, rr[i], bb[i], done[i]);
+  for (int i = 0; i < n; ++i)
+    case_mixed_account(b->cases[i], inner[i], done[i] ? outer[i] : sweep, rr[i], bb[i], done[i]);
   return CCM_OK;
 }
 

@@ -105,7 +105,9 @@ __device__ void area_moments(const Piece& p, double& a, double& mx, double& my) 
 }
 
 // Grid line abscissas from one expression, so that neighbouring cells agree bitwise.
-__device__ __forceinline__ double gline(double o, double off, int i, double h) { return __dadd_rn(__dadd_rn(o, off), __dmul_rn((double)i, h)); }
+__device__ __forceinline__ double gline(double o, double off, int i, double h) {
+  return __dadd_rn(__dadd_rn(o, off), __dmul_rn((double)i, h));
+}
 
 __device__ void build(const Body& b, const Geom& g, int grid, int i, int j, Cell& c) {
   const double ox = grid == 1 ? -0.5 * g.hx : 0.0;

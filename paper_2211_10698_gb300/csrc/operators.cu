@@ -533,7 +533,8 @@ void launch_divergence(const Coefs& c, const Geom& g, const Phys& ph, const doub
                        double* rhs, cudaStream_t st) {
   k_divergence<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, ph, u, v, b, rhs);
 }
-void launch_project(const Coefs& c, const Geom& g, const double* phi, double* u, double* v, double* p, cudaStream_t st) {
+void launch_project(const Coefs& c, const Geom& g, const double* phi, double* u, double* v, double* p,
+                    cudaStream_t st) {
   k_project<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, phi, u, v, p);
 }
 int stage_case_blocks(const Geom& g, int* gx) {
