@@ -58,6 +58,9 @@ def _args():
                     help="skip the measurements that follow the headline")
     ap.add_argument("--extras", default="mixed,configs,batched,serving",
                     help="comma-separated subset of the measurements that follow the headline")
+    ap.add_argument("--launch-plan", default="",
+                    help="headline case: this launch shape instead of the set-up autotuner's (the seven "
+                         "comma-separated values of ccm_launch_plan), e.g. for a profiler run")
     ap.add_argument("--configs", default="",
                     help="comma-separated names of the single-case configurations to run (default: all)")
     ap.add_argument("--batch-cases", type=int, default=64,
@@ -80,22 +83,34 @@ def _peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-KERNEL = "k_pcg_poisson_f1"  # FP64 Poisson CG on the Jacobi-scaled system, one barrier per iteration
-KERNEL_SOURCES = ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fused.cu")
+# The FP64 Poisson CG on the Jacobi-scaled system takes one of three launch shapes, chosen by the
+# set-up autotuner: tiles with one barrier per iteration, their vectors in global memory (f1) or
+# resident in shared memory (f2), or, on small grids, one thread-block cluster.
+KERNEL_SOURCES = {
+    "k_pcg_poisson_f1": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fused.cu"),
+    "k_pcg_poisson_f2": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fused.cu"),
+    "k_pcg_poisson_cluster": ("pcg_common.cuh", "pcg_cluster.cu"),
+}
 
 
-def kernel_source_hash():
+def kernel_of(plan):
+    """The Poisson kernel a launch plan (bench's _plan_dict) runs."""
+    if plan.get("kind") == "cluster":
+        return "k_pcg_poisson_cluster"
+    return "k_pcg_poisson_f2" if plan.get("resident") else "k_pcg_poisson_f1"
+
+
+def kernel_source_hash(kernel="k_pcg_poisson_f2"):
     import hashlib
 
     csrc = os.path.join(ROOT, "paper_2211_10698_gb300", "csrc")
-    return hashlib.sha256(b"".join(open(os.path.join(csrc, f), "rb").read() for f in KERNEL_SOURCES)).hexdigest()[:16]
+    return hashlib.sha256(b"".join(open(os.path.join(csrc, f), "rb").read()
+                                   for f in KERNEL_SOURCES[kernel])).hexdigest()[:16]
 
 
-def _traffic_from_profile():
-    """DRAM bytes per launch of the Poisson PCG from the committed ncu summary, if the
-    kernel source still matches the hash recorded with the counters."""
-    import hashlib
-
+def _traffic_from_profile(kernel="k_pcg_poisson_f2"):
+    """DRAM bytes per launch of the Poisson PCG from the committed ncu summary, if it covers
+    this kernel and the kernel source still matches the hash recorded with the counters."""
     path = os.path.join(ROOT, "profiles", "pcg_poisson_fp64_cylinder.md")
     try:
         text = open(path).read()
@@ -106,9 +121,7 @@ def _traffic_from_profile():
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    csrc = os.path.join(ROOT, "paper_2211_10698_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in KERNEL_SOURCES)
-    if vals.get("kernel source sha256") != hashlib.sha256(src).hexdigest()[:16]:
+    if vals.get("kernel") != kernel or vals.get("kernel source sha256") != kernel_source_hash(kernel):
         return None, None
     try:
         return float(vals["dram bytes per iteration per cell"]), vals
@@ -318,11 +331,11 @@ def _measure_case(torch, stream, flush, case, steps, warmup, precision=None, pre
 
 def _plan_dict(g):
     """The launch shape the set-up autotuner chose for the case's Poisson solve."""
-    tx, ty, nbx, ntiles, mb, cl = g.launch_plan()
+    tx, ty, nbx, ntiles, mb, cl, res = g.launch_plan()
     if cl:
         return dict(kind="cluster", ctas=cl)
     if tx:
-        return dict(kind="tiles", tile=[tx, ty], tiles=ntiles)
+        return dict(kind="tiles", tile=[tx, ty], tiles=ntiles, resident=bool(res))
     if mb:
         return dict(kind="blocks", blocks=mb)
     return dict(kind="built-in")
@@ -443,7 +456,11 @@ def run_ours(args):
         dist.init_process_group("nccl")
     case = inputs.cylinder_re100_1024x512()
     stream = torch.cuda.current_stream()
+    if args.launch_plan:
+        case.autotune = 0
     g = ccm.Case(case, stream=stream.cuda_stream, allocator=ccm.TorchAllocator())
+    if args.launch_plan:
+        g.set_launch_plan(tuple(int(x) for x in args.launch_plan.split(",")))
     pu, pv = inputs.perturbation(case)
     g.set_field(ccm.CCM_F_U, g.get_field(ccm.CCM_F_U) + pu)
     g.set_field(ccm.CCM_F_V, g.get_field(ccm.CCM_F_V) + pv)
@@ -509,15 +526,16 @@ def run_ours(args):
     achieved_gbs = bytes_alg / (avg_ms * 1e-3) / 1e9
     frac_alu = achieved_tf / FP64_PEAK_TFLOPS
     frac_hbm = achieved_gbs / peaks["hbm_gbs"]
-    traffic_pc, prof = _traffic_from_profile()
+    kernel = kernel_of(launch_plan)
+    traffic_pc, prof = _traffic_from_profile(kernel)
     traffic = traffic_pc * case.cells * iters_per_launch if traffic_pc is not None else None
     if frac_alu >= frac_hbm:
         roof = dict(bound="alu", achieved=achieved_tf, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=frac_alu,
-                    traffic=traffic, kernel=KERNEL,
+                    traffic=traffic, kernel=kernel,
                     peak_source="FP64 unit count x clock (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)")
     else:
         roof = dict(bound="hbm", achieved=achieved_gbs, peak=peaks["hbm_gbs"], unit="GB/s", frac=frac_hbm,
-                    traffic=traffic, kernel=KERNEL, peak_source=f"{peak_kind} hbm_gbs")
+                    traffic=traffic, kernel=kernel, peak_source=f"{peak_kind} hbm_gbs")
     roof_alt = dict(hbm_achieved_gbs=achieved_gbs, hbm_peak_gbs=peaks["hbm_gbs"], hbm_frac=frac_hbm,
                     fp64_achieved_tflops=achieved_tf, fp64_peak_tflops=FP64_PEAK_TFLOPS, fp64_frac=frac_alu,
                     avg_launch_ms=avg_ms, iters_per_launch=iters_per_launch,

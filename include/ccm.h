@@ -164,14 +164,16 @@ ccm_status ccm_case_bytes(const ccm_config* cfg, size_t* bytes);
  * height, tiles per row and tiles of the FP64 one-barrier solve (0 where it does not apply or
  * the built-in plan is used), plan[4] = blocks of the mixed solve (0: built-in), plan[5] =
  * CTAs of the one thread-block cluster that holds a small grid's whole FP64 solve (0: not
- * used).  Valid after set_geometry. */
-ccm_status ccm_launch_plan(ccm_case c, int plan[6]);
+ * used), plan[6] = 1 when the tiles keep their vectors in shared memory for the whole solve.
+ * Valid after set_geometry. */
+ccm_status ccm_launch_plan(ccm_case c, int plan[7]);
 /* Sets the launch shape (same layout; zeros select the built-in shapes).  A tile plan needs a
- * width that is a power of two in 32..512 and the tile counts it implies; a cluster has 2, 4,
- * 8 or 16 CTAs, at most ny, and excludes a tile plan.  CCM_E_INVALID otherwise.  Shapes apply
- * to the single-case FP64 Jacobi solve of a nonsingular system (tiles, cluster) and to the
- * mixed one-launch solve (blocks). */
-ccm_status ccm_set_launch_plan(ccm_case c, const int plan[6]);
+ * width that is a power of two in 32..512 and the tile counts it implies (and, resident, tiles
+ * that fit in shared memory at once); a cluster has 2, 4, 8 or 16 CTAs, at most ny, and
+ * excludes a tile plan.  CCM_E_INVALID otherwise.  Shapes apply to the single-case FP64
+ * Jacobi solve of a nonsingular system (tiles, cluster) and to the mixed one-launch solve
+ * (blocks). */
+ccm_status ccm_set_launch_plan(ccm_case c, const int plan[7]);
 
 /* Release every resource of the case (NULL is accepted). */
 ccm_status ccm_destroy_case(ccm_case c);

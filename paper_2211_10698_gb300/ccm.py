@@ -254,14 +254,15 @@ class Case:
         return {f: getattr(st, f) for f, _ in ccm_step_stats._fields_}
 
     def launch_plan(self):
-        """(tile width, tile height, tiles per row, tiles, mixed blocks, cluster CTAs) of the
-        single-case Poisson solve; zeros where the built-in shape is used."""
-        plan = (c_int * 6)()
+        """(tile width, tile height, tiles per row, tiles, mixed blocks, cluster CTAs, resident
+        tiles) of the single-case Poisson solve; zeros where the built-in shape is used."""
+        plan = (c_int * 7)()
         _check(lib().ccm_launch_plan(self.h, plan))
         return tuple(plan)
 
     def set_launch_plan(self, plan):
-        arr = (c_int * 6)(*plan)
+        plan = tuple(plan) + (0,) * (7 - len(plan))
+        arr = (c_int * 7)(*plan)
         _check(lib().ccm_set_launch_plan(self.h, arr))
 
     def step_async(self, n=1):

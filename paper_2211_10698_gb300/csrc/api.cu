@@ -266,7 +266,7 @@ ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
       return CCM_OK;
     }
     const TilePlan& tp = c->tune.plan;
-    f.TX = tp.TX; f.TY = tp.TY; f.nbx = tp.nbx; f.ntiles = tp.ntiles;
+    f.TX = tp.TX; f.TY = tp.TY; f.nbx = tp.nbx; f.ntiles = tp.ntiles; f.resident = tp.resident;
     CUDA_TRY(run_poisson_fused(f, c->st));
     return CCM_OK;
   }
@@ -465,6 +465,7 @@ ccm_status autotune_poisson(ccm_case c) {
         return run_poisson_cluster(cs, ccand[k - nf], st);
       }
       f.TX = cand[k].TX; f.TY = cand[k].TY; f.nbx = cand[k].nbx; f.ntiles = cand[k].ntiles;
+      f.resident = cand[k].resident;
       return run_poisson_fused(f, st);
     }, st, &best, &ms);
     if (best >= nf) r.cluster = ccand[best - nf];
@@ -749,7 +750,7 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
   return CCM_OK;
 }
 
-ccm_status ccm_launch_plan(ccm_case c, int plan[6]) {
+ccm_status ccm_launch_plan(ccm_case c, int plan[7]) {
   g_last_error.clear();
   if (!c || !plan) return fail(CCM_E_INVALID, "null argument");
   if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
@@ -759,10 +760,11 @@ ccm_status ccm_launch_plan(ccm_case c, int plan[6]) {
   plan[3] = c->tune.plan.ntiles;
   plan[4] = c->tune.mixed_blocks;
   plan[5] = c->tune.cluster;
+  plan[6] = c->tune.plan.resident;
   return CCM_OK;
 }
 
-ccm_status ccm_set_launch_plan(ccm_case c, const int plan[6]) {
+ccm_status ccm_set_launch_plan(ccm_case c, const int plan[7]) {
   g_last_error.clear();
   if (!c || !plan) return fail(CCM_E_INVALID, "null argument");
   if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
@@ -774,7 +776,12 @@ ccm_status ccm_set_launch_plan(ccm_case c, const int plan[6]) {
     const int nbx = (g.nx + tx - 1) / std::max(tx, 1);
     if (!pow2 || ty < 1 || plan[2] != nbx || plan[3] != nbx * ((g.ny + ty - 1) / ty) || plan[3] > fused_blocks())
       return fail(CCM_E_INVALID, "tile plan: width a power of two in 32..512, tiles = ceil(nx/w) ceil(ny/h)");
-    r.plan = TilePlan{tx, ty, plan[2], plan[3]};
+    if (plan[6] != 0 && plan[6] != 1) return fail(CCM_E_INVALID, "resident must be 0 or 1");
+    if (plan[6] == 1 && !fused_resident_ok(tx, ty, plan[3]))
+      return fail(CCM_E_INVALID, "resident tiles do not fit in shared memory on this GPU");
+    r.plan = TilePlan{tx, ty, plan[2], plan[3], plan[6]};
+  } else if (plan[6] != 0) {
+    return fail(CCM_E_INVALID, "resident tiles need a tile plan");
   }
   if (plan[4] < 0 || plan[4] > mixed_blocks()) return fail(CCM_E_INVALID, "mixed blocks out of range");
   r.mixed_blocks = plan[4];

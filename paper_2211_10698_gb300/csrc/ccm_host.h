@@ -103,10 +103,13 @@ struct FusedSolve {
   double* S[2];
   int TX, TY, nbx, ntiles;  // tile plan; TX = 0 lets the launcher choose
   int list_cap;             // set by the launcher: entries of the per-tile list of non-uniform cells
+  int resident;             // 1: each tile keeps its vectors in shared memory (k_pcg_poisson_f2)
 };
 cudaError_t run_poisson_fused(FusedSolve f, cudaStream_t st);
 void fused_tiles(int nx, int ny, int blocks, int* TX, int* TY, int* nbx, int* ntiles);
 int fused_blocks();
+size_t fused_resident_smem(int TX, int TY);
+bool fused_resident_ok(int TX, int TY, int ntiles);
 
 // The same solve for small grids inside one thread-block cluster (pcg_cluster.cu).
 struct ClusterSolve {
@@ -120,6 +123,7 @@ cudaError_t run_poisson_cluster(ClusterSolve f, int C, cudaStream_t st);
 // Launch-shape autotuner (tune.cu).
 struct TilePlan {
   int TX, TY, nbx, ntiles;
+  int resident;  // 1: the tiles keep their vectors in shared memory (k_pcg_poisson_f2)
 };
 struct TuneResult {
   TilePlan plan;     // FP64 one-barrier solve (TX = 0: not tuned)

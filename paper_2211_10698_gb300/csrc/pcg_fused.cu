@@ -22,6 +22,12 @@
 // rows by iteration parity.
 // Tiles are TX x TY cells (TX a power of two, 32..512), one per block; the host picks the
 // shape that makes the largest tile smallest.
+//
+// Two instantiations of the same iteration: k_pcg_poisson_f1 keeps x~, r, p, s and w in global
+// memory (L2); k_pcg_poisson_f2 keeps its tile's x~, r, p, s, w and row kinds in shared memory
+// for the whole solve.  Only the tile's perimeter cells are read by other blocks (for their
+// ring), so f2 publishes r, w and s of its perimeter to the double-buffered global arrays once
+// per iteration and touches nothing else in global memory until the final x~ -> x.
 #include <algorithm>
 
 #include "pcg_common.cuh"
@@ -32,13 +38,17 @@ namespace {
 
 constexpr int kNT = 512;  // threads per block
 
-__global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
+// RES: the tile's vectors live in shared memory (f2); otherwise in global memory (f1).
+template <bool RES>
+__device__ __forceinline__ void fused_body(const FusedSolve& f) {
   __shared__ double red[4][kNT];
   __shared__ double bsum[8];
   __shared__ double gsum[8];
   __shared__ double sc_alpha, sc_beta, sc_igamma, sc_ialpha, sc_rr, sc_bb;
   __shared__ int sc_it, sc_stop;
-  extern __shared__ double ring[];  // [W: TY][E: TY][S: TX][N: TX]
+  // dynamic shared memory: with RES x~, r, p, s, w of the tile (TX*TY each), then the ring
+  // [W: TY][E: TY][S: TX][N: TX], then with RES the tile's row kinds, then the list
+  extern __shared__ double dyn[];
   unsigned int target = 0;
   const ScaledSolve& a = f.a;
   const int nb = gridDim.x;
@@ -52,6 +62,18 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
   const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX, RP = kNT / TX;
   const int ci = i0 + tx;  // this thread's column
   const bool col = ci < i1;
+  const int TXY = TX * TY;
+  double* const sx = dyn;  // the RES arrays (unused otherwise)
+  double* const sr = dyn + TXY;
+  double* const sp = dyn + 2 * TXY;
+  double* const ss = dyn + 3 * TXY;
+  double* const sw = dyn + 4 * TXY;
+  double* const ring = RES ? dyn + 5 * TXY : dyn;
+  int8_t* const skind = reinterpret_cast<int8_t*>(ring + 2 * (TX + TY));
+  // tile-local index of own cell (i, j)
+  auto lidx = [&](int i, int j) -> int { return (j - j0) * TX + (i - i0); };
+  // own cells on the tile's perimeter are read by the neighbouring tiles' rings
+  auto perimeter = [&](int i, int j) -> bool { return i == i0 || i == i1 - 1 || j == j0 || j == j1 - 1; };
   // ring cells: W and E columns, then S and N rows, taken by threads t, t + kNT, ...
   const int nring = 2 * (j1 - j0) + 2 * (i1 - i0);
   // cell (ri, rj) of ring position t and its slot in `ring`; false outside the domain,
@@ -80,7 +102,29 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
     if (i >= i1) return ring[TY + (j - j0)];
     if (j < j0) return ring[2 * TY + (i - i0)];
     if (j >= j1) return ring[2 * TY + TX + (i - i0)];
-    return rn[g.idx(i, j)];
+    if constexpr (RES) return sr[lidx(i, j)];
+    else return rn[g.idx(i, j)];
+  };
+  // r~ of own cell (i, j) after step 1
+  auto rown = [&](const double* rn, int i, int j) -> double {
+    if constexpr (RES) return sr[lidx(i, j)];
+    else return rn[g.idx(i, j)];
+  };
+  // w~ of own cell (i, j) into the tile (RES, which also publishes the perimeter's r, w and s
+  // for iteration parity `pub`) or into wn
+  auto wput = [&](double* wn, int pub, int i, int j, double wk) {
+    if constexpr (RES) {
+      const int l = lidx(i, j);
+      sw[l] = wk;
+      if (perimeter(i, j)) {
+        const size_t k = g.idx(i, j);
+        f.R[pub][k] = sr[l];
+        f.W[pub][k] = wk;
+        f.S[pub][k] = ss[l];
+      }
+    } else {
+      wn[g.idx(i, j)] = wk;
+    }
   };
   // Rows of cut cells and rows next to a Neumann side (kind 2) are listed per tile, in a fixed
   // order, at the start.  The stencil pass applies the constant stencil to every own cell, so
@@ -89,7 +133,7 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
   // Inactive cells (identity rows, kind 0) get their exact solution x = b in phase 0 and zero
   // in every vector after it, so the stencil pass only has to write w = 0 there.  A tile with
   // more listed cells than the list holds takes the general row for every cell instead.
-  int* const list = reinterpret_cast<int*>(ring + 2 * (TX + TY));
+  int* const list = RES ? reinterpret_cast<int*>(skind + TXY) : reinterpret_cast<int*>(ring + 2 * (TX + TY));
   __shared__ int s_scan[kNT / 32 + 1];
   int nlist = 0;
   bool general = false;
@@ -130,7 +174,7 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
   auto general_row = [&](const double* rn, int i, int j, double& rc_out) -> double {
     const size_t k = g.idx(i, j);
     const int8_t km = kinds[k];
-    const double rc = rn[k], rw = rnb(rn, i - 1, j), re = rnb(rn, i + 1, j);
+    const double rc = rown(rn, i, j), rw = rnb(rn, i - 1, j), re = rnb(rn, i + 1, j);
     const double rs = rnb(rn, i, j - 1), rq = rnb(rn, i, j + 1);
     rc_out = rc;
     if (km == 1) return rc - ax * (rw + re) - ay * (rs + rq);
@@ -142,14 +186,14 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
     const int8_t km = kinds[k];
     return km == 1 ? dreg : (km == 2 ? sd[k] * sd[k] : 1.0);
   };
-  // step 2 on own cells: w = K~ r (r in buffer rn), sums into v
-  auto stencil = [&](const double* rn, double* wn, double (&v)[4]) {
+  // step 2 on own cells: w = K~ r (r in buffer rn, or the tile with RES), sums into v
+  auto stencil = [&](const double* rn, double* wn, int pub, double (&v)[4]) {
     if (general) {
       if (col)
         for (int j = j0 + ty0; j < j1; j += RP) {
           double rc;
           const double wk = general_row(rn, ci, j, rc);
-          wn[g.idx(ci, j)] = wk;
+          wput(wn, pub, ci, j, wk);
           v[0] += rc * rc;
           v[1] += (diag_of(ci, j) - dreg) * (rc * rc);
           v[2] += wk * rc;
@@ -165,40 +209,56 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
       li = i0 + q0 % TX;
       lj = j0 + q0 / TX;
       const size_t k = g.idx(li, lj);
-      lr[0] = rn[k]; lr[1] = rnb(rn, li - 1, lj); lr[2] = rnb(rn, li + 1, lj);
+      lr[0] = rown(rn, li, lj); lr[1] = rnb(rn, li - 1, lj); lr[2] = rnb(rn, li + 1, lj);
       lr[3] = rnb(rn, li, lj - 1); lr[4] = rnb(rn, li, lj + 1);
       lc[0] = cus[k]; lc[1] = cus[k + 1]; lc[2] = cvs[k]; lc[3] = cvs[k + P]; lc[4] = sd[k];
     }
     // constant stencil on every own cell but the listed ones, two rows of this thread at a time
-    if (col)
-      for (int j = j0 + ty0; j < j1; j += 2 * RP) {
-        const bool two = j + RP < j1;
-        const int jb = two ? j + RP : j;
-        const size_t ka = g.idx(ci, j), kb = g.idx(ci, jb);
-        const int8_t kma = kinds[ka], kmb = kinds[kb];
-        const double rca = rn[ka], rwa = rnb(rn, ci - 1, j), rea = rnb(rn, ci + 1, j);
-        const double rsa = rnb(rn, ci, j - 1), rqa = rnb(rn, ci, j + 1);
-        const double rcb = rn[kb], rwb = rnb(rn, ci - 1, jb), reb = rnb(rn, ci + 1, jb);
-        const double rsb = rnb(rn, ci, jb - 1), rqb = rnb(rn, ci, jb + 1);
-        const double wa = kma == 0 ? 0.0 : rca - ax * (rwa + rea) - ay * (rsa + rqa);
-        if (kma != 2) {
-          wn[ka] = wa;
-          v[0] += rca * rca;
-          v[2] += wa * rca;
-        }
-        if (two) {
-          const double wb = kmb == 0 ? 0.0 : rcb - ax * (rwb + reb) - ay * (rsb + rqb);
-          if (kmb != 2) {
-            wn[kb] = wb;
-            v[0] += rcb * rcb;
-            v[2] += wb * rcb;
+    if constexpr (RES) {
+      if (col)
+        for (int j = j0 + ty0; j < j1; j += RP) {
+          const int l = lidx(ci, j);
+          const int8_t km = skind[l];
+          const double rc = sr[l], rw = rnb(rn, ci - 1, j), re = rnb(rn, ci + 1, j);
+          const double rs = rnb(rn, ci, j - 1), rq = rnb(rn, ci, j + 1);
+          const double wk = km == 0 ? 0.0 : rc - ax * (rw + re) - ay * (rs + rq);
+          if (km != 2) {
+            wput(wn, pub, ci, j, wk);
+            v[0] += rc * rc;
+            v[2] += wk * rc;
           }
         }
-      }
+    } else {
+      if (col)
+        for (int j = j0 + ty0; j < j1; j += 2 * RP) {
+          const bool two = j + RP < j1;
+          const int jb = two ? j + RP : j;
+          const size_t ka = g.idx(ci, j), kb = g.idx(ci, jb);
+          const int8_t kma = kinds[ka], kmb = kinds[kb];
+          const double rca = rn[ka], rwa = rnb(rn, ci - 1, j), rea = rnb(rn, ci + 1, j);
+          const double rsa = rnb(rn, ci, j - 1), rqa = rnb(rn, ci, j + 1);
+          const double rcb = rn[kb], rwb = rnb(rn, ci - 1, jb), reb = rnb(rn, ci + 1, jb);
+          const double rsb = rnb(rn, ci, jb - 1), rqb = rnb(rn, ci, jb + 1);
+          const double wa = kma == 0 ? 0.0 : rca - ax * (rwa + rea) - ay * (rsa + rqa);
+          if (kma != 2) {
+            wn[ka] = wa;
+            v[0] += rca * rca;
+            v[2] += wa * rca;
+          }
+          if (two) {
+            const double wb = kmb == 0 ? 0.0 : rcb - ax * (rwb + reb) - ay * (rsb + rqb);
+            if (kmb != 2) {
+              wn[kb] = wb;
+              v[0] += rcb * rcb;
+              v[2] += wb * rcb;
+            }
+          }
+        }
+    }
     // the listed cells: the general row
     if (q0 >= 0) {
       const double wk = lr[0] - lc[0] * lr[1] - lc[1] * lr[2] - lc[2] * lr[3] - lc[3] * lr[4];
-      wn[g.idx(li, lj)] = wk;
+      wput(wn, pub, li, lj, wk);
       v[0] += lr[0] * lr[0];
       v[1] += (lc[4] * lc[4] - dreg) * (lr[0] * lr[0]);
       v[2] += wk * lr[0];
@@ -208,7 +268,7 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
       const int i = i0 + loc % TX, j = j0 + loc / TX;
       double rc;
       const double wk = general_row(rn, i, j, rc);
-      wn[g.idx(i, j)] = wk;
+      wput(wn, pub, i, j, wk);
       v[0] += rc * rc;
       v[1] += (diag_of(i, j) - dreg) * (rc * rc);
       v[2] += wk * rc;
@@ -234,10 +294,21 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
       const double bk = a.b[k];
       const bool inactive = kinds[k] == 0;  // identity row: x = b exactly
       const double rk = inactive ? 0.0 : bk - K(a.x, k);
-      xs[k] = inactive ? bk : sd[k] * a.x[k];
-      f.R[0][k] = a.isd[k] * rk;
-      f.S[0][k] = 0.0;
-      p[k] = 0.0;
+      const double x0 = inactive ? bk : sd[k] * a.x[k], r0 = a.isd[k] * rk;
+      if (RES) {
+        const int l = lidx(ci, j);
+        sx[l] = x0;
+        sr[l] = r0;
+        ss[l] = 0.0;
+        sp[l] = 0.0;
+        skind[l] = kinds[k];
+        if (perimeter(ci, j)) f.R[0][k] = r0;  // the neighbours' first ring; S[0] and W[0] follow
+      } else {
+        xs[k] = x0;
+        f.R[0][k] = r0;
+        f.S[0][k] = 0.0;
+        p[k] = 0.0;
+      }
       v[3] += bk * bk;
     }
   bool ok = grid_sync(a.bar, target);
@@ -249,7 +320,7 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
       ring[slot] = in ? f.R[0][g.idx(ri, rj)] : 0.0;
     }
     __syncthreads();
-    stencil(f.R[0], f.W[0], v);
+    stencil(f.R[0], f.W[0], 0, v);
     reduce(v, 4, rows0);
     ok = grid_sync(a.bar, target);
   }
@@ -280,8 +351,19 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
     const double* __restrict__ sc_ = f.S[cur];
     double* __restrict__ rn_ = f.R[nxt];
     double* __restrict__ sn_ = f.S[nxt];
-    // step 1: own cells, two rows of this thread at a time with their loads in flight
-    if (col)
+    // step 1: own cells (RES: in the tile; otherwise two rows of this thread at a time with
+    // their loads in flight)
+    if (RES) {
+      if (col)
+        for (int j = j0 + ty0; j < j1; j += RP) {
+          const int l = lidx(ci, j);
+          const double sk = sw[l] + be * ss[l], pk = sr[l] + be * sp[l];
+          ss[l] = sk;
+          sp[l] = pk;
+          sx[l] += al * pk;
+          sr[l] -= al * sk;
+        }
+    } else if (col)
       for (int j = j0 + ty0; j < j1; j += 2 * RP) {
         const bool two = j + RP < j1;
         const size_t k0 = g.idx(ci, j), k1 = two ? g.idx(ci, j + RP) : k0;
@@ -314,7 +396,7 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
     }
     __syncthreads();
     v[0] = v[1] = v[2] = 0.0;
-    stencil(rn_, f.W[nxt], v);
+    stencil(rn_, f.W[nxt], nxt, v);
     double* const rows = (sc_it & 1) ? rows0 : rows1;  // reduction sc_it + 1
     reduce(v, 3, rows);
     if (!grid_sync(a.bar, target)) { ok = false; break; }
@@ -341,7 +423,7 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
   if (col)
     for (int j = j0 + ty0; j < j1; j += RP) {
       const size_t k = g.idx(ci, j);
-      a.x[k] = a.isd[k] * xs[k];
+      a.x[k] = a.isd[k] * (RES ? sx[lidx(ci, j)] : xs[k]);
     }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const bool conv = ok && sc_stop == 1;
@@ -352,6 +434,14 @@ __global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(FusedSolve f) {
     if (a.out.total && ok) a.out.total[0] += sc_it;
     if (!conv && a.out.nconv) a.out.nconv[0] += 1;
   }
+}
+
+// __grid_constant__: the body takes the parameter by reference without a local copy
+__global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f1(const __grid_constant__ FusedSolve f) {
+  fused_body<false>(f);
+}
+__global__ void __launch_bounds__(kNT, 2) k_pcg_poisson_f2(const __grid_constant__ FusedSolve f) {
+  fused_body<true>(f);
 }
 
 }  // namespace
@@ -392,18 +482,51 @@ int fused_blocks() {
   return sms * per;
 }
 
+// Dynamic shared memory of a tile with its vectors resident (f2): x~, r, p, s, w, the ring, the
+// row kinds and a list of up to one entry per cell.
+size_t fused_resident_smem(int TX, int TY) {
+  const size_t txy = (size_t)TX * (size_t)TY;
+  return 5 * sizeof(double) * txy + sizeof(double) * 2 * ((size_t)TX + (size_t)TY) + txy + sizeof(int) * txy;
+}
+
+// Whether ntiles tiles of TX x TY cells with resident vectors fit the GPU at once.
+bool fused_resident_ok(int TX, int TY, int ntiles) {
+  const size_t smem = fused_resident_smem(TX, TY);
+  int dev = 0, sms = 0, per = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > (size_t)optin ||
+      cudaFuncSetAttribute(k_pcg_poisson_f2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_poisson_f2, kNT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return ntiles >= 1 && ntiles <= sms * std::min(per, 2);
+}
+
 cudaError_t run_poisson_fused(FusedSolve f, cudaStream_t st) {
   const int blocks = fused_blocks();
   if (f.TX == 0) fused_tiles(f.a.g.nx, f.a.g.ny, blocks, &f.TX, &f.TY, &f.nbx, &f.ntiles);
-  const size_t ring = sizeof(double) * 2 * ((size_t)f.TX + (size_t)f.TY);
-  if (ring + sizeof(int) * 256 > kFusedSmemMax || f.ntiles > blocks || f.ntiles < 1)
-    return cudaErrorInvalidConfiguration;
-  // the list of non-uniform cells takes what is left, up to one entry per tile cell
-  f.list_cap = (int)std::min<size_t>((kFusedSmemMax - ring) / sizeof(int), (size_t)f.TX * (size_t)f.TY);
-  const size_t smem = ring + sizeof(int) * (size_t)f.list_cap;
+  if (f.ntiles < 1) return cudaErrorInvalidConfiguration;
+  const void* kernel = (const void*)k_pcg_poisson_f1;
+  size_t smem = 0;
+  if (f.resident) {
+    // the tile's vectors in shared memory: as many blocks as fit must hold every tile
+    smem = fused_resident_smem(f.TX, f.TY);
+    f.list_cap = f.TX * f.TY;
+    kernel = (const void*)k_pcg_poisson_f2;
+    if (!fused_resident_ok(f.TX, f.TY, f.ntiles)) return cudaErrorInvalidConfiguration;
+  } else {
+    const size_t ring = sizeof(double) * 2 * ((size_t)f.TX + (size_t)f.TY);
+    if (ring + sizeof(int) * 256 > kFusedSmemMax || f.ntiles > blocks) return cudaErrorInvalidConfiguration;
+    // the list of non-uniform cells takes what is left, up to one entry per tile cell
+    f.list_cap = (int)std::min<size_t>((kFusedSmemMax - ring) / sizeof(int), (size_t)f.TX * (size_t)f.TY);
+    smem = ring + sizeof(int) * (size_t)f.list_cap;
+  }
   cudaMemsetAsync(f.a.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
   void* params[] = {&f};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg_poisson_f1, f.ntiles, kNT, params, smem, st);
+  return cudaLaunchCooperativeKernel(kernel, f.ntiles, kNT, params, smem, st);
 }
 
 }  // namespace ccm

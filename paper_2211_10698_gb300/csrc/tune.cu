@@ -21,6 +21,8 @@ std::vector<TilePlan> fused_plan_candidates(int nx, int ny, int blocks) {
   TilePlan def{};
   fused_tiles(nx, ny, blocks, &def.TX, &def.TY, &def.nbx, &def.ntiles);
   out.push_back(def);
+  // every plan also with its tiles' vectors resident in shared memory, where they fit
+  // (the launcher refuses the others)
   for (int tx = 32; tx <= 512; tx *= 2) {
     const int bxn = (nx + tx - 1) / tx;
     if (bxn > blocks) continue;
@@ -28,13 +30,20 @@ std::vector<TilePlan> fused_plan_candidates(int nx, int ny, int blocks) {
     const int byn_max = std::max(1, std::min(blocks / bxn, ny));
     for (int byn = byn_max; byn >= 1; byn /= 2) {
       const int ty = (ny + byn - 1) / byn;
-      TilePlan p{tx, ty, bxn, bxn * ((ny + ty - 1) / ty)};
+      TilePlan p{tx, ty, bxn, bxn * ((ny + ty - 1) / ty), 0};
       bool seen = false;
       for (const TilePlan& q : out) seen = seen || (q.TX == p.TX && q.TY == p.TY);
       if (!seen && p.ntiles <= blocks && (long long)std::min(tx, nx) * ty <= 64LL * 512) out.push_back(p);
       if (byn == 1) break;
     }
   }
+  const size_t n = out.size();
+  for (size_t q = 0; q < n; ++q)
+    if (fused_resident_smem(out[q].TX, out[q].TY) <= 227 * 1024) {
+      TilePlan r = out[q];
+      r.resident = 1;
+      out.push_back(r);
+    }
   return out;
 }
 

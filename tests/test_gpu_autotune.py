@@ -32,16 +32,16 @@ def _case(nx, ny, precision, autotune, precond="jacobi"):
 def test_fp64_tile_plan(nx, ny):
     tuned = ccm.Case(_case(nx, ny, "fp64", 1))
     plain = ccm.Case(_case(nx, ny, "fp64", 0))
-    tx, ty, nbx, ntiles, mb, cl = tuned.launch_plan()
+    tx, ty, nbx, ntiles, mb, cl, res = tuned.launch_plan()
     assert mb == 0
     if cl:
-        assert cl in (2, 4, 8, 16) and cl <= ny and (tx, ty, nbx, ntiles) == (0, 0, 0, 0)
+        assert cl in (2, 4, 8, 16) and cl <= ny and (tx, ty, nbx, ntiles, res) == (0, 0, 0, 0, 0)
     else:
         assert tx in (32, 64, 128, 256, 512) and ty >= 1
         assert nbx == -(-nx // tx) and ntiles == nbx * -(-ny // ty)
-    assert plain.launch_plan() == (0, 0, 0, 0, 0, 0)
+    assert plain.launch_plan() == (0,) * 7
     # the same size again: the cached plan
-    assert ccm.Case(_case(nx, ny, "fp64", 1)).launch_plan() == (tx, ty, nbx, ntiles, mb, cl)
+    assert ccm.Case(_case(nx, ny, "fp64", 1)).launch_plan() == (tx, ty, nbx, ntiles, mb, cl, res)
     st_t = tuned.step(3)
     st_p = plain.step(3)
     assert st_t["converged"] and st_p["converged"]
@@ -54,7 +54,7 @@ def test_mixed_block_count(precond):
     tuned = ccm.Case(_case(160, 64, "mixed", 1, precond))
     plain = ccm.Case(_case(160, 64, "mixed", 0, precond))
     plan = tuned.launch_plan()
-    assert plan[:4] == (0, 0, 0, 0) and plan[5] == 0
+    assert plan[:4] == (0, 0, 0, 0) and plan[5:] == (0, 0)
     most = plan[4]
     assert most >= 1
     st_t = tuned.step(3)
@@ -68,8 +68,8 @@ def test_singular_and_fp64_chebyshev_keep_builtin_shape():
     closed = I.small_cylinder(nx=37, ny=23, box=(-1.5, 1.5, -1.0, 1.0), r=0.41, cx=0.07, cy=-0.05,
                               bc=I.closed_box_bc(lid=1.0), re=50.0)
     closed.autotune = 1
-    assert ccm.Case(closed).launch_plan() == (0, 0, 0, 0, 0, 0)
-    assert ccm.Case(_case(64, 32, "fp64", 1, "chebyshev")).launch_plan() == (0, 0, 0, 0, 0, 0)
+    assert ccm.Case(closed).launch_plan() == (0,) * 7
+    assert ccm.Case(_case(64, 32, "fp64", 1, "chebyshev")).launch_plan() == (0,) * 7
 
 
 @pytest.mark.parametrize("nx,ny,ctas", [(128, 64, 16), (128, 64, 2), (61, 20, 16), (96, 40, 8), (300, 36, 4)])
@@ -98,4 +98,26 @@ def test_launch_plan_validation():
     with pytest.raises(ccm.CcmError):
         big.set_launch_plan((0, 0, 0, 0, 0, 16))  # a band of 32 rows does not fit shared memory
     c.set_launch_plan((64, 8, 2, 16, 0, 0))
-    assert c.launch_plan() == (64, 8, 2, 16, 0, 0)
+    assert c.launch_plan() == (64, 8, 2, 16, 0, 0, 0)
+    with pytest.raises(ccm.CcmError):
+        c.set_launch_plan((0, 0, 0, 0, 0, 0, 1))  # resident tiles need a tile plan
+    with pytest.raises(ccm.CcmError):
+        big.set_launch_plan((512, 512, 2, 2, 0, 0, 1))  # a tile of 262144 cells cannot stay resident
+
+
+@pytest.mark.parametrize("nx,ny,plan", [(1024, 512, (64, 27, 16, 304)), (128, 64, (128, 1, 1, 64)),
+                                        (300, 36, (32, 4, 10, 90)), (61, 20, (32, 3, 2, 14)),
+                                        (96, 40, (64, 5, 2, 16))])
+def test_resident_tiles_match_global_tiles(nx, ny, plan):
+    """The one-barrier FP64 solve with each tile's vectors kept in shared memory (only the
+    perimeter published per iteration) gives the fields of the same tiles in global memory."""
+    res = ccm.Case(_case(nx, ny, "fp64", 0))
+    res.set_launch_plan(plan + (0, 0, 1))
+    glob = ccm.Case(_case(nx, ny, "fp64", 0))
+    glob.set_launch_plan(plan + (0, 0, 0))
+    st_r = res.step(3)
+    st_g = glob.step(3)
+    assert st_r["converged"] and st_g["converged"]
+    assert st_r["iters_p"] == st_g["iters_p"]
+    for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P):
+        assert _rel(res.get_field(f), glob.get_field(f)) < 1e-12, f
