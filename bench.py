@@ -366,10 +366,11 @@ def measure_configs(torch, stream, flush, only=None):
     return out
 
 
-def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=1):
+def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=4):
     """The 64-case batch (cylinders and NACA00tt sections, 256..1024 cells wide, mixed
     precision, Chebyshev degree 4 as configured): all cases advance together, one batched
-    Poisson solve per step."""
+    Poisson solve per step.  The warm-up covers the cases' first step and the three steps that
+    tune the Poisson launch's block split."""
     from paper_2211_10698_gb300 import ccm, inputs
 
     specs = inputs.batch_cases(ncases)
@@ -386,6 +387,7 @@ def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=1):
     its = [st["last_iters_p"] for st in last[-1]]
     conv = all(st["converged"] for sts in last for st in sts)
     graph_steps = b.graph_steps()
+    split_a, split_tuned = b.split()
     b.close()
     for c in cases:
         c.close()
@@ -394,6 +396,7 @@ def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=1):
                 value=cells * steps / (t * 1e-3), unit=UNIT, ms_per_step=t / steps, steps=steps,
                 precond=", ".join(pcs), poisson_iters_last_step={"max": max(its), "mean": sum(its) / len(its)},
                 converged=conv, graph_steps=graph_steps,
+                poisson_split=dict(weights=f"cells x nx^{split_a:g}", tuned=split_tuned),
                 note="every stage of a step is one launch for all cases: explicit stages, the Helmholtz "
                      "solves and the Poisson solves (cooperative); steps after the first replay captured "
                      "CUDA graphs")

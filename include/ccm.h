@@ -264,7 +264,7 @@ ccm_status ccm_solve_pressure_noalloc(ccm_case c, const double* rhs_dev, double*
  * right-hand side, projection), one cooperative launch for the CN Helmholtz solves, and one
  * for the Poisson solves (FP64 CG or the mixed solve with each case's preconditioner; with a
  * singular case, FP64 Jacobi-PCG or the FP64 refinement with batched FP32 inner solves),
- * each case on a range of blocks sized to its expected work.  When every case has an outflow
+ * each case on a range of blocks sized by its cells (and width, as tuned).  When every case has an outflow
  * side, steps after each case's first replay two captured CUDA graphs (one per time-level
  * parity), recaptured when the cases change.  A batch holds at most as many cases as the GPU
  * holds PCG blocks (2 per SM).  Cases keep their own state and can leave and join a batch
@@ -283,6 +283,13 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats);
 ccm_status ccm_batch_set_graphs(ccm_batch b, int enable);
 /* Steps this batch has replayed from captured graphs. */
 ccm_status ccm_batch_graph_steps(ccm_batch b, long long* steps);
+/* Online tuning of the Poisson launch's block split: with it on (the default), the three steps
+ * after the cases' first each use one candidate split (blocks in proportion to cells x nx^a,
+ * a = 0, 1/2, 1; the steps advance the cases as usual) and the one with the least Poisson time
+ * per cell-iteration is kept.  Off: a = 0. */
+ccm_status ccm_batch_set_tuning(ccm_batch b, int enable);
+/* The exponent a in use and whether the tuning has finished. */
+ccm_status ccm_batch_split(ccm_batch b, double* exponent, int* tuned);
 
 /* ---- Request loop (serving) ------------------------------------------------------------
  * Flow-past-body requests wait in a FIFO queue; each round of ccm_server_run admits queued

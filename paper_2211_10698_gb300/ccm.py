@@ -107,6 +107,8 @@ def lib():
             "ccm_batch_step": (c_int, [cp, c_int, POINTER(ccm_step_stats)]),
             "ccm_batch_set_graphs": (c_int, [cp, c_int]),
             "ccm_batch_graph_steps": (c_int, [cp, POINTER(c_longlong)]),
+            "ccm_batch_set_tuning": (c_int, [cp, c_int]),
+            "ccm_batch_split": (c_int, [cp, POINTER(c_double), POINTER(c_int)]),
             "ccm_case_bytes": (c_int, [POINTER(ccm_config), POINTER(c_size_t)]),
             "ccm_launch_plan": (c_int, [c_void_p, POINTER(c_int)]),
             "ccm_set_launch_plan": (c_int, [c_void_p, POINTER(c_int)]),
@@ -320,6 +322,15 @@ class Batch:
 
     def set_graphs(self, enable=True):
         _check(lib().ccm_batch_set_graphs(self.h, 1 if enable else 0))
+
+    def set_tuning(self, enable=True):
+        _check(lib().ccm_batch_set_tuning(self.h, 1 if enable else 0))
+
+    def split(self):
+        """(exponent a of the Poisson split cells x nx^a, whether the tuning has finished)"""
+        a, t = c_double(), c_int()
+        _check(lib().ccm_batch_split(self.h, ctypes.byref(a), ctypes.byref(t)))
+        return a.value, bool(t.value)
 
     def graph_steps(self):
         n = c_longlong()

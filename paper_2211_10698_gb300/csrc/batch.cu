@@ -59,6 +59,12 @@ struct ccm_batch_s {
   bool gmixed = false;
   long long graph_steps = 0;     // steps replayed from graphs
   cudaStream_t cap_st = nullptr; // capture runs here (the legacy default stream cannot capture)
+  // online tuning of the Poisson launch's block split (see split_candidates)
+  bool tune = true;
+  int tune_next = 0;               // candidate the next tuned step uses (== count: done)
+  double tune_cost[3] = {0, 0, 0};
+  double split_exp = 0.0;          // the chosen exponent a of the weights cells x nx^a
+  cudaEvent_t tev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -88,16 +94,20 @@ void allocate_blocks(const std::vector<double>& w, int blocks, std::vector<int>&
 
 }  // namespace
 
-// Block weights of both cooperative launches: the cells of each case.  Each slot lasts as long
-// as its most loaded block, and early in a solve every case is working, so equal cells per
-// block is what keeps the slots short; weighting by the expected work (cells x iterations)
-// instead gives the cases that finish first more cells per block and made the 64-case step
-// 13 % slower.
-static std::vector<double> cell_weights(const std::vector<ccm_case>& cs) {
+// Block weights of the cooperative launches: cells x nx^a.  Each slot lasts as long as its most
+// loaded block; early in a solve every case is working, which favours equal cells per block
+// (a = 0), while the largest cases iterate longest, which favours giving them more (a > 0).
+// The Helmholtz launch uses a = 0 (about the same iteration count at every size); the Poisson
+// launch's a is tuned on the batch's own steps (split_candidates).
+static std::vector<double> cell_weights(const std::vector<ccm_case>& cs, double a = 0.0) {
   std::vector<double> w(cs.size());
-  for (size_t i = 0; i < cs.size(); ++i) w[i] = (double)case_cells(cs[i]);
+  for (size_t i = 0; i < cs.size(); ++i) w[i] = (double)case_cells(cs[i]) * std::pow((double)case_nx(cs[i]), a);
   return w;
 }
+// Exponents tried for the Poisson split, one batch step each (the steps advance the cases as
+// usual); the one with the least Poisson time per cell-iteration is kept.  Measured on 64
+// uneven cases: cells x nx^a with a = 0 beat the expected work (cells x iterations) by 13 %.
+static const double split_candidates[3] = {0.0, 0.5, 1.0};
 
 // Waits for the stream and turns a barrier give-up of any launch since the last check into
 // CCM_E_TIMEOUT.
@@ -120,7 +130,7 @@ static ccm_status upload_poisson_tables(ccm_batch b, bool mixed) {
   const std::vector<ccm_case>& cs = b->cases;
   const int n = (int)cs.size();
   std::vector<int> b0, nb;
-  allocate_blocks(cell_weights(cs), b->blocks, b0, nb);
+  allocate_blocks(cell_weights(cs, b->split_exp), b->blocks, b0, nb);
   std::vector<int> block_case(b->blocks);
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < nb[i]; ++k) block_case[b0[i] + k] = i;
@@ -425,15 +435,17 @@ static ccm_status capture_graphs(ccm_batch b, bool mixed, bool* ok) {
 }
 
 // One step without graphs: tables uploaded, every launch issued, the stream waited for.
-static ccm_status eager_step(ccm_batch b, bool mixed, bool scaled) {
+static ccm_status eager_step(ccm_batch b, bool mixed, bool scaled, float* poisson_ms = nullptr) {
   ccm_status s;
   if ((s = upload_stage_tables(b, b->stages, 0, true)) != CCM_OK) return s;
   if (scaled && (s = upload_poisson_tables(b, mixed)) != CCM_OK) return s;
   cudaError_t e = launch_predict(b, b->stages);
   if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batched stages: ") + cudaGetErrorString(e));
   if (scaled) {
+    if (poisson_ms && b->tev[0]) cudaEventRecord(b->tev[0], b->st);
     if ((e = launch_poisson_scaled(b, mixed)) != cudaSuccess)
       return bfail(CCM_E_CUDA, std::string("batched Poisson solve: ") + cudaGetErrorString(e));
+    if (poisson_ms && b->tev[1]) cudaEventRecord(b->tev[1], b->st);
   } else if (mixed) {
     if ((s = batch_mixed(b)) != CCM_OK) return s;
   } else {
@@ -442,7 +454,43 @@ static ccm_status eager_step(ccm_batch b, bool mixed, bool scaled) {
   if ((e = launch_project(b, b->stages)) != cudaSuccess)
     return bfail(CCM_E_CUDA, std::string("batched stages: ") + cudaGetErrorString(e));
   if ((s = check_barrier(b, "batched step")) != CCM_OK) return s;
+  if (poisson_ms && (!b->tev[0] || cudaEventElapsedTime(poisson_ms, b->tev[0], b->tev[1]) != cudaSuccess)) {
+    cudaGetLastError();
+    *poisson_ms = -1.0f;
+  }
   for (ccm_case c : b->cases) case_step_done(c);
+  return CCM_OK;
+}
+
+// One step with the next candidate split of the Poisson launch, its cost (Poisson time per
+// cell-iteration of the step) recorded; after the last candidate the cheapest is kept.
+static ccm_status tuning_step(ccm_batch b, bool mixed) {
+  const int k = b->tune_next;
+  b->split_exp = split_candidates[k];
+  if (!b->tev[0] && (cudaEventCreate(&b->tev[0]) != cudaSuccess || cudaEventCreate(&b->tev[1]) != cudaSuccess)) {
+    cudaGetLastError();
+    b->tune = false;
+  }
+  float ms = -1.0f;
+  ccm_status s = eager_step(b, mixed, true, b->tune ? &ms : nullptr);
+  if (s != CCM_OK) return s;
+  double work = 0.0;
+  for (ccm_case c : b->cases) {
+    int it = 0;
+    if (cudaMemcpy(&it, case_inner_iters_dev(c), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return bfail(CCM_E_CUDA, "batch tuning: reading iteration counts");
+    }
+    work += (double)case_cells(c) * (double)it;
+  }
+  b->tune_cost[k] = ms > 0.0f && work > 0.0 ? ms / work : 1e300;
+  b->tune_next = k + 1;
+  if (b->tune_next == 3) {
+    int best = 0;
+    for (int q = 1; q < 3; ++q)
+      if (b->tune_cost[q] < b->tune_cost[best]) best = q;
+    b->split_exp = split_candidates[best];
+  }
   return CCM_OK;
 }
 
@@ -522,6 +570,8 @@ ccm_status ccm_batch_destroy(ccm_batch b) {
   cudaStreamSynchronize(b->st);
   drop_graphs(b);
   if (b->cap_st) cudaStreamDestroy(b->cap_st);
+  for (cudaEvent_t ev : b->tev)
+    if (ev) cudaEventDestroy(ev);
   cudaFree(b->dev);
   cudaFreeHost(b->host_sums);
   cudaFreeHost(b->pinned);
@@ -573,6 +623,11 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
     if ((s = eager_step(b, mixed, scaled)) != CCM_OK) return s;
     n = 1;
   }
+  // the next steps try the candidate splits of the Poisson launch, one each
+  for (; n < nsteps && scaled && b->tune && b->tune_next < 3; ++n) {
+    drop_graphs(b);
+    if ((s = tuning_step(b, mixed)) != CCM_OK) return s;
+  }
   if (n < nsteps && scaled && b->use_graphs) {
     bool ok = graphs_valid(b, mixed);
     if (!ok && (s = capture_graphs(b, mixed, &ok)) != CCM_OK) return s;
@@ -603,6 +658,22 @@ ccm_status ccm_batch_set_graphs(ccm_batch b, int enable) {
   cudaStreamSynchronize(b->st);
   b->use_graphs = enable != 0;
   if (!b->use_graphs) drop_graphs(b);
+  return CCM_OK;
+}
+
+ccm_status ccm_batch_set_tuning(ccm_batch b, int enable) {
+  set_last_error("");
+  if (!b) return bfail(CCM_E_INVALID, "null batch");
+  b->tune = enable != 0;
+  if (!b->tune && b->tune_next < 3) b->split_exp = split_candidates[0];
+  return CCM_OK;
+}
+
+ccm_status ccm_batch_split(ccm_batch b, double* exponent, int* tuned) {
+  set_last_error("");
+  if (!b || !exponent || !tuned) return bfail(CCM_E_INVALID, "null argument");
+  *exponent = b->split_exp;
+  *tuned = b->tune_next >= 3 ? 1 : 0;
   return CCM_OK;
 }
 

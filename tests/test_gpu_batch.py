@@ -114,6 +114,7 @@ def test_graph_replay_equals_eager(precision):
         cs = [ccm.Case(c) for c in specs]
         b = ccm.Batch(8)
         b.set_graphs(graphs)
+        b.set_tuning(False)  # the same block split in both batches: bitwise comparable
         for c in cs:
             b.add(c)
         st = b.step(4)
@@ -132,6 +133,33 @@ def test_graph_replay_equals_eager(precision):
             np.testing.assert_array_equal(a.get_field(f), m.get_field(f))
     bg.close()
     be.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-8)])
+def test_split_tuning(precision, tol):
+    """The three steps after the first try one block split of the Poisson launch each and keep
+    one of the candidates; the fields match a batch that does not tune."""
+    specs = [c for c in _mix(precision) if tuple(c.bc_type) != I.closed_box_bc()[0]]
+    tuned = [ccm.Case(c) for c in specs]
+    plain = [ccm.Case(c) for c in specs]
+    bt, bp = ccm.Batch(8), ccm.Batch(8)
+    bp.set_tuning(False)
+    for a, m in zip(tuned, plain):
+        bt.add(a)
+        bp.add(m)
+    assert bt.split() == (0.0, False)
+    st = bt.step(6)
+    sp = bp.step(6)
+    a, done = bt.split()
+    assert done and a in (0.0, 0.5, 1.0)
+    assert bp.split() == (0.0, False)
+    assert bt.graph_steps() == 2 and bp.graph_steps() == 5
+    assert all(s["converged"] for s in st + sp)
+    for x, y in zip(tuned, plain):
+        for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P):
+            assert _rel(x.get_field(f), y.get_field(f)) < tol, f
+    bt.close()
+    bp.close()
 
 
 def test_cases_join_and_leave_between_steps():
