@@ -75,6 +75,24 @@ def _dist():
     return rank, world, local
 
 
+def job_time_ms(t_ms, world, device="cuda"):
+    """Length of the timed region for the whole job: every rank's own total (ms), reduced with
+    MAX over the ranks (the slowest replica sets the job's time)."""
+    if world <= 1:
+        return t_ms
+    import torch
+
+    t = torch.tensor([t_ms], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, cells, steps, t_ms):
+    """Whole-job throughput in cell-steps/s: the cells every replica advanced, over the slowest
+    replica's time (replicas: no data moves between ranks)."""
+    return world * cells * steps / (t_ms * 1e-3)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -490,12 +508,8 @@ def run_ours(args):
     st = g.read_stats()
     kt = g.kernel_timing()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * case.cells * args.steps / (t_ms * 1e-3)
+    t_ms = job_time_ms(sum(step_ms), world)
+    value = job_value(world, case.cells, args.steps, t_ms)
     iters_p = st["iters_p"] / args.steps
     iters_h = st["iters_h"] / args.steps
 
