@@ -87,6 +87,7 @@ def _load():
             "orc_solve_helmholtz": (c_int, [cp, _DP, _DP, _DP, _DP, _DP, c_double, c_int, ip, _DP]),
             "orc_kinetic": (c_double, [cp, _DP, _DP, _DP]),
             "orc_max_div": (c_double, [cp, _DP, _DP, _DP]),
+            "orc_body_force": (None, [cp, _DP, _DP, _DP, _DP, _DP]),
             "orc_init_velocity": (None, [cp, _DP, c_double, c_double, _DP, _DP, _DP, _DP]),
             "orc_step": (c_int, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP,
                                  POINTER(OrcStats)]),
@@ -271,6 +272,13 @@ class Oracle:
 
     def max_div(self, u, v):
         return self.lib.orc_max_div(ctypes.byref(self.s), _p(self.caps), _p(self._c(u)), _p(self._c(v)))
+
+    def body_force(self, u, v, p):
+        """(Fp_x, Fp_y, Fv_x, Fv_y): pressure and viscous force of the fluid on the body."""
+        f = np.zeros(4)
+        self.lib.orc_body_force(ctypes.byref(self.s), _p(self.caps), _p(self._c(u)), _p(self._c(v)),
+                                _p(self._c(p)), _p(f))
+        return f
 
     def cell_boundary(self, grid, i, j):
         a, b = c_double(0.0), c_double(0.0)

@@ -1139,6 +1139,56 @@ double orc_max_div(const orc_case* c, const double* caps, const double* u, const
 }
 
 /* ------------------------------------------------------------------------------------------
+ * Force on the body (the paper reports drag and lift, Sec. 5, but defines no discrete force).
+ * Reading: the force the fluid exerts on the body is minus the body's share of the momentum
+ * the pressure and viscous terms of Eq. pm_prediction give the fluid.  Summing pres_alpha(P)
+ * and visc_alpha(2 mu S) over the velocity positions of the box and moving the difference
+ * operators onto the capacities (summation by parts) leaves box-boundary fluxes plus terms in
+ * the differences of A and B across cells, which vanish wherever the grid is uncut; those
+ * terms are the body's share.  Per component, with F = (Fp_x, Fp_y, Fv_x, Fv_y):
+ *   Fp_x = sum_cells P (A^x_left - A^x_right)        (= sum P n_x |Gamma| by Eq. SCL: the
+ *   Fp_y = sum_cells P (A^y_bottom - A^y_top)           normal pointing out of the fluid)
+ *   Fv_x = -2 mu [ sum_cells S_xx (B^xx_left - B^xx_right) + sum_nodes S_xy (B^xy_below - B^xy_above) ]
+ *   Fv_y = -2 mu [ sum_cells S_yy (B^yy_below - B^yy_above) + sum_nodes S_xy (B^yx_left - B^yx_right) ]
+ * over p-cells i in [0,nx), j in [0,ny); the S_xy sums run over the nodes whose two u-faces
+ * (i in [0,nx], j in [1,ny)) or two v-faces (i in [1,nx), j in [0,ny]) lie in the box.
+ * S is the strain of Eqs. diag and offdiag with D = 0 (no-slip body).
+ * ---------------------------------------------------------------------------------------- */
+void orc_body_force(const orc_case* c, const double* caps, const double* u, const double* v, const double* p,
+                    double* force) {
+  const double* Ax = CAP(c, caps, G_P, K_AX);
+  const double* Ay = CAP(c, caps, G_P, K_AY);
+  const double* BxU = CAP(c, caps, G_U, K_BX);
+  const double* ByU = CAP(c, caps, G_U, K_BY);
+  const double* BxV = CAP(c, caps, G_V, K_BX);
+  const double* ByV = CAP(c, caps, G_V, K_BY);
+  size_t S = SIZE(c);
+  double* sxx = malloc(S * sizeof(double));
+  double* syy = malloc(S * sizeof(double));
+  double* sxy = malloc(S * sizeof(double));
+  orc_strain(c, caps, u, v, NULL, NULL, sxx, syy, sxy);
+  double fpx = 0.0, fpy = 0.0, gx = 0.0, gy = 0.0;
+  for (int j = 0; j < c->ny; ++j)
+    for (int i = 0; i < c->nx; ++i) {
+      fpx += AT(c, p, i, j) * (AT(c, Ax, i, j) - AT(c, Ax, i + 1, j));
+      fpy += AT(c, p, i, j) * (AT(c, Ay, i, j) - AT(c, Ay, i, j + 1));
+      gx += AT(c, sxx, i, j) * (AT(c, BxU, i, j) - AT(c, BxU, i + 1, j));
+      gy += AT(c, syy, i, j) * (AT(c, ByV, i, j) - AT(c, ByV, i, j + 1));
+    }
+  for (int j = 1; j < c->ny; ++j)
+    for (int i = 0; i <= c->nx; ++i) gx += AT(c, sxy, i, j) * (AT(c, ByU, i, j - 1) - AT(c, ByU, i, j));
+  for (int j = 0; j <= c->ny; ++j)
+    for (int i = 1; i < c->nx; ++i) gy += AT(c, sxy, i, j) * (AT(c, BxV, i - 1, j) - AT(c, BxV, i, j));
+  force[0] = fpx;
+  force[1] = fpy;
+  force[2] = -2.0 * c->mu * gx;
+  force[3] = -2.0 * c->mu * gy;
+  free(sxx);
+  free(syy);
+  free(sxy);
+}
+
+/* ------------------------------------------------------------------------------------------
  * Initial velocity: u = bc_un[W] (the inflow speed) on every u-position whose control
  * volume holds fluid, v = 0; then the seeded perturbation (may be NULL) on the unknowns;
  * then the Dirichlet faces and ghosts.

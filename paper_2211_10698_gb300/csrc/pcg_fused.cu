@@ -47,7 +47,9 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
   __shared__ double sc_alpha, sc_beta, sc_igamma, sc_ialpha, sc_rr, sc_bb;
   __shared__ int sc_it, sc_stop;
   // dynamic shared memory: with RES x~, r, p, s, w of the tile (TX*TY each), then the ring
-  // [W: TY][E: TY][S: TX][N: TX], then with RES the tile's row kinds, then the list
+  // [W: TY][E: TY][S: TX][N: TX], then with RES the tile's row kinds, then the list, then with
+  // RES the five scaled coefficients of the first kNT listed cells (8-byte aligned: TX is a
+  // multiple of 32)
   extern __shared__ double dyn[];
   unsigned int target = 0;
   const ScaledSolve& a = f.a;
@@ -134,6 +136,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
   // in every vector after it, so the stencil pass only has to write w = 0 there.  A tile with
   // more listed cells than the list holds takes the general row for every cell instead.
   int* const list = RES ? reinterpret_cast<int*>(skind + TXY) : reinterpret_cast<int*>(ring + 2 * (TX + TY));
+  double* const lcoef = reinterpret_cast<double*>(list + TXY);  // RES: 5 x kNT
   __shared__ int s_scan[kNT / 32 + 1];
   int nlist = 0;
   bool general = false;
@@ -169,6 +172,18 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
         if (kinds[g.idx(ci, j)] == 2) list[at++] = (j - j0) * TX + tx;
     }
     __syncthreads();
+    if constexpr (RES) {
+      // the first kNT listed cells' scaled coefficients, constant for the whole solve
+      if (!general && threadIdx.x < nlist) {
+        const int q = list[threadIdx.x];
+        const size_t k = g.idx(i0 + q % TX, j0 + q / TX);
+        lcoef[threadIdx.x] = cus[k];
+        lcoef[kNT + threadIdx.x] = cus[k + 1];
+        lcoef[2 * kNT + threadIdx.x] = cvs[k];
+        lcoef[3 * kNT + threadIdx.x] = cvs[k + P];
+        lcoef[4 * kNT + threadIdx.x] = sd[k];
+      }
+    }
   }
   // the general row at own cell (i, j) (any kind); w = K~ r and the sums of a row of kind km
   auto general_row = [&](const double* rn, int i, int j, double& rc_out) -> double {
@@ -211,7 +226,12 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
       const size_t k = g.idx(li, lj);
       lr[0] = rown(rn, li, lj); lr[1] = rnb(rn, li - 1, lj); lr[2] = rnb(rn, li + 1, lj);
       lr[3] = rnb(rn, li, lj - 1); lr[4] = rnb(rn, li, lj + 1);
-      lc[0] = cus[k]; lc[1] = cus[k + 1]; lc[2] = cvs[k]; lc[3] = cvs[k + P]; lc[4] = sd[k];
+      if constexpr (RES) {
+        lc[0] = lcoef[threadIdx.x]; lc[1] = lcoef[kNT + threadIdx.x]; lc[2] = lcoef[2 * kNT + threadIdx.x];
+        lc[3] = lcoef[3 * kNT + threadIdx.x]; lc[4] = lcoef[4 * kNT + threadIdx.x];
+      } else {
+        lc[0] = cus[k]; lc[1] = cus[k + 1]; lc[2] = cvs[k]; lc[3] = cvs[k + P]; lc[4] = sd[k];
+      }
     }
     // constant stencil on every own cell but the listed ones, two rows of this thread at a time
     if constexpr (RES) {
@@ -483,10 +503,11 @@ int fused_blocks() {
 }
 
 // Dynamic shared memory of a tile with its vectors resident (f2): x~, r, p, s, w, the ring, the
-// row kinds and a list of up to one entry per cell.
+// row kinds, a list of up to one entry per cell and the coefficients of kNT listed cells.
 size_t fused_resident_smem(int TX, int TY) {
   const size_t txy = (size_t)TX * (size_t)TY;
-  return 5 * sizeof(double) * txy + sizeof(double) * 2 * ((size_t)TX + (size_t)TY) + txy + sizeof(int) * txy;
+  return 5 * sizeof(double) * txy + sizeof(double) * 2 * ((size_t)TX + (size_t)TY) + txy + sizeof(int) * txy +
+         5 * sizeof(double) * kNT;
 }
 
 // Whether ntiles tiles of TX x TY cells with resident vectors fit the GPU at once.
