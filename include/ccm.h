@@ -219,6 +219,32 @@ ccm_status ccm_step_async(ccm_case c, int nsteps);
  * ccm_step). */
 ccm_status ccm_read_stats(ccm_case c, ccm_step_stats* stats);
 
+/* Force of the fluid on the body at the current state (U^n and P^{n-1/2} after the last
+ * step), force[4] = {Fp_x, Fp_y, Fv_x, Fv_y}: the pressure and viscous parts, in the case's
+ * units (per unit depth).  The paper reports drag and lift (Sec. 5) without a discrete
+ * definition; this is the body's share of the momentum that pres(P) and visc(2 mu S) give the
+ * fluid (Secs. 4.1, 4.3), i.e. with A-differences across cells equal to -n |Gamma| (Eq. SCL):
+ *   Fp_x = sum_cells P (A^x_{i-1/2,j} - A^x_{i+1/2,j}),  Fp_y likewise with A^y in y,
+ *   Fv_x = -2 mu [sum_cells S_xx (B^xx_{i-1/2} - B^xx_{i+1/2}) + sum_nodes S_xy (B^xy_{j-1/2} - B^xy_{j+1/2})],
+ *   Fv_y = -2 mu [sum_cells S_yy (B^yy_{j-1/2} - B^yy_{j+1/2}) + sum_nodes S_xy (B^yx_{i-1/2} - B^yx_{i+1/2})],
+ * S of Eqs. diag and offdiag with D = 0 (no-slip body).  The terms vanish wherever the grid is
+ * uncut.  force is a host array the caller owns.  Waits for the case's stream.  CCM_E_STATE
+ * before ccm_set_geometry. */
+ccm_status ccm_body_force(ccm_case c, double force[4]);
+
+/* Record the body force after every step of ccm_step / ccm_step_async (a reduction enqueued
+ * after the step, no host synchronisation) into a device ring of `capacity` rows of four
+ * doubles, allocated with the case's allocator; 0 stops recording and frees it.  Setting a
+ * capacity clears the record.  Waits for the case's stream.  CCM_E_OOM if the ring cannot be
+ * allocated (recording is then off). */
+ccm_status ccm_set_force_history(ccm_case c, int capacity);
+
+/* Copy the newest min(max_rows, recorded, capacity) rows of the record, oldest first, into
+ * host[rows][4]; *rows receives that count and *total (may be NULL) the number of steps
+ * recorded since ccm_set_force_history.  Row k is what ccm_body_force would have returned
+ * after that step.  Waits for the case's stream. */
+ccm_status ccm_get_force_history(ccm_case c, double* host, int max_rows, int* rows, long long* total);
+
 /* Per-launch timing of the dominant kernel (the Poisson PCG): when enabled, CUDA events are
  * recorded on the case's stream around every Poisson PCG launch.  ccm_kernel_timing
  * returns (and resets) the summed event time in ms, the number of PCG launches, the PCG

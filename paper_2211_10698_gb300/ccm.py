@@ -95,6 +95,9 @@ def lib():
             "ccm_solve_pressure": (c_int, [cp, _DP, POINTER(ccm_solve_stats)]),
             "ccm_step_async": (c_int, [cp, c_int]),
             "ccm_read_stats": (c_int, [cp, POINTER(ccm_step_stats)]),
+            "ccm_body_force": (c_int, [cp, _DP]),
+            "ccm_set_force_history": (c_int, [cp, c_int]),
+            "ccm_get_force_history": (c_int, [cp, _DP, c_int, POINTER(c_int), POINTER(c_longlong)]),
             "ccm_enable_kernel_timing": (c_int, [cp, c_int]),
             "ccm_kernel_timing": (c_int, [cp, POINTER(c_double), POINTER(c_longlong), POINTER(c_longlong),
                                           POINTER(c_longlong)]),
@@ -275,6 +278,30 @@ class Case:
         allow = (CCM_E_NOT_CONVERGED,) if allow_not_converged else ()
         _check(lib().ccm_read_stats(self.h, ctypes.byref(st)), allow)
         return {f: getattr(st, f) for f, _ in ccm_step_stats._fields_}
+
+    def body_force(self):
+        """(Fp_x, Fp_y, Fv_x, Fv_y): pressure and viscous force of the fluid on the body at the
+        current state."""
+        f = np.zeros(4)
+        _check(lib().ccm_body_force(self.h, _ptr(f)))
+        return f
+
+    def set_force_history(self, capacity):
+        """Record the body force after every step (newest ``capacity`` steps kept)."""
+        _check(lib().ccm_set_force_history(self.h, int(capacity)))
+        self._force_capacity = int(capacity)
+
+    def force_history(self, max_rows=None):
+        """(rows x 4 array of recorded forces, oldest first; steps recorded in total)."""
+        n = c_int()
+        tot = c_longlong()
+        _check(lib().ccm_get_force_history(self.h, None, 0, ctypes.byref(n), ctypes.byref(tot)))
+        kept = min(tot.value, getattr(self, "_force_capacity", 0))
+        cap = kept if max_rows is None else int(max_rows)
+        out = np.zeros((max(cap, 0), 4))
+        _check(lib().ccm_get_force_history(self.h, _ptr(out) if cap > 0 else None, cap, ctypes.byref(n),
+                                           ctypes.byref(tot)))
+        return out[:n.value], tot.value
 
     def enable_kernel_timing(self, on=True):
         _check(lib().ccm_enable_kernel_timing(self.h, 1 if on else 0))

@@ -87,6 +87,13 @@ struct ccm_case_s {
   bool mixed_host = false;  // a host-driven refinement ran since the statistics were last read
   TuneResult tune{};        // launch shape of the one-launch Poisson solve (zero: built-in)
   unsigned long long serial = 0;  // unique per case for the life of the process
+  // force on the body: block partials and the last value; optional per-step record (a ring of
+  // fcap rows of four doubles, allocated on demand; frec steps recorded so far)
+  double* fpart = nullptr;
+  double* fout = nullptr;
+  double* fhist = nullptr;
+  int fcap = 0;
+  long long frec = 0;
 };
 
 namespace {
@@ -132,6 +139,8 @@ void carve(ccm_case c, Carver& cv) {
   c->mixed_sums = cv.take<double>(4);
   c->partials = cv.take<double>((size_t)pcg_partials_needed());
   c->dpart = cv.take<double>((size_t)3 * diagnostics_partials(c->g) + 8);
+  c->fpart = cv.take<double>((size_t)body_force_partials(c->g));
+  c->fout = cv.take<double>(4);
   c->bar_count = cv.take<unsigned int>(kBarWords);
   c->bar_err = cv.take<int>(4);
   c->ds = cv.take<DevStats>(1);
@@ -808,10 +817,21 @@ ccm_status ccm_case_bytes(const ccm_config* cfg, size_t* bytes) {
   return CCM_OK;
 }
 
+static void free_force_history(ccm_case c) {
+  if (c->fhist) {
+    if (c->cfg.free) c->cfg.free(c->fhist, c->cfg.alloc_ctx);
+    else cudaFree(c->fhist);
+  }
+  c->fhist = nullptr;
+  c->fcap = 0;
+  c->frec = 0;
+}
+
 ccm_status ccm_destroy_case(ccm_case c) {
   if (!c) return CCM_OK;
   cudaStreamSynchronize(c->st);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  free_force_history(c);
   if (c->slab) {
     if (c->cfg.free) c->cfg.free(c->slab, c->cfg.alloc_ctx);
     else cudaFree(c->slab);
@@ -1050,6 +1070,12 @@ static void stage_project(ccm_case c) {
   launch_project(c->cv, g, c->phi, c->u, c->v, c->p, st);
   launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
   c->launches += 7;  // fill_bc x3, predictor, Helmholtz PCG, divergence, projection
+  if (c->fcap > 0) {
+    // the force of the new state (U^{n+1}, P^{n+1/2}) into the next row of the record
+    launch_body_force(c->cv, g, c->ph, c->u, c->v, c->p, c->fpart, c->fhist + 4 * (c->frec % c->fcap), st);
+    c->frec++;
+    c->launches += 2;
+  }
   c->cur = 1 - c->cur;
   c->nstep++;
   c->steps_pending++;
@@ -1128,6 +1154,61 @@ ccm_status ccm_read_stats(ccm_case c, ccm_step_stats* stats) {
   if (!c) return fail(CCM_E_INVALID, "null case");
   if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
   return finish_stats(c, stats);
+}
+
+ccm_status ccm_body_force(ccm_case c, double force[4]) {
+  g_last_error.clear();
+  if (!c || !force) return fail(CCM_E_INVALID, "null argument");
+  if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
+  launch_body_force(c->cv, c->g, c->ph, c->u, c->v, c->p, c->fpart, c->fout, c->st);
+  CUDA_TRY(cudaMemcpyAsync(force, c->fout, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  return check_cuda_errors("body_force");
+}
+
+ccm_status ccm_set_force_history(ccm_case c, int capacity) {
+  g_last_error.clear();
+  if (!c) return fail(CCM_E_INVALID, "null case");
+  if (capacity < 0) return fail(CCM_E_INVALID, "capacity < 0");
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  free_force_history(c);
+  if (capacity == 0) return CCM_OK;
+  const size_t bytes = (size_t)capacity * 4 * sizeof(double);
+  void* mem = nullptr;
+  if (c->cfg.alloc) {
+    mem = c->cfg.alloc(bytes, c->cfg.alloc_ctx);
+    if (!mem) return fail(CCM_E_OOM, "allocator hook returned NULL");
+  } else {
+    cudaError_t e = cudaMalloc(&mem, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CCM_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
+  c->fhist = (double*)mem;
+  c->fcap = capacity;
+  c->frec = 0;
+  return CCM_OK;
+}
+
+ccm_status ccm_get_force_history(ccm_case c, double* host, int max_rows, int* rows, long long* total) {
+  g_last_error.clear();
+  if (!c || !rows || (max_rows > 0 && !host) || max_rows < 0) return fail(CCM_E_INVALID, "bad argument");
+  if (total) *total = c->frec;
+  const long long kept = std::min<long long>(c->frec, c->fcap);
+  const int n = (int)std::min<long long>(kept, max_rows);
+  *rows = n;
+  if (n == 0) return CCM_OK;
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  // the newest n rows, oldest first: ring positions (frec - n) .. (frec - 1) modulo fcap
+  const long long first = c->frec - n;
+  const int r0 = (int)(first % c->fcap);
+  const int part = std::min(n, c->fcap - r0);
+  CUDA_TRY(cudaMemcpy(host, c->fhist + 4 * (size_t)r0, (size_t)part * 4 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (part < n)
+    CUDA_TRY(cudaMemcpy(host + 4 * (size_t)part, c->fhist, (size_t)(n - part) * 4 * sizeof(double),
+                        cudaMemcpyDeviceToHost));
+  return CCM_OK;
 }
 
 ccm_status ccm_enable_kernel_timing(ccm_case c, int enable) {

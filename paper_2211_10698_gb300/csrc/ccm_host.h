@@ -104,11 +104,14 @@ struct FusedSolve {
   int TX, TY, nbx, ntiles;  // tile plan; TX = 0 lets the launcher choose
   int list_cap;             // set by the launcher: entries of the per-tile list of non-uniform cells
   int resident;             // 1: each tile keeps its vectors in shared memory (k_pcg_poisson_f2)
+  int lcache;               // set by the launcher (resident): the listed cells' coefficients cached in shared memory
 };
 cudaError_t run_poisson_fused(FusedSolve f, cudaStream_t st);
 void fused_tiles(int nx, int ny, int blocks, int* TX, int* TY, int* nbx, int* ntiles);
 int fused_blocks();
-size_t fused_resident_smem(int TX, int TY);
+size_t fused_resident_smem(int TX, int TY, bool cache);
+bool fused_resident_fits(int TX, int TY, int ntiles, bool cache);
+int fused_resident_fit(int TX, int TY, int ntiles);
 bool fused_resident_ok(int TX, int TY, int ntiles);
 
 // The same solve for small grids inside one thread-block cluster (pcg_cluster.cu).
@@ -292,6 +295,11 @@ void launch_divergence(const Coefs& c, const Geom& g, const Phys& ph, const doub
                        double* rhs, cudaStream_t st);
 void launch_project(const Coefs& c, const Geom& g, const double* phi, double* u, double* v, double* p, cudaStream_t st);
 int diagnostics_partials(const Geom& g);
+// Force of the fluid on the body, out[4] = (Fp_x, Fp_y, Fv_x, Fv_y) (operators.cu); partials
+// holds body_force_partials(g) doubles.
+int body_force_partials(const Geom& g);
+void launch_body_force(const Coefs& c, const Geom& g, const Phys& ph, const double* u, const double* v,
+                       const double* p, double* partials, double* out, cudaStream_t st);
 void launch_residual64(const Coefs& c, const Geom& g, const double* x, const double* b, float* r32, double* partials,
                        double* out2, cudaStream_t st);
 void launch_add_correction(const Geom& g, const int8_t* act, double* x, const float* d, cudaStream_t st);

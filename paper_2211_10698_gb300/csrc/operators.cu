@@ -401,6 +401,86 @@ __global__ void k_diagnostics_final(const double* partials, int nb, double* out)
   if (t == 0) { out[0] = sm[0][0]; out[1] = sm[1][0]; out[2] = sm[2][0]; }
 }
 
+// Force of the fluid on the body: the body's share of the momentum that pres(P) and
+// visc(2 mu S) give the fluid (the paper reports drag and lift, Sec. 5, without a discrete
+// force).  Moving the differences of pres and visc onto the capacities (summation by parts)
+// leaves, besides box-boundary fluxes, terms in the differences of A and B across cells, which
+// vanish wherever the grid is uncut:
+//   Fp_x = sum_cells P (A^x_left - A^x_right),  Fp_y = sum_cells P (A^y_bottom - A^y_top),
+//   Fv_x = -2 mu [sum_cells S_xx (B^xx_left - B^xx_right) + sum_nodes S_xy (B^xy_below - B^xy_above)],
+//   Fv_y = -2 mu [sum_cells S_yy (B^yy_below - B^yy_above) + sum_nodes S_xy (B^yx_left - B^yx_right)],
+// cells i in [0,nx), j in [0,ny); the S_xy sums over the nodes whose two u-faces (i in [0,nx],
+// j in [1,ny)) or two v-faces (i in [1,nx), j in [0,ny]) lie in the box.  One thread per
+// (i, j) in [0,nx] x [0,ny] takes the cell and the node of that index; the strain is evaluated
+// only where its B-difference is nonzero (0 * S adds nothing).  Per-block partials of the four
+// sums (before the factor -2 mu), in a fixed tree order.
+__global__ void k_body_force(Coefs c, Geom g, FullView w, const double* p, double* partials) {
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
+  const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
+  double f[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i >= 0 && j >= 0 && i <= g.nx && j <= g.ny) {
+    const size_t k = g.idx(i, j);
+    if (i < g.nx && j < g.ny) {
+      const double pk = p[k];
+      f[0] = pk * (c.ax[k] - c.ax[k + 1]);
+      f[1] = pk * (c.ay[k] - c.ay[k + g.pitch]);
+      const double dbx = c.bxx[k] - c.bxx[k + 1];
+      if (dbx != 0.0) f[2] = strain_xx(c, g, w, i, j) * dbx;
+      const double dby = c.byy[k] - c.byy[k + g.pitch];
+      if (dby != 0.0) f[3] = strain_yy(c, g, w, i, j) * dby;
+    }
+    const double dnx = (j >= 1 && j < g.ny) ? c.bxy[k - g.pitch] - c.bxy[k] : 0.0;
+    const double dny = (i >= 1 && i < g.nx) ? c.byx[k - 1] - c.byx[k] : 0.0;
+    if (dnx != 0.0 || dny != 0.0) {
+      const double sxy = strain_xy(c, g, w, i, j);
+      f[2] += sxy * dnx;
+      f[3] += sxy * dny;
+    }
+  }
+  __shared__ double sm[4][256];
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sm[q][t] = f[q];
+  __syncthreads();
+  for (int s = (blockDim.x * blockDim.y) / 2; s > 0; s >>= 1) {
+    if (t < s)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sm[q][t] += sm[q][t + s];
+    __syncthreads();
+  }
+  if (t == 0) {
+    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    const size_t nb = (size_t)gridDim.x * gridDim.y;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) partials[q * nb + b] = sm[q][0];
+  }
+}
+
+// The four sums over the blocks in a fixed order; out = (Fp_x, Fp_y, Fv_x, Fv_y).
+__global__ void k_body_force_final(const double* partials, int nb, double mu, double* out) {
+  __shared__ double sm[4][256];
+  const int t = threadIdx.x;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = t; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] += partials[(size_t)q * nb + b];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sm[q][t] = s[q];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (t < st)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sm[q][t] += sm[q][t + st];
+    __syncthreads();
+  }
+  if (t == 0) {
+    out[0] = sm[0][0];
+    out[1] = sm[1][0];
+    out[2] = -2.0 * mu * sm[2][0];
+    out[3] = -2.0 * mu * sm[3][0];
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Mixed-precision refinement of the Poisson solve: FP64 residual r = b - K x (stored to
 // FP32 for the inner solve) with per-block sums of r.r and b.b, and x += d.
@@ -552,6 +632,16 @@ cudaError_t launch_stage_batch(int kind, const StageCase* dev_cases, const int* 
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+int body_force_partials(const Geom& g) {
+  dim3 gr = pad_grid(g, kBlk);
+  return 4 * (int)(gr.x * gr.y);
+}
+void launch_body_force(const Coefs& c, const Geom& g, const Phys& ph, const double* u, const double* v,
+                       const double* p, double* partials, double* out, cudaStream_t st) {
+  dim3 gr = pad_grid(g, kBlk);
+  k_body_force<<<gr, kBlk, 0, st>>>(c, g, FullView{u, v, g}, p, partials);
+  k_body_force_final<<<1, 256, 0, st>>>(partials, (int)(gr.x * gr.y), ph.mu, out);
 }
 int diagnostics_partials(const Geom& g) {
   dim3 gr = pad_grid(g, kBlk);

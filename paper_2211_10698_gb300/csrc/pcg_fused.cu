@@ -48,8 +48,8 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
   __shared__ int sc_it, sc_stop;
   // dynamic shared memory: with RES x~, r, p, s, w of the tile (TX*TY each), then the ring
   // [W: TY][E: TY][S: TX][N: TX], then with RES the tile's row kinds, then the list, then with
-  // RES the five scaled coefficients of the first kNT listed cells (8-byte aligned: TX is a
-  // multiple of 32)
+  // RES and f.lcache the five scaled coefficients of the first kNT listed cells (8-byte aligned:
+  // TX is a multiple of 32)
   extern __shared__ double dyn[];
   unsigned int target = 0;
   const ScaledSolve& a = f.a;
@@ -174,7 +174,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
     __syncthreads();
     if constexpr (RES) {
       // the first kNT listed cells' scaled coefficients, constant for the whole solve
-      if (!general && threadIdx.x < nlist) {
+      if (f.lcache && !general && threadIdx.x < nlist) {
         const int q = list[threadIdx.x];
         const size_t k = g.idx(i0 + q % TX, j0 + q / TX);
         lcoef[threadIdx.x] = cus[k];
@@ -226,7 +226,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
       const size_t k = g.idx(li, lj);
       lr[0] = rown(rn, li, lj); lr[1] = rnb(rn, li - 1, lj); lr[2] = rnb(rn, li + 1, lj);
       lr[3] = rnb(rn, li, lj - 1); lr[4] = rnb(rn, li, lj + 1);
-      if constexpr (RES) {
+      if (RES && f.lcache) {
         lc[0] = lcoef[threadIdx.x]; lc[1] = lcoef[kNT + threadIdx.x]; lc[2] = lcoef[2 * kNT + threadIdx.x];
         lc[3] = lcoef[3 * kNT + threadIdx.x]; lc[4] = lcoef[4 * kNT + threadIdx.x];
       } else {
@@ -503,16 +503,24 @@ int fused_blocks() {
 }
 
 // Dynamic shared memory of a tile with its vectors resident (f2): x~, r, p, s, w, the ring, the
-// row kinds, a list of up to one entry per cell and the coefficients of kNT listed cells.
-size_t fused_resident_smem(int TX, int TY) {
+// row kinds, a list of up to one entry per cell and, with `cache`, the coefficients of kNT
+// listed cells.
+size_t fused_resident_smem(int TX, int TY, bool cache) {
   const size_t txy = (size_t)TX * (size_t)TY;
   return 5 * sizeof(double) * txy + sizeof(double) * 2 * ((size_t)TX + (size_t)TY) + txy + sizeof(int) * txy +
-         5 * sizeof(double) * kNT;
+         (cache ? 5 * sizeof(double) * kNT : 0);
 }
 
-// Whether ntiles tiles of TX x TY cells with resident vectors fit the GPU at once.
-bool fused_resident_ok(int TX, int TY, int ntiles) {
-  const size_t smem = fused_resident_smem(TX, TY);
+// Whether ntiles tiles of TX x TY cells with resident vectors fit the GPU at once: with the
+// coefficient cache (2), only without it (1), or not at all (0).
+int fused_resident_fit(int TX, int TY, int ntiles) {
+  if (fused_resident_fits(TX, TY, ntiles, true)) return 2;
+  return fused_resident_fits(TX, TY, ntiles, false) ? 1 : 0;
+}
+bool fused_resident_ok(int TX, int TY, int ntiles) { return fused_resident_fit(TX, TY, ntiles) != 0; }
+
+bool fused_resident_fits(int TX, int TY, int ntiles, bool cache) {
+  const size_t smem = fused_resident_smem(TX, TY, cache);
   int dev = 0, sms = 0, per = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -534,10 +542,12 @@ cudaError_t run_poisson_fused(FusedSolve f, cudaStream_t st) {
   size_t smem = 0;
   if (f.resident) {
     // the tile's vectors in shared memory: as many blocks as fit must hold every tile
-    smem = fused_resident_smem(f.TX, f.TY);
+    const int fit = fused_resident_fit(f.TX, f.TY, f.ntiles);
+    if (fit == 0) return cudaErrorInvalidConfiguration;
+    f.lcache = fit == 2 ? 1 : 0;
+    smem = fused_resident_smem(f.TX, f.TY, f.lcache != 0);
     f.list_cap = f.TX * f.TY;
     kernel = (const void*)k_pcg_poisson_f2;
-    if (!fused_resident_ok(f.TX, f.TY, f.ntiles)) return cudaErrorInvalidConfiguration;
   } else {
     const size_t ring = sizeof(double) * 2 * ((size_t)f.TX + (size_t)f.TY);
     if (ring + sizeof(int) * 256 > kFusedSmemMax || f.ntiles > blocks) return cudaErrorInvalidConfiguration;

@@ -39,7 +39,7 @@ std::vector<TilePlan> fused_plan_candidates(int nx, int ny, int blocks) {
   }
   const size_t n = out.size();
   for (size_t q = 0; q < n; ++q)
-    if (fused_resident_smem(out[q].TX, out[q].TY) <= 227 * 1024) {
+    if (fused_resident_smem(out[q].TX, out[q].TY, false) <= 227 * 1024) {
       TilePlan r = out[q];
       r.resident = 1;
       out.push_back(r);
