@@ -93,6 +93,10 @@ def _load():
                                  POINTER(OrcStats)]),
             "orc_roles": (None, [cp, _DP, ip, ip, ip]),
             "orc_predictor_rhs": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP, _DP]),
+            "orc_predictor_rhs_g": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP, _DP, _DP,
+                                           _DP]),
+            "orc_step_g": (c_int, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP, _DP, _DP,
+                                   POINTER(OrcStats)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -310,9 +314,11 @@ class Oracle:
         hist = []
         for _ in range(nsteps):
             us, vs, bd = (self.z(), self.z(), self.z()) if keep else (None, None, None)
-            ok = self.lib.orc_step(ctypes.byref(self.s), _p(self.caps), _p(st["u"]), _p(st["v"]), _p(st["p"]),
-                                   _p(st["phi"]), _p(st["cu"]), _p(st["cv"]), 1 if st["n"] == 0 else 0,
-                                   _p(us), _p(vs), _p(bd), ctypes.byref(stats))
+            # st may carry a body acceleration "gx" (u-faces), "gy" (v-faces): Eq. pm_prediction's rho V g
+            gx, gy = st.get("gx"), st.get("gy")
+            ok = self.lib.orc_step_g(ctypes.byref(self.s), _p(self.caps), _p(st["u"]), _p(st["v"]), _p(st["p"]),
+                                     _p(st["phi"]), _p(st["cu"]), _p(st["cv"]), 1 if st["n"] == 0 else 0,
+                                     _p(self._c(gx)), _p(self._c(gy)), _p(us), _p(vs), _p(bd), ctypes.byref(stats))
             st["n"] += 1
             hist.append(dict(iters_h=stats.iters_h, iters_p=stats.iters_p, res_h=stats.res_h,
                              res_p=stats.res_p, max_div=stats.max_div, kinetic=stats.kinetic,

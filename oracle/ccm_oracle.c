@@ -1231,8 +1231,11 @@ void orc_init_velocity(const orc_case* c, const double* caps, double u0, double 
 /* Right-hand side of Eq. pm_prediction on the velocity unknowns (u, v: U^n, ghosts filled
  * here; p: P^{n-1/2}; cu, cv: conv^{n-1}, replaced by conv^0 when first is set).  Returns
  * conv^n in cnu, cnv. */
-void orc_predictor_rhs(const orc_case* c, const double* caps, double* u, double* v, const double* p, const double* cu,
-                       const double* cv, int first, double* ru, double* rv, double* cnu, double* cnv) {
+/* The same with the body-force term rho V_alpha g_alpha of Eq. pm_prediction; gx at u-faces and
+ * gy at v-faces (accelerations, padded layout) may be NULL (g = 0). */
+void orc_predictor_rhs_g(const orc_case* c, const double* caps, double* u, double* v, const double* p,
+                         const double* cu, const double* cv, int first, const double* gx, const double* gy,
+                         double* ru, double* rv, double* cnu, double* cnv) {
   size_t S = SIZE(c);
   double* gu = malloc(S * sizeof(double));
   double* gv = malloc(S * sizeof(double));
@@ -1259,6 +1262,8 @@ void orc_predictor_rhs(const orc_case* c, const double* caps, double* u, double*
   for (size_t k = 0; k < S; ++k) {
     ru[k] = (rho / dt) * Vu[k] * u[k] - 1.5 * rho * cnu[k] + 0.5 * rho * pu[k] - gu[k] + mu * vu[k] + mu * lu[k];
     rv[k] = (rho / dt) * Vv[k] * v[k] - 1.5 * rho * cnv[k] + 0.5 * rho * pv[k] - gv[k] + mu * vv[k] + mu * lv[k];
+    if (gx) ru[k] += rho * Vu[k] * gx[k];
+    if (gy) rv[k] += rho * Vv[k] * gy[k];
   }
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
@@ -1268,8 +1273,15 @@ void orc_predictor_rhs(const orc_case* c, const double* caps, double* u, double*
   free(gu); free(gv); free(vu); free(vv); free(lu); free(lv);
 }
 
-int orc_step(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
-             double* cv, int first, double* ustar, double* vstar, double* bdiv, orc_stats* st) {
+void orc_predictor_rhs(const orc_case* c, const double* caps, double* u, double* v, const double* p, const double* cu,
+                       const double* cv, int first, double* ru, double* rv, double* cnu, double* cnv) {
+  orc_predictor_rhs_g(c, caps, u, v, p, cu, cv, first, NULL, NULL, ru, rv, cnu, cnv);
+}
+
+/* One PmII step with the body acceleration g (gx at u-faces, gy at v-faces; NULL: g = 0). */
+int orc_step_g(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
+               double* cv, int first, const double* gx, const double* gy, double* ustar, double* vstar, double* bdiv,
+               orc_stats* st) {
   size_t S = SIZE(c);
   double* cnu = malloc(S * sizeof(double));
   double* cnv = malloc(S * sizeof(double));
@@ -1286,7 +1298,7 @@ int orc_step(const orc_case* c, const double* caps, double* u, double* v, double
   const double* Vp = CAP(c, caps, G_P, K_V);
   double rho = c->rho, dt = c->dt, mu = c->mu;
 
-  orc_predictor_rhs(c, caps, u, v, p, cu, cv, first, ru, rv, cnu, cnv);
+  orc_predictor_rhs_g(c, caps, u, v, p, cu, cv, first, gx, gy, ru, rv, cnu, cnv);
   for (size_t k = 0; k < S; ++k) {
     xu[k] = u[k];
     xv[k] = v[k];
@@ -1334,4 +1346,9 @@ int orc_step(const orc_case* c, const double* caps, double* u, double* v, double
   free(cnu); free(cnv); free(gu); free(gv);
   free(ru); free(rv); free(xu); free(xv); free(b); free(kp);
   return ok_h && ok_p;
+}
+
+int orc_step(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
+             double* cv, int first, double* ustar, double* vstar, double* bdiv, orc_stats* st) {
+  return orc_step_g(c, caps, u, v, p, phi, cu, cv, first, NULL, NULL, ustar, vstar, bdiv, st);
 }

@@ -224,3 +224,55 @@ def small_cylinder(nx=16, ny=8, box=(-2.0, 2.0, -1.0, 1.0), r=0.37, cx=0.05, cy=
     return make_case(f"small_cyl_{nx}x{ny}", nx, ny, box,
                      Geometry(kind=GEOM_CIRCLE, cx=cx, cy=cy, r=r), re=re, cfl=cfl,
                      lref=2 * r, bc=bc, **kw)
+
+
+# ---------------------------------------------------------------------------------------------
+# Manufactured steady solution in a closed no-slip box (body free): the body acceleration g of
+# Eq. pm_prediction that makes
+#   u = sin^2(pi x) sin(2 pi y),  v = -sin(2 pi x) sin^2(pi y),  p = cos(pi x) cos(pi y)
+# a steady solution of rho (U.grad) U + grad p - mu lap U = rho g on [0,1]^2.  U is divergence
+# free and vanishes on the walls; p has mean zero.
+# ---------------------------------------------------------------------------------------------
+def mms_box(n: int, mu: float = 0.2, cfl: float = 0.5) -> Case:
+    case = make_case(f"mms_box_{n}", n, n, (0.0, 1.0, 0.0, 1.0), Geometry(kind=GEOM_NONE), re=1.0, cfl=cfl,
+                     lref=1.0, bc=closed_box_bc())
+    case.mu = mu
+    case.autotune = 0
+    return case
+
+
+def mms_exact(x, y, rho: float, mu: float):
+    """(u, v, p, g_x, g_y) of the manufactured solution at points (x, y)."""
+    pi = np.pi
+    s1, c1 = np.sin(pi * x), np.cos(pi * x)
+    s1y, c1y = np.sin(pi * y), np.cos(pi * y)
+    s2x, c2x = np.sin(2 * pi * x), np.cos(2 * pi * x)
+    s2y, c2y = np.sin(2 * pi * y), np.cos(2 * pi * y)
+    u = s1 ** 2 * s2y
+    v = -s2x * s1y ** 2
+    p = c1 * c1y
+    ux, uy = pi * s2x * s2y, 2 * pi * s1 ** 2 * c2y
+    vx, vy = -2 * pi * c2x * s1y ** 2, -pi * s2x * s2y
+    lap_u = 2 * pi ** 2 * c2x * s2y - 4 * pi ** 2 * s1 ** 2 * s2y
+    lap_v = 4 * pi ** 2 * s2x * s1y ** 2 - 2 * pi ** 2 * s2x * c2y
+    px, py = -pi * s1 * c1y, -pi * c1 * s1y
+    nu = mu / rho
+    gx = u * ux + v * uy + px / rho - nu * lap_u
+    gy = u * vx + v * vy + py / rho - nu * lap_v
+    return u, v, p, gx, gy
+
+
+def mms_fields(case: Case):
+    """Padded arrays of the manufactured solution: u and g_x at u-faces, v and g_y at v-faces,
+    p at cell centres (x0 + (i + 1/2) h, ...), for index i in [-1, nx+1]."""
+    i = np.arange(-1, case.nx + 2, dtype=np.float64)
+    j = np.arange(-1, case.ny + 2, dtype=np.float64)
+    xf, xc = case.x0 + i * case.hx, case.x0 + (i + 0.5) * case.hx
+    yf, yc = case.y0 + j * case.hy, case.y0 + (j + 0.5) * case.hy
+    XU, YU = np.meshgrid(xf, yc)
+    XV, YV = np.meshgrid(xc, yf)
+    XP, YP = np.meshgrid(xc, yc)
+    u, _, _, gx, _ = mms_exact(XU, YU, case.rho, case.mu)
+    _, v, _, _, gy = mms_exact(XV, YV, case.rho, case.mu)
+    _, _, p, _, _ = mms_exact(XP, YP, case.rho, case.mu)
+    return u, v, p, gx, gy
