@@ -131,6 +131,9 @@ enum {
   CCM_F_VSTAR = 7,
   CCM_F_DIV = 8,              /* cont(U*, D) of the last step (read only) */
   CCM_F_STEP = 9,             /* first element: number of steps taken (as a double) */
+  CCM_F_GX = 10,              /* body acceleration g_x at u-faces, the rho V g term of Eq. pm_prediction
+                                 (zero unless set; steady: it applies to every later step) */
+  CCM_F_GY = 11,              /* body acceleration g_y at v-faces */
   CCM_F_CAP = 16              /* + 9*g + k: capacity k of grid g (read only), g: 0 p, 1 u,
                                  2 v; k: 0 V, 1 X, 2 Y, 3 Ax, 4 Ay, 5 Wx, 6 Wy, 7 Bx, 8 By
                                  (Ax/Wx at the cell's left face, Ay/Wy at its bottom face) */

@@ -91,6 +91,9 @@ struct ccm_case_s {
   // fcap rows of four doubles, allocated on demand; frec steps recorded so far)
   double* fpart = nullptr;
   double* fout = nullptr;
+  // body acceleration g at u- and v-faces (zero until set; the predictor reads it once set)
+  double *accx = nullptr, *accy = nullptr;
+  bool forced = false;
   double* fhist = nullptr;
   int fcap = 0;
   long long frec = 0;
@@ -140,6 +143,8 @@ void carve(ccm_case c, Carver& cv) {
   c->partials = cv.take<double>((size_t)pcg_partials_needed());
   c->dpart = cv.take<double>((size_t)3 * diagnostics_partials(c->g) + 8);
   c->fpart = cv.take<double>((size_t)body_force_partials(c->g));
+  c->accx = cv.take<double>(N);
+  c->accy = cv.take<double>(N);
   c->fout = cv.take<double>(4);
   c->bar_count = cv.take<unsigned int>(kBarWords);
   c->bar_err = cv.take<int>(4);
@@ -166,6 +171,8 @@ void make_view(ccm_case c) {
   v.massu = o.massu; v.massv = o.massv;
   v.invdhu = o.invdhu; v.invdhv = o.invdhv;
   v.liftu = o.liftu; v.liftv = o.liftv;
+  v.accx = c->forced ? c->accx : nullptr;
+  v.accy = c->forced ? c->accy : nullptr;
   v.cu32 = o.cu32; v.cv32 = o.cv32; v.invdk32 = o.invdk32;
 }
 
@@ -913,6 +920,8 @@ static double* field_ptr(ccm_case c, int field) {
     case CCM_F_USTAR: return c->ustar;
     case CCM_F_VSTAR: return c->vstar;
     case CCM_F_DIV: return c->div;
+    case CCM_F_GX: return c->accx;
+    case CCM_F_GY: return c->accy;
     default:
       if (field >= CCM_F_CAP && field < CCM_F_CAP + 27) return c->caps.a[field - CCM_F_CAP];
       return nullptr;
@@ -928,10 +937,16 @@ ccm_status ccm_set_field(ccm_case c, int field, const double* host, size_t count
     c->nstep = (long long)host[0];
     return CCM_OK;
   }
-  if (field > CCM_F_CONV_V || field < 0) return fail(CCM_E_INVALID, "field is read-only or unknown");
+  const bool accel = field == CCM_F_GX || field == CCM_F_GY;
+  if ((field > CCM_F_CONV_V || field < 0) && !accel) return fail(CCM_E_INVALID, "field is read-only or unknown");
   if (count != host_count(c)) return fail(CCM_E_INVALID, "count must be (nx+3)*(ny+3)");
   ccm_status s = upload(c, field_ptr(c, field), host);
   if (s != CCM_OK) return s;
+  if (accel && !c->forced) {
+    // from now on the predictor adds rho V g (the other component stays zero until set)
+    c->forced = true;
+    make_view(c);
+  }
   const dim3 b(64, 4);
   if (field == CCM_F_U || field == CCM_F_V) {
     k_mask_inactive<<<grid_of(c->g, b), b, 0, c->st>>>(c->g, c->co.role_u, c->co.role_v, c->u, c->v);

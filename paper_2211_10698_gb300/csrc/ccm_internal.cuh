@@ -60,6 +60,8 @@ struct Coefs {
   const double* invdhv;
   const double* liftu;      // visc(S(0, box data)) at u unknowns
   const double* liftv;
+  const double* accx;       // body acceleration g at u-faces (Eq. pm_prediction's rho V g); null: g = 0
+  const double* accy;       // ... at v-faces
   const float* cu32;
   const float* cv32;
   const float* invdk32;

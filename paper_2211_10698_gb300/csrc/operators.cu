@@ -252,7 +252,9 @@ __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, 
     const double cp = first ? cn : cpu[k];
     const double gp = c.ax[k] * (P(i, j) - P(i - 1, j));
     const double vs = visc_u(c, g, bc, w, i, j);
-    ru_[k] = c.massu[k] * w.u[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftu[k];
+    double r = c.massu[k] * w.u[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftu[k];
+    if (c.accx) r += c.massu[k] * ph.dt * c.accx[k];  // rho V g
+    ru_[k] = r;
     cnu[k] = cn;
   } else {
     ru_[k] = 0.0;
@@ -263,7 +265,9 @@ __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, 
     const double cp = first ? cn : cpv[k];
     const double gp = c.ay[k] * (P(i, j) - P(i, j - 1));
     const double vs = visc_v(c, g, bc, w, i, j);
-    rv_[k] = c.massv[k] * w.v[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftv[k];
+    double r = c.massv[k] * w.v[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftv[k];
+    if (c.accy) r += c.massv[k] * ph.dt * c.accy[k];
+    rv_[k] = r;
     cnv[k] = cn;
   } else {
     rv_[k] = 0.0;
