@@ -97,6 +97,9 @@ def _load():
                                            _DP]),
             "orc_step_g": (c_int, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP, _DP, _DP,
                                    POINTER(OrcStats)]),
+            "orc_step_gd": (c_int, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP, _DP, _DP, _DP, _DP,
+                                    POINTER(OrcStats)]),
+            "orc_body_force_d": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -277,11 +280,12 @@ class Oracle:
     def max_div(self, u, v):
         return self.lib.orc_max_div(ctypes.byref(self.s), _p(self.caps), _p(self._c(u)), _p(self._c(v)))
 
-    def body_force(self, u, v, p):
-        """(Fp_x, Fp_y, Fv_x, Fv_y): pressure and viscous force of the fluid on the body."""
+    def body_force(self, u, v, p, Dx=None, Dy=None):
+        """(Fp_x, Fp_y, Fv_x, Fv_y): pressure and viscous force of the fluid on the body (whose
+        Dirichlet velocity is D, zero when not given)."""
         f = np.zeros(4)
-        self.lib.orc_body_force(ctypes.byref(self.s), _p(self.caps), _p(self._c(u)), _p(self._c(v)),
-                                _p(self._c(p)), _p(f))
+        self.lib.orc_body_force_d(ctypes.byref(self.s), _p(self.caps), _p(self._c(u)), _p(self._c(v)),
+                                  _p(self._c(p)), _p(self._c(Dx)), _p(self._c(Dy)), _p(f))
         return f
 
     def cell_boundary(self, grid, i, j):
@@ -314,11 +318,14 @@ class Oracle:
         hist = []
         for _ in range(nsteps):
             us, vs, bd = (self.z(), self.z(), self.z()) if keep else (None, None, None)
-            # st may carry a body acceleration "gx" (u-faces), "gy" (v-faces): Eq. pm_prediction's rho V g
+            # st may carry a body acceleration "gx" (u-faces), "gy" (v-faces), Eq. pm_prediction's rho V g,
+            # and the body's steady Dirichlet velocity "Dx" (per u-cell), "Dy" (per v-cell)
             gx, gy = st.get("gx"), st.get("gy")
-            ok = self.lib.orc_step_g(ctypes.byref(self.s), _p(self.caps), _p(st["u"]), _p(st["v"]), _p(st["p"]),
-                                     _p(st["phi"]), _p(st["cu"]), _p(st["cv"]), 1 if st["n"] == 0 else 0,
-                                     _p(self._c(gx)), _p(self._c(gy)), _p(us), _p(vs), _p(bd), ctypes.byref(stats))
+            Dx, Dy = st.get("Dx"), st.get("Dy")
+            ok = self.lib.orc_step_gd(ctypes.byref(self.s), _p(self.caps), _p(st["u"]), _p(st["v"]), _p(st["p"]),
+                                      _p(st["phi"]), _p(st["cu"]), _p(st["cv"]), 1 if st["n"] == 0 else 0,
+                                      _p(self._c(gx)), _p(self._c(gy)), _p(self._c(Dx)), _p(self._c(Dy)),
+                                      _p(us), _p(vs), _p(bd), ctypes.byref(stats))
             st["n"] += 1
             hist.append(dict(iters_h=stats.iters_h, iters_p=stats.iters_p, res_h=stats.res_h,
                              res_p=stats.res_p, max_div=stats.max_div, kinetic=stats.kinetic,

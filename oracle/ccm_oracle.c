@@ -701,13 +701,13 @@ void orc_fill_ghosts(const orc_case* c, double* u, double* v) { fill_bc(c, u, v,
  * to the velocity unknowns.  On an outflow side the tangential velocity next to the side
  * does not receive the shear stress at the boundary nodes: with zero-gradient ghosts its
  * total coefficient in that stress vanishes, so dropping it keeps the operator symmetric. */
-static void visc_bc(const orc_case* c, const double* caps, const double* u, const double* v, double* ou,
-                    double* ov) {
+static void visc_bc(const orc_case* c, const double* caps, const double* u, const double* v, const double* Dx,
+                    const double* Dy, double* ou, double* ov) {
   size_t S = SIZE(c);
   double* sxx = malloc(S * sizeof(double));
   double* syy = malloc(S * sizeof(double));
   double* sxy = malloc(S * sizeof(double));
-  orc_strain(c, caps, u, v, NULL, NULL, sxx, syy, sxy);
+  orc_strain(c, caps, u, v, Dx, Dy, sxx, syy, sxy);
   orc_visc(c, caps, sxx, syy, sxy, ou, ov);
   const double* ByU = CAP(c, caps, G_U, K_BY);
   const double* BxV = CAP(c, caps, G_V, K_BX);
@@ -738,26 +738,32 @@ void orc_visc_bc(const orc_case* c, const double* caps, const double* u_in, cons
   memcpy(u, u_in, S * sizeof(double));
   memcpy(v, v_in, S * sizeof(double));
   fill_bc(c, u, v, 1.0);
-  visc_bc(c, caps, u, v, ou, ov);
+  visc_bc(c, caps, u, v, NULL, NULL, ou, ov);
   free(u); free(v);
 }
 
-/* conv(U, U, 0, 0) on ghost-filled U, restricted to the velocity unknowns. */
-void orc_conv_bc(const orc_case* c, const double* caps, const double* u_in, const double* v_in, double* ou,
-                 double* ov) {
+/* conv(U, U, D, D) on ghost-filled U, restricted to the velocity unknowns (D may be NULL). */
+static void conv_bc(const orc_case* c, const double* caps, const double* u_in, const double* v_in,
+                    const double* Dx, const double* Dy, double* ou, double* ov) {
   size_t S = SIZE(c);
   double* u = malloc(S * sizeof(double));
   double* v = malloc(S * sizeof(double));
   memcpy(u, u_in, S * sizeof(double));
   memcpy(v, v_in, S * sizeof(double));
   fill_bc(c, u, v, 1.0);
-  orc_conv(c, caps, u, v, u, v, NULL, NULL, NULL, NULL, ou, ov);
+  orc_conv(c, caps, u, v, u, v, Dx, Dy, Dx, Dy, ou, ov);
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
       if (role_u(c, caps, i, j) != 3) AT(c, ou, i, j) = 0.0;
       if (role_v(c, caps, i, j) != 3) AT(c, ov, i, j) = 0.0;
     }
   free(u); free(v);
+}
+
+/* conv(U, U, 0, 0) on ghost-filled U, restricted to the velocity unknowns. */
+void orc_conv_bc(const orc_case* c, const double* caps, const double* u_in, const double* v_in, double* ou,
+                 double* ov) {
+  conv_bc(c, caps, u_in, v_in, NULL, NULL, ou, ov);
 }
 
 /* pres(P) restricted to the velocity unknowns; the ghost ring of P is read as zero
@@ -795,7 +801,7 @@ void orc_helmholtz(const orc_case* c, const double* caps, const double* u_in, co
       if (role_v(c, caps, i, j) == 3) AT(c, v, i, j) = AT(c, v_in, i, j);
     }
   fill_bc(c, u, v, 0.0);
-  visc_bc(c, caps, u, v, ou, ov);
+  visc_bc(c, caps, u, v, NULL, NULL, ou, ov);
   const double* Vu = CAP(c, caps, G_U, K_V);
   const double* Vv = CAP(c, caps, G_V, K_V);
   double s = c->rho / c->dt;
@@ -1126,16 +1132,21 @@ double orc_kinetic(const orc_case* c, const double* caps, const double* u, const
   return k;
 }
 
-double orc_max_div(const orc_case* c, const double* caps, const double* u, const double* v) {
+static double max_div_d(const orc_case* c, const double* caps, const double* u, const double* v, const double* Dx,
+                        const double* Dy) {
   size_t S = SIZE(c);
   double* d = malloc(S * sizeof(double));
-  orc_cont(c, caps, u, v, NULL, NULL, d);
+  orc_cont(c, caps, u, v, Dx, Dy, d);
   double m = 0.0;
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i < c->nx; ++i)
       if (cell_active(c, caps, i, j) && fabs(AT(c, d, i, j)) > m) m = fabs(AT(c, d, i, j));
   free(d);
   return m;
+}
+
+double orc_max_div(const orc_case* c, const double* caps, const double* u, const double* v) {
+  return max_div_d(c, caps, u, v, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -1152,10 +1163,12 @@ double orc_max_div(const orc_case* c, const double* caps, const double* u, const
  *   Fv_y = -2 mu [ sum_cells S_yy (B^yy_below - B^yy_above) + sum_nodes S_xy (B^yx_left - B^yx_right) ]
  * over p-cells i in [0,nx), j in [0,ny); the S_xy sums run over the nodes whose two u-faces
  * (i in [0,nx], j in [1,ny)) or two v-faces (i in [1,nx), j in [0,ny]) lie in the box.
- * S is the strain of Eqs. diag and offdiag with D = 0 (no-slip body).
+ * S is the strain of Eqs. diag and offdiag with the body's Dirichlet data D (orc_body_force:
+ * D = 0, a no-slip body).  The convective term has no share for a body whose D has no normal
+ * component (no flux through the boundary).
  * ---------------------------------------------------------------------------------------- */
-void orc_body_force(const orc_case* c, const double* caps, const double* u, const double* v, const double* p,
-                    double* force) {
+void orc_body_force_d(const orc_case* c, const double* caps, const double* u, const double* v, const double* p,
+                      const double* Dx, const double* Dy, double* force) {
   const double* Ax = CAP(c, caps, G_P, K_AX);
   const double* Ay = CAP(c, caps, G_P, K_AY);
   const double* BxU = CAP(c, caps, G_U, K_BX);
@@ -1166,7 +1179,7 @@ void orc_body_force(const orc_case* c, const double* caps, const double* u, cons
   double* sxx = malloc(S * sizeof(double));
   double* syy = malloc(S * sizeof(double));
   double* sxy = malloc(S * sizeof(double));
-  orc_strain(c, caps, u, v, NULL, NULL, sxx, syy, sxy);
+  orc_strain(c, caps, u, v, Dx, Dy, sxx, syy, sxy);
   double fpx = 0.0, fpy = 0.0, gx = 0.0, gy = 0.0;
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i < c->nx; ++i) {
@@ -1186,6 +1199,11 @@ void orc_body_force(const orc_case* c, const double* caps, const double* u, cons
   free(sxx);
   free(syy);
   free(sxy);
+}
+
+void orc_body_force(const orc_case* c, const double* caps, const double* u, const double* v, const double* p,
+                    double* force) {
+  orc_body_force_d(c, caps, u, v, p, NULL, NULL, force);
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -1233,9 +1251,9 @@ void orc_init_velocity(const orc_case* c, const double* caps, double u0, double 
  * conv^n in cnu, cnv. */
 /* The same with the body-force term rho V_alpha g_alpha of Eq. pm_prediction; gx at u-faces and
  * gy at v-faces (accelerations, padded layout) may be NULL (g = 0). */
-void orc_predictor_rhs_g(const orc_case* c, const double* caps, double* u, double* v, const double* p,
-                         const double* cu, const double* cv, int first, const double* gx, const double* gy,
-                         double* ru, double* rv, double* cnu, double* cnv) {
+void orc_predictor_rhs_gd(const orc_case* c, const double* caps, double* u, double* v, const double* p,
+                          const double* cu, const double* cv, int first, const double* gx, const double* gy,
+                          const double* Dx, const double* Dy, double* ru, double* rv, double* cnu, double* cnv) {
   size_t S = SIZE(c);
   double* gu = malloc(S * sizeof(double));
   double* gv = malloc(S * sizeof(double));
@@ -1247,16 +1265,18 @@ void orc_predictor_rhs_g(const orc_case* c, const double* caps, double* u, doubl
   const double* Vv = CAP(c, caps, G_V, K_V);
   double rho = c->rho, dt = c->dt, mu = c->mu;
   fill_bc(c, u, v, 1.0);
-  orc_conv_bc(c, caps, u, v, cnu, cnv);
+  conv_bc(c, caps, u, v, Dx, Dy, cnu, cnv);
   const double* pu = first ? cnu : cu;
   const double* pv = first ? cnv : cv;
   orc_pres_bc(c, caps, p, gu, gv);
-  orc_visc_bc(c, caps, u, v, vu, vv);
-  /* lifting of the implicit half: visc(mu S(0, D^{n+1})) from the box boundary values */
+  visc_bc(c, caps, u, v, Dx, Dy, vu, vv);
+  /* lifting of the implicit half: visc(mu S(0, D^{n+1})) from the box boundary values and the
+   * body's Dirichlet data (D^{n+1} = D^n: steady) */
   {
     double* zu = calloc(S, sizeof(double));
     double* zv = calloc(S, sizeof(double));
-    orc_visc_bc(c, caps, zu, zv, lu, lv);
+    fill_bc(c, zu, zv, 1.0);
+    visc_bc(c, caps, zu, zv, Dx, Dy, lu, lv);
     free(zu); free(zv);
   }
   for (size_t k = 0; k < S; ++k) {
@@ -1273,15 +1293,23 @@ void orc_predictor_rhs_g(const orc_case* c, const double* caps, double* u, doubl
   free(gu); free(gv); free(vu); free(vv); free(lu); free(lv);
 }
 
-void orc_predictor_rhs(const orc_case* c, const double* caps, double* u, double* v, const double* p, const double* cu,
-                       const double* cv, int first, double* ru, double* rv, double* cnu, double* cnv) {
-  orc_predictor_rhs_g(c, caps, u, v, p, cu, cv, first, NULL, NULL, ru, rv, cnu, cnv);
+void orc_predictor_rhs_g(const orc_case* c, const double* caps, double* u, double* v, const double* p,
+                         const double* cu, const double* cv, int first, const double* gx, const double* gy,
+                         double* ru, double* rv, double* cnu, double* cnv) {
+  orc_predictor_rhs_gd(c, caps, u, v, p, cu, cv, first, gx, gy, NULL, NULL, ru, rv, cnu, cnv);
 }
 
-/* One PmII step with the body acceleration g (gx at u-faces, gy at v-faces; NULL: g = 0). */
-int orc_step_g(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
-               double* cv, int first, const double* gx, const double* gy, double* ustar, double* vstar, double* bdiv,
-               orc_stats* st) {
+void orc_predictor_rhs(const orc_case* c, const double* caps, double* u, double* v, const double* p, const double* cu,
+                       const double* cv, int first, double* ru, double* rv, double* cnu, double* cnv) {
+  orc_predictor_rhs_gd(c, caps, u, v, p, cu, cv, first, NULL, NULL, NULL, NULL, ru, rv, cnu, cnv);
+}
+
+/* One PmII step with the body acceleration g (gx at u-faces, gy at v-faces; NULL: g = 0) and
+ * the body's steady Dirichlet velocity D (Dx per u-cell, Dy per v-cell; NULL: no-slip, D = 0)
+ * in Eqs. divergence, diag/offdiag (through visc) and convective. */
+int orc_step_gd(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
+                double* cv, int first, const double* gx, const double* gy, const double* Dx, const double* Dy,
+                double* ustar, double* vstar, double* bdiv, orc_stats* st) {
   size_t S = SIZE(c);
   double* cnu = malloc(S * sizeof(double));
   double* cnv = malloc(S * sizeof(double));
@@ -1298,24 +1326,25 @@ int orc_step_g(const orc_case* c, const double* caps, double* u, double* v, doub
   const double* Vp = CAP(c, caps, G_P, K_V);
   double rho = c->rho, dt = c->dt, mu = c->mu;
 
-  orc_predictor_rhs_g(c, caps, u, v, p, cu, cv, first, gx, gy, ru, rv, cnu, cnv);
+  orc_predictor_rhs_gd(c, caps, u, v, p, cu, cv, first, gx, gy, Dx, Dy, ru, rv, cnu, cnv);
   for (size_t k = 0; k < S; ++k) {
     xu[k] = u[k];
     xv[k] = v[k];
   }
   int ok_h = orc_solve_helmholtz(c, caps, ru, rv, xu, xv, c->tol_h, c->max_iter_h, &st->iters_h, &st->res_h);
-  /* U*: unknowns from the solve, Dirichlet faces keep their values, inactive faces 0 */
+  /* U*: unknowns from the solve, Dirichlet faces keep their values, inactive faces (no fluid in
+   * their control volume) the body's velocity D (0 for a no-slip body) */
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
       size_t k = (size_t)(j + 1) * PITCH(c) + (size_t)(i + 1);
       int r_u = role_u(c, caps, i, j), r_v = role_v(c, caps, i, j);
-      if (r_u == 3) u[k] = xu[k]; else if (r_u == 2) u[k] = 0.0;
-      if (r_v == 3) v[k] = xv[k]; else if (r_v == 2) v[k] = 0.0;
+      if (r_u == 3) u[k] = xu[k]; else if (r_u == 2) u[k] = Dx ? Dx[k] : 0.0;
+      if (r_v == 3) v[k] = xv[k]; else if (r_v == 2) v[k] = Dy ? Dy[k] : 0.0;
     }
   fill_bc(c, u, v, 1.0);
   if (ustar) memcpy(ustar, u, S * sizeof(double));
   if (vstar) memcpy(vstar, v, S * sizeof(double));
-  orc_cont(c, caps, u, v, NULL, NULL, b);
+  orc_cont(c, caps, u, v, Dx, Dy, b);
   if (bdiv) memcpy(bdiv, b, S * sizeof(double));
   double* rhs = malloc(S * sizeof(double));
   for (size_t k = 0; k < S; ++k) rhs[k] = -(rho / dt) * b[k];
@@ -1341,14 +1370,20 @@ int orc_step_g(const orc_case* c, const double* caps, double* u, double* v, doub
   memcpy(cv, cnv, S * sizeof(double));
   st->conv_h = ok_h;
   st->conv_p = ok_p;
-  st->max_div = orc_max_div(c, caps, u, v);
+  st->max_div = max_div_d(c, caps, u, v, Dx, Dy);
   st->kinetic = orc_kinetic(c, caps, u, v);
   free(cnu); free(cnv); free(gu); free(gv);
   free(ru); free(rv); free(xu); free(xv); free(b); free(kp);
   return ok_h && ok_p;
 }
 
+int orc_step_g(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
+               double* cv, int first, const double* gx, const double* gy, double* ustar, double* vstar, double* bdiv,
+               orc_stats* st) {
+  return orc_step_gd(c, caps, u, v, p, phi, cu, cv, first, gx, gy, NULL, NULL, ustar, vstar, bdiv, st);
+}
+
 int orc_step(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
              double* cv, int first, double* ustar, double* vstar, double* bdiv, orc_stats* st) {
-  return orc_step_g(c, caps, u, v, p, phi, cu, cv, first, NULL, NULL, ustar, vstar, bdiv, st);
+  return orc_step_gd(c, caps, u, v, p, phi, cu, cv, first, NULL, NULL, NULL, NULL, ustar, vstar, bdiv, st);
 }

@@ -276,3 +276,62 @@ def mms_fields(case: Case):
     _, v, _, _, gy = mms_exact(XV, YV, case.rho, case.mu)
     _, _, p, _, _ = mms_exact(XP, YP, case.rho, case.mu)
     return u, v, p, gx, gy
+
+
+# ---------------------------------------------------------------------------------------------
+# Manufactured steady solution around a rotating cylinder: a compactly supported vortex
+#   u_theta(r) = A r (1 - r^2/R^2)^3 (r < R), 0 beyond,  p = 0,
+# centred on the cylinder (radius r0 < R) in the closed no-slip unit box.  Its streamlines are
+# circles, so the body's velocity D = u_theta(r0) e_theta has no normal component.  The body
+# acceleration g = (U.grad)U - nu lap U (azimuthal part 24 nu A r q (1 - 2 r^2/R^2) / R^2,
+# radial part -u_theta^2 / r, q = 1 - r^2/R^2) makes it a steady solution.
+# ---------------------------------------------------------------------------------------------
+VORTEX = dict(A=2.0, R=0.45, cx=0.5, cy=0.5, r0=0.2)
+
+
+def vortex_box(n: int, mu: float = 0.2) -> Case:
+    case = mms_box(n, mu)
+    case.name = f"vortex_box_{n}"
+    case.geom = Geometry(kind=GEOM_CIRCLE, cx=VORTEX["cx"], cy=VORTEX["cy"], r=VORTEX["r0"])
+    return case
+
+
+def vortex_exact(x, y, rho: float, mu: float):
+    """(u, v, g_x, g_y) of the vortex at points (x, y)."""
+    A, R = VORTEX["A"], VORTEX["R"]
+    dx, dy = x - VORTEX["cx"], y - VORTEX["cy"]
+    r2 = dx * dx + dy * dy
+    q = np.where(r2 < R * R, 1.0 - r2 / R ** 2, 0.0)
+    nu = mu / rho
+    k = 24.0 * nu * A * q * (1.0 - 2.0 * r2 / R ** 2) / R ** 2
+    return (-A * dy * q ** 3, A * dx * q ** 3,
+            -A ** 2 * q ** 6 * dx - k * dy, -A ** 2 * q ** 6 * dy + k * dx)
+
+
+def vortex_fields(case: Case):
+    """Padded arrays: u, g_x at u-faces; v, g_y at v-faces."""
+    i = np.arange(-1, case.nx + 2, dtype=np.float64)
+    j = np.arange(-1, case.ny + 2, dtype=np.float64)
+    XU, YU = np.meshgrid(case.x0 + i * case.hx, case.y0 + (j + 0.5) * case.hy)
+    XV, YV = np.meshgrid(case.x0 + (i + 0.5) * case.hx, case.y0 + j * case.hy)
+    u, _, gx, _ = vortex_exact(XU, YU, case.rho, case.mu)
+    _, v, _, gy = vortex_exact(XV, YV, case.rho, case.mu)
+    return u, v, gx, gy
+
+
+def circle_boundary_points(X, Y, cx: float, cy: float, r: float):
+    """Where the boundary of a circular body meets the ray from its centre through each control
+    volume's fluid centroid (X, Y): the point at which a body velocity is sampled for D."""
+    dx, dy = X - cx, Y - cy
+    d = np.hypot(dx, dy)
+    d = np.where(d > 0, d, 1.0)
+    return cx + r * dx / d, cy + r * dy / d
+
+
+def vortex_body_velocity(case: Case, Xu, Yu, Xv, Yv):
+    """(Dx per u-cell, Dy per v-cell): the vortex's velocity on the cylinder, sampled at the
+    boundary points of the u- and v-control volumes whose centroids are (Xu, Yu), (Xv, Yv)."""
+    c = VORTEX
+    xu, yu = circle_boundary_points(Xu, Yu, c["cx"], c["cy"], c["r0"])
+    xv, yv = circle_boundary_points(Xv, Yv, c["cx"], c["cy"], c["r0"])
+    return vortex_exact(xu, yu, case.rho, case.mu)[0], vortex_exact(xv, yv, case.rho, case.mu)[1]
