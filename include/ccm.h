@@ -134,6 +134,12 @@ enum {
   CCM_F_GX = 10,              /* body acceleration g_x at u-faces, the rho V g term of Eq. pm_prediction
                                  (zero unless set; steady: it applies to every later step) */
   CCM_F_GY = 11,              /* body acceleration g_y at v-faces */
+  CCM_F_DX = 12,              /* the body's steady Dirichlet velocity D_x, one value per u-cell (the velocity of
+                                 the body on the boundary inside that u-control volume; zero: no-slip) in the
+                                 heterogeneous terms of Eqs. divergence, diag/offdiag and convective.  Setting D
+                                 computes those terms once (the body is fixed, D steady) and gives the faces whose
+                                 control volume holds no fluid the value D.  It should have no normal component. */
+  CCM_F_DY = 13,              /* D_y, one value per v-cell */
   CCM_F_CAP = 16              /* + 9*g + k: capacity k of grid g (read only), g: 0 p, 1 u,
                                  2 v; k: 0 V, 1 X, 2 Y, 3 Ax, 4 Ay, 5 Wx, 6 Wy, 7 Bx, 8 By
                                  (Ax/Wx at the cell's left face, Ay/Wy at its bottom face) */
@@ -230,7 +236,8 @@ ccm_status ccm_read_stats(ccm_case c, ccm_step_stats* stats);
  *   Fp_x = sum_cells P (A^x_{i-1/2,j} - A^x_{i+1/2,j}),  Fp_y likewise with A^y in y,
  *   Fv_x = -2 mu [sum_cells S_xx (B^xx_{i-1/2} - B^xx_{i+1/2}) + sum_nodes S_xy (B^xy_{j-1/2} - B^xy_{j+1/2})],
  *   Fv_y = -2 mu [sum_cells S_yy (B^yy_{j-1/2} - B^yy_{j+1/2}) + sum_nodes S_xy (B^yx_{i-1/2} - B^yx_{i+1/2})],
- * S of Eqs. diag and offdiag with D = 0 (no-slip body).  The terms vanish wherever the grid is
+ * S of Eqs. diag and offdiag with the body's D (CCM_F_DX/DY; zero for a no-slip body), which should
+ * have no normal component (no flux through the body).  The terms vanish wherever the grid is
  * uncut.  force is a host array the caller owns.  Waits for the case's stream.  CCM_E_STATE
  * before ccm_set_geometry. */
 ccm_status ccm_body_force(ccm_case c, double force[4]);

@@ -23,6 +23,7 @@ CCM_FP64, CCM_MIXED = 0, 1
 CCM_JACOBI, CCM_CHEBYSHEV = 0, 1
 CCM_F_U, CCM_F_V, CCM_F_P, CCM_F_PHI, CCM_F_CONV_U, CCM_F_CONV_V, CCM_F_USTAR, CCM_F_VSTAR, CCM_F_DIV, CCM_F_STEP = range(10)
 CCM_F_GX, CCM_F_GY = 10, 11   # body acceleration g at u- and v-faces (rho V g in the predictor)
+CCM_F_DX, CCM_F_DY = 12, 13   # the body's steady Dirichlet velocity D per u- and v-cell
 CCM_F_CAP = 16
 (CCM_OP_CONT, CCM_OP_PRES, CCM_OP_CONV, CCM_OP_VISC, CCM_OP_HELMHOLTZ, CCM_OP_POISSON, CCM_OP_POISSON_DIAG,
  CCM_OP_HELMHOLTZ_DIAG) = range(8)

@@ -94,6 +94,9 @@ struct ccm_case_s {
   // body acceleration g at u- and v-faces (zero until set; the predictor reads it once set)
   double *accx = nullptr, *accy = nullptr;
   bool forced = false;
+  // the body's Dirichlet velocity D and its constant terms: one allocation of 8 padded arrays,
+  // made when D is first set (Dx, Dy, h, S_xx, S_yy, S_xy, visc_u, visc_v)
+  double* dblock = nullptr;
   double* fhist = nullptr;
   int fcap = 0;
   long long frec = 0;
@@ -173,6 +176,11 @@ void make_view(ccm_case c) {
   v.liftu = o.liftu; v.liftv = o.liftv;
   v.accx = c->forced ? c->accx : nullptr;
   v.accy = c->forced ? c->accy : nullptr;
+  const size_t N = c->g.count();
+  double* d = c->dblock;
+  v.dx = d; v.dy = d ? d + N : nullptr; v.hd = d ? d + 2 * N : nullptr;
+  v.sxxd = d ? d + 3 * N : nullptr; v.syyd = d ? d + 4 * N : nullptr; v.sxyd = d ? d + 5 * N : nullptr;
+  v.viscdu = d ? d + 6 * N : nullptr; v.viscdv = d ? d + 7 * N : nullptr;
   v.cu32 = o.cu32; v.cv32 = o.cv32; v.invdk32 = o.invdk32;
 }
 
@@ -203,15 +211,6 @@ __global__ void k_init_velocity(Geom g, const int8_t* ru, double u0, double* u, 
 
 // Zero the velocity positions that are not unknowns or Dirichlet faces' neighbours of the
 // fill (inactive faces hold zero).
-__global__ void k_mask_inactive(Geom g, const int8_t* ru, const int8_t* rv, double* u, double* v) {
-  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
-  const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
-  if (i > g.nx + 1 || j > g.ny + 1) return;
-  const size_t k = g.idx(i, j);
-  if (ru[k] == R_INACTIVE) u[k] = 0.0;
-  if (rv[k] == R_INACTIVE) v[k] = 0.0;
-}
-
 __global__ void k_mask_cells(Geom g, const int8_t* act, double* x) {
   const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
   const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
@@ -824,11 +823,24 @@ ccm_status ccm_case_bytes(const ccm_config* cfg, size_t* bytes) {
   return CCM_OK;
 }
 
-static void free_force_history(ccm_case c) {
-  if (c->fhist) {
-    if (c->cfg.free) c->cfg.free(c->fhist, c->cfg.alloc_ctx);
-    else cudaFree(c->fhist);
+// Device memory outside the case's slab (force record, D terms), with the case's allocator.
+static void* case_alloc(ccm_case c, size_t bytes) {
+  void* mem = nullptr;
+  if (c->cfg.alloc) return c->cfg.alloc(bytes, c->cfg.alloc_ctx);
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
   }
+  return mem;
+}
+static void case_free(ccm_case c, void* mem) {
+  if (!mem) return;
+  if (c->cfg.free) c->cfg.free(mem, c->cfg.alloc_ctx);
+  else cudaFree(mem);
+}
+
+static void free_force_history(ccm_case c) {
+  case_free(c, c->fhist);
   c->fhist = nullptr;
   c->fcap = 0;
   c->frec = 0;
@@ -839,6 +851,7 @@ ccm_status ccm_destroy_case(ccm_case c) {
   cudaStreamSynchronize(c->st);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   free_force_history(c);
+  case_free(c, c->dblock);
   if (c->slab) {
     if (c->cfg.free) c->cfg.free(c->slab, c->cfg.alloc_ctx);
     else cudaFree(c->slab);
@@ -922,6 +935,8 @@ static double* field_ptr(ccm_case c, int field) {
     case CCM_F_DIV: return c->div;
     case CCM_F_GX: return c->accx;
     case CCM_F_GY: return c->accy;
+    case CCM_F_DX: return c->dblock;
+    case CCM_F_DY: return c->dblock ? c->dblock + c->g.count() : nullptr;
     default:
       if (field >= CCM_F_CAP && field < CCM_F_CAP + 27) return c->caps.a[field - CCM_F_CAP];
       return nullptr;
@@ -938,8 +953,17 @@ ccm_status ccm_set_field(ccm_case c, int field, const double* host, size_t count
     return CCM_OK;
   }
   const bool accel = field == CCM_F_GX || field == CCM_F_GY;
-  if ((field > CCM_F_CONV_V || field < 0) && !accel) return fail(CCM_E_INVALID, "field is read-only or unknown");
+  const bool body = field == CCM_F_DX || field == CCM_F_DY;
+  if ((field > CCM_F_CONV_V || field < 0) && !accel && !body) return fail(CCM_E_INVALID, "field is read-only or unknown");
   if (count != host_count(c)) return fail(CCM_E_INVALID, "count must be (nx+3)*(ny+3)");
+  if (body && !c->dblock) {
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    void* mem = case_alloc(c, 8 * c->g.count() * sizeof(double));
+    if (!mem) return fail(CCM_E_OOM, "cannot allocate the body-velocity terms");
+    CUDA_TRY(cudaMemsetAsync(mem, 0, 8 * c->g.count() * sizeof(double), c->st));
+    c->dblock = (double*)mem;
+    make_view(c);
+  }
   ccm_status s = upload(c, field_ptr(c, field), host);
   if (s != CCM_OK) return s;
   if (accel && !c->forced) {
@@ -949,8 +973,16 @@ ccm_status ccm_set_field(ccm_case c, int field, const double* host, size_t count
   }
   const dim3 b(64, 4);
   if (field == CCM_F_U || field == CCM_F_V) {
-    k_mask_inactive<<<grid_of(c->g, b), b, 0, c->st>>>(c->g, c->co.role_u, c->co.role_v, c->u, c->v);
+    // faces whose control volume holds no fluid carry the body's velocity (zero: no-slip)
+    launch_inactive_to_body(c->g, c->co.role_u, c->co.role_v, c->cv.dx, c->cv.dy, c->u, c->v, c->st);
     launch_fill_bc(c->g, c->bc, c->u, c->v, 1.0, c->st);
+  }
+  if (body) {
+    // the constant D-terms of the step, and D on the faces without fluid
+    launch_body_dterms(c->g, c->bc, c->caps, c->cv, c->cv.dx, c->cv.dy, (double*)c->cv.hd, (double*)c->cv.sxxd,
+                       (double*)c->cv.syyd, (double*)c->cv.sxyd, (double*)c->cv.viscdu, (double*)c->cv.viscdv,
+                       c->st);
+    launch_inactive_to_body(c->g, c->co.role_u, c->co.role_v, c->cv.dx, c->cv.dy, c->u, c->v, c->st);
   }
   if (field == CCM_F_P || field == CCM_F_PHI) {
     // only active cells carry pressure; the ghost ring stays zero
@@ -1188,18 +1220,8 @@ ccm_status ccm_set_force_history(ccm_case c, int capacity) {
   CUDA_TRY(cudaStreamSynchronize(c->st));
   free_force_history(c);
   if (capacity == 0) return CCM_OK;
-  const size_t bytes = (size_t)capacity * 4 * sizeof(double);
-  void* mem = nullptr;
-  if (c->cfg.alloc) {
-    mem = c->cfg.alloc(bytes, c->cfg.alloc_ctx);
-    if (!mem) return fail(CCM_E_OOM, "allocator hook returned NULL");
-  } else {
-    cudaError_t e = cudaMalloc(&mem, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(CCM_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    }
-  }
+  void* mem = case_alloc(c, (size_t)capacity * 4 * sizeof(double));
+  if (!mem) return fail(CCM_E_OOM, "cannot allocate the force record");
   c->fhist = (double*)mem;
   c->fcap = capacity;
   c->frec = 0;

@@ -295,6 +295,13 @@ void launch_divergence(const Coefs& c, const Geom& g, const Phys& ph, const doub
                        double* rhs, cudaStream_t st);
 void launch_project(const Coefs& c, const Geom& g, const double* phi, double* u, double* v, double* p, cudaStream_t st);
 int diagnostics_partials(const Geom& g);
+// The body's steady Dirichlet velocity (dterms.cu): h = cont(0, D), strain(0, D), visc(S(0, D));
+// and D on the faces whose control volume holds no fluid (Dx, Dy null: zero).
+void launch_body_dterms(const Geom& g, const Bc& bc, const CapPtrs& cp, const Coefs& c, const double* Dx,
+                        const double* Dy, double* hd, double* sxxd, double* syyd, double* sxyd, double* vu,
+                        double* vv, cudaStream_t st);
+void launch_inactive_to_body(const Geom& g, const int8_t* ru, const int8_t* rv, const double* Dx, const double* Dy,
+                             double* u, double* v, cudaStream_t st);
 // Force of the fluid on the body, out[4] = (Fp_x, Fp_y, Fv_x, Fv_y) (operators.cu); partials
 // holds body_force_partials(g) doubles.
 int body_force_partials(const Geom& g);

@@ -62,6 +62,15 @@ struct Coefs {
   const double* liftv;
   const double* accx;       // body acceleration g at u-faces (Eq. pm_prediction's rho V g); null: g = 0
   const double* accy;       // ... at v-faces
+  // the body's steady Dirichlet velocity D and its constant terms (dterms.cu); null: D = 0
+  const double* dx;         // D_x per u-cell
+  const double* dy;         // D_y per v-cell
+  const double* hd;         // cont(0, D) at cells (zero outside the box)
+  const double* sxxd;       // strain(0, D): S_xx at cells, S_yy at cells, S_xy at nodes
+  const double* syyd;
+  const double* sxyd;
+  const double* viscdu;     // visc(S(0, D)) at u unknowns
+  const double* viscdv;     // ... at v unknowns
   const float* cu32;
   const float* cv32;
   const float* invdk32;

@@ -248,12 +248,15 @@ __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, 
                                                  int first, int i, int j, size_t k) {
   auto P = [&](int a, int b) { return (a >= 0 && a < g.nx && b >= 0 && b < g.ny) ? p[g.idx(a, b)] : 0.0; };
   if (c.role_u[k] == R_UNKNOWN) {
-    const double cn = conv_u(c, g, w, i, j);
+    double cn = conv_u(c, g, w, i, j);
+    // conv(U, U, D, D): the face mean of h = cont(0, D) times (U + D)/2 (Eq. convective)
+    if (c.hd) cn += 0.5 * (c.hd[k] + c.hd[k - 1]) * 0.5 * (w.u[k] + c.dx[k]);
     const double cp = first ? cn : cpu[k];
     const double gp = c.ax[k] * (P(i, j) - P(i - 1, j));
     const double vs = visc_u(c, g, bc, w, i, j);
     double r = c.massu[k] * w.u[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftu[k];
     if (c.accx) r += c.massu[k] * ph.dt * c.accx[k];  // rho V g
+    if (c.viscdu) r += 2.0 * ph.mu * c.viscdu[k];     // visc(S(0, D)) of the explicit half and the lift
     ru_[k] = r;
     cnu[k] = cn;
   } else {
@@ -261,12 +264,14 @@ __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, 
     cnu[k] = 0.0;
   }
   if (c.role_v[k] == R_UNKNOWN) {
-    const double cn = conv_v(c, g, w, i, j);
+    double cn = conv_v(c, g, w, i, j);
+    if (c.hd) cn += 0.5 * (c.hd[k] + c.hd[k - g.pitch]) * 0.5 * (w.v[k] + c.dy[k]);
     const double cp = first ? cn : cpv[k];
     const double gp = c.ay[k] * (P(i, j) - P(i, j - 1));
     const double vs = visc_v(c, g, bc, w, i, j);
     double r = c.massv[k] * w.v[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftv[k];
     if (c.accy) r += c.massv[k] * ph.dt * c.accy[k];
+    if (c.viscdv) r += 2.0 * ph.mu * c.viscdv[k];
     rv_[k] = r;
     cnv[k] = cn;
   } else {
@@ -284,7 +289,7 @@ __global__ void k_predictor_rhs(Coefs c, Geom g, Bc bc, Phys ph, FullView w, con
 __device__ __forceinline__ void divergence_at(const Coefs& c, const Geom& g, const Phys& ph, const double* u,
                                               const double* v, double* b, double* rhs, int i, int j, size_t k) {
   const bool dom = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
-  const double d = dom ? cont_cell(c, g, u, v, i, j) : 0.0;
+  const double d = dom ? cont_cell(c, g, u, v, i, j) + (c.hd ? c.hd[k] : 0.0) : 0.0;
   b[k] = d;
   rhs[k] = c.act[k] ? -(ph.rho / ph.dt) * d : 0.0;
 }
@@ -352,7 +357,7 @@ __global__ void k_diagnostics(Coefs c, Geom g, const double* Vu, const double* V
   double dmax = 0.0, ke = 0.0, bad = 0.0;
   if (i <= g.nx + 1 && j <= g.ny + 1) {
     const size_t k = g.idx(i, j);
-    if (c.act[k]) dmax = fabs(cont_cell(c, g, u, v, i, j));
+    if (c.act[k]) dmax = fabs(cont_cell(c, g, u, v, i, j) + (c.hd ? c.hd[k] : 0.0));
     if (i >= 0 && i <= g.nx && j >= 0 && j < g.ny) {
       ke += 0.5 * Vu[k] * u[k] * u[k];
       if (!isfinite(u[k])) bad = 1.0;
@@ -429,14 +434,14 @@ __global__ void k_body_force(Coefs c, Geom g, FullView w, const double* p, doubl
       f[0] = pk * (c.ax[k] - c.ax[k + 1]);
       f[1] = pk * (c.ay[k] - c.ay[k + g.pitch]);
       const double dbx = c.bxx[k] - c.bxx[k + 1];
-      if (dbx != 0.0) f[2] = strain_xx(c, g, w, i, j) * dbx;
+      if (dbx != 0.0) f[2] = (strain_xx(c, g, w, i, j) + (c.sxxd ? c.sxxd[k] : 0.0)) * dbx;
       const double dby = c.byy[k] - c.byy[k + g.pitch];
-      if (dby != 0.0) f[3] = strain_yy(c, g, w, i, j) * dby;
+      if (dby != 0.0) f[3] = (strain_yy(c, g, w, i, j) + (c.syyd ? c.syyd[k] : 0.0)) * dby;
     }
     const double dnx = (j >= 1 && j < g.ny) ? c.bxy[k - g.pitch] - c.bxy[k] : 0.0;
     const double dny = (i >= 1 && i < g.nx) ? c.byx[k - 1] - c.byx[k] : 0.0;
     if (dnx != 0.0 || dny != 0.0) {
-      const double sxy = strain_xy(c, g, w, i, j);
+      const double sxy = strain_xy(c, g, w, i, j) + (c.sxyd ? c.sxyd[k] : 0.0);
       f[2] += sxy * dnx;
       f[3] += sxy * dny;
     }
