@@ -125,6 +125,33 @@ __device__ __forceinline__ bool grid_sync(const Barrier& b, unsigned int& target
   return s_ok != 0;
 }
 
+// The same barrier in two halves, so that a block can do work that no other block reads
+// between its arrival and its wait: grid_arrive (all threads), then grid_wait (all threads).
+__device__ __forceinline__ void grid_arrive(const Barrier& b, unsigned int& target) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    target += gridDim.x;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(b.count), "r"(1u) : "memory");
+  }
+}
+__device__ __forceinline__ bool grid_wait(const Barrier& b, const unsigned int& target) {
+  __shared__ int s_ok2;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const long long t0 = clock64();
+    while (ld_acquire_u32(b.count) < target) {
+      if (clock64() - t0 > b.budget) {
+        atomicExch(b.err, 1);
+        ok = 0;
+        break;
+      }
+    }
+    s_ok2 = ok;
+  }
+  __syncthreads();
+  return s_ok2 != 0;
+}
+
 // Deterministic block sum of NV values (fixed shuffle tree, fixed warp order); the result
 // is valid in thread 0.
 template <int NV>

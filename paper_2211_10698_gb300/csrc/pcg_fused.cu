@@ -27,7 +27,9 @@
 // memory (L2); k_pcg_poisson_f2 keeps its tile's x~, r, p, s, w and row kinds in shared memory
 // for the whole solve.  Only the tile's perimeter cells are read by other blocks (for their
 // ring), so f2 publishes r, w and s of its perimeter to the double-buffered global arrays once
-// per iteration and touches nothing else in global memory until the final x~ -> x.
+// per iteration and touches nothing else in global memory until the final x~ -> x.  Its
+// x~ += alpha p_i, which no other block reads, runs between the block's arrival at the grid
+// barrier and its wait (grid_arrive / grid_wait), in the time the barrier would otherwise idle.
 #include <algorithm>
 
 #include "pcg_common.cuh"
@@ -380,7 +382,6 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
           const double sk = sw[l] + be * ss[l], pk = sr[l] + be * sp[l];
           ss[l] = sk;
           sp[l] = pk;
-          sx[l] += al * pk;
           sr[l] -= al * sk;
         }
     } else if (col)
@@ -419,7 +420,19 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
     stencil(rn_, f.W[nxt], nxt, v);
     double* const rows = (sc_it & 1) ? rows0 : rows1;  // reduction sc_it + 1
     reduce(v, 3, rows);
-    if (!grid_sync(a.bar, target)) { ok = false; break; }
+    if constexpr (RES) {
+      // x~ += alpha p_i is read by no other block and by nothing before the end: it runs between
+      // this block's arrival at the grid barrier and its wait
+      grid_arrive(a.bar, target);
+      if (col)
+        for (int j = j0 + ty0; j < j1; j += RP) {
+          const int l = lidx(ci, j);
+          sx[l] += al * sp[l];
+        }
+      if (!grid_wait(a.bar, target)) { ok = false; break; }
+    } else {
+      if (!grid_sync(a.bar, target)) { ok = false; break; }
+    }
     double t[3];
     grid_sum<3>(rows, nb, t, gsum);
     if (threadIdx.x == 0) {
