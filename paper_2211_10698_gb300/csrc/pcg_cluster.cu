@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_poisson_cluster(ClusterSolve f) 
   __shared__ double bsum[8];
   __shared__ double part[4];  // this CTA's sums, read by every CTA of the cluster
   __shared__ double all[16][4];  // every CTA's sums, gathered
-  __shared__ double sc_alpha, sc_beta, sc_igamma, sc_ialpha, sc_rr, sc_bb;
+  __shared__ double sc_alpha, sc_beta, sc_igamma, sc_den, sc_rr, sc_bb;
+  __shared__ double sc_igamma_next, sc_den_next;
   __shared__ int sc_it, sc_stop;
   extern __shared__ double band[];  // x~, r, p, s, w of the band (nmax each), then the kinds
   cg::cluster_group cluster = cg::this_cluster();
@@ -93,8 +94,8 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_poisson_cluster(ClusterSolve f) 
     }
     if (threadIdx.x < nv) part[threadIdx.x] = bsum[threadIdx.x];
   };
-  // thread rk fetches CTA rk's sums (the C remote loads overlap); thread 0 then adds them in
-  // rank order (call with all threads; the sums land in t of thread 0)
+  // thread rk fetches CTA rk's sums (the C remote loads overlap); threads 0 and 32 then add
+  // them in rank order (call with all threads; the same sums land in t of both)
   auto gather = [&](double (&t)[4], int nv) {
     if (threadIdx.x < C) {
       const double* pr = cluster.map_shared_rank(part, (int)threadIdx.x);
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_poisson_cluster(ClusterSolve f) 
     }
     __syncthreads();
     for (int m = 0; m < nv; ++m) t[m] = 0.0;
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0 || threadIdx.x == 32)
       for (int rk = 0; rk < C; ++rk)
         for (int m = 0; m < nv; ++m) t[m] += all[rk][m];
   };
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_poisson_cluster(ClusterSolve f) 
     if (sc_stop == 0) {
       sc_igamma = recip_newton(gamma);
       sc_alpha = gamma * recip_newton(delta);
-      sc_ialpha = delta * sc_igamma;
+      sc_den = delta;  // 1/alpha = den / gamma
       sc_beta = 0.0;
     }
   }
@@ -162,24 +163,31 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_poisson_cluster(ClusterSolve f) 
     cluster.sync();
     double t3[4];
     gather(t3, 3);
+    // beta = gamma / gamma_old; alpha = gamma / (delta - beta gamma / alpha_old).  The two
+    // reciprocals are independent: 1/gamma (for the next beta) in warp 0, 1/den in warp 1,
+    // which issue to different sub-partitions' FP64 pipes.
     if (threadIdx.x == 0) {
-      const double* t = t3;
-      // beta = gamma / gamma_old; alpha = gamma / (delta - beta gamma / alpha_old)
-      const double gamma = t[0], delta = t[2];
-      sc_rr = dreg * t[0] + t[1];
+      const double gamma = t3[0];
+      sc_rr = dreg * t3[0] + t3[1];
       sc_it += 1;
       sc_stop = sc_rr <= a.tol * a.tol * sc_bb ? 1 : (sc_it >= a.max_iter ? 2 : 0);
       if (sc_stop == 0) {
-        const double beta = gamma * sc_igamma;
-        const double den = delta - beta * gamma * sc_ialpha;
-        const double ig = recip_newton(gamma);
-        sc_beta = beta;
-        sc_alpha = gamma * recip_newton(den);
-        sc_ialpha = den * ig;
-        sc_igamma = ig;
+        sc_beta = gamma * sc_igamma;
+        sc_igamma_next = recip_newton(gamma);
       }
+    } else if (threadIdx.x == 32) {
+      const double gamma = t3[0], delta = t3[2];
+      const double beta = gamma * sc_igamma;
+      const double den = delta - beta * gamma * (sc_den * sc_igamma);
+      sc_den_next = den;
+      if (den != 0.0) sc_alpha = gamma * recip_newton(den);
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+      // read by warp 1 before the barrier above; next read after this iteration's barriers
+      sc_igamma = sc_igamma_next;
+      sc_den = sc_den_next;
+    }
   }
   // x = D^-1/2 x~ on the band
   for (int l = threadIdx.x; l < ncell; l += kCT) {
