@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
   __shared__ double red[4][kPcgThreads];
   __shared__ double bsum[8];
   __shared__ double gsum[8];
-  __shared__ double sc_alpha, sc_beta, sc_igamma, sc_ialpha, sc_rr, sc_bb;
+  __shared__ double sc_alpha, sc_beta, sc_igamma, sc_den, sc_rr, sc_bb;
+  __shared__ double sc_igamma_next, sc_den_next;
   __shared__ int sc_it, sc_stop;
   unsigned int target = 0;
   const int NB = gridDim.x;
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
       if (sc_stop == 0) {
         sc_igamma = recip_newton(gamma);
         sc_alpha = gamma * recip_newton(delta);
-        sc_ialpha = delta * sc_igamma;
+        sc_den = delta;  // 1/alpha = den / gamma
         sc_beta = 0.0;
       }
     }
@@ -186,22 +187,30 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
     if (run) {
       double t[3];
       range_sum<3>(ctl.partials, NB, E.block0, nbc, t, gsum);
+      // the two reciprocals in different warps (different sub-partitions' FP64 pipes):
+      // 1/gamma for the next beta in warp 0, 1/den for alpha in warp 1
       if (threadIdx.x == 0) {
-        const double gamma = t[0], delta = t[2];
+        const double gamma = t[0];
         sc_rr = dreg * t[0] + t[1];
         sc_it += 1;
         sc_stop = sc_rr <= a.tol * a.tol * sc_bb ? 1 : (sc_it >= a.max_iter ? 2 : 0);
         if (sc_stop == 0) {
-          const double beta = gamma * sc_igamma;
-          const double den = delta - beta * gamma * sc_ialpha;
-          const double ig = recip_newton(gamma);
-          sc_beta = beta;
-          sc_alpha = gamma * recip_newton(den);
-          sc_ialpha = den * ig;
-          sc_igamma = ig;
+          sc_beta = gamma * sc_igamma;
+          sc_igamma_next = recip_newton(gamma);
         }
+      } else if (threadIdx.x == 32) {
+        const double gamma = t[0], delta = t[2];
+        const double beta = gamma * sc_igamma;
+        const double den = delta - beta * gamma * (sc_den * sc_igamma);
+        sc_den_next = den;
+        if (den != 0.0) sc_alpha = gamma * recip_newton(den);
       }
       __syncthreads();
+      if (threadIdx.x == 0) {
+        // read by warp 1 before the barrier above; next read after this iteration's barriers
+        sc_igamma = sc_igamma_next;
+        sc_den = sc_den_next;
+      }
     }
   }
   for (CellWalk cw(first, stride, ch.t1, nx); cw.ok(); cw.next()) {
