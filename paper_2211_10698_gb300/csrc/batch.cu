@@ -63,6 +63,7 @@ struct ccm_batch_s {
   bool tune = true;
   int tune_next = 0;               // candidate the next tuned step uses (== count: done)
   double tune_cost[3] = {0, 0, 0};
+  double tune_cells = 0.0;           // cells of the batch the split was (is being) tuned on
   double split_exp = 0.0;          // the chosen exponent a of the weights cells x nx^a
   cudaEvent_t tev[2] = {nullptr, nullptr};
 };
@@ -614,6 +615,18 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
   if (b->cases.empty()) return CCM_OK;
   const bool mixed = case_is_mixed(b->cases[0]);
   const bool scaled = all_scaled(b);
+  // the split is tuned on the batch as it is; once the batch's cells have changed by more than
+  // 30 % (cases joined or left, as in the request loop), it is tuned again
+  if (b->tune) {
+    double cells = 0.0;
+    for (ccm_case c : b->cases) cells += (double)case_cells(c);
+    if (b->tune_next == 0) {
+      b->tune_cells = cells;
+    } else if (std::fabs(cells - b->tune_cells) > 0.3 * b->tune_cells) {
+      b->tune_next = 0;
+      b->tune_cells = cells;
+    }
+  }
   ccm_status s;
   int n = 0;
   // a case's first step starts Adams-Bashforth and runs eagerly
