@@ -200,3 +200,46 @@ def test_batch_errors():
         b2.add(ccm.Case(m))  # precision differs
     b.close()
     b2.close()
+
+
+def _rotation(case, g, omega):
+    """The velocity omega x (x - c) of a rotating cylinder at the u- and v-control volumes'
+    boundary points (the body's D)."""
+    geo = case.geom
+    xu, yu = I.circle_boundary_points(g.cap("u", "X"), g.cap("u", "Y"), geo.cx, geo.cy, geo.r)
+    xv, yv = I.circle_boundary_points(g.cap("v", "X"), g.cap("v", "Y"), geo.cx, geo.cy, geo.r)
+    return -omega * (yu - geo.cy), omega * (xv - geo.cx)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-8)])
+def test_batch_with_body_velocity_and_forcing_equals_alone(precision, tol):
+    """A case with a rotating body (its D-terms) and a case with a body acceleration g, batched
+    with plain cases, give the fields of the same cases advanced alone: the batched stages read
+    the same per-case terms as the single-case ones."""
+    specs = [c for c in _mix(precision) if tuple(c.bc_type) != I.closed_box_bc()[0]]
+    rng = np.random.default_rng(21)
+    gx = 0.2 * rng.standard_normal(specs[2].shape)
+    gy = 0.2 * rng.standard_normal(specs[2].shape)
+
+    def make():
+        cases = [ccm.Case(c) for c in specs]
+        dx, dy = _rotation(specs[1], cases[1], 1.2)
+        cases[1].set_field(ccm.CCM_F_DX, dx)
+        cases[1].set_field(ccm.CCM_F_DY, dy)
+        cases[2].set_field(ccm.CCM_F_GX, gx)
+        cases[2].set_field(ccm.CCM_F_GY, gy)
+        return cases
+
+    alone = make()
+    for a in alone:
+        a.step(4)
+    together = make()
+    b = ccm.Batch(8)
+    for m in together:
+        b.add(m)
+    stats = b.step(4)
+    for a, m, st, sp in zip(alone, together, stats, specs):
+        assert st["converged"] and st["steps"] == 4
+        for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P):
+            assert _rel(_field(m, sp, f), _field(a, sp, f)) < tol, (m.spec.name, f)
+    b.close()
