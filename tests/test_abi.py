@@ -56,3 +56,21 @@ def test_errors_without_gpu_work(libccm):
     assert b"nx" in ccm.lib().ccm_last_error()
     assert ccm.lib().ccm_create_case(None, ctypes.byref(h)) == ccm.CCM_E_INVALID
     assert ccm.lib().ccm_step(None, 1, None) == ccm.CCM_E_INVALID
+
+
+def test_force_and_body_fields_validate_on_the_host(libccm):
+    """The force, force-record and body-field entry points reject bad arguments before any
+    device work."""
+    import ctypes
+
+    from paper_2211_10698_gb300 import ccm
+
+    L = ccm.lib()
+    f = (ctypes.c_double * 4)()
+    assert L.ccm_body_force(None, f) == ccm.CCM_E_INVALID
+    assert L.ccm_set_force_history(None, 4) == ccm.CCM_E_INVALID
+    n, tot = ctypes.c_int(), ctypes.c_longlong()
+    assert L.ccm_get_force_history(None, None, 0, ctypes.byref(n), ctypes.byref(tot)) == ccm.CCM_E_INVALID
+    buf = (ctypes.c_double * 8)()
+    for field in (ccm.CCM_F_GX, ccm.CCM_F_GY, ccm.CCM_F_DX, ccm.CCM_F_DY):
+        assert L.ccm_set_field(None, field, buf, 8) == ccm.CCM_E_INVALID
