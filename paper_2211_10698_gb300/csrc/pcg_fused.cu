@@ -374,6 +374,21 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
     const double* __restrict__ sc_ = f.S[cur];
     double* __restrict__ rn_ = f.R[nxt];
     double* __restrict__ sn_ = f.S[nxt];
+    // this thread's first ring cell: the neighbours' iteration-i values, published before the
+    // last grid barrier, are loaded now so the L2 round trip overlaps step 1
+    int pf_slot = 0;
+    bool pf_in = false;
+    double pf_r = 0.0, pf_w = 0.0, pf_s = 0.0;
+    if (threadIdx.x < nring) {
+      int ri, rj;
+      pf_in = ring_cell(threadIdx.x, ri, rj, pf_slot);
+      if (pf_in) {
+        const size_t k = g.idx(ri, rj);
+        pf_r = rc_[k];
+        pf_w = wc_[k];
+        pf_s = sc_[k];
+      }
+    }
     // step 1: own cells (RES: in the tile; otherwise two rows of this thread at a time with
     // their loads in flight)
     if (RES) {
@@ -407,7 +422,8 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
         }
       }
     // ring cells: r_{i+1} from the neighbours' iteration-i vectors
-    for (int t = threadIdx.x; t < nring; t += kNT) {
+    if (threadIdx.x < nring) ring[pf_slot] = pf_in ? pf_r - al * (pf_w + be * pf_s) : 0.0;
+    for (int t = threadIdx.x + kNT; t < nring; t += kNT) {
       int ri, rj, slot;
       double rv = 0.0;
       if (ring_cell(t, ri, rj, slot)) {
