@@ -100,6 +100,7 @@ def _load():
             "orc_step_gd": (c_int, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP, _DP, _DP, _DP, _DP,
                                     POINTER(OrcStats)]),
             "orc_body_force_d": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP]),
+            "orc_conservation": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -287,6 +288,13 @@ class Oracle:
         self.lib.orc_body_force_d(ctypes.byref(self.s), _p(self.caps), _p(self._c(u)), _p(self._c(v)),
                                   _p(self._c(p)), _p(self._c(Dx)), _p(self._c(Dy)), _p(f))
         return f
+
+    def conservation(self, u, v, Dx=None, Dy=None):
+        """(sum of cont(U, D) over the box cells, sum V^x u, sum V^y v)."""
+        out = np.zeros(3)
+        self.lib.orc_conservation(ctypes.byref(self.s), _p(self.caps), _p(self._c(u)), _p(self._c(v)),
+                                  _p(self._c(Dx)), _p(self._c(Dy)), _p(out))
+        return out
 
     def cell_boundary(self, grid, i, j):
         a, b = c_double(0.0), c_double(0.0)

@@ -1145,6 +1145,31 @@ static double max_div_d(const orc_case* c, const double* caps, const double* u, 
   return m;
 }
 
+/* Conservation sums (the momentum and mass sums of the diagnostics): out[0] = sum of
+ * cont(U, D) over the box cells (Eq. divergence; it telescopes to the net flux through the box
+ * and the body), out[1] = sum of V^x u over the u-positions in the box, out[2] = sum of V^y v
+ * over the v-positions (the discrete momentum per unit density), on the ranges of the kinetic
+ * energy.  D may be NULL. */
+void orc_conservation(const orc_case* c, const double* caps, const double* u, const double* v, const double* Dx,
+                      const double* Dy, double* out) {
+  const double* Vu = CAP(c, caps, G_U, K_V);
+  const double* Vv = CAP(c, caps, G_V, K_V);
+  size_t S = SIZE(c);
+  double* d = malloc(S * sizeof(double));
+  orc_cont(c, caps, u, v, Dx, Dy, d);
+  double m = 0.0, px = 0.0, py = 0.0;
+  for (int j = 0; j < c->ny; ++j)
+    for (int i = 0; i < c->nx; ++i) m += AT(c, d, i, j);
+  for (int j = 0; j < c->ny; ++j)
+    for (int i = 0; i <= c->nx; ++i) px += AT(c, Vu, i, j) * AT(c, u, i, j);
+  for (int j = 0; j <= c->ny; ++j)
+    for (int i = 0; i < c->nx; ++i) py += AT(c, Vv, i, j) * AT(c, v, i, j);
+  out[0] = m;
+  out[1] = px;
+  out[2] = py;
+  free(d);
+}
+
 double orc_max_div(const orc_case* c, const double* caps, const double* u, const double* v) {
   return max_div_d(c, caps, u, v, NULL, NULL);
 }

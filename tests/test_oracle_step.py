@@ -176,3 +176,27 @@ def test_semidiscrete_energy_budget(orc):
     e_visc = (u * vu * mu_).sum() + (v * vv * mv_).sum()
     assert abs(e_conv) < 1e-12 * (abs(e_visc) + 1)
     assert e_visc < 0
+
+
+def test_conservation_sums(orc):
+    """The mass sum of the diagnostics telescopes: the sum of cont(U, 0) over the box cells is the
+    net flux A u through the box's faces (Eq. divergence, interior faces cancel; the body's
+    faces are dry); the momentum sums are the volume-weighted velocity sums."""
+    import numpy as np
+
+    from paper_2211_10698_gb300 import inputs as I
+
+    case = I.small_cylinder(nx=40, ny=20, box=(-2.0, 4.0, -1.5, 1.5), r=0.45, cx=0.1, cy=0.05)
+    o = orc.Oracle(case)
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal(o.shape) * (o.cap("u", "V") > 0)
+    v = rng.standard_normal(o.shape) * (o.cap("v", "V") > 0)
+    m, px, py = o.conservation(u, v)
+    Ax, Ay = o.cap("p", "AX"), o.cap("p", "AY")
+    nx, ny = case.nx, case.ny
+    flux = ((Ax[1:ny + 1, nx + 1] * u[1:ny + 1, nx + 1]).sum() - (Ax[1:ny + 1, 1] * u[1:ny + 1, 1]).sum()
+            + (Ay[ny + 1, 1:nx + 1] * v[ny + 1, 1:nx + 1]).sum() - (Ay[1, 1:nx + 1] * v[1, 1:nx + 1]).sum())
+    assert m == pytest.approx(flux, abs=1e-12 * np.abs(u).sum())
+    assert abs(m) > 1e-3                     # not trivially zero for a random field
+    assert px == pytest.approx((o.cap("u", "V") * u)[1:ny + 1, 1:nx + 2].sum(), rel=1e-13)
+    assert py == pytest.approx((o.cap("v", "V") * v)[1:ny + 2, 1:nx + 1].sum(), rel=1e-13)
