@@ -117,6 +117,10 @@ typedef struct {
   double max_div;             /* max |cont(U^{n+1}, D)| over active cells after the last step */
   double kinetic;             /* sum over velocity positions of V U^2 / 2 after the last step */
   int converged;              /* every solve of every step converged */
+  double mass;                /* sum of cont(U^{n+1}, D) over the box cells: the net volume flux through the
+                                 box and the body (Eq. divergence telescopes) after the last step */
+  double momentum_x;          /* sum over u-positions of V u (momentum per unit density) after the last step */
+  double momentum_y;          /* sum over v-positions of V v */
 } ccm_step_stats;
 
 /* Field identifiers for ccm_set_field / ccm_get_field (padded layout, float64). */

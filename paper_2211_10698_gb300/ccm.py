@@ -62,7 +62,8 @@ class ccm_step_stats(Structure):
     _fields_ = [("steps", c_int), ("iters_p", c_longlong), ("iters_h", c_longlong),
                 ("last_iters_p", c_int), ("last_iters_h", c_int),
                 ("last_res_p", c_double), ("last_res_h", c_double),
-                ("max_div", c_double), ("kinetic", c_double), ("converged", c_int)]
+                ("max_div", c_double), ("kinetic", c_double), ("converged", c_int),
+                ("mass", c_double), ("momentum_x", c_double), ("momentum_y", c_double)]
 
 
 class CcmError(RuntimeError):

@@ -34,7 +34,7 @@ struct DevStats {
   int conv_p, conv_h;
   int nconv;
   int nrep;        // FP64 residual replacements of the last mixed solve on the device
-  double diag[3];  // max |cont|, kinetic, non-finite flag
+  double diag[6];  // max |cont|, kinetic, non-finite flag, mass, momentum x, momentum y
 };
 
 }  // namespace
@@ -144,7 +144,7 @@ void carve(ccm_case c, Carver& cv) {
   for (float** p : fl) *p = cv.take<float>(N);
   c->mixed_sums = cv.take<double>(4);
   c->partials = cv.take<double>((size_t)pcg_partials_needed());
-  c->dpart = cv.take<double>((size_t)3 * diagnostics_partials(c->g) + 8);
+  c->dpart = cv.take<double>((size_t)6 * diagnostics_partials(c->g) + 8);
   c->fpart = cv.take<double>((size_t)body_force_partials(c->g));
   c->accx = cv.take<double>(N);
   c->accy = cv.take<double>(N);
@@ -1168,6 +1168,9 @@ static ccm_status finish_stats(ccm_case c, ccm_step_stats* stats) {
     stats->last_res_h = h.bb_h > 0 ? sqrt(h.rr_h / h.bb_h) : 0.0;
     stats->max_div = h.diag[0];
     stats->kinetic = h.diag[1];
+    stats->mass = h.diag[3];
+    stats->momentum_x = h.diag[4];
+    stats->momentum_y = h.diag[5];
     stats->converged = h.nconv == 0;
   }
   if (c->timing) c->poisson_iters_timed += h.total_p;

@@ -348,66 +348,82 @@ __global__ void __launch_bounds__(256) k_stage_batch(const StageCase* __restrict
   if (KIND == STAGE_PROJECT) project_at(S.c, g, S.phi, S.u, S.v, S.p, i, j, k);
 }
 
-// Diagnostics: per-block max |cont(U)| over active cells, sum of V U^2 / 2 over velocity
-// positions inside the box, and a non-finite flag.
+// Diagnostics: per-block max |cont(U, D)| over active cells, sum of V U^2 / 2 over velocity
+// positions inside the box, a non-finite flag, and the conservation sums: cont(U, D) over the
+// box cells (mass), V u and V v over the velocity positions inside the box (momentum).
 __global__ void k_diagnostics(Coefs c, Geom g, const double* Vu, const double* Vv, const double* u, const double* v,
                               double* partials) {
   const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
   const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
-  double dmax = 0.0, ke = 0.0, bad = 0.0;
+  double dmax = 0.0, ke = 0.0, bad = 0.0, mass = 0.0, mx = 0.0, my = 0.0;
   if (i <= g.nx + 1 && j <= g.ny + 1) {
     const size_t k = g.idx(i, j);
-    if (c.act[k]) dmax = fabs(cont_cell(c, g, u, v, i, j) + (c.hd ? c.hd[k] : 0.0));
+    if (i >= 0 && i < g.nx && j >= 0 && j < g.ny) {
+      const double d = cont_cell(c, g, u, v, i, j) + (c.hd ? c.hd[k] : 0.0);
+      mass = d;
+      if (c.act[k]) dmax = fabs(d);
+    }
     if (i >= 0 && i <= g.nx && j >= 0 && j < g.ny) {
       ke += 0.5 * Vu[k] * u[k] * u[k];
+      mx = Vu[k] * u[k];
       if (!isfinite(u[k])) bad = 1.0;
     }
     if (i >= 0 && i < g.nx && j >= 0 && j <= g.ny) {
       ke += 0.5 * Vv[k] * v[k] * v[k];
+      my = Vv[k] * v[k];
       if (!isfinite(v[k])) bad = 1.0;
     }
   }
-  __shared__ double sm[3][256];
+  __shared__ double sm[6][256];
   const int t = threadIdx.y * blockDim.x + threadIdx.x;
-  sm[0][t] = dmax; sm[1][t] = ke; sm[2][t] = bad;
+  sm[0][t] = dmax; sm[1][t] = ke; sm[2][t] = bad; sm[3][t] = mass; sm[4][t] = mx; sm[5][t] = my;
   __syncthreads();
   for (int s = (blockDim.x * blockDim.y) / 2; s > 0; s >>= 1) {
     if (t < s) {
       sm[0][t] = fmax(sm[0][t], sm[0][t + s]);
       sm[1][t] += sm[1][t + s];
       sm[2][t] = fmax(sm[2][t], sm[2][t + s]);
+      sm[3][t] += sm[3][t + s];
+      sm[4][t] += sm[4][t + s];
+      sm[5][t] += sm[5][t + s];
     }
     __syncthreads();
   }
   if (t == 0) {
     const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
     const size_t nb = (size_t)gridDim.x * gridDim.y;
-    partials[b] = sm[0][0];
-    partials[nb + b] = sm[1][0];
-    partials[2 * nb + b] = sm[2][0];
+    for (int q = 0; q < 6; ++q) partials[q * nb + b] = sm[q][0];
   }
 }
 
+// out = (max |cont|, kinetic energy, non-finite flag, mass, momentum x, momentum y)
 __global__ void k_diagnostics_final(const double* partials, int nb, double* out) {
-  __shared__ double sm[3][256];
+  __shared__ double sm[6][256];
   const int t = threadIdx.x;
-  double m = 0.0, s = 0.0, bad = 0.0;
+  double m = 0.0, bad = 0.0, s[4] = {0.0, 0.0, 0.0, 0.0};
   for (int b = t; b < nb; b += blockDim.x) {
     m = fmax(m, partials[b]);
-    s += partials[nb + b];
+    s[0] += partials[nb + b];
     bad = fmax(bad, partials[2 * nb + b]);
+    s[1] += partials[3 * (size_t)nb + b];
+    s[2] += partials[4 * (size_t)nb + b];
+    s[3] += partials[5 * (size_t)nb + b];
   }
-  sm[0][t] = m; sm[1][t] = s; sm[2][t] = bad;
+  sm[0][t] = m; sm[1][t] = s[0]; sm[2][t] = bad; sm[3][t] = s[1]; sm[4][t] = s[2]; sm[5][t] = s[3];
   __syncthreads();
   for (int st = blockDim.x / 2; st > 0; st >>= 1) {
     if (t < st) {
       sm[0][t] = fmax(sm[0][t], sm[0][t + st]);
-      sm[1][t] += sm[1][t + st];
       sm[2][t] = fmax(sm[2][t], sm[2][t + st]);
+      sm[1][t] += sm[1][t + st];
+      sm[3][t] += sm[3][t + st];
+      sm[4][t] += sm[4][t + st];
+      sm[5][t] += sm[5][t + st];
     }
     __syncthreads();
   }
-  if (t == 0) { out[0] = sm[0][0]; out[1] = sm[1][0]; out[2] = sm[2][0]; }
+  if (t == 0)
+    for (int q = 0; q < 6; ++q) out[q] = sm[q][0];
 }
 
 // Force of the fluid on the body: the body's share of the momentum that pres(P) and

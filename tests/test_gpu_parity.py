@@ -420,3 +420,31 @@ def test_error_paths():
     case.max_iter_p = 20000
     g5 = ccm.Case(case)
     assert g5.step(1)["converged"]
+
+
+@pytest.mark.parametrize("name", ["cylinder", "closed"])
+def test_conservation_sums_match_oracle(name):
+    """The step statistics' mass and momentum sums (the diagnostics) equal the oracle's on the
+    library's own fields; in the closed box the net flux through the walls is zero, so the mass
+    sum is at the solver's tolerance."""
+    case = CASES[name]()
+    case.tol_p = case.tol_h = 1e-13
+    g = ccm.Case(case)
+    o = O.Oracle(case)
+    if name == "closed":
+        rng = np.random.default_rng(3)
+        u0 = rng.standard_normal(o.shape) * (o.role_u == 3)
+        v0 = rng.standard_normal(o.shape) * (o.role_v == 3)
+        s0 = o.init_state(u0=0.0)
+        s0["u"], s0["v"] = o.fill_ghosts(u0, v0)
+        g.set_field(ccm.CCM_F_U, s0["u"])
+        g.set_field(ccm.CCM_F_V, s0["v"])
+    st = g.step(3)
+    u, v = g.get_field(ccm.CCM_F_U), g.get_field(ccm.CCM_F_V)
+    m, px, py = o.conservation(u, v)
+    scale = np.abs(o.cap("u", "V") * u).sum() + np.abs(o.cap("v", "V") * v).sum()
+    assert st["momentum_x"] == pytest.approx(px, abs=1e-13 * scale)
+    assert st["momentum_y"] == pytest.approx(py, abs=1e-13 * scale)
+    assert st["mass"] == pytest.approx(m, abs=1e-13 * scale)
+    if name == "closed":
+        assert abs(st["mass"]) < 1e-9 * scale
