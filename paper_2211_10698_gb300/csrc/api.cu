@@ -597,6 +597,7 @@ void case_stage_case(ccm_case c, StageCase* e, int ahead) {
 }
 int case_cur(ccm_case c) { return c->cur; }
 unsigned long long case_serial(ccm_case c) { return c->serial; }
+bool case_has_extras(ccm_case c) { return c->forced || c->dblock != nullptr; }
 long long case_nstep(ccm_case c) { return c->nstep; }
 void case_helm_solve(ccm_case c, HelmCSolve* a) { helm_solve_of(c, a); }
 // Host bookkeeping of a step whose stages ran batched (as stage_project does for one case).

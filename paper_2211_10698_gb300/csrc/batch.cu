@@ -57,6 +57,7 @@ struct ccm_batch_s {
   std::vector<int> gcur;         // their time-level parity when graph 0 is next
   int gphase = 0;                // the graph the next step replays
   bool gmixed = false;
+  bool gextra = false;               // the captured predictor has the g / D terms
   long long graph_steps = 0;     // steps replayed from graphs
   cudaStream_t cap_st = nullptr; // capture runs here (the legacy default stream cannot capture)
   // online tuning of the Poisson launch's block split (see split_candidates)
@@ -331,7 +332,9 @@ static cudaError_t launch_predict(ccm_batch b, const StageCase* tab) {
   cudaStream_t st = b->st;
   BatchControl ctl{b->partials, b->running, Barrier{b->bar_count, b->bar_err, 2000000000LL}};
   cudaError_t e = launch_stage_batch(STAGE_FILL_BC, tab, b->stage_starts, n, total, st);
-  if (e == cudaSuccess) e = launch_stage_batch(STAGE_PREDICT, tab, b->stage_starts, n, total, st);
+  bool extra = false;
+  for (ccm_case c : b->cases) extra = extra || case_has_extras(c);
+  if (e == cudaSuccess) e = launch_stage_batch(STAGE_PREDICT, tab, b->stage_starts, n, total, st, extra);
   if (e == cudaSuccess) e = run_helm_batch(b->helm, b->helm_block_case, ctl, b->blocks, st);
   if (e == cudaSuccess) e = launch_stage_batch(STAGE_FILL_BC, tab, b->stage_starts, n, total, st);
   if (e == cudaSuccess) e = launch_stage_batch(STAGE_DIVERGENCE, tab, b->stage_starts, n, total, st);
@@ -363,6 +366,9 @@ static void drop_graphs(ccm_batch b) {
 // expects (a case stepped on its own in between invalidates).
 static bool graphs_valid(ccm_batch b, bool mixed) {
   if (!b->gexec[0] || !b->gexec[1] || b->gcases.size() != b->cases.size() || b->gmixed != mixed) return false;
+  bool extra = false;
+  for (ccm_case c : b->cases) extra = extra || case_has_extras(c);
+  if (extra != b->gextra) return false;  // the graphs hold the predictor variant of their capture
   for (size_t i = 0; i < b->cases.size(); ++i)
     if (case_serial(b->cases[i]) != b->gcases[i] || case_cur(b->cases[i]) != (b->gcur[i] ^ b->gphase)) return false;
   return true;
@@ -431,6 +437,8 @@ static ccm_status capture_graphs(ccm_batch b, bool mixed, bool* ok) {
   }
   b->gphase = 0;
   b->gmixed = mixed;
+  b->gextra = false;
+  for (ccm_case c : b->cases) b->gextra = b->gextra || case_has_extras(c);
   *ok = true;
   return CCM_OK;
 }

@@ -232,8 +232,9 @@ struct StageCase {
   int gx;                           // blocks per padded row (stage_case_blocks)
 };
 int stage_case_blocks(const Geom& g, int* gx);
+// extra: some case has a body acceleration or a body velocity (the predictor's extra terms)
 cudaError_t launch_stage_batch(int kind, const StageCase* dev_cases, const int* dev_starts, int n, int blocks,
-                               cudaStream_t st);
+                               cudaStream_t st, bool extra = false);
 struct HelmBatchEntry {
   HelmCSolve a;  // partials and bar unused: the batch has its own
   int block0, nblocks;
@@ -348,6 +349,7 @@ void case_helm_solve(ccm_case c, HelmCSolve* a);
 void case_stage_case(ccm_case c, StageCase* e, int ahead);
 int case_cur(ccm_case c);
 unsigned long long case_serial(ccm_case c);  // unique per case (addresses can be reused)
+bool case_has_extras(ccm_case c);            // a body acceleration or a body velocity is set
 long long case_nstep(ccm_case c);
 void case_step_done(ccm_case c);
 void case_poisson_fp32(ccm_case c, PoissonSolve<float>* a);

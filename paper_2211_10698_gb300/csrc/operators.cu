@@ -242,6 +242,9 @@ __global__ void k_invert_diag(Geom g, const double* du, const double* dv, double
 // Explicit stages of the PmII step (Eq. pm_prediction right-hand side, Eq. pm_poisson
 // right-hand side, Eqs. pm_projection and pm_update).
 // ---------------------------------------------------------------------------------------
+// EXTRA: the case may have a body acceleration g or a body velocity D (their terms are compiled
+// in only then, so the common case keeps the plain kernel's registers and instructions)
+template <bool EXTRA>
 __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph,
                                                  const FullView& w, const double* p, const double* cpu,
                                                  const double* cpv, double* cnu, double* cnv, double* ru_, double* rv_,
@@ -250,13 +253,13 @@ __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, 
   if (c.role_u[k] == R_UNKNOWN) {
     double cn = conv_u(c, g, w, i, j);
     // conv(U, U, D, D): the face mean of h = cont(0, D) times (U + D)/2 (Eq. convective)
-    if (c.hd) cn += 0.5 * (c.hd[k] + c.hd[k - 1]) * 0.5 * (w.u[k] + c.dx[k]);
+    if (EXTRA && c.hd) cn += 0.5 * (c.hd[k] + c.hd[k - 1]) * 0.5 * (w.u[k] + c.dx[k]);
     const double cp = first ? cn : cpu[k];
     const double gp = c.ax[k] * (P(i, j) - P(i - 1, j));
     const double vs = visc_u(c, g, bc, w, i, j);
     double r = c.massu[k] * w.u[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftu[k];
-    if (c.accx) r += c.massu[k] * ph.dt * c.accx[k];  // rho V g
-    if (c.viscdu) r += 2.0 * ph.mu * c.viscdu[k];     // visc(S(0, D)) of the explicit half and the lift
+    if (EXTRA && c.accx) r += c.massu[k] * ph.dt * c.accx[k];  // rho V g
+    if (EXTRA && c.viscdu) r += 2.0 * ph.mu * c.viscdu[k];     // visc(S(0, D)): explicit half and lift
     ru_[k] = r;
     cnu[k] = cn;
   } else {
@@ -265,13 +268,13 @@ __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, 
   }
   if (c.role_v[k] == R_UNKNOWN) {
     double cn = conv_v(c, g, w, i, j);
-    if (c.hd) cn += 0.5 * (c.hd[k] + c.hd[k - g.pitch]) * 0.5 * (w.v[k] + c.dy[k]);
+    if (EXTRA && c.hd) cn += 0.5 * (c.hd[k] + c.hd[k - g.pitch]) * 0.5 * (w.v[k] + c.dy[k]);
     const double cp = first ? cn : cpv[k];
     const double gp = c.ay[k] * (P(i, j) - P(i, j - 1));
     const double vs = visc_v(c, g, bc, w, i, j);
     double r = c.massv[k] * w.v[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftv[k];
-    if (c.accy) r += c.massv[k] * ph.dt * c.accy[k];
-    if (c.viscdv) r += 2.0 * ph.mu * c.viscdv[k];
+    if (EXTRA && c.accy) r += c.massv[k] * ph.dt * c.accy[k];
+    if (EXTRA && c.viscdv) r += 2.0 * ph.mu * c.viscdv[k];
     rv_[k] = r;
     cnv[k] = cn;
   } else {
@@ -279,10 +282,11 @@ __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, 
     cnv[k] = 0.0;
   }
 }
+template <bool EXTRA>
 __global__ void k_predictor_rhs(Coefs c, Geom g, Bc bc, Phys ph, FullView w, const double* p, const double* cpu,
                                 const double* cpv, double* cnu, double* cnv, double* ru_, double* rv_, int first) {
   PAD_IJ(g)
-  predictor_rhs_at(c, g, bc, ph, w, p, cpu, cpv, cnu, cnv, ru_, rv_, first, i, j, k);
+  predictor_rhs_at<EXTRA>(c, g, bc, ph, w, p, cpu, cpv, cnu, cnv, ru_, rv_, first, i, j, k);
 }
 
 // b = cont(U*, D) on cells; Poisson right-hand side -(rho/dt) b on active cells.
@@ -318,7 +322,7 @@ __global__ void k_project(Coefs c, Geom g, const double* phi, double* u, double*
 // also takes the copies U* of the predicted velocity (the whole padded arrays, pitch included,
 // as the single-case step copies them).
 // ---------------------------------------------------------------------------------------
-template <int KIND>
+template <int KIND, bool EXTRA = false>
 __global__ void __launch_bounds__(256) k_stage_batch(const StageCase* __restrict__ cases,
                                                      const int* __restrict__ starts, int n) {
   int lo = 0, hi = n - 1;
@@ -342,8 +346,8 @@ __global__ void __launch_bounds__(256) k_stage_batch(const StageCase* __restrict
   if (i > g.nx + 1) return;
   if (KIND == STAGE_FILL_BC) fill_bc_at(g, S.bc, S.u, S.v, 1.0, i, j, k);
   if (KIND == STAGE_PREDICT)
-    predictor_rhs_at(S.c, g, S.bc, S.ph, FullView{S.u, S.v, g}, S.p, S.cpu, S.cpv, S.cnu, S.cnv, S.ru, S.rv, S.first,
-                     i, j, k);
+    predictor_rhs_at<EXTRA>(S.c, g, S.bc, S.ph, FullView{S.u, S.v, g}, S.p, S.cpu, S.cpv, S.cnu, S.cnv, S.ru, S.rv,
+                            S.first, i, j, k);
   if (KIND == STAGE_DIVERGENCE) divergence_at(S.c, g, S.ph, S.u, S.v, S.div, S.rhs, i, j, k);
   if (KIND == STAGE_PROJECT) project_at(S.c, g, S.phi, S.u, S.v, S.p, i, j, k);
 }
@@ -631,8 +635,12 @@ void launch_helmholtz_coefs(const Coefs& c, const Geom& g, const Bc& bc, const P
 void launch_predictor_rhs(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, const double* u, const double* v,
                           const double* p, const double* cpu, const double* cpv, double* cnu, double* cnv, double* ru,
                           double* rv, int first, cudaStream_t st) {
-  k_predictor_rhs<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, bc, ph, FullView{u, v, g}, p, cpu, cpv, cnu, cnv, ru, rv,
-                                                       first);
+  if (c.accx || c.viscdu || c.hd)
+    k_predictor_rhs<true><<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, bc, ph, FullView{u, v, g}, p, cpu, cpv, cnu, cnv,
+                                                             ru, rv, first);
+  else
+    k_predictor_rhs<false><<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, bc, ph, FullView{u, v, g}, p, cpu, cpv, cnu, cnv,
+                                                              ru, rv, first);
 }
 void launch_divergence(const Coefs& c, const Geom& g, const Phys& ph, const double* u, const double* v, double* b,
                        double* rhs, cudaStream_t st) {
@@ -647,11 +655,14 @@ int stage_case_blocks(const Geom& g, int* gx) {
   return *gx * (int)((g.ny + 3 + kBlk.y - 1) / kBlk.y);
 }
 cudaError_t launch_stage_batch(int kind, const StageCase* dev_cases, const int* dev_starts, int n, int blocks,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool extra) {
   if (n <= 0 || blocks <= 0) return cudaSuccess;
   switch (kind) {
     case STAGE_FILL_BC: k_stage_batch<STAGE_FILL_BC><<<blocks, kBlk, 0, st>>>(dev_cases, dev_starts, n); break;
-    case STAGE_PREDICT: k_stage_batch<STAGE_PREDICT><<<blocks, kBlk, 0, st>>>(dev_cases, dev_starts, n); break;
+    case STAGE_PREDICT:
+      if (extra) k_stage_batch<STAGE_PREDICT, true><<<blocks, kBlk, 0, st>>>(dev_cases, dev_starts, n);
+      else k_stage_batch<STAGE_PREDICT, false><<<blocks, kBlk, 0, st>>>(dev_cases, dev_starts, n);
+      break;
     case STAGE_DIVERGENCE: k_stage_batch<STAGE_DIVERGENCE><<<blocks, kBlk, 0, st>>>(dev_cases, dev_starts, n); break;
     case STAGE_PROJECT: k_stage_batch<STAGE_PROJECT><<<blocks, kBlk, 0, st>>>(dev_cases, dev_starts, n); break;
     default: return cudaErrorInvalidValue;
