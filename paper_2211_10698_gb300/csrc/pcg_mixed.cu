@@ -94,6 +94,10 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
   constexpr float ith = (float)(1.0 / ChebCoef::theta);
   const double tol2 = d.tol * d.tol;
 
+  // with Jacobi, phase A leaves e += alpha p to the wait of phase B's reduction barrier (no other
+  // block reads e)
+  float e_al = 0.0f;
+  bool e_pending = false;
   // R2 (and the start): r64 = D^-1/2 (b - K x); sums ||r64||^2, ||b - K x||^2 (and ||b||^2).
   auto residual64 = [&](bool with_b) -> bool {
     const KRow<double> K{d.cu, d.cv, d.dk, d.kind, d.creg_x, d.creg_y, d.dreg, (size_t)P};
@@ -182,7 +186,12 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
       fpart[nb + blockIdx.x] = fsum[1];
       fpart[2 * nb + blockIdx.x] = fsum[2];
     }
-    if (!grid_sync(d.bar, target)) return false;
+    grid_arrive(d.bar, target);
+    if (e_pending) {
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.add_e(e, p, Q.k(u), e_al);
+      e_pending = false;
+    }
+    if (!grid_wait(d.bar, target)) return false;
     float t[3];
     grid_sum_f32<3>(fpart, nb, t, fsum);
     if (threadIdx.x == 0) {
@@ -301,7 +310,11 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
       const float al = sc_alpha, be = sc_keep ? 0.0f : sc_beta * sc_pscale;
       const bool keep = sc_keep != 0;
       if (cheb == 1) {
-        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.update(p, r, w, s, e, Q.k(u), al, be, keep);
+        // Jacobi: e += alpha p waits for phase B's reduction barrier (measured faster there; with
+        // the Chebyshev steps the barrier waits are shorter and it stays here)
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) ops.update(p, r, w, s, nullptr, Q.k(u), al, be, keep);
+        e_al = al;
+        e_pending = true;
       } else {
         // the same update with u = M^-1 r
         const float* uvec = (cheb & 1) ? a.zA : a.zB;

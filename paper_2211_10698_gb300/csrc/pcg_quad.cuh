@@ -98,7 +98,9 @@ struct QuadOpsF32 {
   // r -= al s
   __device__ __forceinline__ void update(float* p, float* r, const float* w, float* s, float* e, int k0, float al,
                                          float be, bool keep) const {
-    const float4 pm = ld4(p, k0), rm = ld4(r, k0), wm = ld4(w, k0), sm = ld4(s, k0), em = ld4(e, k0);
+    const float4 pm = ld4(p, k0), rm = ld4(r, k0), wm = ld4(w, k0), sm = ld4(s, k0);
+    float4 em = pm;
+    if (e) em = ld4(e, k0);
     float4 pk = pm, sk = sm;
     if (!keep) {
       pk = axpy4(be, pm, rm);
@@ -106,8 +108,12 @@ struct QuadOpsF32 {
       st4(p, k0, pk);
       st4(s, k0, sk);
     }
-    st4(e, k0, axpy4(al, pk, em));
+    if (e) st4(e, k0, axpy4(al, pk, em));
     st4(r, k0, axpy4(-al, sk, rm));
+  }
+  // e += al p on the quad (the correction's update, when it runs apart from phase A)
+  __device__ __forceinline__ void add_e(float* e, const float* p, int k0, float al) const {
+    st4(e, k0, axpy4(al, ld4(p, k0), ld4(e, k0)));
   }
   // the same update with the preconditioned residual u: p = u + be p, s = w + be s
   __device__ __forceinline__ void update_u(float* p, const float* u, float* r, const float* w, float* s, float* e,
