@@ -101,6 +101,7 @@ def _load():
                                     POINTER(OrcStats)]),
             "orc_body_force_d": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP]),
             "orc_conservation": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP]),
+            "orc_poisson_precondition": (None, [cp, _DP, _DP, _DP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -253,6 +254,12 @@ class Oracle:
         du, dv = self.z(), self.z()
         self.lib.orc_helmholtz_diag(ctypes.byref(self.s), _p(self.caps), _p(du), _p(dv))
         return du, dv
+
+    def poisson_precondition(self, r):
+        """z = M^-1 r with the Poisson PCG's preconditioner (Jacobi or k-step Chebyshev)."""
+        z = self.z()
+        self.lib.orc_poisson_precondition(ctypes.byref(self.s), _p(self.caps), _p(self._c(r)), _p(z))
+        return z
 
     def solve_poisson(self, rhs, phi0=None, tol=None, max_iter=None):
         phi = self.z() if phi0 is None else np.array(phi0, dtype=np.float64, order="C")

@@ -1091,6 +1091,20 @@ int orc_solve_poisson(const orc_case* c, const double* caps, const double* rhs_i
   return ok;
 }
 
+/* The Poisson PCG's preconditioner applied once, z = M^-1 r, with the case's choice (Jacobi,
+ * or the k-step Chebyshev iteration over [2/30, 2] on the Jacobi-scaled operator); r and z
+ * are padded cell arrays.  Exported so that tests can check it against its closed form. */
+void orc_poisson_precondition(const orc_case* c, const double* caps, const double* r, double* z) {
+  size_t S = SIZE(c);
+  double* diag = malloc(S * sizeof(double));
+  double* mask = malloc(S * sizeof(double));
+  double* w = malloc(3 * S * sizeof(double));
+  pcg_ctx k;
+  poisson_ctx(c, caps, &k, diag, mask);
+  precondition(&k, r, z, w, w + S, w + 2 * S);
+  free(diag); free(mask); free(w);
+}
+
 int orc_solve_helmholtz(const orc_case* c, const double* caps, const double* rhs_u, const double* rhs_v,
                         double* xu, double* xv, double tol, int max_iter, int* iters, double* relres) {
   size_t S = SIZE(c);

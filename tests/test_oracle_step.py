@@ -41,6 +41,52 @@ def test_chebyshev_cuts_iterations(orc):
     assert its["chebyshev"] < 0.6 * its["jacobi"], its
 
 
+def _chebyshev_q(k, a, b):
+    """q_k(lam) = (1 - T_k((theta - lam)/delta) / T_k(theta/delta)) / lam, theta = (a+b)/2,
+    delta = (b-a)/2: the polynomial that k steps of Chebyshev acceleration from zero apply to
+    the residual (Saad, Iterative Methods for Sparse Linear Systems, Chebyshev acceleration).
+    Built from numpy's Chebyshev-to-power conversion and composed exactly."""
+    from numpy.polynomial import Polynomial, chebyshev as C
+    theta, delta = 0.5 * (b + a), 0.5 * (b - a)
+    tk = Polynomial(C.cheb2poly([0.0] * k + [1.0]))
+    p = tk(Polynomial([theta / delta, -1.0 / delta])) / tk(theta / delta)
+    q, rem = divmod(1.0 - p, Polynomial([0.0, 1.0]))
+    assert np.abs(rem.coef).max() < 1e-12
+    return q
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 4])
+def test_chebyshev_preconditioner_closed_form(orc, degree):
+    """The Chebyshev preconditioner is z = D^-1/2 q_k(K~) D^-1/2 r with K~ = D^-1/2 K D^-1/2
+    the Jacobi-scaled operator on [a, b] = [2/30, 2]: on each eigenvector v of K~ (eigenvalue
+    lam), r = D^1/2 v gives z = q_k(lam) D^-1/2 v.  Dense eigenpairs on a 16x8 cut circle."""
+    case = _cyl()
+    case.precond, case.cheb_degree = "chebyshev", degree
+    o = orc.Oracle(case)
+    dom = np.zeros(o.shape, dtype=bool)
+    dom[1:-2, 1:-2] = True
+    K = O.dense(o.poisson, o.shape, dom, dom)
+    d = o.poisson_diag()[dom]
+    assert np.all(d > 0)
+    Ks = K / np.sqrt(np.outer(d, d))
+    lam, V = np.linalg.eigh(Ks)
+    q = _chebyshev_q(degree, 2.0 / 30.0, 2.0)
+    qmax = np.abs(q(lam)).max()     # the scale of z: rounding is relative to it, not to q(lam)
+    for col in range(V.shape[1]):
+        r = np.zeros(o.shape)
+        r[dom] = np.sqrt(d) * V[:, col]
+        z = o.poisson_precondition(r)
+        want = q(lam[col]) * V[:, col] / np.sqrt(d)
+        assert np.abs(z[dom] - want).max() <= 1e-13 * qmax * np.abs(V[:, col] / np.sqrt(d)).max(), \
+            (col, lam[col])
+        assert np.all(z[~dom] == 0)
+    # a random residual: the same polynomial of the whole operator
+    r = np.random.default_rng(5).standard_normal(o.shape) * dom
+    z = o.poisson_precondition(r)
+    want = (V * q(lam)) @ (V.T @ (r[dom] / np.sqrt(d))) / np.sqrt(d)
+    assert np.abs(z[dom] - want).max() <= 1e-13 * np.abs(want).max()
+
+
 def test_singular_poisson_zero_mean(orc):
     """All-Dirichlet velocity box: K is singular with the constants as null space; the
     iterates are kept zero-mean (end of Sec. 4.6)."""
