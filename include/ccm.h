@@ -20,8 +20,9 @@
  *  - Box sides are W=0, E=1, S=2, N=3.  A DIRICHLET side prescribes the normal velocity
  *    component bc_un and the tangential component bc_ut (an inflow is a Dirichlet side);
  *    an OUTFLOW side has zero-gradient velocity and zero pressure (Sec. 5.1).
- *  - The immersed body is fixed and no-slip (Dirichlet data D = 0 in Eqs. divergence,
- *    diag, offdiag, convective) and must stay two cells away from every box side.
+ *  - The immersed body is fixed and must stay two cells away from every box side.  It is
+ *    no-slip (Dirichlet data D = 0 in Eqs. divergence, diag, offdiag, convective) unless the
+ *    fields CCM_F_DX / CCM_F_DY give it a steady velocity D (a rotating or sliding body).
  */
 #ifndef CCM_H
 #define CCM_H
@@ -222,6 +223,19 @@ ccm_status ccm_apply_op(ccm_case c, int op, const double* in0, const double* in1
  * CCM_E_TIMEOUT if a device barrier gave up, CCM_E_NONFINITE on NaN/Inf. */
 ccm_status ccm_step(ccm_case c, int nsteps, ccm_step_stats* stats);
 
+/* Failure detection (for tests; the paper has no counterpart).  Sets the spin budget, in
+ * clock64 cycles, that every block of the case's cooperative launches (the Helmholtz and
+ * Poisson solves) waits at a device-wide barrier before it gives up (0 restores the default
+ * of 2e9 cycles, about one second), and makes block absent_block of each such launch skip
+ * its arrivals (-1: none, the default).  With a block absent, every other block's wait runs
+ * out after the budget; the blocks then leave the launch, the library reads the error flag
+ * and ccm_step returns CCM_E_TIMEOUT with the context intact.  The fields of the abandoned
+ * step are not meaningful: restore a checkpoint (ccm_set_field) before stepping on.  The
+ * single-cluster solve of small grids (ccm_launch_plan plan[5] > 0) uses the hardware
+ * cluster barrier and is not affected.  CCM_E_INVALID for budget_cycles < 0 or
+ * absent_block < -1. */
+ccm_status ccm_set_barrier_fault(ccm_case c, long long budget_cycles, int absent_block);
+
 /* Enqueue nsteps projection steps on the case's stream and return without waiting; the
  * statistics accumulate on the device until ccm_read_stats.  Same state rules as
  * ccm_step.  Errors detected on the host only (CCM_E_STATE, CCM_E_INVALID, CCM_E_CUDA). */
@@ -282,8 +296,8 @@ ccm_status ccm_solve_pressure(ccm_case c, const double* rhs_host, ccm_solve_stat
  * host framework that owns all device memory through its own pool, a process under a hard
  * device-memory cap, or latency-sensitive code that must avoid the device-wide
  * synchronisation cudaMalloc and cudaFree imply.  It solves the same system as
- * ccm_solve_pressure (Eq. pm_poisson, FP64 Jacobi-PCG to tol_p, whatever the case's
- * precision and preconditioner settings) but allocates nothing: its scratch vectors sit in
+ * ccm_solve_pressure, in FP64 with the Jacobi preconditioner to tol_p, whatever the case's
+ * precision and preconditioner settings, but allocates nothing: its scratch vectors sit in
  * one fixed file-scope device array of about 6.4 MB that every GPU loading the library keeps
  * until the process exits.
  *   rhs_dev  right-hand side, device memory in the case's pitched layout: (ny+3) rows of

@@ -105,6 +105,7 @@ def lib():
             "ccm_kernel_timing": (c_int, [cp, POINTER(c_double), POINTER(c_longlong), POINTER(c_longlong),
                                           POINTER(c_longlong)]),
             "ccm_solve_pressure_noalloc": (c_int, [cp, c_void_p, c_void_p, POINTER(ccm_solve_stats)]),
+            "ccm_set_barrier_fault": (c_int, [cp, c_longlong, c_int]),
             "ccm_batch_create": (c_int, [c_int, c_void_p, POINTER(c_void_p)]),
             "ccm_batch_destroy": (c_int, [cp]),
             "ccm_batch_add": (c_int, [cp, cp]),

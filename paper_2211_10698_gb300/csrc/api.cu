@@ -16,6 +16,10 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// clock64 cycles a block of a cooperative launch waits at a device-wide barrier before it
+// gives up (about one second at 2 GHz)
+constexpr long long kBarrierBudget = 2000000000LL;
+
 ccm_status fail(ccm_status s, const std::string& msg) {
   g_last_error = msg;
   return s;
@@ -100,9 +104,19 @@ struct ccm_case_s {
   double* fhist = nullptr;
   int fcap = 0;
   long long frec = 0;
+  // device-wide barriers of the case's cooperative launches: the spin budget, and the block
+  // that skips its arrivals (failure-detection tests only; -1 otherwise)
+  long long bar_budget = kBarrierBudget;
+  int bar_absent = -1;
 };
 
 namespace {
+
+Barrier case_barrier(ccm_case c) {
+  Barrier b{c->bar_count, c->bar_err, c->bar_budget};
+  b.absent = c->bar_absent;
+  return b;
+}
 
 struct Carver {
   char* base;
@@ -268,7 +282,7 @@ ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
     FusedSolve f{};
     f.a = scaled_solve_of(v, x, b, c->pz, nullptr, nullptr, c->pp0, nullptr);
     f.a.partials = c->partials;
-    f.a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+    f.a.bar = case_barrier(c);
     f.a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
     f.R[0] = c->pr; f.R[1] = c->pz2;
     f.W[0] = c->pq; f.W[1] = c->pw1;
@@ -295,7 +309,7 @@ ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
   a.tol = c->cfg.tol_p; a.max_iter = c->cfg.max_iter_p;
   a.zero_mean = c->zero_mean; a.n_act = c->n_act;
   a.partials = c->partials;
-  a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+  a.bar = case_barrier(c);
   a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
   CUDA_TRY(run_poisson_pcg<double>(a, c->st));
   return CCM_OK;
@@ -313,7 +327,7 @@ void helm_solve_of(ccm_case c, HelmCSolve* out) {
   a.pU = c->hp_u; a.pV = c->hp_v; a.sU = c->hs_u; a.sV = c->hs_v;
   a.tol = c->cfg.tol_h; a.max_iter = c->cfg.max_iter_h;
   a.partials = c->partials;
-  a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+  a.bar = case_barrier(c);
   a.out = PcgOut{&c->ds->iters_h, &c->ds->rr_h, &c->ds->bb_h, &c->ds->conv_h, &c->ds->total_h, &c->ds->nconv};
   *out = a;
 }
@@ -343,7 +357,7 @@ void case_mixed_solve(ccm_case c, double* x, const double* b, MixedSolve* a) {
   *a = MixedSolve{};
   a->d = scaled_solve_of(v, x, b, nullptr, c->pr, nullptr, nullptr, nullptr);
   a->d.partials = c->partials;
-  a->d.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+  a->d.bar = case_barrier(c);
   a->d.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
   a->cus32 = c->co.cus32; a->cvs32 = c->co.cvs32;
   a->r = c->fr; a->w = c->fq; a->p = c->fp0; a->s = c->fp1; a->e = c->fx;
@@ -393,7 +407,7 @@ ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
     a.max_iter = c->cfg.max_iter_p;
     a.zero_mean = c->zero_mean; a.n_act = c->n_act;
     a.partials = c->partials;
-    a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+    a.bar = case_barrier(c);
     a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, nullptr, nullptr};
     CUDA_TRY(run_poisson_pcg<float>(a, st));
     c->launches += 1 + (c->zero_mean ? 4 : 0);
@@ -464,7 +478,7 @@ ccm_status autotune_poisson(ccm_case c) {
     FusedSolve f{};
     f.a = scaled_solve_of(v, x, b, c->pz, nullptr, nullptr, c->pp0, nullptr);
     f.a.partials = c->partials;
-    f.a.bar = Barrier{c->bar_count, c->bar_err, 2000000000LL};
+    f.a.bar = case_barrier(c);
     f.a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, nullptr, nullptr};
     f.a.tol = 0.0;
     f.a.max_iter = kTuneIters;
@@ -1145,7 +1159,13 @@ static ccm_status finish_stats(ccm_case c, ccm_step_stats* stats) {
                      c->ds->diag, c->st);
   DevStats h{};
   ccm_status s;
-  if ((s = read_stats(c, h)) != CCM_OK) return s;
+  if ((s = read_stats(c, h)) != CCM_OK) {
+    // the statistics of the abandoned steps are dropped with them
+    c->steps_pending = 0;
+    cudaMemsetAsync(c->ds, 0, sizeof(DevStats), c->st);
+    cudaStreamSynchronize(c->st);
+    return s;
+  }
   if (c->timing) collect_timing(c);
   if (c->mixed_host) {
     // host-driven refinements report through the case; one-launch mixed solves through the
@@ -1190,6 +1210,15 @@ ccm_status ccm_step(ccm_case c, int nsteps, ccm_step_stats* stats) {
   ccm_status s = enqueue_steps(c, nsteps);
   if (s != CCM_OK) return s;
   return finish_stats(c, stats);
+}
+
+ccm_status ccm_set_barrier_fault(ccm_case c, long long budget_cycles, int absent_block) {
+  g_last_error.clear();
+  if (!c) return fail(CCM_E_INVALID, "null case");
+  if (budget_cycles < 0 || absent_block < -1) return fail(CCM_E_INVALID, "budget_cycles >= 0, absent_block >= -1");
+  c->bar_budget = budget_cycles > 0 ? budget_cycles : kBarrierBudget;
+  c->bar_absent = absent_block;
+  return CCM_OK;
 }
 
 ccm_status ccm_step_async(ccm_case c, int nsteps) {

@@ -92,7 +92,9 @@ constexpr int kBarWords = 1;  // unsigned ints behind Barrier::count
 struct Barrier {
   unsigned int* count;  // zeroed before the launch
   int* err;
-  long long budget;
+  long long budget;     // clock64 cycles a block waits before it gives up
+  int absent = -1;      // failure-detection tests only: this block never arrives, so every other
+                        // block's wait runs out; -1 in every normal launch
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
@@ -110,7 +112,8 @@ __device__ __forceinline__ bool grid_sync(const Barrier& b, unsigned int& target
     // release: the block's writes before the block barrier above become visible with the
     // arrival; the acquire loads below order what follows after every block's arrival (the
     // block barrier below carries both to the other threads of the block)
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(b.count), "r"(1u) : "memory");
+    if ((int)blockIdx.x != b.absent)
+      asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(b.count), "r"(1u) : "memory");
     const long long t0 = clock64();
     while (ld_acquire_u32(b.count) < target) {
       if (clock64() - t0 > b.budget) {
@@ -131,7 +134,8 @@ __device__ __forceinline__ void grid_arrive(const Barrier& b, unsigned int& targ
   __syncthreads();
   if (threadIdx.x == 0) {
     target += gridDim.x;
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(b.count), "r"(1u) : "memory");
+    if ((int)blockIdx.x != b.absent)
+      asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(b.count), "r"(1u) : "memory");
   }
 }
 __device__ __forceinline__ bool grid_wait(const Barrier& b, const unsigned int& target) {

@@ -4,11 +4,15 @@
 // through its own pool and forbids other allocations, a process running under a hard
 // device-memory cap, or latency-sensitive code that must not trigger the device-wide
 // synchronisation that cudaMalloc and cudaFree imply.  ccm_solve_pressure_noalloc serves
-// them: it runs the same FP64 method as ccm_solve_pressure (CG on the Jacobi-scaled system, in
-// the two-barrier layout, which needs fewer work vectors than the tiled one), but its scratch
+// them: it solves the same system as ccm_solve_pressure in FP64 with the Jacobi
+// preconditioner, whatever the case's precision and preconditioner settings, but its scratch
 // vectors live in one file-scope __device__ array of fixed size instead of memory the
-// library allocates.  The caller passes the right-hand side and the solution in device
-// memory of its own.
+// library allocates.  Two kernels serve it: a case with an outflow side and the Jacobi
+// setting runs CG on the Jacobi-scaled system in the two-barrier layout (k_pcg_poisson_sc,
+// which needs fewer work vectors than the tiled one); a singular case (no outflow side,
+// zero-mean iterates) or one configured for Chebyshev runs the unscaled Jacobi-PCG
+// (k_pcg_poisson_cg with a degree-1 preconditioner).  The caller passes the right-hand side
+// and the solution in device memory of its own.
 //
 // The array (about 6.4 MB) stays resident on every GPU that loads the library until the
 // process exits.  Every call uses the same array, so calls that overlap on the GPU (from
@@ -106,11 +110,15 @@ extern "C" ccm_status ccm_solve_pressure_noalloc(ccm_case c, const double* rhs_d
   cudaError_t e = scratch_address(&S);
   if (e != cudaSuccess) return fail(CCM_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   cudaStream_t st = v.st;
-  // the previous call's contents (possibly of another grid size): every work vector is
-  // cleared, since the stencils read them on the ghost ring, and so are the barrier counter
-  // and its error flag
-  if ((e = cudaMemsetAsync(S->r, 0, 5 * kMaxElems * sizeof(double), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(&S->bar_err, 0, 2 * sizeof(int) + sizeof(unsigned int) * kBarWords, st)) != cudaSuccess)
+  // the previous call's contents (possibly of another grid size): the first n elements of
+  // every work vector are cleared, since the stencils read them on the ghost ring (a solve
+  // of this grid touches nothing beyond them), and so are the barrier counter and its
+  // error flag
+  double* const work[5] = {S->r, S->u, S->w, S->p, S->s};
+  for (double* a : work)
+    if ((e = cudaMemsetAsync(a, 0, n * sizeof(double), st)) != cudaSuccess)
+      return fail(CCM_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  if ((e = cudaMemsetAsync(&S->bar_err, 0, 2 * sizeof(int) + sizeof(unsigned int) * kBarWords, st)) != cudaSuccess)
     return fail(CCM_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   const dim3 blk(64, 4), grd((v.g.nx + 3 + 63) / 64, (v.g.ny + 3 + 3) / 4);
   k_masked_copy<<<grd, blk, 0, st>>>(v.g, v.act, rhs_dev, S->b);

@@ -74,3 +74,35 @@ def test_force_and_body_fields_validate_on_the_host(libccm):
     buf = (ctypes.c_double * 8)()
     for field in (ccm.CCM_F_GX, ccm.CCM_F_GY, ccm.CCM_F_DX, ccm.CCM_F_DY):
         assert L.ccm_set_field(None, field, buf, 8) == ccm.CCM_E_INVALID
+
+
+def test_allocator_hook_failure_is_out_of_memory(libccm):
+    """An allocator hook that returns NULL makes ccm_create_case fail with CCM_E_OOM and no case
+    (the hook is the first device-memory request, so this runs without a GPU)."""
+    from paper_2211_10698_gb300 import ccm, inputs
+
+    calls = []
+
+    def _alloc(nbytes, ctx):
+        calls.append(int(nbytes))
+        return None
+
+    def _free(ptr, ctx):
+        raise AssertionError("nothing was allocated")
+
+    cfg = ccm.make_config(inputs.small_cylinder())
+    cfg.alloc, cfg.free = ccm.ccm_alloc_fn(_alloc), ccm.ccm_free_fn(_free)
+    h = ctypes.c_void_p()
+    assert ccm.lib().ccm_create_case(ctypes.byref(cfg), ctypes.byref(h)) == ccm.CCM_E_OOM
+    assert b"allocator hook" in ccm.lib().ccm_last_error()
+    assert h.value is None and len(calls) == 1
+    need = ctypes.c_size_t()
+    assert ccm.lib().ccm_case_bytes(ctypes.byref(cfg), ctypes.byref(need)) == ccm.CCM_OK
+    assert calls[0] >= need.value > 0
+
+
+def test_barrier_fault_hook_validates_on_the_host(libccm):
+    from paper_2211_10698_gb300 import ccm
+
+    L = ccm.lib()
+    assert L.ccm_set_barrier_fault(None, 0, -1) == ccm.CCM_E_INVALID
