@@ -12,8 +12,8 @@ between timed steps, outside each step's CUDA-event interval.
 
 With N > 1 (torchrun, one process per GPU) every rank advances its own replica of the case
 (the case is not split: replicas only) and ``value`` is the sum over ranks.
-``--impl reference`` times the FP64 CPU oracle on this machine's host cores on bounded
-samples of the same workload.
+``--impl reference`` times the FP64 CPU oracle on this machine's host cores: whole steps of
+the same workload's trajectory, the same warm-up and timed step counts.
 """
 from __future__ import annotations
 
@@ -54,6 +54,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-full", action="store_true",
+                    help="also time one whole headline step of the oracle on one thread")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the measurements that follow the headline")
     ap.add_argument("--extras", default="mixed,configs,batched,serving",
@@ -188,92 +190,95 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-class _OracleSampler:
-    """Bounded samples of the oracle on the workload.  One sample is one oracle step from the
-    initial state with the Poisson PCG capped at a few iterations; samples at two caps give
-    the fixed cost a of a step (predictor, Helmholtz PCG, projection) and the cost b of one
-    Poisson iteration, so that a whole step costs a + b * (Poisson iterations per step)."""
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
 
-    def __init__(self, case):
-        import copy
 
-        import oracle
-        from paper_2211_10698_gb300 import inputs
+def oracle_steps(case, steps, threads, warmup=0):
+    """Whole steps of the FP64 oracle on this machine's cores: the seeded initial state (with
+    the case's velocity perturbation), ``warmup`` untimed steps, then ``steps`` steps each timed
+    on the wall clock.  Every solve runs to the case's tolerance (nothing is capped).  Returns
+    the thread count used, the seconds and the Poisson iterations of each timed step."""
+    import oracle
+    from paper_2211_10698_gb300 import inputs
 
-        self.case = case
-        self.pu, self.pv = inputs.perturbation(case)
-        self.o = {}
-        for n in (5, 45):
-            c2 = copy.deepcopy(case)
-            c2.max_iter_p = n
-            self.o[n] = oracle.Oracle(c2)
-        self.pts = []
-
-    def sample(self, n):
-        o = self.o[n]
-        st = o.init_state(pu=self.pu, pv=self.pv)
+    used = oracle.set_threads(threads)
+    o = oracle.Oracle(case)
+    pu, pv = inputs.perturbation(case)
+    st = o.init_state(pu, pv)
+    if warmup:
+        o.step(st, warmup)
+    secs, iters = [], []
+    for _ in range(steps):
         t0 = time.perf_counter()
         hist, _ = o.step(st, 1)
-        self.pts.append((hist[0]["iters_p"], time.perf_counter() - t0))
-        return self.pts[-1]
-
-    def fit(self, pts=None):
-        import numpy as np
-
-        pts = self.pts if pts is None else pts
-        n = np.array([p[0] for p in pts], float)
-        t = np.array([p[1] for p in pts], float)
-        b, a = np.polyfit(n, t, 1)
-        return float(a), float(b)
+        secs.append(time.perf_counter() - t0)
+        iters.append(hist[0]["iters_p"])
+    return dict(threads=used, seconds=secs, iters_p=iters)
 
 
-def _cpu_sample(case, iters_per_step):
-    s = _OracleSampler(case)
-    s.sample(5)
-    s.sample(45)
-    a, b = s.fit()
-    t_step = a + b * iters_per_step
-    (n1, t1), (n2, t2) = s.pts
-    return dict(value=case.cells / t_step, unit=UNIT, cores=1, kind="oracle",
-                sample=(f"{WORKLOAD}: 2 oracle steps from the initial state with the Poisson PCG capped at "
-                        f"{n1} and {n2} iterations ({t1:.1f} s, {t2:.1f} s); whole step = {a:.2f} s + "
-                        f"{b:.4f} s/iteration x {iters_per_step:.0f} oracle Poisson iterations per step"),
-                seconds_per_step=t_step)
+def _window_summary(case, w):
+    t = sum(w["seconds"])
+    return dict(cells=case.cells, steps=len(w["seconds"]), threads=w["threads"], seconds=t,
+                value=case.cells * len(w["seconds"]) / t, unit=UNIT,
+                poisson_iters_per_step=sum(w["iters_p"]) / len(w["iters_p"]))
 
 
-def _oracle_iters_per_step(skip=3):
-    path = os.path.join(ROOT, "tests", "golden", "c2_oracle_iterations.json")
-    with open(path) as f:
-        rows = json.load(f)["steps"]
-    use = [r["iters_p"] for r in rows[skip:]] or [r["iters_p"] for r in rows]
-    return sum(use) / len(use), len(use)
+def cpu_baseline(case, full=False):
+    """The FP64 oracle timed on this machine's cores, whole steps only:
+    - the headline workload: step 1 of its seeded run, one whole step on all cores (the value);
+    - the 128x64 Re 40 cylinder: all 100 steps, on all cores and on one thread;
+    - with ``full``, also the headline step on one thread (a minute or more)."""
+    from paper_2211_10698_gb300 import inputs
+
+    nproc = os.cpu_count()
+    head = oracle_steps(case, 1, 0)
+    c1 = inputs.cylinder_re40_128x64()
+    windows = {f"{WORKLOAD} all cores": _window_summary(case, head),
+               f"{c1.name} all cores": _window_summary(c1, oracle_steps(c1, c1.steps, 0)),
+               f"{c1.name} 1 thread": _window_summary(c1, oracle_steps(c1, c1.steps, 1))}
+    if full:
+        windows[f"{WORKLOAD} 1 thread"] = _window_summary(case, oracle_steps(case, 1, 1))
+    h = windows[f"{WORKLOAD} all cores"]
+    return dict(value=h["value"], unit=UNIT, cores=h["threads"], kind="oracle",
+                sample=(f"{WORKLOAD}: step 1 of the seeded run, one whole oracle step (every solve to its 1e-10 "
+                        f"tolerance, {h['poisson_iters_per_step']:.0f} Poisson iterations) on {h['threads']} "
+                        f"threads, {h['seconds']:.1f} s"),
+                nproc=nproc, cpu_model=_cpu_model(), windows=windows)
 
 
 def run_reference(args):
+    """The FP64 CPU oracle as the reference arm: the headline workload's own trajectory
+    (seeded initial state, ``warmup`` untimed whole steps, then ``steps`` whole steps each
+    timed), on all of this machine's cores.  Rank 0 alone runs it."""
     rank, world, _ = _dist()
     if rank != 0:
         return 0
     from paper_2211_10698_gb300 import inputs
 
     case = inputs.cylinder_re100_1024x512()
-    iters, nrows = _oracle_iters_per_step()
-    sampler = _OracleSampler(case)
-    for k in range(args.warmup):
-        sampler.sample(5 if k % 2 == 0 else 45)
-    timed = [sampler.sample(5 if k % 2 == 0 else 45) for k in range(max(args.steps, 2))]
-    a, b = sampler.fit(timed)
-    sec_step = a + b * iters
-    secs = sec_step * len(timed)
-    value = case.cells / sec_step
-    vals = [dict(sample=(f"{WORKLOAD}: {len(timed)} oracle steps from the initial state with the Poisson PCG "
-                         f"capped alternately at 5 and 45 iterations; whole step = {a:.2f} s + {b:.4f} s/iteration "
-                         f"x {iters:.0f} oracle Poisson iterations per step (tests/golden/c2_oracle_iterations.json)"))] * len(timed)
+    w = oracle_steps(case, args.steps, 0, warmup=args.warmup)
+    secs = sum(w["seconds"])
+    value = case.cells * args.steps / secs
+    iters = sum(w["iters_p"]) / len(w["iters_p"])
+    sample = (f"{WORKLOAD}: steps {args.warmup + 1}..{args.warmup + args.steps} of the seeded run after "
+              f"{args.warmup} untimed steps, whole oracle steps (every solve to its 1e-10 tolerance, "
+              f"{iters:.0f} Poisson iterations per step) on {w['threads']} threads")
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
-                warmup=args.warmup, ms_per_step=1e3 * secs / len(vals), higher_is_better=True, scaling="weak",
+                warmup=args.warmup, ms_per_step=1e3 * secs / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=WORKLOAD, nx=case.nx, ny=case.ny, precision="fp64", precond="jacobi",
-                            tol_p=case.tol_p, oracle_poisson_iters_per_step=iters),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=vals[-1]["sample"]),
+                config=dict(workload=WORKLOAD, nx=case.nx, ny=case.ny, cells=case.cells, precision="fp64",
+                            precond="jacobi", tol_p=case.tol_p, tol_h=case.tol_h,
+                            poisson_iters_per_step=iters),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=w["threads"], kind="oracle", sample=sample,
+                                  nproc=os.cpu_count(), cpu_model=_cpu_model()),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
@@ -588,13 +593,8 @@ def run_ours(args):
             extras["serving"] = {"error": str(e)}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        try:
-            oi, _ = _oracle_iters_per_step()
-        except (OSError, KeyError, ValueError):
-            oi = iters_p
-        cpu = _cpu_sample(case, oi)
-        cpu.pop("seconds_per_step", None)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(case, full=args.cpu_baseline_full)
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,

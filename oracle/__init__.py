@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline /
 reference legs of ``bench.py`` may import this package.  It wraps ``ccm_oracle.c`` (plain C,
-FP64, single thread, no code shared with the CUDA library) through ctypes and adds numpy
+FP64, optional OpenMP loops, no code shared with the CUDA library) through ctypes and adds numpy
 helpers that build dense matrices by applying the oracle's operators to unit vectors.
 
 Every array is a padded ``(ny + 3, nx + 3)`` float64 array (see
@@ -28,13 +28,22 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree)."""
+    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree), with OpenMP for
+    its cell loops when the compiler has it (the results do not depend on the thread count)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads for the oracle's parallel loops (0: all of this machine's); returns the count in
+    use (1 when built without OpenMP)."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 class OrcCase(ctypes.Structure):
@@ -102,6 +111,7 @@ def _load():
             "orc_body_force_d": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP]),
             "orc_conservation": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP]),
             "orc_poisson_precondition": (None, [cp, _DP, _DP, _DP]),
+            "orc_set_threads": (c_int, [c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)

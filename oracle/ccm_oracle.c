@@ -2,7 +2,7 @@
  * FP64 CPU oracle for the conservative Cartesian cut-cell method on staggered (MAC) grids
  * of Quiros Rodriguez, Fullana, Le Chenadec and Sayadi (arXiv 2211.10698).
  *
- * TEST INFRASTRUCTURE.  This file is the plain, slow, single-threaded statement of what the
+ * TEST INFRASTRUCTURE.  This file is the plain, slow statement of what the
  * GPU library must compute.  Only the tests, the package's smoke check and the bench's CPU
  * baseline call it; the library never does.  It shares no code, header or table with the
  * CUDA sources.
@@ -27,6 +27,20 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Loops over cells or vector elements whose iterations write distinct outputs may run on
+ * several threads (OpenMP, when built with it); the results do not depend on the thread count.
+ * Sums (dot products, means) are taken in a fixed order: serially within fixed blocks of
+ * DOT_BLOCK elements, then over the blocks in order. */
+#ifdef _OPENMP
+#define PAR_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define PAR_FOR
+#endif
+#define DOT_BLOCK 4096
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -72,6 +86,29 @@ enum { W_SIDE = 0, E_SIDE = 1, S_SIDE = 2, N_SIDE = 3 };
 #define CAP(c, caps, g, k) ((caps) + ((size_t)(g) * 9 + (size_t)(k)) * SIZE(c))
 
 size_t orc_size(const orc_case* c) { return SIZE(c); }
+
+/* Threads for the parallel loops (n < 1: all); returns the number in use.  1 without OpenMP. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  else omp_set_num_threads(omp_get_num_procs());
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
+static void zero_fill(double* a, size_t n) {
+  PAR_FOR
+  for (size_t k = 0; k < n; ++k) a[k] = 0.0;
+}
+
+static double* zalloc(size_t n) {
+  double* a = malloc(n * sizeof(double));
+  zero_fill(a, n);
+  return a;
+}
 
 /* ------------------------------------------------------------------------------------------
  * Geometry input (Sec. 3.1): the fluid characteristic function H^f of Eq. characteristic,
@@ -350,8 +387,9 @@ static double second_kind_volume(const orc_case* c, int g, int i, int j, int axi
 
 void orc_capacities(const orc_case* c, double* caps) {
   size_t S = SIZE(c);
-  memset(caps, 0, 27 * S * sizeof(double));
+  zero_fill(caps, 27 * S);
   for (int g = 0; g < 3; ++g) {
+    PAR_FOR
     for (int j = -1; j <= c->ny + 1; ++j)
       for (int i = -1; i <= c->nx + 1; ++i) {
         cell_moments m;
@@ -413,7 +451,8 @@ void orc_cont(const orc_case* c, const double* caps, const double* u, const doub
   const double* Ay = CAP(c, caps, G_P, K_AY);
   const double* Bx = CAP(c, caps, G_P, K_BX);
   const double* By = CAP(c, caps, G_P, K_BY);
-  memset(out, 0, SIZE(c) * sizeof(double));
+  zero_fill(out, SIZE(c));
+  PAR_FOR
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i < c->nx; ++i) {
       double hom = AT(c, Ax, i + 1, j) * AT(c, u, i + 1, j) - AT(c, Ax, i, j) * AT(c, u, i, j) +
@@ -438,10 +477,12 @@ void orc_cont(const orc_case* c, const double* caps, const double* u, const doub
 void orc_pres(const orc_case* c, const double* caps, const double* p, double* ou, double* ov) {
   const double* Ax = CAP(c, caps, G_P, K_AX);
   const double* Ay = CAP(c, caps, G_P, K_AY);
-  memset(ou, 0, SIZE(c) * sizeof(double));
-  memset(ov, 0, SIZE(c) * sizeof(double));
+  zero_fill(ou, SIZE(c));
+  zero_fill(ov, SIZE(c));
+  PAR_FOR
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i <= c->nx; ++i) AT(c, ou, i, j) = AT(c, Ax, i, j) * (AT(c, p, i, j) - AT(c, p, i - 1, j));
+  PAR_FOR
   for (int j = 0; j <= c->ny; ++j)
     for (int i = 0; i < c->nx; ++i) AT(c, ov, i, j) = AT(c, Ay, i, j) * (AT(c, p, i, j) - AT(c, p, i, j - 1));
 }
@@ -467,10 +508,11 @@ void orc_strain(const orc_case* c, const double* caps, const double* u, const do
   const double* ByV = CAP(c, caps, G_V, K_BY);
   const double* WxV = CAP(c, caps, G_V, K_WX);
   const double* WyV = CAP(c, caps, G_V, K_WY);
-  memset(sxx, 0, SIZE(c) * sizeof(double));
-  memset(syy, 0, SIZE(c) * sizeof(double));
-  memset(sxy, 0, SIZE(c) * sizeof(double));
+  zero_fill(sxx, SIZE(c));
+  zero_fill(syy, SIZE(c));
+  zero_fill(sxy, SIZE(c));
   /* S_xx at p-cell (i,j): u-faces i and i+1; A^xx at p-cell k is AxU(k+1) */
+  PAR_FOR
   for (int j = 0; j < c->ny; ++j)
     for (int i = -1; i <= c->nx; ++i) {
       double g = AT(c, BxU, i + 1, j) * AT(c, u, i + 1, j) - AT(c, BxU, i, j) * AT(c, u, i, j);
@@ -484,6 +526,7 @@ void orc_strain(const orc_case* c, const double* caps, const double* u, const do
       }
       AT(c, sxx, i, j) = g * winv(c, AT(c, WxU, i + 1, j));
     }
+  PAR_FOR
   for (int j = -1; j <= c->ny; ++j)
     for (int i = 0; i < c->nx; ++i) {
       double g = AT(c, ByV, i, j + 1) * AT(c, v, i, j + 1) - AT(c, ByV, i, j) * AT(c, v, i, j);
@@ -497,6 +540,7 @@ void orc_strain(const orc_case* c, const double* caps, const double* u, const do
       AT(c, syy, i, j) = g * winv(c, AT(c, WyV, i, j + 1));
     }
   /* S_xy at node (i,j) */
+  PAR_FOR
   for (int j = 0; j <= c->ny; ++j)
     for (int i = 0; i <= c->nx; ++i) {
       /* alpha = x, beta = y on the u-grid: B^xy at u-faces (i,j-1),(i,j); A^xy at nodes = AyU */
@@ -533,12 +577,14 @@ void orc_visc(const orc_case* c, const double* caps, const double* sxx, const do
   const double* ByU = CAP(c, caps, G_U, K_BY);
   const double* BxV = CAP(c, caps, G_V, K_BX);
   const double* ByV = CAP(c, caps, G_V, K_BY);
-  memset(ou, 0, SIZE(c) * sizeof(double));
-  memset(ov, 0, SIZE(c) * sizeof(double));
+  zero_fill(ou, SIZE(c));
+  zero_fill(ov, SIZE(c));
+  PAR_FOR
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i <= c->nx; ++i)
       AT(c, ou, i, j) = AT(c, BxU, i, j) * (AT(c, sxx, i, j) - AT(c, sxx, i - 1, j)) +
                         AT(c, ByU, i, j) * (AT(c, sxy, i, j + 1) - AT(c, sxy, i, j));
+  PAR_FOR
   for (int j = 0; j <= c->ny; ++j)
     for (int i = 0; i < c->nx; ++i)
       AT(c, ov, i, j) = AT(c, ByV, i, j) * (AT(c, syy, i, j) - AT(c, syy, i, j - 1)) +
@@ -555,12 +601,13 @@ void orc_conv(const orc_case* c, const double* caps, const double* u, const doub
   const double* Ay = CAP(c, caps, G_P, K_AY);
   const double* Bx = CAP(c, caps, G_P, K_BX);
   const double* By = CAP(c, caps, G_P, K_BY);
-  memset(ou, 0, SIZE(c) * sizeof(double));
-  memset(ov, 0, SIZE(c) * sizeof(double));
+  zero_fill(ou, SIZE(c));
+  zero_fill(ov, SIZE(c));
 #define EX(i, j) ((0.5 * (AT(c, Bx, (i), (j)) + AT(c, Bx, (i) - 1, (j))) - AT(c, Ax, (i), (j))) * dval(c, Dx, (i), (j)))
 #define FX(i, j) ((AT(c, Bx, (i), (j)) - AT(c, Bx, (i) - 1, (j))) * dval(c, Dx, (i), (j)))
 #define EY(i, j) ((0.5 * (AT(c, By, (i), (j)) + AT(c, By, (i), (j) - 1)) - AT(c, Ay, (i), (j))) * dval(c, Dy, (i), (j)))
 #define FY(i, j) ((AT(c, By, (i), (j)) - AT(c, By, (i), (j) - 1)) * dval(c, Dy, (i), (j)))
+  PAR_FOR
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i <= c->nx; ++i) {
       /* beta = x: mass flux bar(A_x U_x)^x and bar(U'_x)^x at p-cells i-1 and i */
@@ -593,6 +640,7 @@ void orc_conv(const orc_case* c, const double* caps, const double* u, const doub
       }
       AT(c, ou, i, j) = cx_ + cy_ + br * 0.5 * (AT(c, ut, i, j) + dval(c, Dxt, i, j));
     }
+  PAR_FOR
   for (int j = 0; j <= c->ny; ++j)
     for (int i = 0; i < c->nx; ++i) {
       /* beta = y: bar(A_y U_y)^y and bar(U'_y)^y at p-cells j-1 and j */
@@ -720,6 +768,7 @@ static void visc_bc(const orc_case* c, const double* caps, const double* u, cons
     for (int i = 0; i <= nx; ++i) AT(c, ou, i, ny - 1) -= AT(c, ByU, i, ny - 1) * AT(c, sxy, i, ny);
   if (c->bc_type[S_SIDE] == BC_OUT)
     for (int i = 0; i <= nx; ++i) AT(c, ou, i, 0) += AT(c, ByU, i, 0) * AT(c, sxy, i, 0);
+  PAR_FOR
   for (int j = -1; j <= ny + 1; ++j)
     for (int i = -1; i <= nx + 1; ++i) {
       if (role_u(c, caps, i, j) != 3) AT(c, ou, i, j) = 0.0;
@@ -752,6 +801,7 @@ static void conv_bc(const orc_case* c, const double* caps, const double* u_in, c
   memcpy(v, v_in, S * sizeof(double));
   fill_bc(c, u, v, 1.0);
   orc_conv(c, caps, u, v, u, v, Dx, Dy, Dx, Dy, ou, ov);
+  PAR_FOR
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
       if (role_u(c, caps, i, j) != 3) AT(c, ou, i, j) = 0.0;
@@ -770,10 +820,12 @@ void orc_conv_bc(const orc_case* c, const double* caps, const double* u_in, cons
  * (Dirichlet pressure on outflow sides). */
 void orc_pres_bc(const orc_case* c, const double* caps, const double* p_in, double* ou, double* ov) {
   size_t S = SIZE(c);
-  double* p = calloc(S, sizeof(double));
+  double* p = zalloc(S);
+  PAR_FOR
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i < c->nx; ++i) AT(c, p, i, j) = AT(c, p_in, i, j);
   orc_pres(c, caps, p, ou, ov);
+  PAR_FOR
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
       if (role_u(c, caps, i, j) != 3) AT(c, ou, i, j) = 0.0;
@@ -793,8 +845,9 @@ void orc_pres_bc(const orc_case* c, const double* caps, const double* p_in, doub
 void orc_helmholtz(const orc_case* c, const double* caps, const double* u_in, const double* v_in, double* ou,
                    double* ov) {
   size_t S = SIZE(c);
-  double* u = calloc(S, sizeof(double));
-  double* v = calloc(S, sizeof(double));
+  double* u = zalloc(S);
+  double* v = zalloc(S);
+  PAR_FOR
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
       if (role_u(c, caps, i, j) == 3) AT(c, u, i, j) = AT(c, u_in, i, j);
@@ -805,6 +858,7 @@ void orc_helmholtz(const orc_case* c, const double* caps, const double* u_in, co
   const double* Vu = CAP(c, caps, G_U, K_V);
   const double* Vv = CAP(c, caps, G_V, K_V);
   double s = c->rho / c->dt;
+  PAR_FOR
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
       int ru = role_u(c, caps, i, j), rv = role_v(c, caps, i, j);
@@ -848,9 +902,10 @@ void orc_roles(const orc_case* c, const double* caps, int* ru, int* rv, int* act
 
 void orc_poisson(const orc_case* c, const double* caps, const double* phi_in, double* out) {
   size_t S = SIZE(c);
-  double* phi = calloc(S, sizeof(double));
+  double* phi = zalloc(S);
   double* gu = malloc(S * sizeof(double));
   double* gv = malloc(S * sizeof(double));
+  PAR_FOR
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i < c->nx; ++i)
       if (cell_active(c, caps, i, j)) AT(c, phi, i, j) = AT(c, phi_in, i, j);
@@ -858,11 +913,13 @@ void orc_poisson(const orc_case* c, const double* caps, const double* phi_in, do
   orc_pres_bc(c, caps, phi, gu, gv);
   const double* Vu = CAP(c, caps, G_U, K_V);
   const double* Vv = CAP(c, caps, G_V, K_V);
+  PAR_FOR
   for (size_t k = 0; k < S; ++k) {
     gu[k] *= winv(c, Vu[k]);
     gv[k] *= winv(c, Vv[k]);
   }
   orc_cont(c, caps, gu, gv, NULL, NULL, out);
+  PAR_FOR
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
       if (cell_active(c, caps, i, j)) AT(c, out, i, j) = -AT(c, out, i, j);
@@ -882,11 +939,13 @@ void orc_poisson_diag(const orc_case* c, const double* caps, double* diag) {
   memset(diag, 0, S * sizeof(double));
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
-      memset(e, 0, S * sizeof(double));
+      zero_fill(e, S);
+      PAR_FOR
       for (int j = 0; j < c->ny; ++j)
         for (int i = 0; i < c->nx; ++i)
           if (i % 3 == a && j % 3 == b) AT(c, e, i, j) = 1.0;
       orc_poisson(c, caps, e, o);
+      PAR_FOR
       for (int j = 0; j < c->ny; ++j)
         for (int i = 0; i < c->nx; ++i)
           if (i % 3 == a && j % 3 == b) AT(c, diag, i, j) = AT(c, o, i, j);
@@ -954,25 +1013,41 @@ static void op_apply(const pcg_ctx* k, const double* x, double* y) {
 
 static size_t op_n(const pcg_ctx* k) { return (k->system == 0 ? 1 : 2) * SIZE(k->c); }
 
-static double dot(const double* a, const double* b, size_t n) {
+/* sum of a[i] * b[i] (b NULL: of a[i]) over the i with mask[i] != 0 (mask NULL: all), in
+ * the fixed blocked order */
+static double block_sum(const double* a, const double* b, const double* mask, size_t n) {
+  size_t nb = (n + DOT_BLOCK - 1) / DOT_BLOCK;
+  double* part = malloc((nb ? nb : 1) * sizeof(double));
+  PAR_FOR
+  for (size_t q = 0; q < nb; ++q) {
+    size_t e = (q + 1) * DOT_BLOCK < n ? (q + 1) * DOT_BLOCK : n;
+    double s = 0.0;
+    for (size_t i = q * DOT_BLOCK; i < e; ++i)
+      if (!mask || mask[i] != 0.0) s += b ? a[i] * b[i] : a[i];
+    part[q] = s;
+  }
   double s = 0.0;
-  for (size_t i = 0; i < n; ++i) s += a[i] * b[i];
+  for (size_t q = 0; q < nb; ++q) s += part[q];
+  free(part);
   return s;
 }
+
+static double dot(const double* a, const double* b, size_t n) { return block_sum(a, b, NULL, n); }
 
 static void zero_mean(const pcg_ctx* k, double* x) {
   if (!k->mask) return;
   size_t n = op_n(k);
-  double s = 0.0, m = 0.0;
-  for (size_t i = 0; i < n; ++i) if (k->mask[i] != 0.0) { s += x[i]; m += 1.0; }
+  double s = block_sum(x, NULL, k->mask, n), m = block_sum(k->mask, NULL, k->mask, n);
   if (m == 0.0) return;
   s /= m;
+  PAR_FOR
   for (size_t i = 0; i < n; ++i) if (k->mask[i] != 0.0) x[i] -= s;
 }
 
 static void precondition(const pcg_ctx* k, const double* r, double* z, double* w1, double* w2, double* w3) {
   size_t n = op_n(k);
   if (k->precond == 0 || k->system != 0) {
+    PAR_FOR
     for (size_t i = 0; i < n; ++i) z[i] = k->diag[i] != 0.0 ? r[i] / k->diag[i] : 0.0;
   } else {
     /* Chebyshev iteration for K z = r from z = 0, Jacobi-scaled, eigenvalue interval
@@ -980,6 +1055,7 @@ static void precondition(const pcg_ctx* k, const double* r, double* z, double* w
     double b = 2.0, a = b / 30.0;
     double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
     double rho_prev = 1.0 / sigma;
+    PAR_FOR
     for (size_t i = 0; i < n; ++i) {
       double s = k->diag[i] != 0.0 ? r[i] / k->diag[i] : 0.0;
       w1[i] = s / theta;
@@ -988,6 +1064,7 @@ static void precondition(const pcg_ctx* k, const double* r, double* z, double* w
     for (int it = 1; it < k->cheb_degree; ++it) {
       op_apply(k, z, w3);
       double rho = 1.0 / (2.0 * sigma - rho_prev);
+      PAR_FOR
       for (size_t i = 0; i < n; ++i) {
         w2[i] = r[i] - w3[i];
         double s = k->diag[i] != 0.0 ? w2[i] / k->diag[i] : 0.0;
@@ -1021,6 +1098,7 @@ static int pcg(const pcg_ctx* k, const double* b, double* x, double tol, int max
   }
   zero_mean(k, x);
   op_apply(k, x, q);
+  PAR_FOR
   for (size_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
   precondition(k, r, z, w1, w2, w3);
   memcpy(p, z, n * sizeof(double));
@@ -1032,6 +1110,7 @@ static int pcg(const pcg_ctx* k, const double* b, double* x, double tol, int max
     if (it >= max_iter) break;
     op_apply(k, p, q);
     double alpha = rz / dot(p, q, n);
+    PAR_FOR
     for (size_t i = 0; i < n; ++i) {
       x[i] += alpha * p[i];
       r[i] -= alpha * q[i];
@@ -1040,6 +1119,7 @@ static int pcg(const pcg_ctx* k, const double* b, double* x, double tol, int max
     double rz_new = dot(r, z, n);
     double beta = rz_new / rz;
     rz = rz_new;
+    PAR_FOR
     for (size_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     ++it;
   }
@@ -1112,6 +1192,7 @@ int orc_solve_helmholtz(const orc_case* c, const double* caps, const double* rhs
   double* b = malloc(2 * S * sizeof(double));
   double* x = malloc(2 * S * sizeof(double));
   orc_helmholtz_diag(c, caps, diag, diag + S);
+  PAR_FOR
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
       size_t k = (size_t)(j + 1) * PITCH(c) + (size_t)(i + 1);
@@ -1318,12 +1399,14 @@ void orc_predictor_rhs_gd(const orc_case* c, const double* caps, double* u, doub
     visc_bc(c, caps, zu, zv, Dx, Dy, lu, lv);
     free(zu); free(zv);
   }
+  PAR_FOR
   for (size_t k = 0; k < S; ++k) {
     ru[k] = (rho / dt) * Vu[k] * u[k] - 1.5 * rho * cnu[k] + 0.5 * rho * pu[k] - gu[k] + mu * vu[k] + mu * lu[k];
     rv[k] = (rho / dt) * Vv[k] * v[k] - 1.5 * rho * cnv[k] + 0.5 * rho * pv[k] - gv[k] + mu * vv[k] + mu * lv[k];
     if (gx) ru[k] += rho * Vu[k] * gx[k];
     if (gy) rv[k] += rho * Vv[k] * gy[k];
   }
+  PAR_FOR
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
       if (role_u(c, caps, i, j) != 3) AT(c, ru, i, j) = 0.0;
@@ -1373,6 +1456,7 @@ int orc_step_gd(const orc_case* c, const double* caps, double* u, double* v, dou
   int ok_h = orc_solve_helmholtz(c, caps, ru, rv, xu, xv, c->tol_h, c->max_iter_h, &st->iters_h, &st->res_h);
   /* U*: unknowns from the solve, Dirichlet faces keep their values, inactive faces (no fluid in
    * their control volume) the body's velocity D (0 for a no-slip body) */
+  PAR_FOR
   for (int j = -1; j <= c->ny + 1; ++j)
     for (int i = -1; i <= c->nx + 1; ++i) {
       size_t k = (size_t)(j + 1) * PITCH(c) + (size_t)(i + 1);
@@ -1391,6 +1475,7 @@ int orc_step_gd(const orc_case* c, const double* caps, double* u, double* v, dou
   free(rhs);
   /* projection */
   orc_pres_bc(c, caps, phi, gu, gv);
+  PAR_FOR
   for (size_t k = 0; k < S; ++k) {
     u[k] -= (dt / rho) * winv(c, Vu[k]) * gu[k];
     v[k] -= (dt / rho) * winv(c, Vv[k]) * gv[k];
@@ -1398,6 +1483,7 @@ int orc_step_gd(const orc_case* c, const double* caps, double* u, double* v, dou
   fill_bc(c, u, v, 1.0);
   /* pressure update: -cont(M^-1 pres Phi, 0) = K Phi on active cells */
   orc_poisson(c, caps, phi, kp);
+  PAR_FOR
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i < c->nx; ++i)
       if (cell_active(c, caps, i, j)) {
