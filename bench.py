@@ -224,6 +224,48 @@ def oracle_steps(case, steps, threads, warmup=0):
     return dict(threads=used, seconds=secs, iters_p=iters)
 
 
+FIELDS = (("u", 0), ("v", 1), ("p", 2))  # ccm.CCM_F_U, CCM_F_V, CCM_F_P
+
+
+def gpu_state(g):
+    """A case's whole state (U, V, P, Phi, conv^{n-1}, step count) in the oracle's layout."""
+    from paper_2211_10698_gb300 import ccm
+
+    get = g.get_field
+    return dict(u=get(ccm.CCM_F_U).copy(), v=get(ccm.CCM_F_V).copy(), p=get(ccm.CCM_F_P).copy(),
+                phi=get(ccm.CCM_F_PHI).copy(), cu=get(ccm.CCM_F_CONV_U).copy(), cv=get(ccm.CCM_F_CONV_V).copy(),
+                n=int(get(ccm.CCM_F_STEP)[0, 0]))
+
+
+def gpu_next_step(g):
+    """The state, one more step of the case on the GPU (its own settings) and that step's u, v, P."""
+    state = gpu_state(g)
+    g.step(1)
+    return state, {name: g.get_field(f).copy() for name, f in FIELDS}
+
+
+def oracle_step_from(case, state, threads):
+    """One whole oracle step from a given state, timed; returns the timing record and u, v, P."""
+    import numpy as np
+
+    import oracle
+
+    used = oracle.set_threads(threads)
+    o = oracle.Oracle(case)
+    st = {k: (np.array(v, dtype=np.float64, order="C") if isinstance(v, np.ndarray) else v) for k, v in state.items()}
+    t0 = time.perf_counter()
+    hist, _ = o.step(st, 1)
+    sec = time.perf_counter() - t0
+    return dict(threads=used, seconds=[sec], iters_p=[hist[0]["iters_p"]]), {name: st[name] for name, _ in FIELDS}
+
+
+def _rel_errors(got, want):
+    import numpy as np
+
+    return {name: float(np.linalg.norm(got[name] - want[name]) / max(np.linalg.norm(want[name]), 1e-300))
+            for name, _ in FIELDS}
+
+
 def _window_summary(case, w):
     t = sum(w["seconds"])
     return dict(cells=case.cells, steps=len(w["seconds"]), threads=w["threads"], seconds=t,
@@ -231,27 +273,44 @@ def _window_summary(case, w):
                 poisson_iters_per_step=sum(w["iters_p"]) / len(w["iters_p"]))
 
 
-def cpu_baseline(case, full=False):
-    """The FP64 oracle timed on this machine's cores, whole steps only:
-    - the headline workload: step 1 of its seeded run, one whole step on all cores (the value);
-    - the 128x64 Re 40 cylinder: all 100 steps, on all cores and on one thread;
-    - with ``full``, also the headline step on one thread (a minute or more)."""
+def cpu_baseline(case, head_next, c3_next=None, full=False):
+    """The FP64 oracle timed on this machine's cores, whole steps only, each solve to its
+    configured tolerance:
+    - the headline workload: one whole step from the GPU run's state after its timed steps, on
+      all cores (the value); the GPU's own step from the same state gives the error of each
+      field against the oracle;
+    - the 2048x1024 airfoil (``c3_next``): likewise one step from the GPU's state after its
+      timed window, the GPU step in mixed precision;
+    - the 128x64 Re 40 cylinder: all 100 steps from the seeded start, on all cores and on one
+      thread;
+    - with ``full``, also a headline step on one thread (a minute or more)."""
     from paper_2211_10698_gb300 import inputs
 
     nproc = os.cpu_count()
-    head = oracle_steps(case, 1, 0)
+    state, gnext = head_next
+    w, onext = oracle_step_from(case, state, 0)
+    windows = {f"{WORKLOAD} all cores": dict(_window_summary(case, w), from_step=state["n"])}
+    parity = {WORKLOAD: dict(step=state["n"] + 1, precision="fp64", rel_l2=_rel_errors(gnext, onext))}
+    if c3_next is not None:
+        c3case, c3state, c3gpu = c3_next
+        w3, o3 = oracle_step_from(c3case, c3state, 0)
+        windows[f"{c3case.name} all cores"] = dict(_window_summary(c3case, w3), from_step=c3state["n"])
+        parity[c3case.name] = dict(step=c3state["n"] + 1, precision="mixed on the GPU, FP64 oracle",
+                                   rel_l2=_rel_errors(c3gpu, o3))
     c1 = inputs.cylinder_re40_128x64()
-    windows = {f"{WORKLOAD} all cores": _window_summary(case, head),
-               f"{c1.name} all cores": _window_summary(c1, oracle_steps(c1, c1.steps, 0)),
-               f"{c1.name} 1 thread": _window_summary(c1, oracle_steps(c1, c1.steps, 1))}
+    windows[f"{c1.name} all cores"] = _window_summary(c1, oracle_steps(c1, c1.steps, 0))
+    windows[f"{c1.name} 1 thread"] = _window_summary(c1, oracle_steps(c1, c1.steps, 1))
     if full:
-        windows[f"{WORKLOAD} 1 thread"] = _window_summary(case, oracle_steps(case, 1, 1))
+        w1, _ = oracle_step_from(case, state, 1)
+        windows[f"{WORKLOAD} 1 thread"] = dict(_window_summary(case, w1), from_step=state["n"])
     h = windows[f"{WORKLOAD} all cores"]
     return dict(value=h["value"], unit=UNIT, cores=h["threads"], kind="oracle",
-                sample=(f"{WORKLOAD}: step 1 of the seeded run, one whole oracle step (every solve to its 1e-10 "
-                        f"tolerance, {h['poisson_iters_per_step']:.0f} Poisson iterations) on {h['threads']} "
-                        f"threads, {h['seconds']:.1f} s"),
-                nproc=nproc, cpu_model=_cpu_model(), windows=windows)
+                sample=(f"{WORKLOAD}: one whole oracle step from the GPU run's state at step {state['n']} (every "
+                        f"solve to its 1e-10 tolerance, {h['poisson_iters_per_step']:.0f} Poisson iterations) on "
+                        f"{h['threads']} threads, {h['seconds']:.1f} s"),
+                nproc=nproc, cpu_model=_cpu_model(), windows=windows,
+                parity=dict(note="relative L2 error of the GPU's step against the oracle's step from the same "
+                                 "state, both at the configured tolerances", **parity))
 
 
 def run_reference(args):
@@ -296,7 +355,7 @@ def _timed_steps(torch, stream, step_fn, steps, flush):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def measure_mixed(torch, stream, flush, steps=6, warmup=2):
+def measure_mixed(torch, stream, flush, steps=20, warmup=5):
     """The headline workload with the mixed-precision Poisson solve (FP32 CG with FP64
     residual replacements to the same 1e-10): same accuracy target, different arithmetic."""
     import numpy as np
@@ -335,7 +394,9 @@ def measure_mixed(torch, stream, flush, steps=6, warmup=2):
                 rel_l2_vs_fp64_path=err)
 
 
-def _measure_case(torch, stream, flush, case, steps, warmup, precision=None, precond=None):
+def _measure_case(torch, stream, flush, case, steps, warmup, precision=None, precond=None, keep=None):
+    """Steps of one case timed with CUDA events; with ``keep`` (a dict), keep["next"] receives
+    the state after the timed steps and the GPU's next step from it."""
     from paper_2211_10698_gb300 import ccm
 
     g = ccm.Case(case, precision=precision, precond=precond, stream=stream.cuda_stream,
@@ -345,6 +406,8 @@ def _measure_case(torch, stream, flush, case, steps, warmup, precision=None, pre
     ms = _timed_steps(torch, stream, lambda: g.step_async(1), steps, flush)
     st = g.read_stats(allow_not_converged=True)
     plan = _plan_dict(g)
+    if keep is not None:
+        keep["next"] = gpu_next_step(g)
     g.close()
     t = sum(ms)
     return dict(value=case.cells * steps / (t * 1e-3), unit=UNIT, ms_per_step=t / steps, steps=steps,
@@ -364,7 +427,7 @@ def _plan_dict(g):
     return dict(kind="built-in")
 
 
-def measure_configs(torch, stream, flush, only=None):
+def measure_configs(torch, stream, flush, only=None, keep=None):
     """The other single-case configurations: the 128x64 cylinder at Re 40 (FP64), and the
     2048x1024 NACA0012 at Re 1000 in the mixed setting, with its configured Chebyshev
     preconditioner and with Jacobi (both one-launch solves).  `only`: names to run."""
@@ -381,7 +444,7 @@ def measure_configs(torch, stream, flush, only=None):
     if want("naca0012_re1000_2048x1024"):
         out["naca0012_re1000_2048x1024"] = dict(
             precision="mixed", precond=f"chebyshev degree {c3.cheb_degree}",
-            **_measure_case(torch, stream, flush, c3, 2, 1))
+            **_measure_case(torch, stream, flush, c3, 10, 1, keep=keep))
     if want("naca0012_re1000_2048x1024_jacobi"):
         out["naca0012_re1000_2048x1024_jacobi"] = dict(
             precision="mixed", precond="jacobi (one launch, FP64 residual replacements)",
@@ -389,7 +452,7 @@ def measure_configs(torch, stream, flush, only=None):
     return out
 
 
-def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=4):
+def measure_batch(torch, stream, flush, ncases=64, steps=10, warmup=4):
     """The 64-case batch (cylinders and NACA00tt sections, 256..1024 cells wide, mixed
     precision, Chebyshev degree 4 as configured): all cases advance together, one batched
     Poisson solve per step.  The warm-up covers the cases' first step and the three steps that
@@ -408,6 +471,7 @@ def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=4):
     cells = sum(c.cells for c in specs)
     t = sum(ms)
     its = [st["last_iters_p"] for st in last[-1]]
+    its_window = [sum(st["last_iters_p"] for st in sts) / len(sts) for sts in last]
     conv = all(st["converged"] for sts in last for st in sts)
     graph_steps = b.graph_steps()
     split_a, split_tuned = b.split()
@@ -418,6 +482,7 @@ def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=4):
     return dict(workload=f"batch of {ncases} cases ({cells} cells)", precision="mixed", cells=cells,
                 value=cells * steps / (t * 1e-3), unit=UNIT, ms_per_step=t / steps, steps=steps,
                 precond=", ".join(pcs), poisson_iters_last_step={"max": max(its), "mean": sum(its) / len(its)},
+                poisson_iters_mean_per_step=its_window, window=f"steps {warmup + 1}..{warmup + steps} of each case",
                 converged=conv, graph_steps=graph_steps,
                 poisson_split=dict(weights=f"cells x nx^{split_a:g}", tuned=split_tuned),
                 note="every stage of a step is one launch for all cases: explicit stages, the Helmholtz "
@@ -425,7 +490,7 @@ def measure_batch(torch, stream, flush, ncases=64, steps=2, warmup=4):
                      "CUDA graphs")
 
 
-def measure_serving(precision, nreq=16, step_div=200, budget_gb=150.0, max_batch=64, chunk=5):
+def measure_serving(precision, nreq=32, step_div=100, budget_gb=150.0, max_batch=64, chunk=5):
     """A bounded window of the request stream (exponential arrivals at 20/s; cylinders and
     NACA00tt sections 128..2048 cells wide; the first ``nreq`` requests, their step counts
     divided by ``step_div``): requests are submitted when their arrival time has passed and the
@@ -563,7 +628,9 @@ def run_ours(args):
                     avg_launch_ms=avg_ms, iters_per_launch=iters_per_launch,
                     us_per_iteration=1e3 * avg_ms / max(iters_per_launch, 1), peak_kind=peak_kind)
 
+    head_next = gpu_next_step(g) if rank == 0 and world == 1 and not args.no_cpu_baseline else None
     extras = {}
+    c3_keep = {}
     want = set() if args.no_extras else set(args.extras.split(","))
     if rank == 0 and "mixed" in want:
         try:
@@ -573,7 +640,7 @@ def run_ours(args):
     if rank == 0 and "configs" in want:
         try:
             extras["configs"] = measure_configs(torch, stream, flush,
-                                                set(filter(None, args.configs.split(","))))
+                                                set(filter(None, args.configs.split(","))), keep=c3_keep)
         except Exception as e:
             extras["configs"] = {"error": str(e)}
     if rank == 0 and "batched" in want:
@@ -584,7 +651,7 @@ def run_ours(args):
     if rank == 0 and "serving" in want:
         try:
             torch.cuda.synchronize()
-            sv = dict(workload=f"request stream window: first 16 requests at 20/s, steps/200, "
+            sv = dict(workload=f"request stream window: first 32 requests at 20/s, steps/100, "
                                f"budget 150 GB, batches of up to 64, chunks of 5 steps")
             sv["mixed"] = measure_serving("mixed")
             sv["fp64"] = measure_serving("fp64")
@@ -594,7 +661,10 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(case, full=args.cpu_baseline_full)
+        c3_next = None
+        if "next" in c3_keep:
+            c3_next = (inputs.naca0012_re1000_2048x1024(),) + tuple(c3_keep["next"])
+        cpu = cpu_baseline(case, head_next, c3_next, full=args.cpu_baseline_full)
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
