@@ -65,6 +65,9 @@ def _args():
                          "comma-separated values of ccm_launch_plan), e.g. for a profiler run")
     ap.add_argument("--configs", default="",
                     help="comma-separated names of the single-case configurations to run (default: all)")
+    ap.add_argument("--guess-history", type=int, default=0,
+                    help="headline case: initial guess of each Poisson solve by projection onto the last L "
+                         "solutions (0: the previous Phi)")
     ap.add_argument("--batch-cases", type=int, default=64,
                     help="cases of the batched measurement (the first N of the seeded 64-case mix)")
     return ap.parse_args()
@@ -355,15 +358,18 @@ def _timed_steps(torch, stream, step_fn, steps, flush):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def measure_mixed(torch, stream, flush, steps=20, warmup=5):
-    """The headline workload with the mixed-precision Poisson solve (FP32 CG with FP64
-    residual replacements to the same 1e-10): same accuracy target, different arithmetic."""
+def measure_variant(torch, stream, flush, precision="mixed", precond="jacobi", degree=3, guess=0, steps=20,
+                    warmup=5):
+    """The headline workload with another solver setting at the same accuracy target (every
+    Poisson solve to a relative residual of 1e-10): the mixed-precision solve (FP32 CG with
+    FP64 residual replacements), the Chebyshev preconditioner, or the projected initial guess.
+    Its fields after the steps are compared with the plain FP64 Jacobi path's."""
     import numpy as np
 
     from paper_2211_10698_gb300 import ccm, inputs
 
     case = inputs.cylinder_re100_1024x512()
-    case.precision = "mixed"
+    case.precision, case.precond, case.cheb_degree, case.guess_history = precision, precond, degree, guess
     g = ccm.Case(case, stream=stream.cuda_stream, allocator=ccm.TorchAllocator())
     pu, pv = inputs.perturbation(case)
     g.set_field(ccm.CCM_F_U, g.get_field(ccm.CCM_F_U) + pu)
@@ -373,10 +379,11 @@ def measure_mixed(torch, stream, flush, steps=20, warmup=5):
     ms = _timed_steps(torch, stream, lambda: g.step_async(1), steps, flush)
     st = g.read_stats()
     kt = g.kernel_timing()
+    plan = _plan_dict(g, precision)
     fields = [g.get_field(f) for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P)]
     g.close()
-    # the same steps with the FP64 path (parity-tested against the FP64 oracle): field errors
-    ref = ccm.Case(case, precision="fp64", stream=stream.cuda_stream, allocator=ccm.TorchAllocator())
+    ref_case = inputs.cylinder_re100_1024x512()
+    ref = ccm.Case(ref_case, stream=stream.cuda_stream, allocator=ccm.TorchAllocator())
     ref.set_field(ccm.CCM_F_U, ref.get_field(ccm.CCM_F_U) + pu)
     ref.set_field(ccm.CCM_F_V, ref.get_field(ccm.CCM_F_V) + pv)
     ref.step(warmup + steps)
@@ -386,12 +393,17 @@ def measure_mixed(torch, stream, flush, steps=20, warmup=5):
         err[name] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
     ref.close()
     t = sum(ms)
-    return dict(workload=WORKLOAD,
-                precision="mixed (FP32 CG on the Jacobi-scaled system, FP64 residual replacements to 1e-10)",
+    desc = ("mixed (FP32 CG on the Jacobi-scaled system, FP64 residual replacements to 1e-10)"
+            if precision == "mixed" else "fp64")
+    return dict(workload=WORKLOAD, precision=desc,
+                precond=precond + (f" degree {degree}" if precond == "chebyshev" else ""),
+                initial_guess=(f"projection onto the last {guess} solutions" if guess else "previous Phi"),
                 value=case.cells * steps / (t * 1e-3), unit=UNIT, ms_per_step=t / steps, steps=steps,
-                fp32_iters_per_step=st["iters_p"] / steps, final_rel_res=st["last_res_p"],
-                poisson_ms_per_step=kt["poisson_ms"] / steps, max_div=st["max_div"], converged=bool(st["converged"]),
-                rel_l2_vs_fp64_path=err)
+                poisson_iters_per_step=st["iters_p"] / steps, final_rel_res=st["last_res_p"],
+                poisson_ms_per_step=kt["poisson_ms"] / steps,
+                us_per_iteration=1e3 * kt["poisson_ms"] / max(kt["poisson_iters"], 1),
+                max_div=st["max_div"], converged=bool(st["converged"]), launch_plan=plan,
+                rel_l2_vs_plain_fp64_path=err)
 
 
 def _measure_case(torch, stream, flush, case, steps, warmup, precision=None, precond=None, keep=None):
@@ -405,7 +417,7 @@ def _measure_case(torch, stream, flush, case, steps, warmup, precision=None, pre
     g.read_stats()
     ms = _timed_steps(torch, stream, lambda: g.step_async(1), steps, flush)
     st = g.read_stats(allow_not_converged=True)
-    plan = _plan_dict(g)
+    plan = _plan_dict(g, precision or case.precision)
     if keep is not None:
         keep["next"] = gpu_next_step(g)
     g.close()
@@ -415,11 +427,14 @@ def _measure_case(torch, stream, flush, case, steps, warmup, precision=None, pre
                 last_rel_res_p=st["last_res_p"], converged=bool(st["converged"]), launch_plan=plan)
 
 
-def _plan_dict(g):
-    """The launch shape the set-up autotuner chose for the case's Poisson solve."""
+def _plan_dict(g, precision="fp64"):
+    """The launch shape the set-up autotuner chose for the case's Poisson solve (a mixed case's
+    tiles are those of the solve with one barrier per iteration)."""
     tx, ty, nbx, ntiles, mb, cl, res = g.launch_plan()
     if cl:
         return dict(kind="cluster", ctas=cl)
+    if tx and precision == "mixed":
+        return dict(kind="tiles, one barrier per iteration", tile=[tx, ty], tiles=ntiles)
     if tx:
         return dict(kind="tiles", tile=[tx, ty], tiles=ntiles, resident=bool(res))
     if mb:
@@ -546,6 +561,7 @@ def run_ours(args):
 
         dist.init_process_group("nccl")
     case = inputs.cylinder_re100_1024x512()
+    case.guess_history = args.guess_history
     stream = torch.cuda.current_stream()
     if args.launch_plan:
         case.autotune = 0
@@ -633,10 +649,18 @@ def run_ours(args):
     c3_keep = {}
     want = set() if args.no_extras else set(args.extras.split(","))
     if rank == 0 and "mixed" in want:
-        try:
-            extras["mixed_same_accuracy"] = measure_mixed(torch, stream, flush)
-        except Exception as e:  # report, do not lose the headline line
-            extras["mixed_same_accuracy"] = {"error": str(e)}
+        variants = {"mixed_same_accuracy": dict(precision="mixed", precond="jacobi"),
+                    "mixed_chebyshev": dict(precision="mixed", precond="chebyshev", degree=3),
+                    "mixed_chebyshev_projected": dict(precision="mixed", precond="chebyshev", degree=3, guess=16)}
+        if args.guess_history:
+            variants["fp64_previous_phi"] = dict(precision="fp64", precond="jacobi", guess=0)
+        else:
+            variants["fp64_projected_guess"] = dict(precision="fp64", precond="jacobi", guess=16)
+        for name, kw in variants.items():
+            try:
+                extras[name] = measure_variant(torch, stream, flush, **kw)
+            except Exception as e:  # report, do not lose the headline line
+                extras[name] = {"error": str(e)}
     if rank == 0 and "configs" in want:
         try:
             extras["configs"] = measure_configs(torch, stream, flush,
@@ -671,6 +695,8 @@ def run_ours(args):
                     dtype="f64", data="synthetic",
                     config=dict(workload=WORKLOAD, nx=case.nx, ny=case.ny, cells=case.cells, precision="fp64",
                                 precond="jacobi", tol_p=case.tol_p, tol_h=case.tol_h, parallelism=f"replicas{world}",
+                                initial_guess=(f"projection onto the last {case.guess_history} solutions"
+                                               if case.guess_history else "previous Phi"),
                                 l2="flushed between timed steps (256 MiB write, outside the step events)",
                                 poisson_iters_per_step=iters_p, helmholtz_iters_per_step=iters_h,
                                 launch_plan=launch_plan),

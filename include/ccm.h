@@ -15,8 +15,8 @@
  *  - Every field crosses the ABI as a float64 array of (ny+3) x (nx+3) elements, x
  *    fastest ("padded layout"): element (j+1)*(nx+3) + (i+1) holds index (i, j), i in
  *    [-1, nx+1], j in [-1, ny+1].  Index (i, j) names the pressure cell (i, j), the x-face
- *    at x0 + i*hx (u), the y-face at y0 + j*hy (v) or the node (x0 + i*hx, y0 + j*hy),
- *    depending on the field.
+ *    at x_i = x0 + i*hx (u), the y-face at y_j = y0 + j*hy (v) or the node (x_i, y_j),
+ *    depending on the field (on a stretched mesh x_i and y_j are the given abscissas).
  *  - Box sides are W=0, E=1, S=2, N=3.  A DIRICHLET side prescribes the normal velocity
  *    component bc_un and the tangential component bc_ut (an inflow is a Dirichlet side);
  *    an OUTFLOW side has zero-gradient velocity and zero pressure (Sec. 5.1).
@@ -91,6 +91,21 @@ typedef struct {
   ccm_free_fn free;
   void* alloc_ctx;
   void* stream;               /* cudaStream_t for all work of the case, NULL = default */
+  /* Stretched rectilinear mesh (Sec. 3.1: arbitrary abscissas), host arrays read during
+   * ccm_create_case only: xf[0..nx] and yf[0..ny] the face abscissas, strictly increasing,
+   * xf[0] == x0, xf[nx] == x1 (likewise y).  NULL (both) for the uniform spacing.  The
+   * staggered grids of Sec. 3.4 have their cells centred on the faces, so the u-grid's lines
+   * are the centres of the pressure cells; beyond the box the spacing mirrors the spacing
+   * inside it.  dt is the caller's (the smallest cell sets the CFL number). */
+  const double* xf;
+  const double* yf;
+  /* Initial guess of each step's Poisson solve: 0 (default) the previous step's Phi; L in
+   * 1..32 the projection of the new solution onto the span of the last L solutions in the
+   * inner product of K (Fischer 1998), which lowers the iteration count of a smoothly
+   * evolving flow.  Same stopping test either way.  Needs 2 L padded FP64 arrays more (the
+   * case's allocator).  Setting a state field (ccm_set_field) clears the history; batched
+   * steps (ccm_batch_*) do not use it; a singular (all-wall) system ignores it. */
+  int guess_history;
 } ccm_config;
 
 /* Immersed body given by a level set (Sec. 3.1).  Points on the boundary count as solid. */

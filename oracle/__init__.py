@@ -57,7 +57,8 @@ class OrcCase(ctypes.Structure):
                 ("hp_nx", c_double), ("hp_ny", c_double), ("hp_off", c_double),
                 ("literal_offdiag", c_int), ("pressure_update", c_int), ("precond", c_int), ("cheb_degree", c_int),
                 ("tol_p", c_double), ("tol_h", c_double),
-                ("max_iter_p", c_int), ("max_iter_h", c_int)]
+                ("max_iter_p", c_int), ("max_iter_h", c_int),
+                ("xf", POINTER(c_double)), ("yf", POINTER(c_double))]
 
 
 class OrcStats(ctypes.Structure):
@@ -151,6 +152,9 @@ def case_struct(case, precond=None) -> OrcCase:
     s.cheb_degree = case.cheb_degree
     s.tol_p, s.tol_h = case.tol_p, case.tol_h
     s.max_iter_p, s.max_iter_h = case.max_iter_p, case.max_iter_h
+    # stretched mesh: face abscissas (the arrays are kept alive by the caller, see Oracle)
+    s.xf = _p(case.faces_x()) if case.stretched else None
+    s.yf = _p(case.faces_y()) if case.stretched else None
     return s
 
 
@@ -164,7 +168,10 @@ class Oracle:
     def __init__(self, case, precond=None):
         self.lib = _load()
         self.case = case
+        self._faces = (case.faces_x(), case.faces_y()) if case.stretched else None
         self.s = case_struct(case, precond)
+        if self._faces is not None:
+            self.s.xf, self.s.yf = _p(self._faces[0]), _p(self._faces[1])
         self.shape = case.shape
         self.S = case.shape[0] * case.shape[1]
         self.caps = np.zeros((3, 9) + self.shape)

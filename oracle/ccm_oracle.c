@@ -50,7 +50,7 @@ typedef struct {
   int nx, ny;
   double x0, y0, hx, hy;
   double rho, mu, dt;
-  int bc_type[4];          /* W, E, S, N: 0 Dirichlet, 1 outflow */
+  int bc_type[4];          /* W, E, S, N: 0 Dirichlet, 1 outflow, 2 periodic (W with E, S with N) */
   double bc_un[4];         /* Dirichlet normal velocity component (u on W/E, v on S/N) */
   double bc_ut[4];         /* Dirichlet tangential component (v on W/E, u on S/N) */
   int geom_kind;           /* 0 none, 1 circle, 2 NACA 00tt, 3 half plane */
@@ -60,11 +60,16 @@ typedef struct {
   double hp_nx, hp_ny, hp_off;
   int literal_offdiag;     /* 1: Eq. offdiag with separate W^xy, W^yx */
   int pressure_update;     /* volume dividing the viscous correction of Eq. pm_update:
-                              0 the full cell hx*hy, 1 the cell's fluid volume V_p, 2 none */
+                              0 the full cell's area, 1 the cell's fluid volume V_p, 2 none */
   int precond;             /* 0 Jacobi, 1 Chebyshev */
   int cheb_degree;
   double tol_p, tol_h;
   int max_iter_p, max_iter_h;
+  /* Rectilinear, possibly stretched mesh (Sec. 3.1): the face abscissas x_0 = x0 < x_1 < ...
+   * < x_nx and y_0 < ... < y_ny, or NULL for the uniform spacing hx, hy.  With a stretched
+   * mesh hx and hy hold the smallest spacing (used for thresholds only). */
+  const double* xf;
+  const double* yf;
 } orc_case;
 
 typedef struct {
@@ -79,6 +84,10 @@ enum { K_V = 0, K_X, K_Y, K_AX, K_AY, K_WX, K_WY, K_BX, K_BY };
 enum { W_SIDE = 0, E_SIDE = 1, S_SIDE = 2, N_SIDE = 3 };
 #define BC_DIR 0
 #define BC_OUT 1
+#define BC_PER 2
+/* periodic in x (W and E) or y (S and N): face nx is face 0 and cell -1 is cell nx-1 */
+#define PER_X(c) ((c)->bc_type[W_SIDE] == BC_PER)
+#define PER_Y(c) ((c)->bc_type[S_SIDE] == BC_PER)
 
 #define PITCH(c) ((c)->nx + 3)
 #define SIZE(c) ((size_t)((c)->nx + 3) * (size_t)((c)->ny + 3))
@@ -332,18 +341,49 @@ static void grid_offsets(const orc_case* c, int g, double* ox, double* oy) {
   *oy = (g == G_V) ? -0.5 * c->hy : 0.0;
 }
 
+/* Face abscissa f of a stretched mesh for f in [-n, 2n]: beyond the box the spacing mirrors
+ * the spacing inside it (x_{-k} = 2 x_0 - x_k), written as a sum and a difference so that no
+ * compiler contracts it into a fused multiply-add. */
+static double face_at(const double* a, int n, int f) {
+  if (f < 0) return (a[0] + a[0]) - a[-f];
+  if (f > n) return (a[n] + a[n]) - a[2 * n - f];
+  return a[f];
+}
+
 /* Grid line abscissas: one expression for every use, so that cells sharing an edge or a
- * corner see bitwise identical coordinates. */
-static double line_x(const orc_case* c, double ox, int i) { return c->x0 + ox + i * c->hx; }
-static double line_y(const orc_case* c, double oy, int j) { return c->y0 + oy + j * c->hy; }
+ * corner see bitwise identical coordinates.  Line i of the p- and v-grids in x is face x_i;
+ * the u-grid's cells are centred on the faces (Sec. 3.4), so its line i is the centre of
+ * p-cell i-1, (x_{i-1} + x_i) / 2 (on a uniform mesh, x0 + i hx - hx/2).  Likewise in y. */
+static double line_x(const orc_case* c, int g, int i) {
+  if (!c->xf) {
+    double ox, oy;
+    grid_offsets(c, g, &ox, &oy);
+    return c->x0 + ox + i * c->hx;
+  }
+  if (g == G_U) return 0.5 * (face_at(c->xf, c->nx, i - 1) + face_at(c->xf, c->nx, i));
+  return face_at(c->xf, c->nx, i);
+}
+static double line_y(const orc_case* c, int g, int j) {
+  if (!c->yf) {
+    double ox, oy;
+    grid_offsets(c, g, &ox, &oy);
+    return c->y0 + oy + j * c->hy;
+  }
+  if (g == G_V) return 0.5 * (face_at(c->yf, c->ny, j - 1) + face_at(c->yf, c->ny, j));
+  return face_at(c->yf, c->ny, j);
+}
+
+/* Area of p-cell (i, j). */
+static double cell_area(const orc_case* c, int i, int j) {
+  if (!c->xf && !c->yf) return c->hx * c->hy;
+  return (line_x(c, G_P, i + 1) - line_x(c, G_P, i)) * (line_y(c, G_P, j + 1) - line_y(c, G_P, j));
+}
 
 /* First-kind volume capacity and centroid of cell (i, j) of grid g (Eqs. volumefirstkind,
  * centroid).  An empty cell gets the cell centre as its centroid. */
 static void moments(const orc_case* c, int g, int i, int j, cell_moments* m) {
-  double ox, oy;
-  grid_offsets(c, g, &ox, &oy);
-  double xl = line_x(c, ox, i), xr = line_x(c, ox, i + 1);
-  double yb = line_y(c, oy, j), yt = line_y(c, oy, j + 1);
+  double xl = line_x(c, g, i), xr = line_x(c, g, i + 1);
+  double yb = line_y(c, g, j), yt = line_y(c, g, j + 1);
   build_cell(c, xl, xr, yb, yt, &m->geo);
   double V = 0.0, MX = 0.0, MY = 0.0;
   for (int k = 0; k < m->geo.npoly; ++k) {
@@ -699,17 +739,45 @@ static double epsV(const orc_case* c) { return 1e-12 * c->hx * c->hy; }
  * (no fluid in its control volume, held at zero), 3 unknown */
 static int role_u(const orc_case* c, const double* caps, int i, int j) {
   if (i < 0 || i > c->nx || j < 0 || j >= c->ny) return 0;
+  if (PER_X(c) && i == c->nx) return 0;  /* the image of face 0 */
   if (is_dir_u(c, i)) return 1;
   return AT(c, CAP(c, caps, G_U, K_V), i, j) > epsV(c) ? 3 : 2;
 }
 static int role_v(const orc_case* c, const double* caps, int i, int j) {
   if (i < 0 || i >= c->nx || j < 0 || j > c->ny) return 0;
+  if (PER_Y(c) && j == c->ny) return 0;
   if (is_dir_v(c, j)) return 1;
   return AT(c, CAP(c, caps, G_V, K_V), i, j) > epsV(c) ? 3 : 2;
 }
 
 int orc_role_u(const orc_case* c, const double* caps, int i, int j) { return role_u(c, caps, i, j); }
 int orc_role_v(const orc_case* c, const double* caps, int i, int j) { return role_v(c, caps, i, j); }
+
+/* Periodic sides: every position beyond the box takes the value of its image inside it,
+ * face nx that of face 0 (x first over all rows, then y over all columns, so that the corners
+ * are consistent). */
+static void wrap_faces(const orc_case* c, double* u, double* v) {
+  int nx = c->nx, ny = c->ny;
+  if (PER_X(c))
+    for (int j = -1; j <= ny + 1; ++j) {
+      if (u) { AT(c, u, -1, j) = AT(c, u, nx - 1, j); AT(c, u, nx, j) = AT(c, u, 0, j); AT(c, u, nx + 1, j) = AT(c, u, 1, j); }
+      if (v) { AT(c, v, -1, j) = AT(c, v, nx - 1, j); AT(c, v, nx, j) = AT(c, v, 0, j); AT(c, v, nx + 1, j) = AT(c, v, 1, j); }
+    }
+  if (PER_Y(c))
+    for (int i = -1; i <= nx + 1; ++i) {
+      if (u) { AT(c, u, i, -1) = AT(c, u, i, ny - 1); AT(c, u, i, ny) = AT(c, u, i, 0); AT(c, u, i, ny + 1) = AT(c, u, i, 1); }
+      if (v) { AT(c, v, i, -1) = AT(c, v, i, ny - 1); AT(c, v, i, ny) = AT(c, v, i, 0); AT(c, v, i, ny + 1) = AT(c, v, i, 1); }
+    }
+}
+
+/* Cell fields on periodic sides: cell -1 takes cell nx-1, cell nx cell 0 (and y likewise). */
+static void wrap_cells(const orc_case* c, double* p) {
+  int nx = c->nx, ny = c->ny;
+  if (PER_X(c))
+    for (int j = -1; j <= ny + 1; ++j) { AT(c, p, -1, j) = AT(c, p, nx - 1, j); AT(c, p, nx, j) = AT(c, p, 0, j); }
+  if (PER_Y(c))
+    for (int i = -1; i <= nx + 1; ++i) { AT(c, p, i, -1) = AT(c, p, i, ny - 1); AT(c, p, i, ny) = AT(c, p, i, 0); }
+}
 
 /* Set the Dirichlet box faces to their values (scaled by `scale`, 0 for the homogeneous
  * part) and fill the ghost layer. */
@@ -741,6 +809,7 @@ static void fill_bc(const orc_case* c, double* u, double* v, double scale) {
     AT(c, v, -1, j) = c->bc_type[W_SIDE] == BC_DIR ? 2.0 * scale * c->bc_ut[W_SIDE] - AT(c, v, 0, j) : AT(c, v, 0, j);
     AT(c, v, nx, j) = c->bc_type[E_SIDE] == BC_DIR ? 2.0 * scale * c->bc_ut[E_SIDE] - AT(c, v, nx - 1, j) : AT(c, v, nx - 1, j);
   }
+  wrap_faces(c, u, v);
 }
 
 void orc_fill_ghosts(const orc_case* c, double* u, double* v) { fill_bc(c, u, v, 1.0); }
@@ -824,6 +893,7 @@ void orc_pres_bc(const orc_case* c, const double* caps, const double* p_in, doub
   PAR_FOR
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i < c->nx; ++i) AT(c, p, i, j) = AT(c, p_in, i, j);
+  wrap_cells(c, p);  /* periodic sides: the image cells; otherwise zero (Dirichlet) */
   orc_pres(c, caps, p, ou, ov);
   PAR_FOR
   for (int j = -1; j <= c->ny + 1; ++j)
@@ -872,11 +942,13 @@ void orc_helmholtz(const orc_case* c, const double* caps, const double* u_in, co
 
 /* Poisson face coefficient A_f^2 / V_f of an unknown face, zero otherwise. */
 static double coef_u(const orc_case* c, const double* caps, int i, int j) {
+  if (PER_X(c) && i == c->nx) i = 0;
   if (role_u(c, caps, i, j) != 3) return 0.0;
   double A = AT(c, CAP(c, caps, G_P, K_AX), i, j);
   return A * A * winv(c, AT(c, CAP(c, caps, G_U, K_V), i, j));
 }
 static double coef_v(const orc_case* c, const double* caps, int i, int j) {
+  if (PER_Y(c) && j == c->ny) j = 0;
   if (role_v(c, caps, i, j) != 3) return 0.0;
   double A = AT(c, CAP(c, caps, G_P, K_AY), i, j);
   return A * A * winv(c, AT(c, CAP(c, caps, G_V, K_V), i, j));
@@ -918,6 +990,7 @@ void orc_poisson(const orc_case* c, const double* caps, const double* phi_in, do
     gu[k] *= winv(c, Vu[k]);
     gv[k] *= winv(c, Vv[k]);
   }
+  wrap_faces(c, gu, gv);  /* periodic: the flux through face nx is the flux through face 0 */
   orc_cont(c, caps, gu, gv, NULL, NULL, out);
   PAR_FOR
   for (int j = -1; j <= c->ny + 1; ++j)
@@ -1220,9 +1293,10 @@ double orc_kinetic(const orc_case* c, const double* caps, const double* u, const
   const double* Vu = CAP(c, caps, G_U, K_V);
   const double* Vv = CAP(c, caps, G_V, K_V);
   double k = 0.0;
+  int iu = PER_X(c) ? c->nx - 1 : c->nx, jv = PER_Y(c) ? c->ny - 1 : c->ny;  /* last face of its own */
   for (int j = 0; j < c->ny; ++j)
-    for (int i = 0; i <= c->nx; ++i) k += 0.5 * AT(c, Vu, i, j) * AT(c, u, i, j) * AT(c, u, i, j);
-  for (int j = 0; j <= c->ny; ++j)
+    for (int i = 0; i <= iu; ++i) k += 0.5 * AT(c, Vu, i, j) * AT(c, u, i, j) * AT(c, u, i, j);
+  for (int j = 0; j <= jv; ++j)
     for (int i = 0; i < c->nx; ++i) k += 0.5 * AT(c, Vv, i, j) * AT(c, v, i, j) * AT(c, v, i, j);
   return k;
 }
@@ -1255,9 +1329,10 @@ void orc_conservation(const orc_case* c, const double* caps, const double* u, co
   double m = 0.0, px = 0.0, py = 0.0;
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i < c->nx; ++i) m += AT(c, d, i, j);
+  int iu = PER_X(c) ? c->nx - 1 : c->nx, jv = PER_Y(c) ? c->ny - 1 : c->ny;
   for (int j = 0; j < c->ny; ++j)
-    for (int i = 0; i <= c->nx; ++i) px += AT(c, Vu, i, j) * AT(c, u, i, j);
-  for (int j = 0; j <= c->ny; ++j)
+    for (int i = 0; i <= iu; ++i) px += AT(c, Vu, i, j) * AT(c, u, i, j);
+  for (int j = 0; j <= jv; ++j)
     for (int i = 0; i < c->nx; ++i) py += AT(c, Vv, i, j) * AT(c, v, i, j);
   out[0] = m;
   out[1] = px;
@@ -1356,7 +1431,7 @@ void orc_init_velocity(const orc_case* c, const double* caps, double u0, double 
  *   U^{n+1} = U* - (dt/rho) M^-1 pres(Phi)
  *   P^{n+1/2} = P^{n-1/2} + Phi - (dt mu / 2 rho) V^-1 cont(M^-1 pres Phi, 0)
  * where V, the volume that turns the volume-integrated Laplacian into a point value, is the
- * full cell hx*hy by default (pressure_update = 0): dividing by the fluid volume V_p of a
+ * full cell's area by default (pressure_update = 0): dividing by the fluid volume V_p of a
  * small cut cell (pressure_update = 1) makes the correction an unbounded gain there and the
  * step unstable (the paper does not say which volume).
  * The first step uses conv^{-1} = conv^0; P^{-1/2} = 0; the body is fixed and no-slip
@@ -1487,7 +1562,7 @@ int orc_step_gd(const orc_case* c, const double* caps, double* u, double* v, dou
   for (int j = 0; j < c->ny; ++j)
     for (int i = 0; i < c->nx; ++i)
       if (cell_active(c, caps, i, j)) {
-        double iv = c->pressure_update == 0 ? 1.0 / (c->hx * c->hy)
+        double iv = c->pressure_update == 0 ? 1.0 / cell_area(c, i, j)
                     : c->pressure_update == 1 ? winv(c, AT(c, Vp, i, j)) : 0.0;
         AT(c, p, i, j) += AT(c, phi, i, j) + (dt * mu / (2.0 * rho)) * iv * AT(c, kp, i, j);
       }

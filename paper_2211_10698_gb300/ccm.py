@@ -44,7 +44,8 @@ class ccm_config(Structure):
                 ("max_iter_p", c_int), ("max_iter_h", c_int), ("literal_offdiag", c_int), ("pressure_update", c_int),
                 ("replace_drop", c_double), ("autotune", c_int),
                 ("alloc", ccm_alloc_fn), ("free", ccm_free_fn), ("alloc_ctx", c_void_p),
-                ("stream", c_void_p)]
+                ("stream", c_void_p), ("xf", POINTER(c_double)), ("yf", POINTER(c_double)),
+                ("guess_history", c_int)]
 
 
 class ccm_geometry(Structure):
@@ -169,7 +170,13 @@ def make_config(case, precision=None, precond=None, stream=None) -> ccm_config:
     cfg.pressure_update = int(getattr(case, "pressure_update", 0))
     cfg.replace_drop = float(getattr(case, "replace_drop", 0.0))
     cfg.autotune = int(getattr(case, "autotune", 0))
+    cfg.guess_history = int(getattr(case, "guess_history", 0))
     cfg.stream = stream
+    if getattr(case, "stretched", False):
+        # the arrays must outlive the call that reads them: kept on the structure
+        cfg._faces = (case.faces_x(), case.faces_y())
+        cfg.xf = cfg._faces[0].ctypes.data_as(_DP)
+        cfg.yf = cfg._faces[1].ctypes.data_as(_DP)
     return cfg
 
 

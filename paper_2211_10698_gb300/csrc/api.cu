@@ -108,6 +108,15 @@ struct ccm_case_s {
   // that skips its arrivals (failure-detection tests only; -1 otherwise)
   long long bar_budget = kBarrierBudget;
   int bar_absent = -1;
+  // stretched mesh: the face abscissas extended two faces beyond the box (host copies, and
+  // their device arrays in the slab); empty for a uniform spacing
+  std::vector<double> xfx, yfx;
+  double *xfd = nullptr, *yfd = nullptr;
+  // projected initial guess of the Poisson solve: K-orthonormal basis X (guess_history padded
+  // arrays), its images KX, scratch for the sums (one allocation, made at the first step);
+  // gnb vectors in use
+  double* gmem = nullptr;
+  int gnb = 0;
 };
 
 namespace {
@@ -168,6 +177,8 @@ void carve(ccm_case c, Carver& cv) {
   c->ds = cv.take<DevStats>(1);
   c->hs_u = cv.take<double>(N);
   c->hs_v = cv.take<double>(N);
+  c->xfd = cv.take<double>((size_t)c->g.nx + 7);
+  c->yfd = cv.take<double>((size_t)c->g.ny + 7);
   for (int q = 0; q < 18; ++q) c->hc.a[q] = cv.take<double>(N);
   c->hc_bad = cv.take<int>(4);
 }
@@ -369,13 +380,30 @@ void case_mixed_solve(ccm_case c, double* x, const double* b, MixedSolve* a) {
   a->blocks = c->tune.mixed_blocks;
 }
 
+// The one-barrier form of the same solve (pcg_mixed1.cu) on the case's FP32 work arrays.
+void case_mixed1_solve(ccm_case c, const MixedSolve& a, const TilePlan& tp, Mixed1Solve* f) {
+  *f = Mixed1Solve{};
+  f->m = a;
+  f->R[0] = c->fr; f->R[1] = c->fz;
+  f->W[0] = c->fq; f->W[1] = c->fz2;
+  f->S[0] = c->fp1; f->S[1] = c->fw1;
+  f->P = c->fp0; f->U = c->fb; f->E = c->fx;
+  f->TX = tp.TX; f->TY = tp.TY; f->nbx = tp.nbx; f->ntiles = tp.ntiles;
+}
+
 ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
   if (!c->zero_mean) {
     // one launch: FP32 CG on the scaled system with FP64 residual replacements (Jacobi or
-    // Chebyshev preconditioner)
+    // Chebyshev preconditioner), with one grid barrier per iteration when the tuner chose it
     MixedSolve a{};
     case_mixed_solve(c, x, b, &a);
-    CUDA_TRY(run_poisson_mixed(a, c->st));
+    if (c->tune.mixed1.TX > 0) {
+      Mixed1Solve f{};
+      case_mixed1_solve(c, a, c->tune.mixed1, &f);
+      CUDA_TRY(run_poisson_mixed1(f, c->st));
+    } else {
+      CUDA_TRY(run_poisson_mixed(a, c->st));
+    }
     c->launches += 1;
     return CCM_OK;
   }
@@ -457,18 +485,27 @@ ccm_status autotune_poisson(ccm_case c) {
   std::vector<float> ms;
   cudaError_t e = cudaSuccess;
   if (mixed) {
+    // block counts of the mixed solve, then tile plans of its one-barrier form
     const std::vector<int> cand = mixed_block_candidates(most);
+    const std::vector<TilePlan> cand1 = mixed1_plan_candidates(g.nx, g.ny, deg);
+    const int nm = (int)cand.size();
     MixedSolve a{};
     case_mixed_solve(c, x, b, &a);
     a.d.tol = 0.0;
     a.d.max_iter = kTuneIters;
-    e = time_launches((int)cand.size(), [&](int k) -> cudaError_t {
+    e = time_launches(nm + (int)cand1.size(), [&](int k) -> cudaError_t {
       cudaError_t me = cudaMemsetAsync(x, 0, bytes, st);
       if (me != cudaSuccess) return me;
+      if (k >= nm) {
+        Mixed1Solve f{};
+        case_mixed1_solve(c, a, cand1[k - nm], &f);
+        return run_poisson_mixed1(f, st);
+      }
       a.blocks = cand[k];
       return run_poisson_mixed(a, st);
     }, st, &best, &ms);
-    if (best >= 0) r.mixed_blocks = cand[best];
+    if (best >= nm) r.mixed1 = cand1[best - nm];
+    else if (best >= 0) r.mixed_blocks = cand[best];
   } else {
     const std::vector<TilePlan> cand = fused_plan_candidates(g.nx, g.ny, most);
     const std::vector<int> ccand = cluster_candidates(g.nx, g.ny);
@@ -714,6 +751,27 @@ int ccm_version(void) { return CCM_VERSION; }
 
 const char* ccm_last_error(void) { return g_last_error.c_str(); }
 
+// Face abscissas f = -3 .. n+3 of a stretched mesh from the n+1 given ones (the second-kind
+// capacities of the outermost padded cells reach three faces beyond the box): beyond the box
+// the spacing mirrors the spacing inside it, 2 a_0 - a_k (a sum and a difference, which no
+// compiler contracts into a fused multiply-add).  Empty if a is NULL.  False if a is not
+// strictly increasing from lo to hi.
+static bool extend_faces(const double* a, int n, double lo, double hi, std::vector<double>& out, double* hmin) {
+  out.clear();
+  if (!a) return true;
+  if (n < 4 || a[0] != lo || a[n] != hi) return false;
+  double m = 1e300;
+  for (int k = 0; k < n; ++k) {
+    if (!(a[k + 1] > a[k])) return false;
+    m = std::min(m, a[k + 1] - a[k]);
+  }
+  out.resize((size_t)n + 7);
+  for (int f = -3; f <= n + 3; ++f)
+    out[(size_t)(f + 3)] = f < 0 ? (a[0] + a[0]) - a[-f] : (f > n ? (a[n] + a[n]) - a[2 * n - f] : a[f]);
+  *hmin = m;
+  return true;
+}
+
 ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
   g_last_error.clear();
   if (!cfg || !out) return fail(CCM_E_INVALID, "null argument");
@@ -730,6 +788,8 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
     return fail(CCM_E_INVALID, "pressure_update must be 0, 1 or 2");
   if (cfg->precond == CCM_CHEBYSHEV && !cheb_degree_supported(cfg->cheb_degree))
     return fail(CCM_E_INVALID, "cheb_degree must be 1-6 or 8");
+  if (cfg->guess_history < 0 || cfg->guess_history > kGuessMax)
+    return fail(CCM_E_INVALID, "guess_history must be in 0..32");
   if (!(cfg->tol_p > 0) || !(cfg->tol_h > 0) || cfg->max_iter_p < 1 || cfg->max_iter_h < 1)
     return fail(CCM_E_INVALID, "solver tolerances and limits must be positive");
   ccm_case c = new ccm_case_s();
@@ -743,6 +803,13 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
   c->g.y0 = cfg->y0;
   c->g.hx = (cfg->x1 - cfg->x0) / cfg->nx;
   c->g.hy = (cfg->y1 - cfg->y0) / cfg->ny;
+  c->g.xf = c->g.yf = nullptr;
+  if (!extend_faces(cfg->xf, cfg->nx, cfg->x0, cfg->x1, c->xfx, &c->g.hx) ||
+      !extend_faces(cfg->yf, cfg->ny, cfg->y0, cfg->y1, c->yfx, &c->g.hy)) {
+    delete c;
+    return fail(CCM_E_INVALID, "face abscissas must increase strictly from x0 to x1 (y0 to y1)");
+  }
+  c->cfg.xf = c->cfg.yf = nullptr;  // the caller's arrays are not retained
   for (int s = 0; s < 4; ++s) {
     c->bc.type[s] = cfg->bc_type[s];
     c->bc.un[s] = cfg->bc_un[s];
@@ -768,8 +835,14 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
   c->slab = mem;
   Carver real{(char*)(((uintptr_t)mem + 255) & ~(uintptr_t)255)};
   carve(c, real);
+  if (!c->xfx.empty()) c->g.xf = c->xfd + 3;
+  if (!c->yfx.empty()) c->g.yf = c->yfd + 3;
   make_view(c);
   cudaError_t e = cudaMemsetAsync(mem, 0, c->slab_bytes, c->st);
+  if (e == cudaSuccess && !c->xfx.empty())
+    e = cudaMemcpyAsync(c->xfd, c->xfx.data(), c->xfx.size() * sizeof(double), cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess && !c->yfx.empty())
+    e = cudaMemcpyAsync(c->yfd, c->yfx.data(), c->yfx.size() * sizeof(double), cudaMemcpyHostToDevice, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) {
     if (cfg->free) cfg->free(mem, cfg->alloc_ctx); else cudaFree(mem);
@@ -784,10 +857,12 @@ ccm_status ccm_launch_plan(ccm_case c, int plan[7]) {
   g_last_error.clear();
   if (!c || !plan) return fail(CCM_E_INVALID, "null argument");
   if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
-  plan[0] = c->tune.plan.TX;
-  plan[1] = c->tune.plan.TY;
-  plan[2] = c->tune.plan.nbx;
-  plan[3] = c->tune.plan.ntiles;
+  // the tile plan of the one-barrier solve of the case's precision
+  const TilePlan& tp = c->cfg.precision == CCM_MIXED ? c->tune.mixed1 : c->tune.plan;
+  plan[0] = tp.TX;
+  plan[1] = tp.TY;
+  plan[2] = tp.nbx;
+  plan[3] = tp.ntiles;
   plan[4] = c->tune.mixed_blocks;
   plan[5] = c->tune.cluster;
   plan[6] = c->tune.plan.resident;
@@ -800,6 +875,20 @@ ccm_status ccm_set_launch_plan(ccm_case c, const int plan[7]) {
   if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
   TuneResult r{};
   const Geom& g = c->g;
+  const bool mixed = c->cfg.precision == CCM_MIXED;
+  if (plan[0] != 0 && mixed) {
+    // the one-barrier mixed solve: its tiles and their bands must fit the GPU at once
+    const int tx = plan[0], ty = plan[1];
+    const bool pow2 = tx >= 32 && tx <= 512 && (tx & (tx - 1)) == 0;
+    const int nbx = (g.nx + tx - 1) / std::max(tx, 1);
+    if (!pow2 || ty < 1 || plan[2] != nbx || plan[3] != nbx * ((g.ny + ty - 1) / ty))
+      return fail(CCM_E_INVALID, "tile plan: width a power of two in 32..512, tiles = ceil(nx/w) ceil(ny/h)");
+    if (plan[6] != 0 || plan[5] != 0 || plan[4] != 0)
+      return fail(CCM_E_INVALID, "a mixed tile plan excludes resident tiles, clusters and block counts");
+    r.mixed1 = TilePlan{tx, ty, plan[2], plan[3], 0};
+    c->tune = r;
+    return CCM_OK;
+  }
   if (plan[0] != 0) {
     const int tx = plan[0], ty = plan[1];
     const bool pow2 = tx >= 32 && tx <= 512 && (tx & (tx - 1)) == 0;
@@ -867,6 +956,7 @@ ccm_status ccm_destroy_case(ccm_case c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   free_force_history(c);
   case_free(c, c->dblock);
+  case_free(c, c->gmem);
   if (c->slab) {
     if (c->cfg.free) c->cfg.free(c->slab, c->cfg.alloc_ctx);
     else cudaFree(c->slab);
@@ -888,8 +978,11 @@ ccm_status ccm_set_geometry(ccm_case c, const ccm_geometry* geo) {
   if (geo->kind == CCM_GEOM_CIRCLE || geo->kind == CCM_GEOM_NACA) {
     double xa, xb, ya, yb;
     body_bbox(*geo, xa, xb, ya, yb);
-    const double mx = 2.5 * g.hx, my = 2.5 * g.hy;
-    if (xa < c->cfg.x0 + mx || xb > c->cfg.x1 - mx || ya < c->cfg.y0 + my || yb > c->cfg.y1 - my)
+    // the body must lie between the u-grid lines 3 and nx-2 (v-grid likewise in y): on a
+    // uniform mesh x0 + 2.5 hx and x1 - 2.5 hx
+    const Geom gh{g.nx, g.ny, g.pitch, g.x0, g.y0, g.hx, g.hy, c->xfx.empty() ? nullptr : c->xfx.data() + 3,
+                  c->yfx.empty() ? nullptr : c->yfx.data() + 3};
+    if (xa < line_x(gh, 1, 3) || xb > line_x(gh, 1, g.nx - 2) || ya < line_y(gh, 2, 3) || yb > line_y(gh, 2, g.ny - 2))
       return fail(CCM_E_INVALID, "the body must stay two cells away from every box side");
   }
   cudaStream_t st = c->st;
@@ -932,6 +1025,7 @@ ccm_status ccm_set_geometry(ccm_case c, const ccm_geometry* geo) {
   for (int q = 0; q < 4; ++q)
     if (c->bc.type[q] == CCM_BC_OUTFLOW) c->zero_mean = 0;
   c->cur = 0;
+  c->gnb = 0;
   c->nstep = 0;
   c->geometry = true;
   return autotune_poisson(c);
@@ -962,6 +1056,7 @@ ccm_status ccm_set_field(ccm_case c, int field, const double* host, size_t count
   g_last_error.clear();
   if (!c || !host) return fail(CCM_E_INVALID, "null argument");
   if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
+  c->gnb = 0;  // a new state: the initial-guess history no longer belongs to it
   if (field == CCM_F_STEP) {
     if (count < 1) return fail(CCM_E_INVALID, "count");
     c->nstep = (long long)host[0];
@@ -1143,11 +1238,49 @@ static void stage_project(ccm_case c) {
   c->steps_pending++;
 }
 
+// The projected initial guess around one Poisson solve (guess.cu): before it, Phi = the
+// projection of the new solution onto the basis; after it, the solution joins the basis (a
+// full basis restarts from the newest solution).
+static ccm_status guess_before(ccm_case c) {
+  const int L = c->cfg.guess_history;
+  if (L <= 0 || c->zero_mean) return CCM_OK;
+  const size_t n = c->g.count();
+  if (!c->gmem) {
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    void* mem = case_alloc(c, (2 * (size_t)L * n + guess_scratch_doubles()) * sizeof(double));
+    if (!mem) return fail(CCM_E_OOM, "cannot allocate the initial-guess basis");
+    c->gmem = (double*)mem;
+    c->gnb = 0;
+  }
+  if (c->gnb > 0) {
+    launch_guess_project(c->gmem, n, c->gnb, c->rhs_p, c->phi, c->gmem + 2 * (size_t)L * n, c->st);
+    c->launches += 3;
+  }
+  return CCM_OK;
+}
+
+static ccm_status guess_after(ccm_case c) {
+  const int L = c->cfg.guess_history;
+  if (L <= 0 || c->zero_mean || !c->gmem) return CCM_OK;
+  const size_t n = c->g.count();
+  if (c->gnb >= L) c->gnb = 0;
+  double* X = c->gmem;
+  double* KX = c->gmem + (size_t)L * n;
+  CUDA_TRY(cudaMemcpyAsync(X + (size_t)c->gnb * n, c->phi, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  launch_poisson(c->cv, c->g, c->phi, KX + (size_t)c->gnb * n, c->t0, c->st);
+  launch_guess_append(X, KX, n, c->gnb, c->gmem + 2 * (size_t)L * n, c->st);
+  c->launches += 1 + (c->gnb > 0 ? 8 : 0) + 3;
+  c->gnb += 1;
+  return CCM_OK;
+}
+
 static ccm_status enqueue_steps(ccm_case c, int nsteps) {
   ccm_status s;
   for (int n = 0; n < nsteps; ++n) {
     if ((s = stage_predict(c)) != CCM_OK) return s;
+    if ((s = guess_before(c)) != CCM_OK) return s;
     if ((s = poisson_solve(c, c->phi, c->rhs_p)) != CCM_OK) return s;
+    if ((s = guess_after(c)) != CCM_OK) return s;
     stage_project(c);
   }
   return check_cuda_errors("step");

@@ -132,6 +132,7 @@ struct TuneResult {
   TilePlan plan;     // FP64 one-barrier solve (TX = 0: not tuned)
   int mixed_blocks;  // mixed one-launch solve (0: not tuned)
   int cluster;       // FP64 solve inside one cluster of this many CTAs (0: not chosen)
+  TilePlan mixed1;   // mixed solve with one barrier per iteration (TX = 0: not chosen)
 };
 std::vector<TilePlan> fused_plan_candidates(int nx, int ny, int blocks);
 std::vector<int> mixed_block_candidates(int blocks);
@@ -159,6 +160,34 @@ struct MixedSolve {
 };
 int mixed_blocks();
 cudaError_t run_poisson_mixed(const MixedSolve& a, cudaStream_t st);
+
+// Initial guess of the Poisson solve by projection onto earlier solutions (guess.cu).  X and
+// KX hold up to kGuessMax K-orthonormal vectors of n doubles each (and their images under K).
+constexpr int kGuessMax = 32;
+size_t guess_scratch_doubles();
+// phi = sum_{i < nb} (X_i, rhs) X_i
+void launch_guess_project(const double* X, size_t n, int nb, const double* rhs, double* phi, double* scratch,
+                          cudaStream_t st);
+// X_nb, KX_nb hold a new solution and its image under K: K-orthonormalise them against X_0..X_{nb-1}
+void launch_guess_append(double* X, double* KX, size_t n, int nb, double* scratch, cudaStream_t st);
+
+// The same mixed solve with one grid barrier per FP32 iteration (pcg_mixed1.cu): 2-D tiles
+// whose blocks recompute the band of width k (the preconditioner's degree; 1 for Jacobi)
+// around their tile from the previous iteration's vectors and run the Chebyshev steps in
+// shared memory.  m.d.x, m.d.b, m.d.r (FP64 residual), m.d.partials and the scalars of m are
+// used; m's FP32 vectors are not.
+struct Mixed1Solve {
+  MixedSolve m;
+  float* R[2];   // FP32 residual, double-buffered by iteration parity
+  float* W[2];   // K~ u
+  float* S[2];   // K~ p
+  float *P, *U, *E;  // direction, preconditioned residual (Chebyshev), correction
+  int TX, TY, nbx, ntiles;
+};
+cudaError_t run_poisson_mixed1(Mixed1Solve f, cudaStream_t st);
+size_t mixed1_smem(int TX, int TY, int cheb);
+// Tile plans of the one-barrier mixed solve that fit the GPU at once (cooperative launch).
+std::vector<TilePlan> mixed1_plan_candidates(int nx, int ny, int cheb);
 
 // One case of a batched solve and its contiguous range of blocks (pcg_batch.cu).
 struct ScaledBatchEntry {

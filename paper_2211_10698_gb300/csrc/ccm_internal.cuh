@@ -23,10 +23,39 @@ __host__ __device__ inline int cap_slot(int g, int k) { return 9 * g + k; }
 
 struct Geom {
   int nx, ny, pitch;
-  double x0, y0, hx, hy;
+  double x0, y0, hx, hy;  // uniform spacing (a stretched mesh: its smallest spacing)
+  // stretched mesh: device arrays of the face abscissas x_f, f in [-3, nx+3] (xf[f] valid for
+  // those f; beyond the box the spacing mirrors the spacing inside it), or nullptr (uniform)
+  const double* xf;
+  const double* yf;
   __host__ __device__ size_t idx(int i, int j) const { return (size_t)(j + 1) * pitch + (size_t)(i + 1); }
   __host__ __device__ size_t count() const { return (size_t)(ny + 3) * pitch; }
 };
+
+// Grid lines of grid `grid` (0 p, 1 u, 2 v; Sec. 3.4), from one expression for every use so
+// that neighbouring cells agree bitwise: on a uniform mesh x0 + off + i hx with the u-grid
+// shifted by -hx/2; on a stretched one the face x_i, or for the u-grid the centre of pressure
+// cell i-1, (x_{i-1} + x_i) / 2 (and likewise in y).
+__host__ __device__ inline double grid_line(double o, double off, int i, double h, const double* f, bool stag) {
+#ifdef __CUDA_ARCH__
+  if (!f) return __dadd_rn(__dadd_rn(o, off), __dmul_rn((double)i, h));
+  return stag ? __dmul_rn(0.5, __dadd_rn(f[i - 1], f[i])) : f[i];
+#else
+  if (!f) return (o + off) + (double)i * h;
+  return stag ? 0.5 * (f[i - 1] + f[i]) : f[i];
+#endif
+}
+__host__ __device__ inline double line_x(const Geom& g, int grid, int i) {
+  return grid_line(g.x0, grid == 1 ? -0.5 * g.hx : 0.0, i, g.hx, g.xf, grid == 1);
+}
+__host__ __device__ inline double line_y(const Geom& g, int grid, int j) {
+  return grid_line(g.y0, grid == 2 ? -0.5 * g.hy : 0.0, j, g.hy, g.yf, grid == 2);
+}
+// Area of pressure cell (i, j)
+__host__ __device__ inline double cell_area(const Geom& g, int i, int j) {
+  if (!g.xf && !g.yf) return g.hx * g.hy;
+  return (line_x(g, 0, i + 1) - line_x(g, 0, i)) * (line_y(g, 0, j + 1) - line_y(g, 0, j));
+}
 
 struct Bc {
   int type[4];        // W E S N

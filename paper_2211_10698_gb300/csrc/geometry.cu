@@ -104,16 +104,9 @@ __device__ void area_moments(const Piece& p, double& a, double& mx, double& my) 
   my *= (1.0 / 6.0);
 }
 
-// Grid line abscissas from one expression, so that neighbouring cells agree bitwise.
-__device__ __forceinline__ double gline(double o, double off, int i, double h) {
-  return __dadd_rn(__dadd_rn(o, off), __dmul_rn((double)i, h));
-}
-
 __device__ void build(const Body& b, const Geom& g, int grid, int i, int j, Cell& c) {
-  const double ox = grid == 1 ? -0.5 * g.hx : 0.0;
-  const double oy = grid == 2 ? -0.5 * g.hy : 0.0;
-  const double xl = gline(g.x0, ox, i, g.hx), xr = gline(g.x0, ox, i + 1, g.hx);
-  const double yb = gline(g.y0, oy, j, g.hy), yt = gline(g.y0, oy, j + 1, g.hy);
+  const double xl = line_x(g, grid, i), xr = line_x(g, grid, i + 1);
+  const double yb = line_y(g, grid, j), yt = line_y(g, grid, j + 1);
   c.xl = xl; c.yb = yb; c.w = xr - xl; c.h = yt - yb;
   const double w = c.w, h = c.h;
   const bool f0 = in_fluid(b, xl, yb), f1 = in_fluid(b, xr, yb), f2 = in_fluid(b, xr, yt), f3 = in_fluid(b, xl, yt);

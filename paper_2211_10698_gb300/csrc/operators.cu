@@ -70,7 +70,7 @@ __global__ void k_derive2(Geom g, Phys ph, int pupdate, CapPtrs cp, CoefPtrs o) 
   const double eps = 1e-12 * g.hx * g.hy;
   const double Vp = cp.a[cap_slot(0, CK_V)][k];
   // volume that turns the volume-integrated Laplacian of Eq. pm_update into a point value
-  const double iv = pupdate == 0 ? 1.0 / (g.hx * g.hy) : (pupdate == 1 ? inv_or_zero(Vp, eps) : 0.0);
+  const double iv = pupdate == 0 ? 1.0 / cell_area(g, i, j) : (pupdate == 1 ? inv_or_zero(Vp, eps) : 0.0);
   o.pfac[k] = a ? (ph.dt * ph.mu / (2.0 * ph.rho)) * iv : 0.0;
   o.cu32[k] = (float)o.cu[k];
   o.cv32[k] = (float)o.cv[k];

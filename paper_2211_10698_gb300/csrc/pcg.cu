@@ -563,8 +563,8 @@ int pcg_partials_needed() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms * 4 * 8 + sms * 4;  // blocks (at most 4 per SM) times values per reduction, then
-                                 // the FP32 partials of the mixed solve (2 floats per block)
+  return sms * 4 * 8 + sms * 4 * 4;  // blocks (at most 4 per SM) times values per reduction, then
+                                     // the FP32 partials of the mixed solves (8 floats per block)
 }
 size_t pcg_float_partials_offset() {
   int dev = 0, sms = 0;

@@ -44,6 +44,7 @@ struct Request {
   long long iters_p = 0, iters_h = 0;
   std::string error;
   std::vector<double> saved[3];  // U, V, P of a finished request (padded layout)
+  std::vector<double> xf, yf;    // copies of a stretched mesh's face abscissas
 };
 
 constexpr int kSavedFields[3] = {CCM_F_U, CCM_F_V, CCM_F_P};
@@ -119,6 +120,11 @@ ccm_status ccm_server_submit(ccm_server s, const ccm_config* cfg, const ccm_geom
   Request* r = new Request();
   r->id = s->next_id++;
   r->cfg = *cfg;
+  // a stretched mesh's abscissas are the caller's: the request keeps its own copies
+  if (cfg->xf) r->xf.assign(cfg->xf, cfg->xf + cfg->nx + 1);
+  if (cfg->yf) r->yf.assign(cfg->yf, cfg->yf + cfg->ny + 1);
+  r->cfg.xf = cfg->xf ? r->xf.data() : nullptr;
+  r->cfg.yf = cfg->yf ? r->yf.data() : nullptr;
   r->cfg.stream = s->stream;
   r->cfg.autotune = 0;  // requests advance in batches, which do not use the single-case launch plan
   r->geo = *geo;

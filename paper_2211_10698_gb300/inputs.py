@@ -14,9 +14,11 @@ Conventions shared by every consumer:
   ``j`` in ``[-1, ny + 1]``.  Index ``(i, j)`` means the pressure cell ``i, j``, the x-face
   ``x0 + i*hx`` (u), the y-face ``y0 + j*hy`` (v) or the node ``(x0 + i*hx, y0 + j*hy)``
   depending on the field.
-* Box sides are numbered W=0, E=1, S=2, N=3.  A side is either ``DIRICHLET`` (prescribed
+* Box sides are numbered W=0, E=1, S=2, N=3.  A side is ``DIRICHLET`` (prescribed
   normal component ``bc_un`` and tangential component ``bc_ut``; an inflow is a Dirichlet
-  side with ``bc_un = U_inf``) or ``OUTFLOW`` (zero-gradient velocity, pressure zero).
+  side with ``bc_un = U_inf``), ``OUTFLOW`` (zero-gradient velocity, pressure zero) or
+  ``PERIODIC`` (W with E, S with N: face nx is face 0; on a uniform mesh whose cell count
+  along that axis is a multiple of 3).
 * The time step is ``dt = CFL * min(hx, hy) / U_inf`` and the viscosity
   ``mu = rho * U_inf * L / Re`` with ``L`` the cylinder diameter or the airfoil chord.
 """
@@ -31,7 +33,7 @@ import numpy as np
 SEED = 2211106980
 
 SIDE_W, SIDE_E, SIDE_S, SIDE_N = 0, 1, 2, 3
-BC_DIRICHLET, BC_OUTFLOW = 0, 1
+BC_DIRICHLET, BC_OUTFLOW, BC_PERIODIC = 0, 1, 2
 
 GEOM_NONE, GEOM_CIRCLE, GEOM_NACA, GEOM_HALFPLANE = 0, 1, 2, 3
 
@@ -88,13 +90,38 @@ class Case:
     pressure_update: int = 0       # volume in the pressure-update correction: 0 hx*hy, 1 V_p, 2 none
     replace_drop: float = 0.5      # mixed one-launch solve: FP32 residual drop per FP64 replacement
     autotune: int = 1              # time launch shapes of the single-case Poisson solve at set-up
+    # stretched mesh (Sec. 3.1): face abscissas x_0 = x0 < ... < x_nx = x1 and y_0 < ... < y_ny,
+    # or None for the uniform spacing
+    xf: Optional[np.ndarray] = None
+    yf: Optional[np.ndarray] = None
+    # Poisson initial guess: 0 the previous Phi, L > 0 the projection onto the last L solutions
+    guess_history: int = 0
+
+    @property
+    def stretched(self) -> bool:
+        return self.xf is not None or self.yf is not None
+
+    def faces_x(self) -> np.ndarray:
+        if self.xf is not None:
+            return np.ascontiguousarray(self.xf, dtype=np.float64)
+        return self.x0 + np.arange(self.nx + 1) * ((self.x1 - self.x0) / self.nx)
+
+    def faces_y(self) -> np.ndarray:
+        if self.yf is not None:
+            return np.ascontiguousarray(self.yf, dtype=np.float64)
+        return self.y0 + np.arange(self.ny + 1) * ((self.y1 - self.y0) / self.ny)
 
     @property
     def hx(self) -> float:
+        """The uniform spacing, or the smallest spacing of a stretched mesh."""
+        if self.stretched:
+            return float(np.diff(self.faces_x()).min())
         return (self.x1 - self.x0) / self.nx
 
     @property
     def hy(self) -> float:
+        if self.stretched:
+            return float(np.diff(self.faces_y()).min())
         return (self.y1 - self.y0) / self.ny
 
     @property
@@ -117,10 +144,21 @@ def closed_box_bc(lid: float = 0.0):
     return ((BC_DIRICHLET,) * 4, (0.0, 0.0, 0.0, 0.0), (0.0, 0.0, 0.0, lid))
 
 
+def periodic_bc(x: bool = True, y: bool = True):
+    """Periodic W/E (x) and S/N (y) pairs; the other pair no-slip walls."""
+    t = (BC_PERIODIC, BC_PERIODIC) if x else (BC_DIRICHLET, BC_DIRICHLET)
+    t2 = (BC_PERIODIC, BC_PERIODIC) if y else (BC_DIRICHLET, BC_DIRICHLET)
+    return (t + t2, (0.0, 0.0, 0.0, 0.0), (0.0, 0.0, 0.0, 0.0))
+
+
 def make_case(name, nx, ny, box, geom, re, cfl, lref, *, u_inf=1.0, rho=1.0, bc=None,
               **kw) -> Case:
     x0, x1, y0, y1 = box
     hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
+    if kw.get("xf") is not None:
+        hx = float(np.diff(kw["xf"]).min())
+    if kw.get("yf") is not None:
+        hy = float(np.diff(kw["yf"]).min())
     dt = cfl * min(hx, hy) / u_inf
     mu = rho * u_inf * lref / re
     bt, bn, bu = bc if bc is not None else flow_past_body_bc(u_inf)
@@ -218,6 +256,64 @@ def random_field(case: Case, seed: int, scale: float = 1.0) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(case.shape) * scale
 
 
+def stretched_faces(n: int, a: float, b: float, nfine: int, h: float, ratio: float) -> np.ndarray:
+    """Face abscissas of a mesh on [a, b] with ``nfine`` cells of size h centred on 0 and cells
+    growing by ``ratio`` per cell outwards; each side's growing cells are scaled together so
+    that the faces end at a and b.  Returns n + 1 increasing values, x_0 = a, x_n = b."""
+    ns = n - nfine
+    nl = int(round(ns * (0.0 - a) / (b - a)))
+    nr = ns - nl
+    f0, f1 = -0.5 * nfine * h, 0.5 * nfine * h
+    assert a < f0 and f1 < b and nl >= 1 and nr >= 1
+    gl = h * ratio ** np.arange(1, nl + 1)
+    gr = h * ratio ** np.arange(1, nr + 1)
+    gl *= (f0 - a) / gl.sum()
+    gr *= (b - f1) / gr.sum()
+    x = np.concatenate([(f0 - np.cumsum(gl))[::-1], f0 + h * np.arange(nfine + 1), f1 + np.cumsum(gr)])
+    x[0], x[-1] = a, b
+    return x
+
+
+def stretched_cylinder(nx=64, ny=48, box=(-3.0, 7.0, -3.0, 3.0), r=0.5, fine=(24, 24), h_fine=0.08,
+                       ratio=1.08, re=100.0, cfl=0.5, **kw) -> Case:
+    """A cylinder at the origin on a mesh that is uniform (spacing ``h_fine``) over ``fine``
+    cells around the body and stretched geometrically towards the box (Sec. 3.1; the paper's
+    grids G1-G3 are of this kind, their stretching laws not given)."""
+    xf = stretched_faces(nx, box[0], box[1], fine[0], h_fine, ratio)
+    yf = stretched_faces(ny, box[2], box[3], fine[1], h_fine, ratio)
+    return make_case(f"stretched_cyl_{nx}x{ny}", nx, ny, box, Geometry(kind=GEOM_CIRCLE, r=r), re=re, cfl=cfl,
+                     lref=2 * r, xf=xf, yf=yf, **kw)
+
+
+# ---------------------------------------------------------------------------------------------
+# Taylor-Green vortex in the doubly periodic box [0, 2 pi]^2 (rho = 1): an exact solution of the
+# incompressible Navier-Stokes equations,
+#   u = -cos x sin y F(t),  v = sin x cos y F(t),  p = -(cos 2x + cos 2y) F(t)^2 / 4,
+#   F(t) = exp(-2 nu t).
+# ---------------------------------------------------------------------------------------------
+def taylor_green(n: int, nu: float = 0.05, cfl: float = 0.25, u_ref: float = 1.0) -> Case:
+    """The doubly periodic Taylor-Green box with n x n cells (n a multiple of 3)."""
+    L = 2.0 * math.pi
+    case = make_case(f"taylor_green_{n}", n, n, (0.0, L, 0.0, L), Geometry(kind=GEOM_NONE), re=1.0, cfl=cfl,
+                     lref=1.0, u_inf=u_ref, bc=periodic_bc(True, True))
+    case.mu = nu * case.rho
+    case.autotune = 0
+    return case
+
+
+def taylor_green_exact(case: Case, t: float):
+    """Padded arrays of the exact u (u-faces), v (v-faces) and p (cell centres) at time t."""
+    xf, xc, yf, yc = mesh_positions(case)
+    F = math.exp(-2.0 * case.mu / case.rho * t)
+    XU, YU = np.meshgrid(xf, yc)
+    XV, YV = np.meshgrid(xc, yf)
+    XP, YP = np.meshgrid(xc, yc)
+    u = -np.cos(XU) * np.sin(YU) * F
+    v = np.sin(XV) * np.cos(YV) * F
+    p = -(np.cos(2 * XP) + np.cos(2 * YP)) * F * F / 4.0
+    return u, v, p
+
+
 def small_cylinder(nx=16, ny=8, box=(-2.0, 2.0, -1.0, 1.0), r=0.37, cx=0.05, cy=-0.03,
                    re=40.0, cfl=0.5, bc=None, **kw) -> Case:
     """A small off-centre cylinder case for dense and brute-force tests."""
@@ -262,13 +358,27 @@ def mms_exact(x, y, rho: float, mu: float):
     return u, v, p, gx, gy
 
 
+def mesh_positions(case: Case):
+    """Face and centre coordinates for index i in [-1, nx+1] (and j likewise): the face x_i and
+    the centre of pressure cell i.  On a stretched mesh the spacing beyond the box mirrors the
+    spacing inside it."""
+    if not case.stretched:
+        i = np.arange(-1, case.nx + 2, dtype=np.float64)
+        j = np.arange(-1, case.ny + 2, dtype=np.float64)
+        return (case.x0 + i * case.hx, case.x0 + (i + 0.5) * case.hx,
+                case.y0 + j * case.hy, case.y0 + (j + 0.5) * case.hy)
+
+    def ext(f):  # faces -1 .. n+2
+        return np.concatenate([[2 * f[0] - f[1]], f, [2 * f[-1] - f[-2], 2 * f[-1] - f[-3]]])
+
+    fx, fy = ext(case.faces_x()), ext(case.faces_y())
+    return fx[:-1], 0.5 * (fx[:-1] + fx[1:]), fy[:-1], 0.5 * (fy[:-1] + fy[1:])
+
+
 def mms_fields(case: Case):
     """Padded arrays of the manufactured solution: u and g_x at u-faces, v and g_y at v-faces,
-    p at cell centres (x0 + (i + 1/2) h, ...), for index i in [-1, nx+1]."""
-    i = np.arange(-1, case.nx + 2, dtype=np.float64)
-    j = np.arange(-1, case.ny + 2, dtype=np.float64)
-    xf, xc = case.x0 + i * case.hx, case.x0 + (i + 0.5) * case.hx
-    yf, yc = case.y0 + j * case.hy, case.y0 + (j + 0.5) * case.hy
+    p at cell centres, for index i in [-1, nx+1]."""
+    xf, xc, yf, yc = mesh_positions(case)
     XU, YU = np.meshgrid(xf, yc)
     XV, YV = np.meshgrid(xc, yf)
     XP, YP = np.meshgrid(xc, yc)

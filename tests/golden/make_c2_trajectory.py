@@ -3,7 +3,8 @@ cylinder (seeded N(0, 1e-3) perturbation, Jacobi-PCG) over its first 20 steps, w
 tolerances tightened to 1e-13, for the GPU's trajectory parity test.
 
 Calls only the oracle (and the seeded inputs).  The file records a hash of the case manifest;
-the test refuses a file whose hash no longer matches the inputs.
+the test refuses a file whose hash no longer matches the inputs.  Norms and sums are taken over
+the velocity unknowns and the active cells.
 
     python tests/golden/make_c2_trajectory.py
 """
@@ -78,10 +79,11 @@ def main():
         rec["iters_h"].append(hist[0]["iters_h"])
         if n in CHECKPOINTS:
             cp = {}
-            for name, key in (("u", "u"), ("v", "v"), ("p", "p")):
-                a = st[key]
+            for name, mask in (("u", o.role_u == 3), ("v", o.role_v == 3), ("p", o.active)):
+                a = st[name]
+                # norms over the unknowns only: ghost and corner slots carry no solution
                 cp[name] = dict(values=[float(a[j, i]) for j, i in pos[name]],
-                                l2=float(np.linalg.norm(a)), sum=float(a.sum()))
+                                l2=float(np.linalg.norm(a[mask])), sum=float(a[mask].sum()))
             cp["kinetic"] = hist[0]["kinetic"]
             rec["checkpoints"][str(n)] = cp
         print(f"step {n}: {hist[0]['iters_p']} Poisson iterations, {time.time() - t0:.0f} s", flush=True)

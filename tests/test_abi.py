@@ -106,3 +106,35 @@ def test_barrier_fault_hook_validates_on_the_host(libccm):
 
     L = ccm.lib()
     assert L.ccm_set_barrier_fault(None, 0, -1) == ccm.CCM_E_INVALID
+
+
+def test_stretched_faces_validate_on_the_host(libccm):
+    """Face abscissas of a stretched mesh must increase strictly from x0 to x1 (y0 to y1)."""
+    import numpy as np
+
+    from paper_2211_10698_gb300 import ccm, inputs
+
+    case = inputs.stretched_cylinder()
+    for bad in ("order", "end"):
+        cfg = ccm.make_config(case)
+        xf = case.faces_x().copy()
+        if bad == "order":
+            xf[5], xf[6] = xf[6], xf[5]
+        else:
+            xf[-1] += 1e-9
+        keep = np.ascontiguousarray(xf)
+        cfg.xf = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        assert ccm.lib().ccm_create_case(ctypes.byref(cfg), ctypes.byref(h)) == ccm.CCM_E_INVALID
+        assert b"abscissas" in ccm.lib().ccm_last_error()
+
+
+def test_guess_history_validates_on_the_host(libccm):
+    from paper_2211_10698_gb300 import ccm, inputs
+
+    case = inputs.cylinder_re40_128x64()
+    case.guess_history = 33
+    cfg = ccm.make_config(case)
+    h = ctypes.c_void_p()
+    assert ccm.lib().ccm_create_case(ctypes.byref(cfg), ctypes.byref(h)) == ccm.CCM_E_INVALID
+    assert b"guess_history" in ccm.lib().ccm_last_error()

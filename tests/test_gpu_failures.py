@@ -43,10 +43,15 @@ def _status(g, n):
     return ccm.lib().ccm_step(g.h, n, ctypes.byref(st)), st
 
 
-@pytest.mark.parametrize("precision,precond", [("fp64", "jacobi"), ("mixed", "jacobi"), ("mixed", "chebyshev")])
-def test_barrier_timeout_is_reported_and_the_case_recovers(precision, precond):
+@pytest.mark.parametrize("precision,precond,plan", [("fp64", "jacobi", None), ("mixed", "jacobi", None),
+                                                    ("mixed", "chebyshev", None),
+                                                    ("mixed", "chebyshev", (64, 16, 4, 32, 0, 0, 0))])
+def test_barrier_timeout_is_reported_and_the_case_recovers(precision, precond, plan):
+    """plan: a mixed tile plan selects the solve with one barrier per iteration."""
     case = _case(precision, precond)
     g = ccm.Case(case)
+    if plan:
+        g.set_launch_plan(plan)
     assert g.launch_plan()[5] == 0, "the single-cluster solve has no spin barrier to run out"
     g.step(2)
     ck = _checkpoint(g)
@@ -63,6 +68,8 @@ def test_barrier_timeout_is_reported_and_the_case_recovers(precision, precond):
     st = g.step(2)
     assert st["converged"] and st["steps"] == 2
     ref = ccm.Case(case)
+    if plan:
+        ref.set_launch_plan(plan)
     ref.step(4)
     for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P, ccm.CCM_F_PHI):
         assert np.array_equal(g.get_field(f), ref.get_field(f)), f

@@ -46,12 +46,27 @@ def _ragged():
     return I.small_cylinder(nx=53, ny=31, box=(-2.0, 3.0, -1.4, 1.5), r=0.45, cx=0.11, cy=0.04)
 
 
+def _stretched():
+    return I.stretched_cylinder(nx=64, ny=48, box=(-3.0, 7.0, -3.0, 3.0), fine=(24, 24), h_fine=0.08, ratio=1.08)
+
+
+def _stretched_naca():
+    """NACA 0012 at 6 degrees on a mesh refined around the section (Sec. 3.1, stretched)."""
+    xf = I.stretched_faces(96, -1.5, 2.5, 40, 0.03, 1.05)
+    yf = I.stretched_faces(50, -1.0, 1.0, 20, 0.03, 1.08)
+    return I.make_case("stretched_naca", 96, 50, (-1.5, 2.5, -1.0, 1.0),
+                       I.Geometry(kind=I.GEOM_NACA, naca_tt=12, aoa_deg=6.0, le_x=-0.5), re=200.0, cfl=0.5,
+                       lref=1.0, xf=xf, yf=yf)
+
+
 CASES = {
     "cylinder": lambda: I.small_cylinder(nx=48, ny=24, box=(-2.0, 4.0, -1.5, 1.5), r=0.5, cx=0.0, cy=0.0),
     "ragged": _ragged,
     "naca": _naca_small,
     "closed": _closed_cyl,
     "cavity": _cavity,
+    "stretched": _stretched,
+    "stretched_naca": _stretched_naca,
 }
 
 
@@ -111,10 +126,12 @@ def test_operators(name):
     ru, rv = o.helmholtz(u, v)
     assert rel(gu, ru) < OP_TOL and rel(gv, rv) < OP_TOL
     assert rel(g.apply(ccm.CCM_OP_POISSON, p, nout=1), o.poisson(p)) < OP_TOL
-    assert rel(g.apply(ccm.CCM_OP_POISSON_DIAG, nout=1), o.poisson_diag()) < 1e-13
+    # the diagonals by probing: sums of many terms, whose rounding grows with the spread of the
+    # capacities (small cut cells on a fine part of a stretched mesh)
+    assert rel(g.apply(ccm.CCM_OP_POISSON_DIAG, nout=1), o.poisson_diag()) < 1e-12
     gu, gv = g.apply(ccm.CCM_OP_HELMHOLTZ_DIAG)
     du, dv = o.helmholtz_diag()
-    assert rel(gu, du) < 1e-13 and rel(gv, dv) < 1e-13
+    assert rel(gu, du) < 1e-12 and rel(gv, dv) < 1e-12
 
 
 def test_literal_offdiag_operator():
@@ -128,7 +145,7 @@ def test_literal_offdiag_operator():
     assert rel(gu, ru) < OP_TOL and rel(gv, rv) < OP_TOL
 
 
-@pytest.mark.parametrize("name", ["cylinder", "ragged", "naca", "closed"])
+@pytest.mark.parametrize("name", ["cylinder", "ragged", "naca", "closed", "stretched", "stretched_naca"])
 def test_poisson_solve(name):
     case = CASES[name]()
     case.tol_p = 1e-13
@@ -169,7 +186,7 @@ def test_poisson_solve_tile_shapes(nx, ny, precision):
     assert rel(o.poisson(phi_g)[o.active], rhs[o.active]) < 1.01e-12
 
 
-@pytest.mark.parametrize("name", ["cylinder", "naca", "closed"])
+@pytest.mark.parametrize("name", ["cylinder", "naca", "closed", "stretched"])
 @pytest.mark.parametrize("degree", [2, 4])
 def test_chebyshev_poisson_solve(name, degree):
     """Chebyshev-preconditioned PCG (k-step Chebyshev iteration on the Jacobi-scaled
@@ -213,7 +230,7 @@ def test_mixed_precision_poisson_solve(name, precond):
     assert rel(phi_g, phi_o) < 1e-7
 
 
-@pytest.mark.parametrize("name", ["cylinder", "naca", "closed"])
+@pytest.mark.parametrize("name", ["cylinder", "naca", "closed", "stretched"])
 @pytest.mark.parametrize("precond", ["jacobi", "chebyshev"])
 def test_mixed_precision_steps(name, precond):
     """Steps with the mixed-precision Poisson solve refined to an FP64 residual of 1e-12
@@ -242,7 +259,8 @@ def test_mixed_precision_steps(name, precond):
         assert rel(g.get_field(f), ref) < 1e-8, f
 
 
-@pytest.mark.parametrize("name,nsteps", [("cylinder", 5), ("ragged", 4), ("naca", 3), ("closed", 4), ("cavity", 4)])
+@pytest.mark.parametrize("name,nsteps", [("cylinder", 5), ("ragged", 4), ("naca", 3), ("closed", 4), ("cavity", 4),
+                                         ("stretched", 4), ("stretched_naca", 3)])
 def test_steps(name, nsteps):
     case = CASES[name]()
     case.tol_p = case.tol_h = 1e-13
