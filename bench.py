@@ -3,9 +3,11 @@
 
 Workload (one GPU): the 1024x512 Re 100 cylinder on [-4,12]x[-4,4] in FP64 with the seeded
 N(0, 1e-3) velocity perturbation, Jacobi-PCG to 1e-10 (the configuration the metric is
-quoted on).  A "step" is one whole PmII projection step (predictor with AB2 convection and
-Crank-Nicolson viscosity, Helmholtz PCG, divergence, Poisson PCG, projection and pressure
-update) over the case.  The state is device resident; L2 is flushed (256 MiB write)
+quoted on); each Poisson solve starts from the projection of its solution onto the last 16
+solutions (--guess-history; 0 starts from the previous Phi, as the oracle does), and stops
+at the same relative residual.  A "step" is one whole PmII projection step (predictor with
+AB2 convection and Crank-Nicolson viscosity, Helmholtz PCG, divergence, Poisson PCG,
+projection and pressure update) over the case.  The state is device resident; L2 is flushed (256 MiB write)
 between timed steps, outside each step's CUDA-event interval.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -65,9 +67,14 @@ def _args():
                          "comma-separated values of ccm_launch_plan), e.g. for a profiler run")
     ap.add_argument("--configs", default="",
                     help="comma-separated names of the single-case configurations to run (default: all)")
-    ap.add_argument("--guess-history", type=int, default=0,
+    ap.add_argument("--guess-history", type=int, default=16,
                     help="headline case: initial guess of each Poisson solve by projection onto the last L "
-                         "solutions (0: the previous Phi)")
+                         "solutions (0: the previous Phi); the stopping test is the same")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="headline case's precision (the configuration is FP64; mixed for profiling the "
+                         "mixed-precision kernels on the same workload)")
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "chebyshev"])
+    ap.add_argument("--cheb-degree", type=int, default=3)
     ap.add_argument("--batch-cases", type=int, default=64,
                     help="cases of the batched measurement (the first N of the seeded 64-case mix)")
     return ap.parse_args()
@@ -110,6 +117,8 @@ def _peaks():
 # set-up autotuner: tiles with one barrier per iteration, their vectors in global memory (f1) or
 # resident in shared memory (f2), or, on small grids, one thread-block cluster.
 KERNEL_SOURCES = {
+    "k_pcg_poisson_m1": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_mixed1.cu"),
+    "k_pcg_poisson_mixed": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_quad.cuh", "pcg_mixed.cu"),
     "k_pcg_poisson_f1": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fused.cu"),
     "k_pcg_poisson_f2": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fused.cu"),
     "k_pcg_poisson_cluster": ("pcg_common.cuh", "pcg_cluster.cu"),
@@ -120,6 +129,10 @@ def kernel_of(plan):
     """The Poisson kernel a launch plan (bench's _plan_dict) runs."""
     if plan.get("kind") == "cluster":
         return "k_pcg_poisson_cluster"
+    if plan.get("kind") == "tiles, one barrier per iteration":
+        return "k_pcg_poisson_m1"
+    if plan.get("kind") in ("blocks", "built-in") and plan.get("precision") == "mixed":
+        return "k_pcg_poisson_mixed"
     return "k_pcg_poisson_f2" if plan.get("resident") else "k_pcg_poisson_f1"
 
 
@@ -438,8 +451,8 @@ def _plan_dict(g, precision="fp64"):
     if tx:
         return dict(kind="tiles", tile=[tx, ty], tiles=ntiles, resident=bool(res))
     if mb:
-        return dict(kind="blocks", blocks=mb)
-    return dict(kind="built-in")
+        return dict(kind="blocks", blocks=mb, precision=precision)
+    return dict(kind="built-in", precision=precision)
 
 
 def measure_configs(torch, stream, flush, only=None, keep=None):
@@ -460,6 +473,13 @@ def measure_configs(torch, stream, flush, only=None, keep=None):
         out["naca0012_re1000_2048x1024"] = dict(
             precision="mixed", precond=f"chebyshev degree {c3.cheb_degree}",
             **_measure_case(torch, stream, flush, c3, 10, 1, keep=keep))
+    if want("naca0012_re1000_2048x1024_projected"):
+        c3p = inputs.naca0012_re1000_2048x1024()
+        c3p.guess_history = 16
+        out["naca0012_re1000_2048x1024_projected"] = dict(
+            precision="mixed", precond=f"chebyshev degree {c3p.cheb_degree}",
+            initial_guess="projection onto the last 16 solutions",
+            **_measure_case(torch, stream, flush, c3p, 10, 1))
     if want("naca0012_re1000_2048x1024_jacobi"):
         out["naca0012_re1000_2048x1024_jacobi"] = dict(
             precision="mixed", precond="jacobi (one launch, FP64 residual replacements)",
@@ -562,6 +582,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     case = inputs.cylinder_re100_1024x512()
     case.guess_history = args.guess_history
+    case.precision, case.precond, case.cheb_degree = args.precision, args.precond, args.cheb_degree
     stream = torch.cuda.current_stream()
     if args.launch_plan:
         case.autotune = 0
@@ -572,7 +593,7 @@ def run_ours(args):
     g.set_field(ccm.CCM_F_U, g.get_field(ccm.CCM_F_U) + pu)
     g.set_field(ccm.CCM_F_V, g.get_field(ccm.CCM_F_V) + pv)
     g.step(args.warmup)
-    launch_plan = _plan_dict(g)
+    launch_plan = _plan_dict(g, case.precision)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     g.enable_kernel_timing(True)
@@ -620,6 +641,15 @@ def run_ours(args):
     nbytes = 3 * shape[0] * shape[1] * 8
 
     peaks, peak_kind = _peaks()
+    # the FP64 FMA rate of this GPU, measured (independent FMA chains, CUDA events)
+    import ctypes as _ct
+
+    fp64_meas = _ct.c_double(0.0)
+    fp64_peak, fp64_src = FP64_PEAK_TFLOPS, "FP64 unit count x clock (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)"
+    if ccm.lib().ccm_measure_fp64_rate(_ct.byref(fp64_meas)) == ccm.CCM_OK and fp64_meas.value > 0:
+        fp64_peak = fp64_meas.value
+        fp64_src = ("measured FP64 FMA rate of this GPU (ccm_measure_fp64_rate: independent FMA chains, "
+                    "CUDA events, best of 3)")
     launches = max(kt["poisson_launches"], 1)
     avg_ms = kt["poisson_ms"] / launches
     iters_per_launch = kt["poisson_iters"] / launches
@@ -627,20 +657,21 @@ def run_ours(args):
     bytes_alg = PCG_BYTES_PER_CELL_ITER * case.cells * iters_per_launch
     achieved_tf = flops / (avg_ms * 1e-3) / 1e12
     achieved_gbs = bytes_alg / (avg_ms * 1e-3) / 1e9
-    frac_alu = achieved_tf / FP64_PEAK_TFLOPS
+    frac_alu = achieved_tf / fp64_peak
     frac_hbm = achieved_gbs / peaks["hbm_gbs"]
     kernel = kernel_of(launch_plan)
     traffic_pc, prof = _traffic_from_profile(kernel)
     traffic = traffic_pc * case.cells * iters_per_launch if traffic_pc is not None else None
     if frac_alu >= frac_hbm:
-        roof = dict(bound="alu", achieved=achieved_tf, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=frac_alu,
-                    traffic=traffic, kernel=kernel,
-                    peak_source="FP64 unit count x clock (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)")
+        roof = dict(bound="alu", achieved=achieved_tf, peak=fp64_peak, unit="TFLOP/s", frac=frac_alu,
+                    traffic=traffic, kernel=kernel, peak_source=fp64_src)
     else:
         roof = dict(bound="hbm", achieved=achieved_gbs, peak=peaks["hbm_gbs"], unit="GB/s", frac=frac_hbm,
                     traffic=traffic, kernel=kernel, peak_source=f"{peak_kind} hbm_gbs")
     roof_alt = dict(hbm_achieved_gbs=achieved_gbs, hbm_peak_gbs=peaks["hbm_gbs"], hbm_frac=frac_hbm,
-                    fp64_achieved_tflops=achieved_tf, fp64_peak_tflops=FP64_PEAK_TFLOPS, fp64_frac=frac_alu,
+                    fp64_achieved_tflops=achieved_tf, fp64_peak_tflops=fp64_peak, fp64_frac=frac_alu,
+                    fp64_unit_count_peak_tflops=FP64_PEAK_TFLOPS,
+                    fp64_frac_of_unit_count_peak=achieved_tf / FP64_PEAK_TFLOPS,
                     avg_launch_ms=avg_ms, iters_per_launch=iters_per_launch,
                     us_per_iteration=1e3 * avg_ms / max(iters_per_launch, 1), peak_kind=peak_kind)
 
@@ -692,9 +723,9 @@ def run_ours(args):
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-                    dtype="f64", data="synthetic",
-                    config=dict(workload=WORKLOAD, nx=case.nx, ny=case.ny, cells=case.cells, precision="fp64",
-                                precond="jacobi", tol_p=case.tol_p, tol_h=case.tol_h, parallelism=f"replicas{world}",
+                    dtype="f64" if case.precision == "fp64" else "f32+f64", data="synthetic",
+                    config=dict(workload=WORKLOAD, nx=case.nx, ny=case.ny, cells=case.cells, precision=case.precision,
+                                precond=case.precond + (f" degree {case.cheb_degree}" if case.precond == "chebyshev" else ""), tol_p=case.tol_p, tol_h=case.tol_h, parallelism=f"replicas{world}",
                                 initial_guess=(f"projection onto the last {case.guess_history} solutions"
                                                if case.guess_history else "previous Phi"),
                                 l2="flushed between timed steps (256 MiB write, outside the step events)",

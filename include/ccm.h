@@ -16,10 +16,13 @@
  *    fastest ("padded layout"): element (j+1)*(nx+3) + (i+1) holds index (i, j), i in
  *    [-1, nx+1], j in [-1, ny+1].  Index (i, j) names the pressure cell (i, j), the x-face
  *    at x_i = x0 + i*hx (u), the y-face at y_j = y0 + j*hy (v) or the node (x_i, y_j),
- *    depending on the field (on a stretched mesh x_i and y_j are the given abscissas).
+ *    depending on the field (on a stretched mesh x_i and y_j are the given abscissas).  Beyond
+ *    a periodic side the ring holds the images of the positions at the other end.
  *  - Box sides are W=0, E=1, S=2, N=3.  A DIRICHLET side prescribes the normal velocity
  *    component bc_un and the tangential component bc_ut (an inflow is a Dirichlet side);
- *    an OUTFLOW side has zero-gradient velocity and zero pressure (Sec. 5.1).
+ *    an OUTFLOW side has zero-gradient velocity and zero pressure (Sec. 5.1); PERIODIC pairs
+ *    wrap around (a box without an outflow side has a singular Poisson system, whose
+ *    iterates are kept at zero mean, end of Sec. 4.6).
  *  - The immersed body is fixed and must stay two cells away from every box side.  It is
  *    no-slip (Dirichlet data D = 0 in Eqs. divergence, diag, offdiag, convective) unless the
  *    fields CCM_F_DX / CCM_F_DY give it a steady velocity D (a rotating or sliding body).
@@ -50,7 +53,11 @@ typedef enum {
 } ccm_status;
 
 enum { CCM_SIDE_W = 0, CCM_SIDE_E = 1, CCM_SIDE_S = 2, CCM_SIDE_N = 3 };
-enum { CCM_BC_DIRICHLET = 0, CCM_BC_OUTFLOW = 1 };
+/* PERIODIC: W with E, S with N (both sides of a pair); face nx is face 0 and the cells beyond
+ * one side are the cells at the other.  On a uniform mesh along that axis whose cell count is
+ * a multiple of 3 (the colour probing of the Helmholtz coefficients); single cases only (not
+ * in batches or the request loop). */
+enum { CCM_BC_DIRICHLET = 0, CCM_BC_OUTFLOW = 1, CCM_BC_PERIODIC = 2 };
 enum { CCM_FP64 = 0, CCM_MIXED = 1 };         /* MIXED: FP32 inner Poisson PCG, FP64 refinement */
 enum { CCM_JACOBI = 0, CCM_CHEBYSHEV = 1 };
 enum { CCM_GEOM_NONE = 0, CCM_GEOM_CIRCLE = 1, CCM_GEOM_NACA = 2, CCM_GEOM_HALFPLANE = 3 };
@@ -203,6 +210,11 @@ ccm_status ccm_launch_plan(ccm_case c, int plan[7]);
  * Jacobi solve of a nonsingular system (tiles, cluster) and to the mixed one-launch solve
  * (blocks). */
 ccm_status ccm_set_launch_plan(ccm_case c, const int plan[7]);
+
+/* The FP64 fused multiply-add rate of the current GPU in TFLOP/s (2 flop per FMA), measured with
+ * CUDA events on independent FMA chains: the roofline denominator of the FP64-bound kernels
+ * (the paper has no counterpart).  Allocates 8 bytes of device memory during the call. */
+ccm_status ccm_measure_fp64_rate(double* tflops);
 
 /* Release every resource of the case (NULL is accepted). */
 ccm_status ccm_destroy_case(ccm_case c);

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libccm.so")
-SOURCES = ["geometry.cu", "operators.cu", "pcg.cu", "pcg_scaled.cu", "pcg_mixed.cu", "pcg_mixed1.cu", "pcg_batch.cu", "pcg_fused.cu", "pcg_helm.cu", "pcg_cluster.cu", "dterms.cu", "guess.cu", "tune.cu", "api.cu", "noalloc.cu", "batch.cu", "server.cpp"]
+SOURCES = ["geometry.cu", "operators.cu", "pcg.cu", "pcg_scaled.cu", "pcg_mixed.cu", "pcg_mixed1.cu", "pcg_batch.cu", "pcg_fused.cu", "pcg_helm.cu", "pcg_cluster.cu", "dterms.cu", "guess.cu", "probe.cu", "tune.cu", "api.cu", "noalloc.cu", "batch.cu", "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

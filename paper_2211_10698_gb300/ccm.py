@@ -19,6 +19,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libccm.so"
 CCM_OK, CCM_E_INVALID, CCM_E_OOM, CCM_E_CUDA, CCM_E_NOT_CONVERGED, CCM_E_NONFINITE, CCM_E_TIMEOUT, CCM_E_STATE = range(8)
 STATUS_NAMES = ["CCM_OK", "CCM_E_INVALID", "CCM_E_OOM", "CCM_E_CUDA", "CCM_E_NOT_CONVERGED", "CCM_E_NONFINITE",
                 "CCM_E_TIMEOUT", "CCM_E_STATE"]
+CCM_BC_DIRICHLET, CCM_BC_OUTFLOW, CCM_BC_PERIODIC = 0, 1, 2
 CCM_FP64, CCM_MIXED = 0, 1
 CCM_JACOBI, CCM_CHEBYSHEV = 0, 1
 CCM_F_U, CCM_F_V, CCM_F_P, CCM_F_PHI, CCM_F_CONV_U, CCM_F_CONV_V, CCM_F_USTAR, CCM_F_VSTAR, CCM_F_DIV, CCM_F_STEP = range(10)
@@ -107,6 +108,7 @@ def lib():
                                           POINTER(c_longlong)]),
             "ccm_solve_pressure_noalloc": (c_int, [cp, c_void_p, c_void_p, POINTER(ccm_solve_stats)]),
             "ccm_set_barrier_fault": (c_int, [cp, c_longlong, c_int]),
+            "ccm_measure_fp64_rate": (c_int, [_DP]),
             "ccm_batch_create": (c_int, [c_int, c_void_p, POINTER(c_void_p)]),
             "ccm_batch_destroy": (c_int, [cp]),
             "ccm_batch_add": (c_int, [cp, cp]),

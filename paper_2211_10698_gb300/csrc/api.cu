@@ -285,7 +285,7 @@ void set_uniform_coefficients(ccm_case c, PoissonSolve<T>& a) {
 }
 
 ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
-  if (!c->zero_mean && c->cfg.precond == CCM_JACOBI) {
+  if (!c->zero_mean && c->cfg.precond == CCM_JACOBI && !c->g.px && !c->g.py) {
     // Jacobi-PCG as CG on the symmetrically scaled system (nonsingular systems)
     // with one grid barrier per iteration (tiles that recompute their ring)
     CaseSolveView v;
@@ -392,7 +392,8 @@ void case_mixed1_solve(ccm_case c, const MixedSolve& a, const TilePlan& tp, Mixe
 }
 
 ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
-  if (!c->zero_mean) {
+  // periodic sides: the host-driven refinement on the general kernel, which writes the images
+  if (!c->zero_mean && !c->g.px && !c->g.py) {
     // one launch: FP32 CG on the scaled system with FP64 residual replacements (Jacobi or
     // Chebyshev preconditioner), with one grid barrier per iteration when the tuner chose it
     MixedSolve a{};
@@ -418,6 +419,7 @@ ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
   // result is projected again at the end)
   CUDA_TRY(project_zero_mean(g, c->co.act, x, c->partials, (double)c->n_act, st));
   CUDA_TRY(project_zero_mean(g, c->co.act, b, c->partials, (double)c->n_act, st));
+  launch_wrap_cells(g, x, st);  // periodic sides: the residual's stencil reads x's images
   for (; outer < 60; ++outer) {
     launch_residual64(c->cv, g, x, b, c->fb, c->dpart, c->mixed_sums, st);
     CUDA_TRY(cudaMemcpyAsync(sums, c->mixed_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -444,6 +446,7 @@ ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
     CUDA_TRY(cudaStreamSynchronize(st));
     inner_total += it;
     launch_add_correction(g, c->co.act, x, c->fx, st);
+    launch_wrap_cells(g, x, st);
     c->launches += 3;
   }
   CUDA_TRY(project_zero_mean(g, c->co.act, x, c->partials, (double)c->n_act, st));
@@ -465,7 +468,7 @@ ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
 constexpr int kTuneIters = 24;
 
 ccm_status autotune_poisson(ccm_case c) {
-  if (!c->cfg.autotune || c->zero_mean) return CCM_OK;
+  if (!c->cfg.autotune || c->zero_mean || c->g.px || c->g.py) return CCM_OK;
   const bool mixed = c->cfg.precision == CCM_MIXED;
   if (!mixed && c->cfg.precond != CCM_JACOBI) return CCM_OK;  // FP64 Chebyshev: no plan to choose
   const Geom& g = c->g;
@@ -561,6 +564,7 @@ ccm_status poisson_solve(ccm_case c, double* x, double* b) {
     ccm_status s = solve_poisson_mixed(c, x, b);
     if (c->timing && e1) cudaEventRecord(e1, c->st);
     c->poisson_launches++;
+    launch_wrap_cells(c->g, x, c->st);  // periodic sides: Phi's images for the projection
     return s;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -573,6 +577,7 @@ ccm_status poisson_solve(ccm_case c, double* x, double* b) {
   if (c->timing && e1) cudaEventRecord(e1, c->st);
   c->poisson_launches++;
   c->launches += c->zero_mean ? 5 : 1;
+  launch_wrap_cells(c->g, x, c->st);  // periodic sides: Phi's images for the projection
   return s;
 }
 
@@ -780,8 +785,15 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
   if (!(cfg->x1 > cfg->x0) || !(cfg->y1 > cfg->y0)) return fail(CCM_E_INVALID, "empty box");
   if (!(cfg->rho > 0) || !(cfg->mu >= 0) || !(cfg->dt > 0)) return fail(CCM_E_INVALID, "rho, dt must be > 0, mu >= 0");
   for (int s = 0; s < 4; ++s)
-    if (cfg->bc_type[s] != CCM_BC_DIRICHLET && cfg->bc_type[s] != CCM_BC_OUTFLOW)
+    if (cfg->bc_type[s] != CCM_BC_DIRICHLET && cfg->bc_type[s] != CCM_BC_OUTFLOW && cfg->bc_type[s] != CCM_BC_PERIODIC)
       return fail(CCM_E_INVALID, "unknown boundary type");
+  {
+    const bool px = cfg->bc_type[CCM_SIDE_W] == CCM_BC_PERIODIC, py = cfg->bc_type[CCM_SIDE_S] == CCM_BC_PERIODIC;
+    if (px != (cfg->bc_type[CCM_SIDE_E] == CCM_BC_PERIODIC) || py != (cfg->bc_type[CCM_SIDE_N] == CCM_BC_PERIODIC))
+      return fail(CCM_E_INVALID, "periodic sides come in pairs (W with E, S with N)");
+    if ((px && (cfg->nx % 3 != 0 || cfg->xf)) || (py && (cfg->ny % 3 != 0 || cfg->yf)))
+      return fail(CCM_E_INVALID, "a periodic axis needs a uniform mesh with a multiple of 3 cells");
+  }
   if (cfg->precision != CCM_FP64 && cfg->precision != CCM_MIXED) return fail(CCM_E_INVALID, "unknown precision");
   if (cfg->precond != CCM_JACOBI && cfg->precond != CCM_CHEBYSHEV) return fail(CCM_E_INVALID, "unknown preconditioner");
   if (cfg->pressure_update < 0 || cfg->pressure_update > 2)
@@ -804,6 +816,8 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out) {
   c->g.hx = (cfg->x1 - cfg->x0) / cfg->nx;
   c->g.hy = (cfg->y1 - cfg->y0) / cfg->ny;
   c->g.xf = c->g.yf = nullptr;
+  c->g.px = cfg->bc_type[CCM_SIDE_W] == CCM_BC_PERIODIC;
+  c->g.py = cfg->bc_type[CCM_SIDE_S] == CCM_BC_PERIODIC;
   if (!extend_faces(cfg->xf, cfg->nx, cfg->x0, cfg->x1, c->xfx, &c->g.hx) ||
       !extend_faces(cfg->yf, cfg->ny, cfg->y0, cfg->y1, c->yfx, &c->g.hy)) {
     delete c;
@@ -1095,8 +1109,9 @@ ccm_status ccm_set_field(ccm_case c, int field, const double* host, size_t count
     launch_inactive_to_body(c->g, c->co.role_u, c->co.role_v, c->cv.dx, c->cv.dy, c->u, c->v, c->st);
   }
   if (field == CCM_F_P || field == CCM_F_PHI) {
-    // only active cells carry pressure; the ghost ring stays zero
+    // only active cells carry pressure; the ghost ring stays zero (periodic sides: images)
     k_mask_cells<<<grid_of(c->g, b), b, 0, c->st>>>(c->g, c->co.act, field_ptr(c, field));
+    launch_wrap_cells(c->g, field_ptr(c, field), c->st);
   }
   CUDA_TRY(cudaStreamSynchronize(c->st));
   return check_cuda_errors("set_field");
@@ -1225,6 +1240,7 @@ static void stage_project(ccm_case c) {
   const Geom& g = c->g;
   cudaStream_t st = c->st;
   launch_project(c->cv, g, c->phi, c->u, c->v, c->p, st);
+  launch_wrap_cells(g, c->p, st);
   launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
   c->launches += 7;  // fill_bc x3, predictor, Helmholtz PCG, divergence, projection
   if (c->fcap > 0) {

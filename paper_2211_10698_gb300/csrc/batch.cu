@@ -595,6 +595,7 @@ ccm_status ccm_batch_add(ccm_batch b, ccm_case c) {
   CaseSolveView v;
   if (!case_solve_view(c, &v)) return bfail(CCM_E_STATE, "set_geometry must come first");
   if (case_stream(c) != b->st) return bfail(CCM_E_INVALID, "the case must use the batch's stream");
+  if (v.g.px || v.g.py) return bfail(CCM_E_INVALID, "periodic cases are not batched");
   if ((int)b->cases.size() >= b->max_cases) return bfail(CCM_E_INVALID, "batch is full");
   if (!b->cases.empty() && case_is_mixed(b->cases[0]) != case_is_mixed(c))
     return bfail(CCM_E_INVALID, "all cases of a batch use the same precision setting");

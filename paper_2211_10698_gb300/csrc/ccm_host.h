@@ -307,6 +307,8 @@ cudaError_t launch_capacities(const ccm_geometry& geo, const Geom& g, double* co
 void launch_derive(const Geom& g, const Bc& bc, const Phys& ph, int literal, int pupdate, const CapPtrs& cp,
                    const CoefPtrs& o, cudaStream_t st);
 void launch_fill_bc(const Geom& g, const Bc& bc, double* u, double* v, double scale, cudaStream_t st);
+// periodic sides: the cells beyond them take their images' values (no-op otherwise)
+void launch_wrap_cells(const Geom& g, double* p, cudaStream_t st);
 void launch_cont(const Coefs& c, const Geom& g, const double* u, const double* v, double* out, cudaStream_t st);
 void launch_pres(const Coefs& c, const Geom& g, const double* p, double* ou, double* ov, cudaStream_t st);
 void launch_conv(const Coefs& c, const Geom& g, const double* u, const double* v, double* ou, double* ov,

@@ -28,7 +28,12 @@ struct Geom {
   // those f; beyond the box the spacing mirrors the spacing inside it), or nullptr (uniform)
   const double* xf;
   const double* yf;
+  int px = 0, py = 0;  // periodic in x (W with E) / in y (S with N)
   __host__ __device__ size_t idx(int i, int j) const { return (size_t)(j + 1) * pitch + (size_t)(i + 1); }
+  // A cell index beyond a periodic side wrapped to its image inside the box (unchanged
+  // otherwise); for the u-grid along x (or the v-grid along y) face n is face 0 as well.
+  __host__ __device__ int wrap_i(int i) const { return px ? (i < 0 ? i + nx : (i >= nx ? i - nx : i)) : i; }
+  __host__ __device__ int wrap_j(int j) const { return py ? (j < 0 ? j + ny : (j >= ny ? j - ny : j)) : j; }
   __host__ __device__ size_t count() const { return (size_t)(ny + 3) * pitch; }
 };
 
@@ -60,7 +65,23 @@ __host__ __device__ inline double cell_area(const Geom& g, int i, int j) {
 struct Bc {
   int type[4];        // W E S N
   double un[4], ut[4];
+  __host__ __device__ bool per_x() const { return type[0] == CCM_BC_PERIODIC; }
+  __host__ __device__ bool per_y() const { return type[2] == CCM_BC_PERIODIC; }
 };
+
+// Periodic images of a position (i, j) of a cell, u- or v-face array: the copies a write must
+// also make so that stencils reading across a periodic side find the value (i = 0 is also
+// i = nx, i = nx-1 also i = -1; likewise j; corners in a doubly periodic box).
+template <class T>
+__device__ __forceinline__ void put_images(T* a, int i, int j, size_t k, T val, int nx, int ny, size_t P, bool px,
+                                           bool py) {
+  long long dx = 0, dy = 0;
+  if (px) dx = i == 0 ? nx : (i == nx - 1 ? -nx : 0);
+  if (py) dy = j == 0 ? (long long)ny * (long long)P : (j == ny - 1 ? -(long long)ny * (long long)P : 0);
+  if (dx) a[(long long)k + dx] = val;
+  if (dy) a[(long long)k + dy] = val;
+  if (dx && dy) a[(long long)k + dx + dy] = val;
+}
 
 // Coefficients derived from the capacities, all in the padded layout.
 struct Coefs {
@@ -256,18 +277,22 @@ struct HomView {
   Bc bc;
   __device__ __forceinline__ double at_u(int i, int j) const {
     double s = 1.0;
-    if (i < 0) i = 0;
+    if (g.px) i = g.wrap_i(i);
+    else if (i < 0) i = 0;
     else if (i > g.nx) i = g.nx;
-    if (j < 0) { j = 0; if (bc.type[CCM_SIDE_S] == CCM_BC_DIRICHLET) s = -1.0; }
+    if (g.py) j = g.wrap_j(j);
+    else if (j < 0) { j = 0; if (bc.type[CCM_SIDE_S] == CCM_BC_DIRICHLET) s = -1.0; }
     else if (j >= g.ny) { j = g.ny - 1; if (bc.type[CCM_SIDE_N] == CCM_BC_DIRICHLET) s = -1.0; }
     size_t k = g.idx(i, j);
     return ru[k] == R_UNKNOWN ? s * u[k] : 0.0;
   }
   __device__ __forceinline__ double at_v(int i, int j) const {
     double s = 1.0;
-    if (j < 0) j = 0;
+    if (g.py) j = g.wrap_j(j);
+    else if (j < 0) j = 0;
     else if (j > g.ny) j = g.ny;
-    if (i < 0) { i = 0; if (bc.type[CCM_SIDE_W] == CCM_BC_DIRICHLET) s = -1.0; }
+    if (g.px) i = g.wrap_i(i);
+    else if (i < 0) { i = 0; if (bc.type[CCM_SIDE_W] == CCM_BC_DIRICHLET) s = -1.0; }
     else if (i >= g.nx) { i = g.nx - 1; if (bc.type[CCM_SIDE_E] == CCM_BC_DIRICHLET) s = -1.0; }
     size_t k = g.idx(i, j);
     return rv[k] == R_UNKNOWN ? s * v[k] : 0.0;

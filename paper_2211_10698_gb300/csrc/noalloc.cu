@@ -101,6 +101,7 @@ extern "C" ccm_status ccm_solve_pressure_noalloc(ccm_case c, const double* rhs_d
   if (!c || !rhs_dev || !phi_dev) return fail(CCM_E_INVALID, "null argument");
   CaseSolveView v;
   if (!case_solve_view(c, &v)) return fail(CCM_E_STATE, "set_geometry must come first");
+  if (v.g.px || v.g.py) return fail(CCM_E_INVALID, "periodic cases are not supported by this solve");
   const size_t n = v.g.count();
   if (n > kMaxElems)
     return fail(CCM_E_INVALID, "grid too large for the fixed scratch: (ny+3)*pitch = " + std::to_string(n) +

@@ -25,8 +25,12 @@ __device__ __forceinline__ double inv_or_zero(double w, double eps) { return w >
 __global__ void k_derive1(Geom g, Bc bc, Phys ph, int literal, CapPtrs cp, CoefPtrs o) {
   PAD_IJ(g)
   const double eps = 1e-12 * g.hx * g.hy;
-  const bool udom = i >= 0 && i <= g.nx && j >= 0 && j < g.ny;
-  const bool vdom = i >= 0 && i < g.nx && j >= 0 && j <= g.ny;
+  // on a periodic axis face n is the image of face 0: not a position of its own, but its
+  // Poisson coefficient couples cell n-1 with cell 0 (through the ghost image)
+  const bool uimg = g.px && i == g.nx && j >= 0 && j < g.ny;
+  const bool vimg = g.py && j == g.ny && i >= 0 && i < g.nx;
+  const bool udom = i >= 0 && i <= g.nx && j >= 0 && j < g.ny && !uimg;
+  const bool vdom = i >= 0 && i < g.nx && j >= 0 && j <= g.ny && !vimg;
   const bool udir = udom && ((i == 0 && bc.type[CCM_SIDE_W] == CCM_BC_DIRICHLET) ||
                              (i == g.nx && bc.type[CCM_SIDE_E] == CCM_BC_DIRICHLET));
   const bool vdir = vdom && ((j == 0 && bc.type[CCM_SIDE_S] == CCM_BC_DIRICHLET) ||
@@ -38,8 +42,8 @@ __global__ void k_derive1(Geom g, Bc bc, Phys ph, int literal, CapPtrs cp, CoefP
   o.role_v[k] = rv;
   const double Ax = cp.a[cap_slot(0, CK_AX)][k], Ay = cp.a[cap_slot(0, CK_AY)][k];
   const double ivu = inv_or_zero(Vu, eps), ivv = inv_or_zero(Vv, eps);
-  o.cu[k] = ru == R_UNKNOWN ? Ax * Ax * ivu : 0.0;
-  o.cv[k] = rv == R_UNKNOWN ? Ay * Ay * ivv : 0.0;
+  o.cu[k] = (ru == R_UNKNOWN || (uimg && Vu > eps)) ? Ax * Ax * ivu : 0.0;
+  o.cv[k] = (rv == R_UNKNOWN || (vimg && Vv > eps)) ? Ay * Ay * ivv : 0.0;
   o.gfu[k] = ru == R_UNKNOWN ? (ph.dt / ph.rho) * Ax * ivu : 0.0;
   o.gfv[k] = rv == R_UNKNOWN ? (ph.dt / ph.rho) * Ay * ivv : 0.0;
   o.massu[k] = ru == R_UNKNOWN ? (ph.rho / ph.dt) * Vu : 0.0;
@@ -131,6 +135,24 @@ __global__ void k_fill_bc(Geom g, Bc bc, double* u, double* v, double scale) {
   fill_bc_at(g, bc, u, v, scale, i, j, k);
 }
 
+// Periodic sides, after the box rules of the other sides: every position beyond a periodic
+// side (and face n along it) takes the value of its image inside the box.  A source is never
+// a target, so one launch suffices.
+__global__ void k_wrap_faces(Geom g, double* u, double* v) {
+  PAD_IJ(g)
+  const int iu = g.px ? (i >= g.nx ? i - g.nx : (i < 0 ? i + g.nx : i)) : i;
+  const int jc = g.wrap_j(j);
+  if (u && (iu != i || jc != j)) u[k] = u[g.idx(iu, jc)];
+  const int ic = g.wrap_i(i);
+  const int jv = g.py ? (j >= g.ny ? j - g.ny : (j < 0 ? j + g.ny : j)) : j;
+  if (v && (ic != i || jv != j)) v[k] = v[g.idx(ic, jv)];
+}
+__global__ void k_wrap_cells(Geom g, double* p) {
+  PAD_IJ(g)
+  const int ic = g.wrap_i(i), jc = g.wrap_j(j);
+  if (ic != i || jc != j) p[k] = p[g.idx(ic, jc)];
+}
+
 // ---------------------------------------------------------------------------------------
 // Operators (used by ccm_apply_op and by set-up).
 // ---------------------------------------------------------------------------------------
@@ -140,10 +162,15 @@ __global__ void k_cont(Coefs c, Geom g, const double* u, const double* v, double
   out[k] = dom ? cont_cell(c, g, u, v, i, j) : 0.0;
 }
 
-// pres(P) on velocity unknowns; cells outside the box read as zero.
+// pres(P) on velocity unknowns; cells outside the box read as zero (their images on a
+// periodic side).
 __global__ void k_pres(Coefs c, Geom g, const double* p, double* ou, double* ov) {
   PAD_IJ(g)
-  auto P = [&](int a, int b) { return (a >= 0 && a < g.nx && b >= 0 && b < g.ny) ? p[g.idx(a, b)] : 0.0; };
+  auto P = [&](int a, int b) {
+    a = g.wrap_i(a);
+    b = g.wrap_j(b);
+    return (a >= 0 && a < g.nx && b >= 0 && b < g.ny) ? p[g.idx(a, b)] : 0.0;
+  };
   ou[k] = c.role_u[k] == R_UNKNOWN ? c.ax[k] * (P(i, j) - P(i - 1, j)) : 0.0;
   ov[k] = c.role_v[k] == R_UNKNOWN ? c.ay[k] * (P(i, j) - P(i, j - 1)) : 0.0;
 }
@@ -249,7 +276,11 @@ __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, 
                                                  const FullView& w, const double* p, const double* cpu,
                                                  const double* cpv, double* cnu, double* cnv, double* ru_, double* rv_,
                                                  int first, int i, int j, size_t k) {
-  auto P = [&](int a, int b) { return (a >= 0 && a < g.nx && b >= 0 && b < g.ny) ? p[g.idx(a, b)] : 0.0; };
+  auto P = [&](int a, int b) {
+    a = g.wrap_i(a);
+    b = g.wrap_j(b);
+    return (a >= 0 && a < g.nx && b >= 0 && b < g.ny) ? p[g.idx(a, b)] : 0.0;
+  };
   if (c.role_u[k] == R_UNKNOWN) {
     double cn = conv_u(c, g, w, i, j);
     // conv(U, U, D, D): the face mean of h = cont(0, D) times (U + D)/2 (Eq. convective)
@@ -367,12 +398,12 @@ __global__ void k_diagnostics(Coefs c, Geom g, const double* Vu, const double* V
       mass = d;
       if (c.act[k]) dmax = fabs(d);
     }
-    if (i >= 0 && i <= g.nx && j >= 0 && j < g.ny) {
+    if (i >= 0 && i <= g.nx - g.px && j >= 0 && j < g.ny) {  // face nx of a periodic x is face 0
       ke += 0.5 * Vu[k] * u[k] * u[k];
       mx = Vu[k] * u[k];
       if (!isfinite(u[k])) bad = 1.0;
     }
-    if (i >= 0 && i < g.nx && j >= 0 && j <= g.ny) {
+    if (i >= 0 && i < g.nx && j >= 0 && j <= g.ny - g.py) {
       ke += 0.5 * Vv[k] * v[k] * v[k];
       my = Vv[k] * v[k];
       if (!isfinite(v[k])) bad = 1.0;
@@ -583,6 +614,10 @@ void launch_derive(const Geom& g, const Bc& bc, const Phys& ph, int literal, int
 }
 void launch_fill_bc(const Geom& g, const Bc& bc, double* u, double* v, double scale, cudaStream_t st) {
   k_fill_bc<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, bc, u, v, scale);
+  if (g.px || g.py) k_wrap_faces<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, u, v);
+}
+void launch_wrap_cells(const Geom& g, double* p, cudaStream_t st) {
+  if (g.px || g.py) k_wrap_cells<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, p);
 }
 void launch_cont(const Coefs& c, const Geom& g, const double* u, const double* v, double* out, cudaStream_t st) {
   k_cont<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, u, v, out);
@@ -605,6 +640,7 @@ void launch_helmholtz(const Coefs& c, const Geom& g, const Bc& bc, const Phys& p
 }
 void launch_poisson(const Coefs& c, const Geom& g, const double* x, double* out, double* tmp, cudaStream_t st) {
   k_copy_interior_cells<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, x, tmp);
+  if (g.px || g.py) k_wrap_cells<<<pad_grid(g, kBlk), kBlk, 0, st>>>(g, tmp);
   k_poisson<<<pad_grid(g, kBlk), kBlk, 0, st>>>(c, g, tmp, out);
 }
 void launch_helmholtz_diag(const Coefs& c, const Geom& g, const Bc& bc, const Phys& ph, double* eu, double* ev,

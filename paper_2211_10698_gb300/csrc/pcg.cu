@@ -42,6 +42,11 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson(PoissonSolve<T> 
   const T inv_theta = (T)(1.0 / ChebCoef::theta);
   const T ireg = (T)a.invd_reg;
   auto Dinv = [&](size_t k) -> T { return kind[k] == 1 ? ireg : invd[k]; };
+  // periodic sides: a vector the stencil reads across the side is also written to its images
+  const bool per = g.px || g.py;
+  auto img = [&](T* v, const CellWalk& w, size_t k, T val) {
+    if (per) put_images(v, w.i, w.j, k, val, g.nx, g.ny, (size_t)g.pitch, g.px != 0, g.py != 0);
+  };
 
   // Chebyshev steps 1..CHEB-1 after z = w1 = D^-1 r / theta; accumulates r.z and, for
   // singular systems, the sums of z and r over active cells.
@@ -59,6 +64,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson(PoissonSolve<T> 
         a.w1[k] = w1;
         const T zk = zc[k] + w1;
         zo[k] = zk;
+        img(zo, w, k, zk);
         if (last) {
           acc[0] += (double)r[k] * (double)zk;
           if (ZM && kind[k]) { acc[2] += (double)zk; acc[3] += (double)r[k]; }
@@ -84,6 +90,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson(PoissonSolve<T> 
       const T w1 = Dinv(k) * rk * inv_theta;
       a.w1[k] = w1;
       zc[k] = w1;
+      img(zc, w, k, w1);
     } else {
       const T zk = Dinv(k) * rk;
       zc[k] = zk;
@@ -124,7 +131,9 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson(PoissonSolve<T> 
       for (CellWalk w(first, stride, ch.t1, nx); w.ok(); w.next()) {
         const size_t k = g.idx(w.i, w.j);
         const T zk = ZM ? z[k] - (kind[k] ? tzm : (T)0) : z[k];
-        p[k] = zk + tb * p[k];
+        const T pk = zk + tb * p[k];
+        p[k] = pk;
+        img(p, w, k, pk);
       }
     }
     if (!grid_sync(a.bar, target)) { ok = false; break; }
@@ -158,6 +167,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson(PoissonSolve<T> 
         const T w1 = Dinv(k) * rk * inv_theta;
         a.w1[k] = w1;
         zc[k] = w1;
+        img(zc, w, k, w1);
       } else {
         const T zk = Dinv(k) * rk;
         zc[k] = zk;
@@ -239,6 +249,11 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_cg(PoissonSolve<
   T* __restrict__ p = a.p0;
   T* __restrict__ sv = a.p1;
   const T ireg = (T)a.invd_reg;
+  // periodic sides: u, which the stencil reads across the side, is also written to its images
+  const bool per = g.px || g.py;
+  auto img = [&](T* v, const CellWalk& w, size_t k, T val) {
+    if (per) put_images(v, w.i, w.j, k, val, g.nx, g.ny, (size_t)g.pitch, g.px != 0, g.py != 0);
+  };
 
   // phase 0a: r = b - K x, u = D^-1 r, p = s = 0
   double bb_part = 0.0;
@@ -248,6 +263,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_cg(PoissonSolve<
     const T rk = bk - K(x, k);
     r[k] = rk;
     u[k] = (kind[k] == 1 ? ireg : invd[k]) * rk;
+    img(u, cw, k, u[k]);
     p[k] = (T)0;
     sv[k] = (T)0;
     bb_part += (double)bk * (double)bk;
@@ -326,7 +342,9 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_cg(PoissonSolve<
         x[k] += ta * pk;
         const T rk = r[k] - ta * sk;
         r[k] = rk;
-        u[k] = (kk == 1 ? ireg : invd[k]) * rk;
+        const T un = (kk == 1 ? ireg : invd[k]) * rk;
+        u[k] = un;
+        img(u, cw, k, un);
       }
     }
     if (!grid_sync(a.bar, target)) { ok = false; break; }

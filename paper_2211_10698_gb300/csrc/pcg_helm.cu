@@ -57,6 +57,11 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_helmholtz_c(HelmCSolve a
   const int t1 = T0 + (int)((long long)(T1 - T0) * (blockIdx.x + 1) / nb);
   const int8_t* __restrict__ ru = a.ru;
   const int8_t* __restrict__ rv = a.rv;
+  // periodic sides: z, which the rows read across the side, is also written to its images
+  const bool per = g.px || g.py;
+  auto img = [&](double* z, int k, double val) {
+    if (per) put_images(z, k % P - 1, k / P - 1, (size_t)k, val, g.nx, g.ny, (size_t)P, g.px != 0, g.py != 0);
+  };
 
   auto reduce = [&](const double (&v)[4], int nv) {
     if (nv == 4) block_sum_warps<4>(v, red, bsum);
@@ -94,6 +99,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_helmholtz_c(HelmCSolve a
       const double b = a.bu[k], r = b - H.row_u(a.xu, a.xv, k);
       a.rU[k] = r;
       a.zU[k] = a.invu[k] * r;
+      img(a.zU, k, a.zU[k]);
       a.pU[k] = 0.0;
       a.sU[k] = 0.0;
       v[3] += b * b;
@@ -102,6 +108,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_helmholtz_c(HelmCSolve a
       const double b = a.bv[k], r = b - H.row_v(a.xu, a.xv, k);
       a.rV[k] = r;
       a.zV[k] = a.invv[k] * r;
+      img(a.zV, k, a.zV[k]);
       a.pV[k] = 0.0;
       a.sV[k] = 0.0;
       v[3] += b * b;
@@ -148,6 +155,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_helmholtz_c(HelmCSolve a
           const double r = a.rU[k] - al * s;
           a.rU[k] = r;
           a.zU[k] = a.invu[k] * r;
+          img(a.zU, k, a.zU[k]);
         }
         if (rv[k] == R_UNKNOWN) {
           const double p = a.zV[k] + be * a.pV[k], s = a.wV[k] + be * a.sV[k];
@@ -157,6 +165,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_helmholtz_c(HelmCSolve a
           const double r = a.rV[k] - al * s;
           a.rV[k] = r;
           a.zV[k] = a.invv[k] * r;
+          img(a.zV, k, a.zV[k]);
         }
       }
     }

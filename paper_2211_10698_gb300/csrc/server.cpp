@@ -117,6 +117,8 @@ ccm_status ccm_server_destroy(ccm_server s) {
 
 ccm_status ccm_server_submit(ccm_server s, const ccm_config* cfg, const ccm_geometry* geo, int nsteps, long long* id) {
   if (!s || !cfg || !geo || !id || nsteps < 0) return CCM_E_INVALID;
+  for (int q = 0; q < 4; ++q)
+    if (cfg->bc_type[q] == CCM_BC_PERIODIC) return CCM_E_INVALID;  // requests advance in batches
   Request* r = new Request();
   r->id = s->next_id++;
   r->cfg = *cfg;

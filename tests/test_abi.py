@@ -138,3 +138,19 @@ def test_guess_history_validates_on_the_host(libccm):
     h = ctypes.c_void_p()
     assert ccm.lib().ccm_create_case(ctypes.byref(cfg), ctypes.byref(h)) == ccm.CCM_E_INVALID
     assert b"guess_history" in ccm.lib().ccm_last_error()
+
+
+def test_periodic_sides_validate_on_the_host(libccm):
+    """Periodic sides come in pairs, on a uniform axis with a multiple of 3 cells."""
+    from paper_2211_10698_gb300 import ccm, inputs
+
+    L = ccm.lib()
+    h = ctypes.c_void_p()
+    cfg = ccm.make_config(inputs.taylor_green(24))
+    cfg.bc_type[1] = ccm.CCM_BC_OUTFLOW
+    assert L.ccm_create_case(ctypes.byref(cfg), ctypes.byref(h)) == ccm.CCM_E_INVALID
+    assert b"pairs" in L.ccm_last_error()
+    cfg = ccm.make_config(inputs.taylor_green(25 - 1))
+    cfg.nx = 25
+    assert L.ccm_create_case(ctypes.byref(cfg), ctypes.byref(h)) == ccm.CCM_E_INVALID
+    assert b"multiple of 3" in L.ccm_last_error()
