@@ -197,18 +197,20 @@ ccm_status ccm_create_case(const ccm_config* cfg, ccm_case* out);
 ccm_status ccm_case_bytes(const ccm_config* cfg, size_t* bytes);
 
 /* The launch shape of the case's one-launch Poisson solve: plan[0..3] = tile width, tile
- * height, tiles per row and tiles of the FP64 one-barrier solve (0 where it does not apply or
- * the built-in plan is used), plan[4] = blocks of the mixed solve (0: built-in), plan[5] =
- * CTAs of the one thread-block cluster that holds a small grid's whole FP64 solve (0: not
- * used), plan[6] = 1 when the tiles keep their vectors in shared memory for the whole solve.
- * Valid after set_geometry. */
+ * height, tiles per row and tiles of the one-barrier solve of the case's precision (FP64, or
+ * for a mixed case the one-barrier mixed solve; 0 where it does not apply or the built-in
+ * plan is used), plan[4] = blocks of the mixed solve with a barrier per Chebyshev step (0:
+ * built-in), plan[5] = CTAs of the one thread-block cluster that holds a small grid's whole
+ * FP64 solve (0: not used), plan[6] = 1 when the FP64 tiles keep their vectors in shared
+ * memory for the whole solve.  Valid after set_geometry. */
 ccm_status ccm_launch_plan(ccm_case c, int plan[7]);
 /* Sets the launch shape (same layout; zeros select the built-in shapes).  A tile plan needs a
  * width that is a power of two in 32..512 and the tile counts it implies (and, resident, tiles
  * that fit in shared memory at once); a cluster has 2, 4, 8 or 16 CTAs, at most ny, and
- * excludes a tile plan.  CCM_E_INVALID otherwise.  Shapes apply to the single-case FP64
- * Jacobi solve of a nonsingular system (tiles, cluster) and to the mixed one-launch solve
- * (blocks). */
+ * excludes a tile plan; a mixed case's tile plan selects the one-barrier mixed solve and
+ * excludes the other entries.  CCM_E_INVALID otherwise.  Shapes apply to the single-case
+ * solve of a nonsingular system: the FP64 Jacobi solve (tiles, cluster) and the mixed solve
+ * (tiles or blocks). */
 ccm_status ccm_set_launch_plan(ccm_case c, const int plan[7]);
 
 /* The FP64 fused multiply-add rate of the current GPU in TFLOP/s (2 flop per FMA), measured with

@@ -496,8 +496,10 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
           sc_keep = 0;
           // replace when the FP32 residual fell by `drop`, or when the estimate of the unscaled
           // residual norm meets the tolerance
-          const double ratio = (double)rr32 / (double)sc_gref;
-          int replace = (ratio <= A.drop * A.drop || sc_rr_ref * ratio <= tol2 * sc_bb) ? 1 : 0;
+          // (multiplied out: no FP64 division on the serial path)
+          const double gref = sc_gref;
+          int replace = gref > 0.0 && ((double)rr32 <= A.drop * A.drop * gref ||
+                                       sc_rr_ref * (double)rr32 <= tol2 * sc_bb * gref) ? 1 : 0;
           if (!replace) {
             // Chronopoulos-Gear: beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old)
             const float beta = gamma * sc_igamma;

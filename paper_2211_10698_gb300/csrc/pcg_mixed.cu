@@ -204,8 +204,11 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg_poisson_mixed(MixedSolve
       if (fresh) sc_gref = rr32;
       // replace when the FP32 residual fell by `drop`, or when the estimate of the unscaled
       // residual norm (scaled by the last FP64 value) meets the tolerance
-      const double ratio = (double)rr32 / (double)sc_gref;
-      sc_replace = !fresh && (ratio <= a.drop * a.drop || sc_rr_ref * ratio <= tol2 * sc_bb) ? 1 : 0;
+      // rr32 / gref <= drop^2, or the estimate rr_ref rr32 / gref of the unscaled residual
+      // meets the tolerance (multiplied out: no FP64 division on the serial path)
+      const double gref = sc_gref;
+      sc_replace = !fresh && gref > 0.0 &&
+                   ((double)rr32 <= a.drop * a.drop * gref || sc_rr_ref * (double)rr32 <= tol2 * sc_bb * gref) ? 1 : 0;
       // A residual about to be replaced is not used: the scalars are formed from the replacing
       // residual instead (next call, fresh), against the same previous gamma and alpha.
       if (!sc_replace) {

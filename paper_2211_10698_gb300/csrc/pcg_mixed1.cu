@@ -24,6 +24,7 @@
 // rows, which are rewritten only two reductions (and so one barrier) later.
 #include <algorithm>
 
+#include "pcg_cheb.cuh"
 #include "pcg_common.cuh"
 
 namespace ccm {
@@ -57,18 +58,6 @@ __device__ __forceinline__ void grid_sum_f32_rows(const float* rows, int nb, flo
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NV; ++k) out[k] = smem[k];
-}
-
-// The Chebyshev step j >= 1 coefficients (d_{j+1} = c1 d_j + c2 (r - K~ z_j)), as in pcg_quad.cuh
-__device__ __forceinline__ void cheb_coef(int j, float& c1, float& c2) {
-  const double sig1 = ChebCoef::theta / ChebCoef::delta;
-  double rho_prev = 1.0 / sig1, rho = rho_prev;
-  for (int q = 1; q <= j; ++q) {
-    if (q > 1) rho_prev = rho;
-    rho = 1.0 / (2.0 * sig1 - rho_prev);
-  }
-  c1 = (float)(rho * rho_prev);
-  c2 = (float)(2.0 * rho / ChebCoef::delta);
 }
 
 __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant__ Mixed1Solve f) {
@@ -197,7 +186,7 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
       __syncthreads();
       for (int js = 1; js < cheb; ++js) {
         float c1, c2;
-        cheb_coef(js, c1, c2);
+        cheb_step_coef(js, c1, c2);
         float* zin = (js & 1) ? za : zb;   // z_j
         float* zio = (js & 1) ? zb : za;   // z_{j-1} in, z_{j+1} out
         const int m = h - js;              // the band width this step leaves valid
@@ -250,8 +239,11 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
         sc_keep = 0;
       }
       if (fresh) sc_gref = rr32;
-      const double ratio = (double)rr32 / (double)sc_gref;
-      sc_replace = !fresh && (ratio <= a.drop * a.drop || sc_rr_ref * ratio <= tol2 * sc_bb) ? 1 : 0;
+      // rr32 / gref <= drop^2, or the estimate rr_ref rr32 / gref of the unscaled residual
+      // meets the tolerance (multiplied out: no FP64 division on the serial path)
+      const double gref = sc_gref;
+      sc_replace = !fresh && gref > 0.0 &&
+                   ((double)rr32 <= a.drop * a.drop * gref || sc_rr_ref * (double)rr32 <= tol2 * sc_bb * gref) ? 1 : 0;
       if (!sc_replace) {
         if (fresh && sc_it == 0 && sc_nrep == 0) {
           sc_beta = 0.0f;

@@ -6,6 +6,7 @@
 // row kind is the identity), so quads are processed whole.  Used by the single-case solve
 // (pcg_mixed.cu) and the batched one (pcg_batch.cu).
 #pragma once
+#include "pcg_cheb.cuh"
 #include "pcg_common.cuh"
 
 namespace ccm {
@@ -39,20 +40,6 @@ struct Quads {
     return (j + 1) * P + 4 * (u - j * nq);
   }
 };
-
-// Coefficients of Chebyshev step j >= 1 for K~ z = r (Saad's recurrence on the eigenvalue
-// interval of ChebCoef, z1 = r / theta): d_{j+1} = c1 d_j + c2 (r - K~ z_j),
-// z_{j+1} = z_j + d_{j+1}, with d_1 = z_1.
-__device__ __forceinline__ void cheb_step_coef(int j, float& c1, float& c2) {
-  const double sig1 = ChebCoef::theta / ChebCoef::delta;
-  double rho_prev = 1.0 / sig1, rho = rho_prev;
-  for (int q = 1; q <= j; ++q) {
-    if (q > 1) rho_prev = rho;
-    rho = 1.0 / (2.0 * sig1 - rho_prev);
-  }
-  c1 = (float)(rho * rho_prev);
-  c2 = (float)(2.0 * rho / ChebCoef::delta);
-}
 
 struct QuadOpsF32 {
   const int8_t* kinds;

@@ -246,3 +246,23 @@ def test_conservation_sums(orc):
     assert abs(m) > 1e-3                     # not trivially zero for a random field
     assert px == pytest.approx((o.cap("u", "V") * u)[1:ny + 1, 1:nx + 2].sum(), rel=1e-13)
     assert py == pytest.approx((o.cap("v", "V") * v)[1:ny + 2, 1:nx + 1].sum(), rel=1e-13)
+
+
+def test_oracle_threads_bitwise(orc):
+    """The oracle's sums run over fixed blocks in a fixed order, so a run on one thread and a run
+    on four give the same fields bit for bit (the grid spans several summation blocks)."""
+    case = I.small_cylinder(nx=160, ny=80, box=(-2.0, 6.0, -2.0, 2.0), r=0.5)
+    out = []
+    for t in (1, 4):
+        prev = O.set_threads(t)
+        try:
+            o = orc.Oracle(case)
+            s = o.init_state()
+            hist, _ = o.step(s, 3)
+        finally:
+            O.set_threads(0)
+        assert all(h["ok"] for h in hist) and prev >= 1
+        out.append((s["u"].copy(), s["v"].copy(), s["p"].copy(), [h["iters_p"] for h in hist]))
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
+    assert out[0][3] == out[1][3]
