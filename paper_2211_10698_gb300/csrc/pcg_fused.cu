@@ -176,9 +176,11 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
     }
     __syncthreads();
     if constexpr (RES) {
-      // the first kNT listed cells' scaled coefficients, constant for the whole solve
-      if (f.lcache && !general && threadIdx.x < nlist) {
-        const int q = list[threadIdx.x];
+      // the first kNT listed cells' scaled coefficients, constant for the whole solve (listed
+      // cell q is taken by thread kNT - 1 - q, see below)
+      const int myq = kNT - 1 - (int)threadIdx.x;
+      if (f.lcache && !general && myq < nlist) {
+        const int q = list[myq];
         const size_t k = g.idx(i0 + q % TX, j0 + q / TX);
         lcoef[threadIdx.x] = cus[k];
         lcoef[kNT + threadIdx.x] = cus[k + 1];
@@ -188,6 +190,13 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
       }
     }
   }
+  // Listed cell q is computed by thread kNT - 1 - q (then kNT - 1 - q + kNT, ...): threads are
+  // ordered by the first row they take, so the last threads have the fewest own rows (with
+  // TY = 27 and 4 rows per pass, the last 128 threads take 6 rows and the others 7), and a
+  // tile's listed cells fill those free slots before they lengthen any warp.  An FP64-bound
+  // sub-partition's time is the sum over its warps, and the slowest tile sets every
+  // iteration's barrier.
+  const int myq = kNT - 1 - (int)threadIdx.x;
   // the general row at own cell (i, j) (any kind); w = K~ r and the sums of a row of kind km
   auto general_row = [&](const double* rn, int i, int j, double& rc_out) -> double {
     const size_t k = g.idx(i, j);
@@ -220,7 +229,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
     }
     // This thread's first listed cell: its values and coefficients are loaded before the
     // constant-stencil pass, so that their latency overlaps it.
-    const int q0 = threadIdx.x < nlist ? list[threadIdx.x] : -1;
+    const int q0 = myq < nlist ? list[myq] : -1;
     int li = 0, lj = 0;
     double lr[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, lc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (q0 >= 0) {
@@ -286,7 +295,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
       v[1] += (lc[4] * lc[4] - dreg) * (lr[0] * lr[0]);
       v[2] += wk * lr[0];
     }
-    for (int q = threadIdx.x + kNT; q < nlist; q += kNT) {
+    for (int q = myq + kNT; q < nlist; q += kNT) {
       const int loc = list[q];
       const int i = i0 + loc % TX, j = j0 + loc / TX;
       double rc;
