@@ -44,7 +44,7 @@ PCG_FLOPS_PER_CELL_ITER = 24
 # x, r and p each read and written once per iteration (8-byte words).
 PCG_BYTES_PER_CELL_ITER = 48
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clock x 2 flop x
-# 2.07 GHz (the probe measured 1.20 TFLOP/s of dependent-chain-free FMAs).
+# 2.07 GHz; reported beside the rate ccm_measure_fp64_rate measures, which is the denominator.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
@@ -118,6 +118,7 @@ def _peaks():
 # resident in shared memory (f2), or, on small grids, one thread-block cluster.
 KERNEL_SOURCES = {
     "k_pcg_poisson_m1": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_cheb.cuh", "pcg_mixed1.cu"),
+    "k_pcg_poisson_m2": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_cheb.cuh", "pcg_mixed1.cu"),
     "k_pcg_poisson_mixed": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_cheb.cuh", "pcg_quad.cuh", "pcg_mixed.cu"),
     "k_pcg_poisson_f1": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fused.cu"),
     "k_pcg_poisson_f2": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fused.cu"),
@@ -130,7 +131,7 @@ def kernel_of(plan):
     if plan.get("kind") == "cluster":
         return "k_pcg_poisson_cluster"
     if plan.get("kind") == "tiles, one barrier per iteration":
-        return "k_pcg_poisson_m1"
+        return "k_pcg_poisson_m2" if plan.get("resident") else "k_pcg_poisson_m1"
     if plan.get("kind") in ("blocks", "built-in") and plan.get("precision") == "mixed":
         return "k_pcg_poisson_mixed"
     return "k_pcg_poisson_f2" if plan.get("resident") else "k_pcg_poisson_f1"
@@ -447,7 +448,7 @@ def _plan_dict(g, precision="fp64"):
     if cl:
         return dict(kind="cluster", ctas=cl)
     if tx and precision == "mixed":
-        return dict(kind="tiles, one barrier per iteration", tile=[tx, ty], tiles=ntiles)
+        return dict(kind="tiles, one barrier per iteration", tile=[tx, ty], tiles=ntiles, resident=bool(res))
     if tx:
         return dict(kind="tiles", tile=[tx, ty], tiles=ntiles, resident=bool(res))
     if mb:

@@ -201,14 +201,15 @@ ccm_status ccm_case_bytes(const ccm_config* cfg, size_t* bytes);
  * for a mixed case the one-barrier mixed solve; 0 where it does not apply or the built-in
  * plan is used), plan[4] = blocks of the mixed solve with a barrier per Chebyshev step (0:
  * built-in), plan[5] = CTAs of the one thread-block cluster that holds a small grid's whole
- * FP64 solve (0: not used), plan[6] = 1 when the FP64 tiles keep their vectors in shared
- * memory for the whole solve.  Valid after set_geometry. */
+ * FP64 solve (0: not used), plan[6] = 1 when the tiles (FP64 or mixed) keep their vectors
+ * in shared memory for the whole solve.  Valid after set_geometry. */
 ccm_status ccm_launch_plan(ccm_case c, int plan[7]);
 /* Sets the launch shape (same layout; zeros select the built-in shapes).  A tile plan needs a
  * width that is a power of two in 32..512 and the tile counts it implies (and, resident, tiles
  * that fit in shared memory at once); a cluster has 2, 4, 8 or 16 CTAs, at most ny, and
- * excludes a tile plan; a mixed case's tile plan selects the one-barrier mixed solve and
- * excludes the other entries.  CCM_E_INVALID otherwise.  Shapes apply to the single-case
+ * excludes a tile plan; a mixed case's tile plan selects the one-barrier mixed solve
+ * (resident or not: its tiles, bands and, resident, vectors must fit the GPU at once) and
+ * excludes block counts and clusters.  CCM_E_INVALID otherwise.  Shapes apply to the single-case
  * solve of a nonsingular system: the FP64 Jacobi solve (tiles, cluster) and the mixed solve
  * (tiles or blocks). */
 ccm_status ccm_set_launch_plan(ccm_case c, const int plan[7]);

@@ -389,6 +389,7 @@ void case_mixed1_solve(ccm_case c, const MixedSolve& a, const TilePlan& tp, Mixe
   f->S[0] = c->fp1; f->S[1] = c->fw1;
   f->P = c->fp0; f->U = c->fb; f->E = c->fx;
   f->TX = tp.TX; f->TY = tp.TY; f->nbx = tp.nbx; f->ntiles = tp.ntiles;
+  f->resident = tp.resident;
 }
 
 ccm_status solve_poisson_mixed(ccm_case c, double* x, double* b) {
@@ -879,7 +880,7 @@ ccm_status ccm_launch_plan(ccm_case c, int plan[7]) {
   plan[3] = tp.ntiles;
   plan[4] = c->tune.mixed_blocks;
   plan[5] = c->tune.cluster;
-  plan[6] = c->tune.plan.resident;
+  plan[6] = tp.resident;
   return CCM_OK;
 }
 
@@ -897,9 +898,13 @@ ccm_status ccm_set_launch_plan(ccm_case c, const int plan[7]) {
     const int nbx = (g.nx + tx - 1) / std::max(tx, 1);
     if (!pow2 || ty < 1 || plan[2] != nbx || plan[3] != nbx * ((g.ny + ty - 1) / ty))
       return fail(CCM_E_INVALID, "tile plan: width a power of two in 32..512, tiles = ceil(nx/w) ceil(ny/h)");
-    if (plan[6] != 0 || plan[5] != 0 || plan[4] != 0)
-      return fail(CCM_E_INVALID, "a mixed tile plan excludes resident tiles, clusters and block counts");
-    r.mixed1 = TilePlan{tx, ty, plan[2], plan[3], 0};
+    if (plan[5] != 0 || plan[4] != 0)
+      return fail(CCM_E_INVALID, "a mixed tile plan excludes clusters and block counts");
+    if (plan[6] != 0 && plan[6] != 1) return fail(CCM_E_INVALID, "resident must be 0 or 1");
+    const int deg = c->cfg.precond == CCM_CHEBYSHEV ? c->cfg.cheb_degree : 1;
+    if (!mixed1_plan_fits(tx, ty, plan[3], deg, plan[6]))
+      return fail(CCM_E_INVALID, "the mixed tiles (and, resident, their vectors) do not fit the GPU at once");
+    r.mixed1 = TilePlan{tx, ty, plan[2], plan[3], plan[6]};
     c->tune = r;
     return CCM_OK;
   }

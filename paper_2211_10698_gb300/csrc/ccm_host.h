@@ -183,10 +183,13 @@ struct Mixed1Solve {
   float* S[2];   // K~ p
   float *P, *U, *E;  // direction, preconditioned residual (Chebyshev), correction
   int TX, TY, nbx, ntiles;
+  int resident;      // 1: the tile's vectors in shared memory (k_pcg_poisson_m2)
 };
 cudaError_t run_poisson_mixed1(Mixed1Solve f, cudaStream_t st);
-size_t mixed1_smem(int TX, int TY, int cheb);
-// Tile plans of the one-barrier mixed solve that fit the GPU at once (cooperative launch).
+size_t mixed1_smem(int TX, int TY, int cheb, int resident);
+// Whether a tile plan of the one-barrier mixed solve fits the GPU at once (cooperative launch).
+bool mixed1_plan_fits(int TX, int TY, int ntiles, int cheb, int resident);
+// Tile plans of the one-barrier mixed solve that fit the GPU at once, resident ones first.
 std::vector<TilePlan> mixed1_plan_candidates(int nx, int ny, int cheb);
 
 // One case of a batched solve and its contiguous range of blocks (pcg_batch.cu).

@@ -234,7 +234,9 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* >= 32
 // Sum of the per-block partials (layout partials[k * nblocks + b]) in a fixed order; every
 // block computes the identical value.  Warp k reduces quantity k: each lane first issues all
 // of its loads (one L2 round trip for up to 32 * kGridSumPerLane blocks), then adds them in
-// a fixed order, then the warp's shuffle tree finishes.  Result broadcast through smem.
+// a fixed pairwise tree (four dependent adds instead of ten: the sum sits on every
+// iteration's serial path), then the warp's shuffle tree finishes.  Result broadcast through
+// smem.
 constexpr int kGridSumPerLane = 10;
 template <int NV>
 __device__ __forceinline__ void grid_sum(const double* partials, int nblocks, double (&out)[NV], double* smem) {
@@ -248,9 +250,11 @@ __device__ __forceinline__ void grid_sum(const double* partials, int nblocks, do
       const int b = lane + 32 * m;
       buf[m] = b < nblocks ? __ldcg(&src[b]) : 0.0;
     }
-    double s = 0.0;
 #pragma unroll
-    for (int m = 0; m < kGridSumPerLane; ++m) s += buf[m];
+    for (int h = 1; h < kGridSumPerLane; h <<= 1)
+#pragma unroll
+      for (int m = 0; m + h < kGridSumPerLane; m += 2 * h) buf[m] += buf[m + h];
+    double s = buf[0];
     for (int b = lane + 32 * kGridSumPerLane; b < nblocks; b += 32) s += __ldcg(&src[b]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);

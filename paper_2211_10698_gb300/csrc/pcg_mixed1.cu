@@ -60,7 +60,12 @@ __device__ __forceinline__ void grid_sum_f32_rows(const float* rows, int nb, flo
   for (int k = 0; k < NV; ++k) out[k] = smem[k];
 }
 
-__global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant__ Mixed1Solve f) {
+// RES: the tile's p, s, e and w stay in shared memory for the whole solve (k_pcg_poisson_m2),
+// and u (Chebyshev) stays in the region's last iterate; only the frame of own cells that the
+// neighbours' bands read (within h of the tile's edge) is published as r, w and s per
+// iteration.  Otherwise every own-cell vector lives in global memory (k_pcg_poisson_m1).
+template <bool RES>
+__device__ __forceinline__ void mixed1_body(const Mixed1Solve& f) {
   __shared__ double red[3][kNT];
   __shared__ float wred[3][kNT / 32];
   __shared__ double dsum[8];
@@ -88,6 +93,36 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
   float* const zb = dyn1 + 2 * RN;
   int8_t* const sk = reinterpret_cast<int8_t*>(dyn1 + (cheb > 1 ? 3 : 1) * RN);
   auto ridx = [&](int i, int j) -> int { return (j - j0 + h) * RX + (i - i0 + h); };
+  // RES: own-cell p, s, e, w after the row kinds (16-byte aligned)
+  float* const sown = dyn1 + (cheb > 1 ? 3 : 1) * RN + ((RN + 15) / 16) * 4;
+  float* const sp = sown;
+  float* const ss = sown + TX * TY;
+  float* const se = sown + 2 * TX * TY;
+  float* const sw = sown + 3 * TX * TY;
+  auto lidx = [&](int i, int j) -> int { return (j - j0) * TX + (i - i0); };
+  // own cells the neighbours' bands read
+  auto frame = [&](int i, int j) -> bool { return i < i0 + h || i >= i1 - h || j < j0 + h || j >= j1 - h; };
+  // u = M^-1 r after precond_apply: the last Chebyshev iterate, or r itself
+  float* const ubuf = cheb > 1 ? ((cheb & 1) ? za : zb) : sr;
+  // The band's cells inside the domain, numbered: the rows above the tile, the rows below
+  // (each over the band's columns), then the columns to its left and right (over the tile's
+  // rows).  band_cell(t) gives cell t; false for t >= nband.
+  const int b_ia = max(i0 - h, 0), b_ib = min(i1 + h, nx), b_ja = max(j0 - h, 0), b_jb = min(j1 + h, ny);
+  const int b_w = b_ib - b_ia, b_h = j1 - j0;
+  const int b_nt = (j0 - b_ja) * b_w, b_nb = (b_jb - j1) * b_w, b_nl = (i0 - b_ia) * b_h;
+  const int nband = active ? b_nt + b_nb + b_nl + (b_ib - i1) * b_h : 0;
+  auto band_cell = [&](int t, int& bi, int& bj) -> bool {
+    if (t >= nband) return false;
+    if (t < b_nt) { bj = b_ja + t / b_w; bi = b_ia + t % b_w; return true; }
+    t -= b_nt;
+    if (t < b_nb) { bj = j1 + t / b_w; bi = b_ia + t % b_w; return true; }
+    t -= b_nb;
+    if (t < b_nl) { bi = b_ia + t / b_h; bj = j0 + t % b_h; return true; }
+    t -= b_nl;
+    bi = i1 + t / b_h;
+    bj = j0 + t % b_h;
+    return true;
+  };
   const int8_t* __restrict__ kinds = d.kinds;
   const float* __restrict__ cus = a.cus32;
   const float* __restrict__ cvs = a.cvs32;
@@ -135,7 +170,12 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
     const int i = i0 + q % TX, j = j0 + q / TX;
     if (i >= i1 || j >= j1) continue;
     const size_t k = g.idx(i, j);
-    Pv[k] = 0.0f; Ev[k] = 0.0f; f.S[0][k] = 0.0f; f.S[1][k] = 0.0f;
+    if constexpr (RES) {
+      sp[q] = 0.0f; ss[q] = 0.0f; se[q] = 0.0f; sw[q] = 0.0f;
+    } else {
+      Pv[k] = 0.0f; Ev[k] = 0.0f;
+    }
+    f.S[0][k] = 0.0f; f.S[1][k] = 0.0f;
   }
   __syncthreads();
 
@@ -209,8 +249,13 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
       const size_t k = g.idx(i, j);
       const float uk = u[rq], rk = sr[rq];
       const float wk = krow(u, i, j, sk[rq]);
-      Wn[k] = wk;
-      if (cheb > 1) Uv[k] = uk;
+      if constexpr (RES) {
+        sw[lidx(i, j)] = wk;
+        if (frame(i, j)) Wn[k] = wk;
+      } else {
+        Wn[k] = wk;
+        if (cheb > 1) Uv[k] = uk;
+      }
       v[0] += rk * uk;
       v[1] += wk * uk;
       v[2] += rk * rk;
@@ -287,11 +332,19 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
       const int i = i0 + q % TX, j = j0 + q / TX;
       if (i >= i1 || j >= j1) continue;
       const size_t k = g.idx(i, j);
-      Rc[k] = (float)(sig * r64[k]);
+      const float rv = (float)(sig * r64[k]);
+      if constexpr (RES) {
+        sr[ridx(i, j)] = rv;
+        if (frame(i, j)) Rc[k] = rv;
+      } else {
+        Rc[k] = rv;
+      }
     }
     if (!grid_sync(d.bar, target)) return false;
     for (int q = threadIdx.x; q < RN; q += kNT) {
       const int i = i0 - h + q % RX, j = j0 - h + q / RX;
+      const bool own = i >= i0 && i < i1 && j >= j0 && j < j1;
+      if (RES && own) continue;  // already in sr
       sr[q] = (active && in_dom(i, j) && i < i1 + h && j < j1 + h) ? __ldcg(&Rc[g.idx(i, j)]) : 0.0f;
     }
     __syncthreads();
@@ -313,11 +366,21 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
       const int i = i0 + q % TX, j = j0 + q / TX;
       if (i >= i1 || j >= j1) continue;
       const size_t k = g.idx(i, j);
-      const float uk = cheb > 1 ? Uv[k] : Rc[k];
-      const float pk = uk + be * Pv[k];
-      const float sk_ = Wc[k] + be * Sc[k];
-      Pv[k] = pk;
-      Sc[k] = sk_;
+      float pk, sk_;
+      if constexpr (RES) {
+        const int l = lidx(i, j);
+        pk = ubuf[ridx(i, j)] + be * sp[l];
+        sk_ = sw[l] + be * ss[l];
+        sp[l] = pk;
+        ss[l] = sk_;
+        if (frame(i, j)) Sc[k] = sk_;
+      } else {
+        const float uk = cheb > 1 ? Uv[k] : Rc[k];
+        pk = uk + be * Pv[k];
+        sk_ = Wc[k] + be * Sc[k];
+        Pv[k] = pk;
+        Sc[k] = sk_;
+      }
       v[0] += pk * sk_;
     }
     const float* rows = reduce_arrive(v, 1);
@@ -340,8 +403,13 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
       const int i = i0 + q % TX, j = j0 + q / TX;
       if (i >= i1 || j >= j1) continue;
       const size_t k = g.idx(i, j);
-      x[k] += isd[k] * (double)Ev[k] * isig;
-      if (clear) Ev[k] = 0.0f;
+      if constexpr (RES) {
+        x[k] += isd[k] * (double)se[q] * isig;
+        if (clear) se[q] = 0.0f;
+      } else {
+        x[k] += isd[k] * (double)Ev[k] * isig;
+        if (clear) Ev[k] = 0.0f;
+      }
     }
   };
 
@@ -363,8 +431,30 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
     const float* __restrict__ Sc = f.S[cur];
     float* __restrict__ Rn = f.R[nxt];
     float* __restrict__ Sn = f.S[nxt];
-    // 1. own cells (warps take rows, lanes columns), kB of a lane's cells of a row at a time
-    // with all their loads issued first (one L2 round trip per group instead of one per cell)
+    // 1. own cells (warps take rows, lanes columns); RES: in shared memory, the frame
+    // published for the neighbours' bands
+    if constexpr (RES) {
+      for (int j = j0 + warp; j < j1; j += kW)
+        for (int i = i0 + lane; i < i1; i += 32) {
+          const int q = ridx(i, j), l = lidx(i, j);
+          const float rk = sr[q], uk = ubuf[q];
+          const float sold = ss[l], pold = sp[l];
+          const float sk_ = keep ? sold : sw[l] + be * sold;
+          const float pk = keep ? pold : uk + be * pold;
+          const float rn = rk - al * sk_;
+          sp[l] = pk;
+          ss[l] = sk_;
+          se[l] += al * pk;
+          sr[q] = rn;
+          if (frame(i, j)) {
+            const size_t k = g.idx(i, j);
+            Sn[k] = sk_;
+            Rn[k] = rn;
+          }
+        }
+    } else
+    // (global) kB of a lane's cells of a row at a time with all their loads issued first (one
+    // L2 round trip per group instead of one per cell)
     for (int j = j0 + warp; j < j1; j += kW)
     for (int ib = i0 + lane; ib < i1; ib += 32 * kB) {
       float rk[kB], sold[kB], pold[kB], wk[kB], ek[kB], uk[kB];
@@ -395,24 +485,16 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
         sr[rq[m]] = rn;
       }
     }
-    // band cells: r_{i+1} from the neighbours' vectors of this parity; rows above and below
-    // the tile (warps over rows, lanes over columns), then the columns either side (lanes
-    // over the 2h columns of a row)
-    auto band_at = [&](int i, int j) {
-      const size_t k = g.idx(i, j);
+    // band cells: r_{i+1} from the neighbours' vectors of this parity, published before the
+    // last grid barrier.  (Loading them at the top of the iteration, to overlap the own-cell
+    // update, gave wrong results with resident tiles for a reason not found; not used.)
+    for (int t = threadIdx.x; t < nband; t += kNT) {
+      int bi, bj;
+      band_cell(t, bi, bj);
+      const size_t k = g.idx(bi, bj);
       const float rk = __ldcg(&Rc[k]), wk = __ldcg(&Wc[k]), sold = __ldcg(&Sc[k]);
-      sr[ridx(i, j)] = rk - al * (keep ? sold : wk + be * sold);
-    };
-    for (int t = warp; t < 2 * h; t += kW) {
-      const int j = t < h ? j0 - h + t : j1 + (t - h);
-      if (j < 0 || j >= ny) continue;
-      for (int i = max(i0 - h, 0) + lane; i < min(i1 + h, nx); i += 32) band_at(i, j);
+      sr[ridx(bi, bj)] = rk - al * (keep ? sold : wk + be * sold);
     }
-    for (int j = j0 + warp; j < j1; j += kW)
-      if (lane < 2 * h) {
-        const int i = lane < h ? i0 - h + lane : i1 + (lane - h);
-        if (i >= 0 && i < nx) band_at(i, j);
-      }
     __syncthreads();
     // 2-3. preconditioner, w_{i+1} = K~ u_{i+1} and the sums
     float v[3] = {0.0f, 0.0f, 0.0f};
@@ -453,13 +535,22 @@ __global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant
   }
 }
 
-int mixed1_per_sm(size_t smem) {
+__global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m1(const __grid_constant__ Mixed1Solve f) {
+  mixed1_body<false>(f);
+}
+
+__global__ void __launch_bounds__(kNT, 1) k_pcg_poisson_m2(const __grid_constant__ Mixed1Solve f) {
+  mixed1_body<true>(f);
+}
+
+int mixed1_per_sm(size_t smem, int resident) {
   int dev = 0, per = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const void* kern = resident ? (const void*)k_pcg_poisson_m2 : (const void*)k_pcg_poisson_m1;
   if (smem > (size_t)optin ||
-      cudaFuncSetAttribute(k_pcg_poisson_m1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_poisson_m1, kNT, smem) != cudaSuccess) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kNT, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -468,11 +559,22 @@ int mixed1_per_sm(size_t smem) {
 
 }  // namespace
 
-// r, the two Chebyshev iterates (cheb > 1) and the row kinds of a tile and its band
-size_t mixed1_smem(int TX, int TY, int cheb) {
+// r, the two Chebyshev iterates (cheb > 1) and the row kinds of a tile and its band; resident:
+// then the tile's p, s, e and w
+size_t mixed1_smem(int TX, int TY, int cheb, int resident) {
   const int h = cheb > 1 ? cheb : 1;
   const size_t rn = (size_t)(TX + 2 * h) * (size_t)(TY + 2 * h);
-  return (cheb > 1 ? 3 : 1) * sizeof(float) * rn + rn;
+  const size_t base = (cheb > 1 ? 3 : 1) * sizeof(float) * rn;
+  if (!resident) return base + rn;
+  return base + ((rn + 15) / 16) * 16 + 4 * sizeof(float) * (size_t)TX * (size_t)TY;
+}
+
+bool mixed1_plan_fits(int TX, int TY, int ntiles, int cheb, int resident) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per = mixed1_per_sm(mixed1_smem(TX, TY, cheb, resident), resident);
+  return per >= 1 && ntiles >= 1 && ntiles <= sms * std::min(per, 2);
 }
 
 std::vector<TilePlan> mixed1_plan_candidates(int nx, int ny, int cheb) {
@@ -480,16 +582,17 @@ std::vector<TilePlan> mixed1_plan_candidates(int nx, int ny, int cheb) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  for (int blocks : {2 * sms, sms, sms / 2}) {
-    TilePlan p{};
-    fused_tiles(nx, ny, blocks, &p.TX, &p.TY, &p.nbx, &p.ntiles);
-    if (p.ntiles < 1) continue;
-    const int per = mixed1_per_sm(mixed1_smem(p.TX, p.TY, cheb));
-    if (per < 1 || p.ntiles > sms * std::min(per, 2)) continue;
-    bool seen = false;
-    for (const TilePlan& q : out) seen = seen || (q.TX == p.TX && q.TY == p.TY);
-    if (!seen) out.push_back(p);
-  }
+  for (int resident : {1, 0})
+    for (int blocks : {2 * sms, sms, sms / 2}) {
+      TilePlan p{};
+      fused_tiles(nx, ny, blocks, &p.TX, &p.TY, &p.nbx, &p.ntiles);
+      if (p.ntiles < 1) continue;
+      p.resident = resident;
+      if (!mixed1_plan_fits(p.TX, p.TY, p.ntiles, cheb, resident)) continue;
+      bool seen = false;
+      for (const TilePlan& q : out) seen = seen || (q.TX == p.TX && q.TY == p.TY && q.resident == resident);
+      if (!seen) out.push_back(p);
+    }
   return out;
 }
 
@@ -499,12 +602,13 @@ cudaError_t run_poisson_mixed1(Mixed1Solve f, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (f.TX == 0) fused_tiles(f.m.d.g.nx, f.m.d.g.ny, sms, &f.TX, &f.TY, &f.nbx, &f.ntiles);
   const int cheb = f.m.cheb > 1 ? f.m.cheb : 1;
-  const size_t smem = mixed1_smem(f.TX, f.TY, cheb);
-  const int per = mixed1_per_sm(smem);
+  const size_t smem = mixed1_smem(f.TX, f.TY, cheb, f.resident);
+  const int per = mixed1_per_sm(smem, f.resident);
   if (f.ntiles < 1 || per < 1 || f.ntiles > sms * std::min(per, 2)) return cudaErrorInvalidConfiguration;
   cudaMemsetAsync(f.m.d.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
   void* params[] = {&f};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg_poisson_m1, f.ntiles, kNT, params, smem, st);
+  const void* kern = f.resident ? (const void*)k_pcg_poisson_m2 : (const void*)k_pcg_poisson_m1;
+  return cudaLaunchCooperativeKernel(kern, f.ntiles, kNT, params, smem, st);
 }
 
 }  // namespace ccm

@@ -55,11 +55,12 @@ def test_mixed_block_count(precond):
     plain = ccm.Case(_case(160, 64, "mixed", 0, precond))
     plan = tuned.launch_plan()
     if plan[0]:
-        # the one-barrier mixed solve's tiles (pcg_mixed1.cu), which exclude a block count
+        # the one-barrier mixed solve's tiles (pcg_mixed1.cu), vectors resident or not, which
+        # exclude a block count and a cluster
         tx, ty, nbx, ntiles = plan[:4]
         assert tx in (32, 64, 128, 256, 512) and ty >= 1
         assert nbx == -(-160 // tx) and ntiles == nbx * -(-64 // ty)
-        assert plan[4:] == (0, 0, 0)
+        assert plan[4:6] == (0, 0) and plan[6] in (0, 1)
     else:
         assert plan[:4] == (0, 0, 0, 0) and plan[5:] == (0, 0) and plan[4] >= 1
     assert ccm.Case(_case(160, 64, "mixed", 1, precond)).launch_plan() == plan

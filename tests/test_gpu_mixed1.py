@@ -1,6 +1,7 @@
 """The mixed-precision Poisson solve with one grid barrier per iteration (pcg_mixed1.cu), forced
-through a mixed tile plan: FP32 CG on the Jacobi-scaled system (Jacobi or Chebyshev of degree
-k, the band of width k recomputed per tile) with FP64 residual replacements.
+through a mixed tile plan, the tile's vectors in global or in shared memory: FP32 CG on the
+Jacobi-scaled system (Jacobi or Chebyshev of degree k, the band of width k recomputed per
+tile) with FP64 residual replacements.
 
 Checked through the C ABI against the oracle (Eq. pm_poisson): the solution's residual under
 the oracle's FP64 operator meets the tolerance, the solution agrees with the oracle's tight
@@ -21,9 +22,9 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def _plan(nx, ny, tx, ty):
+def _plan(nx, ny, tx, ty, resident=0):
     nbx = -(-nx // tx)
-    return (tx, ty, nbx, nbx * -(-ny // ty), 0, 0, 0)
+    return (tx, ty, nbx, nbx * -(-ny // ty), 0, 0, resident)
 
 
 def _case(nx, ny, precond, degree, tol=1e-10):
@@ -37,13 +38,14 @@ GRIDS = [(128, 64, 64, 8), (53, 31, 32, 8), (256, 128, 64, 16)]
 PRECS = [("jacobi", 1), ("chebyshev", 2), ("chebyshev", 3), ("chebyshev", 4)]
 
 
+@pytest.mark.parametrize("resident", [0, 1])
 @pytest.mark.parametrize("nx,ny,tx,ty", GRIDS)
 @pytest.mark.parametrize("precond,degree", PRECS)
-def test_one_barrier_mixed_solve_against_oracle(orc, nx, ny, tx, ty, precond, degree):
+def test_one_barrier_mixed_solve_against_oracle(orc, nx, ny, tx, ty, precond, degree, resident):
     case = _case(nx, ny, precond, degree)
     g = ccm.Case(case)
-    g.set_launch_plan(_plan(nx, ny, tx, ty))
-    assert g.launch_plan()[:4] == _plan(nx, ny, tx, ty)[:4]
+    g.set_launch_plan(_plan(nx, ny, tx, ty, resident))
+    assert g.launch_plan() == _plan(nx, ny, tx, ty, resident)
     o = orc.Oracle(case)
     rhs = np.random.default_rng(11).standard_normal(case.shape) * o.active
     st = g.solve_pressure(rhs)
@@ -65,13 +67,14 @@ def test_one_barrier_mixed_solve_against_oracle(orc, nx, ny, tx, ty, precond, de
     g2.close()
 
 
+@pytest.mark.parametrize("resident", [0, 1])
 @pytest.mark.parametrize("precond,degree", [("jacobi", 1), ("chebyshev", 3)])
-def test_one_barrier_mixed_steps_against_oracle(orc, precond, degree):
+def test_one_barrier_mixed_steps_against_oracle(orc, precond, degree, resident):
     """Six projection steps of a 128x64 cylinder: mixed precision with the one-barrier solve
     against the FP64 oracle with tight tolerances, 1e-8 on u, v and P."""
     case = _case(128, 64, precond, degree)
     g = ccm.Case(case)
-    g.set_launch_plan(_plan(128, 64, 64, 8))
+    g.set_launch_plan(_plan(128, 64, 64, 8, resident))
     st = g.step(6)
     assert st["converged"]
     ocase = copy.deepcopy(case)
@@ -91,5 +94,29 @@ def test_one_barrier_mixed_plan_validation():
     with pytest.raises(ccm.CcmError):
         g.set_launch_plan((48, 8, 3, 24, 0, 0, 0))  # width not a power of two
     with pytest.raises(ccm.CcmError):
-        g.set_launch_plan(_plan(128, 64, 64, 8)[:4] + (0, 0, 1))  # resident tiles are FP64 only
+        g.set_launch_plan(_plan(128, 64, 64, 8)[:4] + (0, 0, 2))  # resident is 0 or 1
+    with pytest.raises(ccm.CcmError):
+        g.set_launch_plan(_plan(128, 64, 64, 8)[:4] + (0, 4, 0))  # tiles exclude a cluster
+    with pytest.raises(ccm.CcmError):
+        g.set_launch_plan((512, 512, 1, 1, 0, 0, 1))  # a 512x512 resident tile does not fit
     g.close()
+
+
+@pytest.mark.parametrize("precond,degree", [("jacobi", 1), ("chebyshev", 3)])
+def test_resident_tiles_match_global_tiles(precond, degree):
+    """The same tiles with their vectors in shared memory (k_pcg_poisson_m2) and in global
+    memory (k_pcg_poisson_m1) run the same arithmetic in the same order: equal iteration
+    counts and fields to rounding."""
+    case = _case(256, 128, precond, degree)
+    res = ccm.Case(case)
+    res.set_launch_plan(_plan(256, 128, 64, 16, 1))
+    glob = ccm.Case(case)
+    glob.set_launch_plan(_plan(256, 128, 64, 16, 0))
+    st_r = res.step(3)
+    st_g = glob.step(3)
+    assert st_r["converged"] and st_g["converged"]
+    assert st_r["iters_p"] == st_g["iters_p"]
+    for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P):
+        assert _rel(res.get_field(f), glob.get_field(f)) < 1e-12, f
+    res.close()
+    glob.close()
