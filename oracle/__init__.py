@@ -109,6 +109,8 @@ def _load():
                                    POINTER(OrcStats)]),
             "orc_step_gd": (c_int, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP, _DP, _DP, _DP, _DP,
                                     POINTER(OrcStats)]),
+            "orc_step_gdt": (c_int, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP, c_int, _DP, _DP, _DP, _DP, _DP, _DP,
+                                     _DP, _DP, _DP, POINTER(OrcStats)]),
             "orc_body_force_d": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP, _DP]),
             "orc_conservation": (None, [cp, _DP, _DP, _DP, _DP, _DP, _DP]),
             "orc_poisson_precondition": (None, [cp, _DP, _DP, _DP]),
@@ -351,13 +353,23 @@ class Oracle:
         for _ in range(nsteps):
             us, vs, bd = (self.z(), self.z(), self.z()) if keep else (None, None, None)
             # st may carry a body acceleration "gx" (u-faces), "gy" (v-faces), Eq. pm_prediction's rho V g,
-            # and the body's steady Dirichlet velocity "Dx" (per u-cell), "Dy" (per v-cell)
+            # and the body's Dirichlet velocity "Dx" (per u-cell), "Dy" (per v-cell); with "motion"
+            # (a0, a1, omega, phase) the body velocity at step n is D0 times the factor
+            # inputs.body_motion_factor gives for t = n dt (D0 = Dx, Dy), else it is steady
             gx, gy = st.get("gx"), st.get("gy")
-            Dx, Dy = st.get("Dx"), st.get("Dy")
-            ok = self.lib.orc_step_gd(ctypes.byref(self.s), _p(self.caps), _p(st["u"]), _p(st["v"]), _p(st["p"]),
-                                      _p(st["phi"]), _p(st["cu"]), _p(st["cv"]), 1 if st["n"] == 0 else 0,
-                                      _p(self._c(gx)), _p(self._c(gy)), _p(self._c(Dx)), _p(self._c(Dy)),
-                                      _p(us), _p(vs), _p(bd), ctypes.byref(stats))
+            Dx, Dy = self._c(st.get("Dx")), self._c(st.get("Dy"))
+            motion = st.get("motion")
+            if motion is None or Dx is None:
+                Dxn, Dyn, Dx1, Dy1 = Dx, Dy, Dx, Dy
+            else:
+                from paper_2211_10698_gb300.inputs import body_motion_factor
+                fn = body_motion_factor(motion, st["n"], self.case.dt)
+                f1 = body_motion_factor(motion, st["n"] + 1, self.case.dt)
+                Dxn, Dyn, Dx1, Dy1 = fn * Dx, fn * Dy, f1 * Dx, f1 * Dy
+            ok = self.lib.orc_step_gdt(ctypes.byref(self.s), _p(self.caps), _p(st["u"]), _p(st["v"]), _p(st["p"]),
+                                       _p(st["phi"]), _p(st["cu"]), _p(st["cv"]), 1 if st["n"] == 0 else 0,
+                                       _p(self._c(gx)), _p(self._c(gy)), _p(Dxn), _p(Dyn), _p(Dx1), _p(Dy1),
+                                       _p(us), _p(vs), _p(bd), ctypes.byref(stats))
             st["n"] += 1
             hist.append(dict(iters_h=stats.iters_h, iters_p=stats.iters_p, res_h=stats.res_h,
                              res_p=stats.res_p, max_div=stats.max_div, kinetic=stats.kinetic,

@@ -1446,9 +1446,14 @@ void orc_init_velocity(const orc_case* c, const double* caps, double u0, double 
  * conv^n in cnu, cnv. */
 /* The same with the body-force term rho V_alpha g_alpha of Eq. pm_prediction; gx at u-faces and
  * gy at v-faces (accelerations, padded layout) may be NULL (g = 0). */
-void orc_predictor_rhs_gd(const orc_case* c, const double* caps, double* u, double* v, const double* p,
-                          const double* cu, const double* cv, int first, const double* gx, const double* gy,
-                          const double* Dx, const double* Dy, double* ru, double* rv, double* cnu, double* cnv) {
+/* The body velocity may change in time: D^n (Dxn, Dyn) enters conv^n and the explicit half
+ * visc(mu S^n), S^n = strain(U^n, D^n); D^{n+1} (Dx1, Dy1) enters the implicit half through its
+ * lifting, S* = strain(U*, D^{n+1}) (Sec. 4.6: the boundary data of U* are those of the next
+ * time level).  conv^{n-1} (cu, cv) was formed in the previous step with D^{n-1}. */
+void orc_predictor_rhs_gdt(const orc_case* c, const double* caps, double* u, double* v, const double* p,
+                           const double* cu, const double* cv, int first, const double* gx, const double* gy,
+                           const double* Dxn, const double* Dyn, const double* Dx1, const double* Dy1, double* ru,
+                           double* rv, double* cnu, double* cnv) {
   size_t S = SIZE(c);
   double* gu = malloc(S * sizeof(double));
   double* gv = malloc(S * sizeof(double));
@@ -1460,18 +1465,18 @@ void orc_predictor_rhs_gd(const orc_case* c, const double* caps, double* u, doub
   const double* Vv = CAP(c, caps, G_V, K_V);
   double rho = c->rho, dt = c->dt, mu = c->mu;
   fill_bc(c, u, v, 1.0);
-  conv_bc(c, caps, u, v, Dx, Dy, cnu, cnv);
+  conv_bc(c, caps, u, v, Dxn, Dyn, cnu, cnv);
   const double* pu = first ? cnu : cu;
   const double* pv = first ? cnv : cv;
   orc_pres_bc(c, caps, p, gu, gv);
-  visc_bc(c, caps, u, v, Dx, Dy, vu, vv);
+  visc_bc(c, caps, u, v, Dxn, Dyn, vu, vv);
   /* lifting of the implicit half: visc(mu S(0, D^{n+1})) from the box boundary values and the
-   * body's Dirichlet data (D^{n+1} = D^n: steady) */
+   * body's Dirichlet data of the next time level */
   {
     double* zu = calloc(S, sizeof(double));
     double* zv = calloc(S, sizeof(double));
     fill_bc(c, zu, zv, 1.0);
-    visc_bc(c, caps, zu, zv, Dx, Dy, lu, lv);
+    visc_bc(c, caps, zu, zv, Dx1, Dy1, lu, lv);
     free(zu); free(zv);
   }
   PAR_FOR
@@ -1490,6 +1495,12 @@ void orc_predictor_rhs_gd(const orc_case* c, const double* caps, double* u, doub
   free(gu); free(gv); free(vu); free(vv); free(lu); free(lv);
 }
 
+void orc_predictor_rhs_gd(const orc_case* c, const double* caps, double* u, double* v, const double* p,
+                          const double* cu, const double* cv, int first, const double* gx, const double* gy,
+                          const double* Dx, const double* Dy, double* ru, double* rv, double* cnu, double* cnv) {
+  orc_predictor_rhs_gdt(c, caps, u, v, p, cu, cv, first, gx, gy, Dx, Dy, Dx, Dy, ru, rv, cnu, cnv);
+}
+
 void orc_predictor_rhs_g(const orc_case* c, const double* caps, double* u, double* v, const double* p,
                          const double* cu, const double* cv, int first, const double* gx, const double* gy,
                          double* ru, double* rv, double* cnu, double* cnv) {
@@ -1502,11 +1513,14 @@ void orc_predictor_rhs(const orc_case* c, const double* caps, double* u, double*
 }
 
 /* One PmII step with the body acceleration g (gx at u-faces, gy at v-faces; NULL: g = 0) and
- * the body's steady Dirichlet velocity D (Dx per u-cell, Dy per v-cell; NULL: no-slip, D = 0)
- * in Eqs. divergence, diag/offdiag (through visc) and convective. */
-int orc_step_gd(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
-                double* cv, int first, const double* gx, const double* gy, const double* Dx, const double* Dy,
-                double* ustar, double* vstar, double* bdiv, orc_stats* st) {
+ * the body's Dirichlet velocity D (per u-cell and per v-cell; NULL: no-slip, D = 0) in Eqs.
+ * divergence, diag/offdiag (through visc) and convective, at two time levels: D^n (Dxn, Dyn)
+ * in conv^n and S^n, D^{n+1} (Dx1, Dy1) in S*, on the faces of U* whose control volume holds
+ * no fluid, in cont(U*, D^{n+1}) (Eq. pm_poisson) and in the reported max |cont(U^{n+1},
+ * D^{n+1})|. */
+int orc_step_gdt(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
+                 double* cv, int first, const double* gx, const double* gy, const double* Dxn, const double* Dyn,
+                 const double* Dx1, const double* Dy1, double* ustar, double* vstar, double* bdiv, orc_stats* st) {
   size_t S = SIZE(c);
   double* cnu = malloc(S * sizeof(double));
   double* cnv = malloc(S * sizeof(double));
@@ -1523,7 +1537,7 @@ int orc_step_gd(const orc_case* c, const double* caps, double* u, double* v, dou
   const double* Vp = CAP(c, caps, G_P, K_V);
   double rho = c->rho, dt = c->dt, mu = c->mu;
 
-  orc_predictor_rhs_gd(c, caps, u, v, p, cu, cv, first, gx, gy, Dx, Dy, ru, rv, cnu, cnv);
+  orc_predictor_rhs_gdt(c, caps, u, v, p, cu, cv, first, gx, gy, Dxn, Dyn, Dx1, Dy1, ru, rv, cnu, cnv);
   for (size_t k = 0; k < S; ++k) {
     xu[k] = u[k];
     xv[k] = v[k];
@@ -1536,13 +1550,13 @@ int orc_step_gd(const orc_case* c, const double* caps, double* u, double* v, dou
     for (int i = -1; i <= c->nx + 1; ++i) {
       size_t k = (size_t)(j + 1) * PITCH(c) + (size_t)(i + 1);
       int r_u = role_u(c, caps, i, j), r_v = role_v(c, caps, i, j);
-      if (r_u == 3) u[k] = xu[k]; else if (r_u == 2) u[k] = Dx ? Dx[k] : 0.0;
-      if (r_v == 3) v[k] = xv[k]; else if (r_v == 2) v[k] = Dy ? Dy[k] : 0.0;
+      if (r_u == 3) u[k] = xu[k]; else if (r_u == 2) u[k] = Dx1 ? Dx1[k] : 0.0;
+      if (r_v == 3) v[k] = xv[k]; else if (r_v == 2) v[k] = Dy1 ? Dy1[k] : 0.0;
     }
   fill_bc(c, u, v, 1.0);
   if (ustar) memcpy(ustar, u, S * sizeof(double));
   if (vstar) memcpy(vstar, v, S * sizeof(double));
-  orc_cont(c, caps, u, v, Dx, Dy, b);
+  orc_cont(c, caps, u, v, Dx1, Dy1, b);
   if (bdiv) memcpy(bdiv, b, S * sizeof(double));
   double* rhs = malloc(S * sizeof(double));
   for (size_t k = 0; k < S; ++k) rhs[k] = -(rho / dt) * b[k];
@@ -1570,11 +1584,18 @@ int orc_step_gd(const orc_case* c, const double* caps, double* u, double* v, dou
   memcpy(cv, cnv, S * sizeof(double));
   st->conv_h = ok_h;
   st->conv_p = ok_p;
-  st->max_div = max_div_d(c, caps, u, v, Dx, Dy);
+  st->max_div = max_div_d(c, caps, u, v, Dx1, Dy1);
   st->kinetic = orc_kinetic(c, caps, u, v);
   free(cnu); free(cnv); free(gu); free(gv);
   free(ru); free(rv); free(xu); free(xv); free(b); free(kp);
   return ok_h && ok_p;
+}
+
+/* The same with a steady body velocity D (both time levels the same). */
+int orc_step_gd(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,
+                double* cv, int first, const double* gx, const double* gy, const double* Dx, const double* Dy,
+                double* ustar, double* vstar, double* bdiv, orc_stats* st) {
+  return orc_step_gdt(c, caps, u, v, p, phi, cu, cv, first, gx, gy, Dx, Dy, Dx, Dy, ustar, vstar, bdiv, st);
 }
 
 int orc_step_g(const orc_case* c, const double* caps, double* u, double* v, double* p, double* phi, double* cu,

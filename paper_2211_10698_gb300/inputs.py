@@ -438,6 +438,32 @@ def circle_boundary_points(X, Y, cx: float, cy: float, r: float):
     return cx + r * dx / d, cy + r * dy / d
 
 
+def body_motion_factor(motion, n: int, dt: float) -> float:
+    """The prescribed time law of a body velocity D(t) = D0 f(t): with motion = (a0, a1, omega,
+    phase), f = a0 + a1 sin(omega t + phase) at t = n dt (the time of step n).  Boundary data,
+    evaluated the same way by the library (ccm_set_body_motion)."""
+    a0, a1, omega, phase = motion
+    t = float(n) * dt
+    return a0 + a1 * math.sin(omega * t + phase)
+
+
+def rotation_velocity(Xu, Yu, Xv, Yv, cx: float, cy: float, r: float, omega: float = 1.0):
+    """(Dx per u-cell, Dy per v-cell) of a circle of radius r about (cx, cy) turning at the
+    angular velocity omega, sampled at the boundary points of the control volumes whose fluid
+    centroids are (Xu, Yu), (Xv, Yv)."""
+    xu, yu = circle_boundary_points(Xu, Yu, cx, cy, r)
+    xv, yv = circle_boundary_points(Xv, Yv, cx, cy, r)
+    return -omega * (yu - cy), omega * (xv - cx)
+
+
+def transpiration_velocity(Xu, Yu, Xv, Yv, cx: float, cy: float, r: float, w: float = 1.0):
+    """(Dx, Dy) of a porous circle that blows out (w > 0) or sucks in at the normal speed w,
+    sampled like rotation_velocity."""
+    xu, yu = circle_boundary_points(Xu, Yu, cx, cy, r)
+    xv, yv = circle_boundary_points(Xv, Yv, cx, cy, r)
+    return w * (xu - cx) / r, w * (yv - cy) / r
+
+
 def vortex_body_velocity(case: Case, Xu, Yu, Xv, Yv):
     """(Dx per u-cell, Dy per v-cell): the vortex's velocity on the cylinder, sampled at the
     boundary points of the u- and v-control volumes whose centroids are (Xu, Yu), (Xv, Yv)."""
