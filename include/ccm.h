@@ -25,7 +25,8 @@
  *    iterates are kept at zero mean, end of Sec. 4.6).
  *  - The immersed body is fixed and must stay two cells away from every box side.  It is
  *    no-slip (Dirichlet data D = 0 in Eqs. divergence, diag, offdiag, convective) unless the
- *    fields CCM_F_DX / CCM_F_DY give it a steady velocity D (a rotating or sliding body).
+ *    fields CCM_F_DX / CCM_F_DY give its wall a velocity D (a rotating, sliding or porous
+ *    body), steady or, through ccm_set_body_motion, scaled by a prescribed function of time.
  */
 #ifndef CCM_H
 #define CCM_H
@@ -137,7 +138,7 @@ typedef struct {
   long long iters_p, iters_h; /* PCG iterations summed over the steps */
   int last_iters_p, last_iters_h;
   double last_res_p, last_res_h;
-  double max_div;             /* max |cont(U^{n+1}, D)| over active cells after the last step */
+  double max_div;             /* max |cont(U^{n+1}, D^{n+1})| over active cells after the last step */
   double kinetic;             /* sum over velocity positions of V U^2 / 2 after the last step */
   int converged;              /* every solve of every step converged */
   double mass;                /* sum of cont(U^{n+1}, D) over the box cells: the net volume flux through the
@@ -156,16 +157,18 @@ enum {
   CCM_F_CONV_V = 5,
   CCM_F_USTAR = 6,            /* predicted velocity U* of the last step (read only) */
   CCM_F_VSTAR = 7,
-  CCM_F_DIV = 8,              /* cont(U*, D) of the last step (read only) */
+  CCM_F_DIV = 8,              /* cont(U*, D^{n+1}) of the last step (read only) */
   CCM_F_STEP = 9,             /* first element: number of steps taken (as a double) */
   CCM_F_GX = 10,              /* body acceleration g_x at u-faces, the rho V g term of Eq. pm_prediction
                                  (zero unless set; steady: it applies to every later step) */
   CCM_F_GY = 11,              /* body acceleration g_y at v-faces */
-  CCM_F_DX = 12,              /* the body's steady Dirichlet velocity D_x, one value per u-cell (the velocity of
-                                 the body on the boundary inside that u-control volume; zero: no-slip) in the
+  CCM_F_DX = 12,              /* the body's Dirichlet velocity D_x, one value per u-cell (the velocity of the
+                                 body on the boundary inside that u-control volume; zero: no-slip) in the
                                  heterogeneous terms of Eqs. divergence, diag/offdiag and convective.  Setting D
-                                 computes those terms once (the body is fixed, D steady) and gives the faces whose
-                                 control volume holds no fluid the value D.  It should have no normal component. */
+                                 computes those terms once (the body is fixed; they are linear in D) and gives the
+                                 faces whose control volume holds no fluid the value D.  With a time law
+                                 (ccm_set_body_motion) this field is D0 and the body velocity is f(t) D0.  In a
+                                 box without an outflow side D must carry no net flux. */
   CCM_F_DY = 13,              /* D_y, one value per v-cell */
   CCM_F_CAP = 16              /* + 9*g + k: capacity k of grid g (read only), g: 0 p, 1 u,
                                  2 v; k: 0 V, 1 X, 2 Y, 3 Ax, 4 Ay, 5 Wx, 6 Wy, 7 Bx, 8 By
@@ -265,6 +268,18 @@ ccm_status ccm_step(ccm_case c, int nsteps, ccm_step_stats* stats);
  * cluster barrier and is not affected.  CCM_E_INVALID for budget_cycles < 0 or
  * absent_block < -1. */
 ccm_status ccm_set_barrier_fault(ccm_case c, long long budget_cycles, int absent_block);
+
+/* Time law of the body velocity (Sec. 4.6, Eq. pm_prediction and the boundary condition of U*
+ * that follows it: conv and S^n take D^n, S* and cont(U*, D^{n+1}) of Eq. pm_poisson take the
+ * next level D^{n+1}).  From the next step on the body velocity is D(t) = f(t) D0 with
+ *     f(t) = a0 + a1 sin(omega t + phase),  t = n dt at step n (the CCM_F_STEP counter),
+ * and D0 the field set through CCM_F_DX / CCM_F_DY (no effect while none is set).  Every
+ * D-term is the steady term of D0 scaled by f (the convective bracket by f and f^2), so a step
+ * costs the same as with a steady D.  The faces without fluid of the present state take f(t_n)
+ * D0 now.  a0 = 1, a1 = 0 restores the steady D = D0.  CCM_E_INVALID for a non-finite
+ * parameter.  A case with a time law cannot join a batch (ccm_batch_add and ccm_batch_step
+ * return CCM_E_INVALID). */
+ccm_status ccm_set_body_motion(ccm_case c, double a0, double a1, double omega, double phase);
 
 /* Enqueue nsteps projection steps on the case's stream and return without waiting; the
  * statistics accumulate on the device until ccm_read_stats.  Same state rules as

@@ -108,6 +108,7 @@ def lib():
                                           POINTER(c_longlong)]),
             "ccm_solve_pressure_noalloc": (c_int, [cp, c_void_p, c_void_p, POINTER(ccm_solve_stats)]),
             "ccm_set_barrier_fault": (c_int, [cp, c_longlong, c_int]),
+            "ccm_set_body_motion": (c_int, [cp, c_double, c_double, c_double, c_double]),
             "ccm_measure_fp64_rate": (c_int, [_DP]),
             "ccm_batch_create": (c_int, [c_int, c_void_p, POINTER(c_void_p)]),
             "ccm_batch_destroy": (c_int, [cp]),
@@ -291,6 +292,11 @@ class Case:
         allow = (CCM_E_NOT_CONVERGED,) if allow_not_converged else ()
         _check(lib().ccm_read_stats(self.h, ctypes.byref(st)), allow)
         return {f: getattr(st, f) for f, _ in ccm_step_stats._fields_}
+
+    def set_body_motion(self, a0, a1, omega, phase):
+        """Body velocity D(t) = (a0 + a1 sin(omega t + phase)) D0 from the next step on, with D0
+        the field set through CCM_F_DX / CCM_F_DY and t = n dt at step n."""
+        _check(lib().ccm_set_body_motion(self.h, float(a0), float(a1), float(omega), float(phase)))
 
     def body_force(self):
         """(Fp_x, Fp_y, Fv_x, Fv_y): pressure and viscous force of the fluid on the body at the

@@ -101,6 +101,10 @@ struct ccm_case_s {
   // the body's Dirichlet velocity D and its constant terms: one allocation of 8 padded arrays,
   // made when D is first set (Dx, Dy, h, S_xx, S_yy, S_xy, visc_u, visc_v)
   double* dblock = nullptr;
+  // time law of the body velocity, D(t) = D0 (a0 + a1 sin(omega t + phase)) at t = n dt with D0
+  // the field in dblock; steady (D = D0) unless ccm_set_body_motion made it otherwise
+  bool moving = false;
+  double motion[4] = {1.0, 0.0, 0.0, 0.0};
   double* fhist = nullptr;
   int fcap = 0;
   long long frec = 0;
@@ -594,6 +598,13 @@ void collect_timing(ccm_case c) {
 }  // namespace
 
 extern "C" {
+// The factor f of the body velocity D = f D0 at the time t = n dt of step n (1 when steady).
+static double motion_factor(ccm_case c, long long n) {
+  if (!c->moving) return 1.0;
+  const double t = (double)n * c->ph.dt;
+  return c->motion[0] + c->motion[1] * std::sin(c->motion[2] * t + c->motion[3]);
+}
+
 static ccm_status stage_predict(ccm_case c);
 static void stage_project(ccm_case c);
 static ccm_status finish_stats(ccm_case c, ccm_step_stats* stats);
@@ -655,6 +666,7 @@ void case_stage_case(ccm_case c, StageCase* e, int ahead) {
 int case_cur(ccm_case c) { return c->cur; }
 unsigned long long case_serial(ccm_case c) { return c->serial; }
 bool case_has_extras(ccm_case c) { return c->forced || c->dblock != nullptr; }
+bool case_is_moving(ccm_case c) { return c->moving; }
 long long case_nstep(ccm_case c) { return c->nstep; }
 void case_helm_solve(ccm_case c, HelmCSolve* a) { helm_solve_of(c, a); }
 // Host bookkeeping of a step whose stages ran batched (as stage_project does for one case).
@@ -1103,7 +1115,8 @@ ccm_status ccm_set_field(ccm_case c, int field, const double* host, size_t count
   const dim3 b(64, 4);
   if (field == CCM_F_U || field == CCM_F_V) {
     // faces whose control volume holds no fluid carry the body's velocity (zero: no-slip)
-    launch_inactive_to_body(c->g, c->co.role_u, c->co.role_v, c->cv.dx, c->cv.dy, c->u, c->v, c->st);
+    launch_inactive_to_body(c->g, c->co.role_u, c->co.role_v, c->cv.dx, c->cv.dy, c->u, c->v, c->st,
+                            motion_factor(c, c->nstep));
     launch_fill_bc(c->g, c->bc, c->u, c->v, 1.0, c->st);
   }
   if (body) {
@@ -1111,7 +1124,8 @@ ccm_status ccm_set_field(ccm_case c, int field, const double* host, size_t count
     launch_body_dterms(c->g, c->bc, c->caps, c->cv, c->cv.dx, c->cv.dy, (double*)c->cv.hd, (double*)c->cv.sxxd,
                        (double*)c->cv.syyd, (double*)c->cv.sxyd, (double*)c->cv.viscdu, (double*)c->cv.viscdv,
                        c->st);
-    launch_inactive_to_body(c->g, c->co.role_u, c->co.role_v, c->cv.dx, c->cv.dy, c->u, c->v, c->st);
+    launch_inactive_to_body(c->g, c->co.role_u, c->co.role_v, c->cv.dx, c->cv.dy, c->u, c->v, c->st,
+                            motion_factor(c, c->nstep));
   }
   if (field == CCM_F_P || field == CCM_F_PHI) {
     // only active cells carry pressure; the ghost ring stays zero (periodic sides: images)
@@ -1228,11 +1242,19 @@ static ccm_status stage_predict(ccm_case c) {
   const Geom& g = c->g;
   cudaStream_t st = c->st;
   const int prev = c->cur, next = 1 - c->cur;
+  // D^n in conv^n and S^n, D^{n+1} in the implicit half's lift and in cont(U*, D^{n+1})
+  c->ph.dn = motion_factor(c, c->nstep);
+  c->ph.dn1 = motion_factor(c, c->nstep + 1);
   launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
   launch_predictor_rhs(c->cv, g, c->bc, c->ph, c->u, c->v, c->p, c->cnu[prev], c->cnv[prev], c->cnu[next],
                        c->cnv[next], c->rhs_u, c->rhs_v, c->nstep == 0 ? 1 : 0, st);
   ccm_status s;
   if ((s = solve_helmholtz(c)) != CCM_OK) return s;
+  // the faces of U* without fluid carry the next level's body velocity
+  if (c->moving && c->dblock) {
+    launch_inactive_to_body(g, c->co.role_u, c->co.role_v, c->cv.dx, c->cv.dy, c->u, c->v, st, c->ph.dn1);
+    c->launches += 1;
+  }
   launch_fill_bc(g, c->bc, c->u, c->v, 1.0, st);
   CUDA_TRY(cudaMemcpyAsync(c->ustar, c->u, g.count() * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(c->vstar, c->v, g.count() * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1250,7 +1272,9 @@ static void stage_project(ccm_case c) {
   c->launches += 7;  // fill_bc x3, predictor, Helmholtz PCG, divergence, projection
   if (c->fcap > 0) {
     // the force of the new state (U^{n+1}, P^{n+1/2}) into the next row of the record
-    launch_body_force(c->cv, g, c->ph, c->u, c->v, c->p, c->fpart, c->fhist + 4 * (c->frec % c->fcap), st);
+    Phys pf = c->ph;
+    pf.dn = motion_factor(c, c->nstep + 1);
+    launch_body_force(c->cv, g, pf, c->u, c->v, c->p, c->fpart, c->fhist + 4 * (c->frec % c->fcap), st);
     c->frec++;
     c->launches += 2;
   }
@@ -1310,7 +1334,7 @@ static ccm_status enqueue_steps(ccm_case c, int nsteps) {
 static ccm_status finish_stats(ccm_case c, ccm_step_stats* stats) {
   const Geom& g = c->g;
   launch_diagnostics(c->cv, g, c->caps.a[cap_slot(1, CK_V)], c->caps.a[cap_slot(2, CK_V)], c->u, c->v, c->dpart,
-                     c->ds->diag, c->st);
+                     c->ds->diag, c->st, motion_factor(c, c->nstep));
   DevStats h{};
   ccm_status s;
   if ((s = read_stats(c, h)) != CCM_OK) {
@@ -1375,6 +1399,23 @@ ccm_status ccm_set_barrier_fault(ccm_case c, long long budget_cycles, int absent
   return CCM_OK;
 }
 
+ccm_status ccm_set_body_motion(ccm_case c, double a0, double a1, double omega, double phase) {
+  g_last_error.clear();
+  if (!c) return fail(CCM_E_INVALID, "null case");
+  if (!std::isfinite(a0) || !std::isfinite(a1) || !std::isfinite(omega) || !std::isfinite(phase))
+    return fail(CCM_E_INVALID, "non-finite motion parameter");
+  c->motion[0] = a0; c->motion[1] = a1; c->motion[2] = omega; c->motion[3] = phase;
+  c->moving = !(a0 == 1.0 && a1 == 0.0);
+  if (c->geometry && c->dblock) {
+    // the present state's faces without fluid take the body velocity of its time level
+    launch_inactive_to_body(c->g, c->co.role_u, c->co.role_v, c->cv.dx, c->cv.dy, c->u, c->v, c->st,
+                            motion_factor(c, c->nstep));
+    launch_fill_bc(c->g, c->bc, c->u, c->v, 1.0, c->st);
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+  }
+  return check_cuda_errors("set_body_motion");
+}
+
 ccm_status ccm_step_async(ccm_case c, int nsteps) {
   g_last_error.clear();
   if (!c) return fail(CCM_E_INVALID, "null case");
@@ -1394,7 +1435,9 @@ ccm_status ccm_body_force(ccm_case c, double force[4]) {
   g_last_error.clear();
   if (!c || !force) return fail(CCM_E_INVALID, "null argument");
   if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
-  launch_body_force(c->cv, c->g, c->ph, c->u, c->v, c->p, c->fpart, c->fout, c->st);
+  Phys pf = c->ph;
+  pf.dn = motion_factor(c, c->nstep);
+  launch_body_force(c->cv, c->g, pf, c->u, c->v, c->p, c->fpart, c->fout, c->st);
   CUDA_TRY(cudaMemcpyAsync(force, c->fout, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CUDA_TRY(cudaStreamSynchronize(c->st));
   return check_cuda_errors("body_force");

@@ -596,6 +596,7 @@ ccm_status ccm_batch_add(ccm_batch b, ccm_case c) {
   if (!case_solve_view(c, &v)) return bfail(CCM_E_STATE, "set_geometry must come first");
   if (case_stream(c) != b->st) return bfail(CCM_E_INVALID, "the case must use the batch's stream");
   if (v.g.px || v.g.py) return bfail(CCM_E_INVALID, "periodic cases are not batched");
+  if (case_is_moving(c)) return bfail(CCM_E_INVALID, "cases whose body velocity changes in time are not batched");
   if ((int)b->cases.size() >= b->max_cases) return bfail(CCM_E_INVALID, "batch is full");
   if (!b->cases.empty() && case_is_mixed(b->cases[0]) != case_is_mixed(c))
     return bfail(CCM_E_INVALID, "all cases of a batch use the same precision setting");
@@ -622,6 +623,8 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
   if (!b) return bfail(CCM_E_INVALID, "null batch");
   if (nsteps < 0) return bfail(CCM_E_INVALID, "nsteps < 0");
   if (b->cases.empty()) return CCM_OK;
+  for (ccm_case c : b->cases)
+    if (case_is_moving(c)) return bfail(CCM_E_INVALID, "cases whose body velocity changes in time are not batched");
   const bool mixed = case_is_mixed(b->cases[0]);
   const bool scaled = all_scaled(b);
   // the split is tuned on the batch as it is; once the batch's cells have changed by more than

@@ -335,8 +335,9 @@ int diagnostics_partials(const Geom& g);
 void launch_body_dterms(const Geom& g, const Bc& bc, const CapPtrs& cp, const Coefs& c, const double* Dx,
                         const double* Dy, double* hd, double* sxxd, double* syyd, double* sxyd, double* vu,
                         double* vv, cudaStream_t st);
+// f: the factor of a time-dependent body velocity D = f D0 at the level of u, v (1: steady)
 void launch_inactive_to_body(const Geom& g, const int8_t* ru, const int8_t* rv, const double* Dx, const double* Dy,
-                             double* u, double* v, cudaStream_t st);
+                             double* u, double* v, cudaStream_t st, double f = 1.0);
 // Force of the fluid on the body, out[4] = (Fp_x, Fp_y, Fv_x, Fv_y) (operators.cu); partials
 // holds body_force_partials(g) doubles.
 int body_force_partials(const Geom& g);
@@ -345,8 +346,9 @@ void launch_body_force(const Coefs& c, const Geom& g, const Phys& ph, const doub
 void launch_residual64(const Coefs& c, const Geom& g, const double* x, const double* b, float* r32, double* partials,
                        double* out2, cudaStream_t st);
 void launch_add_correction(const Geom& g, const int8_t* act, double* x, const float* d, cudaStream_t st);
+// fd: the factor of a time-dependent body velocity at the level of u, v (1: steady)
 void launch_diagnostics(const Coefs& c, const Geom& g, const double* Vu, const double* Vv, const double* u,
-                        const double* v, double* partials, double* out, cudaStream_t st);
+                        const double* v, double* partials, double* out, cudaStream_t st, double fd = 1.0);
 
 // pcg.cu
 int pcg_partials_needed();
@@ -384,6 +386,7 @@ void case_stage_case(ccm_case c, StageCase* e, int ahead);
 int case_cur(ccm_case c);
 unsigned long long case_serial(ccm_case c);  // unique per case (addresses can be reused)
 bool case_has_extras(ccm_case c);            // a body acceleration or a body velocity is set
+bool case_is_moving(ccm_case c);             // the body velocity has a time law (not batched)
 long long case_nstep(ccm_case c);
 void case_step_done(ccm_case c);
 void case_poisson_fp32(ccm_case c, PoissonSolve<float>* a);

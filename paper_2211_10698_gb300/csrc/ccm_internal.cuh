@@ -128,6 +128,9 @@ struct Coefs {
 
 struct Phys {
   double rho, mu, dt;
+  // a body velocity D(t) = D0 f(t): f at the time level of the velocity a stage reads (dn) and
+  // of the next level (dn1); 1 for a steady D (D = D0)
+  double dn = 1.0, dn1 = 1.0;
 };
 
 // ---------------------------------------------------------------------------------------

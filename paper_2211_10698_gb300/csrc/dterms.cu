@@ -120,12 +120,12 @@ __global__ void k_dterms_visc(Geom g, Bc bc, Coefs c, const double* sxxd, const 
   vv[k] = b;
 }
 
-// Faces whose control volume holds no fluid carry the body's velocity.
+// Faces whose control volume holds no fluid carry the body's velocity f D0.
 __global__ void k_inactive_to_body(Geom g, const int8_t* ru, const int8_t* rv, const double* Dx, const double* Dy,
-                                   double* u, double* v) {
+                                   double f, double* u, double* v) {
   DT_IJ(g)
-  if (ru[k] == R_INACTIVE) u[k] = Dx ? Dx[k] : 0.0;
-  if (rv[k] == R_INACTIVE) v[k] = Dy ? Dy[k] : 0.0;
+  if (ru[k] == R_INACTIVE) u[k] = Dx ? f * Dx[k] : 0.0;
+  if (rv[k] == R_INACTIVE) v[k] = Dy ? f * Dy[k] : 0.0;
 }
 
 }  // namespace
@@ -141,10 +141,10 @@ void launch_body_dterms(const Geom& g, const Bc& bc, const CapPtrs& cp, const Co
 }
 
 void launch_inactive_to_body(const Geom& g, const int8_t* ru, const int8_t* rv, const double* Dx, const double* Dy,
-                             double* u, double* v, cudaStream_t st) {
+                             double* u, double* v, cudaStream_t st, double f) {
   const dim3 b(64, 4);
   const dim3 gr((g.nx + 3 + b.x - 1) / b.x, (g.ny + 3 + b.y - 1) / b.y);
-  k_inactive_to_body<<<gr, b, 0, st>>>(g, ru, rv, Dx, Dy, u, v);
+  k_inactive_to_body<<<gr, b, 0, st>>>(g, ru, rv, Dx, Dy, f, u, v);
 }
 
 }  // namespace ccm

@@ -284,13 +284,16 @@ __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, 
   if (c.role_u[k] == R_UNKNOWN) {
     double cn = conv_u(c, g, w, i, j);
     // conv(U, U, D, D): the face mean of h = cont(0, D) times (U + D)/2 (Eq. convective)
-    if (EXTRA && c.hd) cn += 0.5 * (c.hd[k] + c.hd[k - 1]) * 0.5 * (w.u[k] + c.dx[k]);
+    // with D = f D0 the bracket is the steady one scaled by f (h) and f (D); f = 1 is exact
+    if (EXTRA && c.hd)
+      cn += 0.5 * (ph.dn * c.hd[k] + ph.dn * c.hd[k - 1]) * 0.5 * (w.u[k] + ph.dn * c.dx[k]);
     const double cp = first ? cn : cpu[k];
     const double gp = c.ax[k] * (P(i, j) - P(i - 1, j));
     const double vs = visc_u(c, g, bc, w, i, j);
     double r = c.massu[k] * w.u[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftu[k];
     if (EXTRA && c.accx) r += c.massu[k] * ph.dt * c.accx[k];  // rho V g
-    if (EXTRA && c.viscdu) r += 2.0 * ph.mu * c.viscdu[k];     // visc(S(0, D)): explicit half and lift
+    // visc(S(0, D)): explicit half (D^n) and the implicit half's lift (D^{n+1})
+    if (EXTRA && c.viscdu) r += (ph.dn + ph.dn1) * ph.mu * c.viscdu[k];
     ru_[k] = r;
     cnu[k] = cn;
   } else {
@@ -299,13 +302,14 @@ __device__ __forceinline__ void predictor_rhs_at(const Coefs& c, const Geom& g, 
   }
   if (c.role_v[k] == R_UNKNOWN) {
     double cn = conv_v(c, g, w, i, j);
-    if (EXTRA && c.hd) cn += 0.5 * (c.hd[k] + c.hd[k - g.pitch]) * 0.5 * (w.v[k] + c.dy[k]);
+    if (EXTRA && c.hd)
+      cn += 0.5 * (ph.dn * c.hd[k] + ph.dn * c.hd[k - g.pitch]) * 0.5 * (w.v[k] + ph.dn * c.dy[k]);
     const double cp = first ? cn : cpv[k];
     const double gp = c.ay[k] * (P(i, j) - P(i, j - 1));
     const double vs = visc_v(c, g, bc, w, i, j);
     double r = c.massv[k] * w.v[k] - 1.5 * ph.rho * cn + 0.5 * ph.rho * cp - gp + ph.mu * vs + ph.mu * c.liftv[k];
     if (EXTRA && c.accy) r += c.massv[k] * ph.dt * c.accy[k];
-    if (EXTRA && c.viscdv) r += 2.0 * ph.mu * c.viscdv[k];
+    if (EXTRA && c.viscdv) r += (ph.dn + ph.dn1) * ph.mu * c.viscdv[k];
     rv_[k] = r;
     cnv[k] = cn;
   } else {
@@ -320,11 +324,11 @@ __global__ void k_predictor_rhs(Coefs c, Geom g, Bc bc, Phys ph, FullView w, con
   predictor_rhs_at<EXTRA>(c, g, bc, ph, w, p, cpu, cpv, cnu, cnv, ru_, rv_, first, i, j, k);
 }
 
-// b = cont(U*, D) on cells; Poisson right-hand side -(rho/dt) b on active cells.
+// b = cont(U*, D^{n+1}) on cells; Poisson right-hand side -(rho/dt) b on active cells.
 __device__ __forceinline__ void divergence_at(const Coefs& c, const Geom& g, const Phys& ph, const double* u,
                                               const double* v, double* b, double* rhs, int i, int j, size_t k) {
   const bool dom = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
-  const double d = dom ? cont_cell(c, g, u, v, i, j) + (c.hd ? c.hd[k] : 0.0) : 0.0;
+  const double d = dom ? cont_cell(c, g, u, v, i, j) + (c.hd ? ph.dn1 * c.hd[k] : 0.0) : 0.0;
   b[k] = d;
   rhs[k] = c.act[k] ? -(ph.rho / ph.dt) * d : 0.0;
 }
@@ -387,14 +391,14 @@ __global__ void __launch_bounds__(256) k_stage_batch(const StageCase* __restrict
 // positions inside the box, a non-finite flag, and the conservation sums: cont(U, D) over the
 // box cells (mass), V u and V v over the velocity positions inside the box (momentum).
 __global__ void k_diagnostics(Coefs c, Geom g, const double* Vu, const double* Vv, const double* u, const double* v,
-                              double* partials) {
+                              double fd, double* partials) {
   const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
   const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
   double dmax = 0.0, ke = 0.0, bad = 0.0, mass = 0.0, mx = 0.0, my = 0.0;
   if (i <= g.nx + 1 && j <= g.ny + 1) {
     const size_t k = g.idx(i, j);
     if (i >= 0 && i < g.nx && j >= 0 && j < g.ny) {
-      const double d = cont_cell(c, g, u, v, i, j) + (c.hd ? c.hd[k] : 0.0);
+      const double d = cont_cell(c, g, u, v, i, j) + (c.hd ? fd * c.hd[k] : 0.0);
       mass = d;
       if (c.act[k]) dmax = fabs(d);
     }
@@ -474,7 +478,7 @@ __global__ void k_diagnostics_final(const double* partials, int nb, double* out)
 // (i, j) in [0,nx] x [0,ny] takes the cell and the node of that index; the strain is evaluated
 // only where its B-difference is nonzero (0 * S adds nothing).  Per-block partials of the four
 // sums (before the factor -2 mu), in a fixed tree order.
-__global__ void k_body_force(Coefs c, Geom g, FullView w, const double* p, double* partials) {
+__global__ void k_body_force(Coefs c, Geom g, FullView w, const double* p, double fd, double* partials) {
   const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
   const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
   double f[4] = {0.0, 0.0, 0.0, 0.0};
@@ -485,14 +489,14 @@ __global__ void k_body_force(Coefs c, Geom g, FullView w, const double* p, doubl
       f[0] = pk * (c.ax[k] - c.ax[k + 1]);
       f[1] = pk * (c.ay[k] - c.ay[k + g.pitch]);
       const double dbx = c.bxx[k] - c.bxx[k + 1];
-      if (dbx != 0.0) f[2] = (strain_xx(c, g, w, i, j) + (c.sxxd ? c.sxxd[k] : 0.0)) * dbx;
+      if (dbx != 0.0) f[2] = (strain_xx(c, g, w, i, j) + (c.sxxd ? fd * c.sxxd[k] : 0.0)) * dbx;
       const double dby = c.byy[k] - c.byy[k + g.pitch];
-      if (dby != 0.0) f[3] = (strain_yy(c, g, w, i, j) + (c.syyd ? c.syyd[k] : 0.0)) * dby;
+      if (dby != 0.0) f[3] = (strain_yy(c, g, w, i, j) + (c.syyd ? fd * c.syyd[k] : 0.0)) * dby;
     }
     const double dnx = (j >= 1 && j < g.ny) ? c.bxy[k - g.pitch] - c.bxy[k] : 0.0;
     const double dny = (i >= 1 && i < g.nx) ? c.byx[k - 1] - c.byx[k] : 0.0;
     if (dnx != 0.0 || dny != 0.0) {
-      const double sxy = strain_xy(c, g, w, i, j) + (c.sxyd ? c.sxyd[k] : 0.0);
+      const double sxy = strain_xy(c, g, w, i, j) + (c.sxyd ? fd * c.sxyd[k] : 0.0);
       f[2] += sxy * dnx;
       f[3] += sxy * dny;
     }
@@ -712,7 +716,7 @@ int body_force_partials(const Geom& g) {
 void launch_body_force(const Coefs& c, const Geom& g, const Phys& ph, const double* u, const double* v,
                        const double* p, double* partials, double* out, cudaStream_t st) {
   dim3 gr = pad_grid(g, kBlk);
-  k_body_force<<<gr, kBlk, 0, st>>>(c, g, FullView{u, v, g}, p, partials);
+  k_body_force<<<gr, kBlk, 0, st>>>(c, g, FullView{u, v, g}, p, ph.dn, partials);
   k_body_force_final<<<1, 256, 0, st>>>(partials, (int)(gr.x * gr.y), ph.mu, out);
 }
 int diagnostics_partials(const Geom& g) {
@@ -720,9 +724,9 @@ int diagnostics_partials(const Geom& g) {
   return (int)(gr.x * gr.y);
 }
 void launch_diagnostics(const Coefs& c, const Geom& g, const double* Vu, const double* Vv, const double* u,
-                        const double* v, double* partials, double* out, cudaStream_t st) {
+                        const double* v, double* partials, double* out, cudaStream_t st, double fd) {
   dim3 gr = pad_grid(g, kBlk);
-  k_diagnostics<<<gr, kBlk, 0, st>>>(c, g, Vu, Vv, u, v, partials);
+  k_diagnostics<<<gr, kBlk, 0, st>>>(c, g, Vu, Vv, u, v, fd, partials);
   k_diagnostics_final<<<1, 256, 0, st>>>(partials, (int)(gr.x * gr.y), out);
 }
 

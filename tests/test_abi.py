@@ -108,6 +108,13 @@ def test_barrier_fault_hook_validates_on_the_host(libccm):
     assert L.ccm_set_barrier_fault(None, 0, -1) == ccm.CCM_E_INVALID
 
 
+def test_body_motion_validates_on_the_host(libccm):
+    from paper_2211_10698_gb300 import ccm
+
+    L = ccm.lib()
+    assert L.ccm_set_body_motion(None, 1.0, 0.0, 0.0, 0.0) == ccm.CCM_E_INVALID
+
+
 def test_stretched_faces_validate_on_the_host(libccm):
     """Face abscissas of a stretched mesh must increase strictly from x0 to x1 (y0 to y1)."""
     import numpy as np
