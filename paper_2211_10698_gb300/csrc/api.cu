@@ -71,6 +71,7 @@ struct ccm_case_s {
   double* partials;
   double* dpart;
   unsigned int* bar_count;
+  unsigned long long* fxacc;  // words of the fixed-point reduce-barrier (pcg_fixed.cuh)
   int* bar_err;
   DevStats* ds;
   bool geometry = false;
@@ -177,6 +178,7 @@ void carve(ccm_case c, Carver& cv) {
   c->accy = cv.take<double>(N);
   c->fout = cv.take<double>(4);
   c->bar_count = cv.take<unsigned int>(kBarWords);
+  c->fxacc = cv.take<unsigned long long>(kFxAccWords);
   c->bar_err = cv.take<int>(4);
   c->ds = cv.take<DevStats>(1);
   c->hs_u = cv.take<double>(N);
@@ -296,6 +298,7 @@ ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
     case_solve_view(c, &v);
     FusedSolve f{};
     f.a = scaled_solve_of(v, x, b, c->pz, nullptr, nullptr, c->pp0, nullptr);
+    f.fxacc = c->fxacc;
     f.a.partials = c->partials;
     f.a.bar = case_barrier(c);
     f.a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
@@ -522,6 +525,7 @@ ccm_status autotune_poisson(ccm_case c) {
     case_solve_view(c, &v);
     FusedSolve f{};
     f.a = scaled_solve_of(v, x, b, c->pz, nullptr, nullptr, c->pp0, nullptr);
+    f.fxacc = c->fxacc;
     f.a.partials = c->partials;
     f.a.bar = case_barrier(c);
     f.a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, nullptr, nullptr};

@@ -96,8 +96,15 @@ cudaError_t run_poisson_scaled(const ScaledSolve& a, cudaStream_t st);
 // The same solve with one grid barrier per iteration (pcg_fused.cu): 2-D tiles, the ring of
 // each tile recomputed by its block, r, w, s double-buffered.  a.xs and a.p are used, a.r,
 // a.w, a.s are not.
+// Words of the fixed-point reduce-barrier (pcg_fixed.cuh): three rotating buffers of kFxWords
+// 64-bit words, each word on its own 128-byte line.
+constexpr int kFxWords = 16;
+constexpr int kFxStride = 16;
+constexpr int kFxAccWords = 3 * kFxWords * kFxStride;
+
 struct FusedSolve {
   ScaledSolve a;
+  unsigned long long* fxacc;  // kFxAccWords words (cleared by the kernel itself)
   double* R[2];
   double* W[2];
   double* S[2];

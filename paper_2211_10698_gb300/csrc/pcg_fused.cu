@@ -29,10 +29,16 @@
 // ring), so f2 publishes r, w and s of its perimeter to the double-buffered global arrays once
 // per iteration and touches nothing else in global memory until the final x~ -> x.  Its
 // x~ += alpha p_i, which no other block reads, runs between the block's arrival at the grid
-// barrier and its wait (grid_arrive / grid_wait), in the time the barrier would otherwise idle.
+// barrier and its wait, in the time the barrier would otherwise idle.
+// The sums of the iterations (reductions 1, 2, ...) are exact fixed-point sums that travel
+// with the grid barrier (pcg_fixed.cuh): the block's arrival adds its digit sums to words in
+// global memory and the wait on those words ends with the grid's sums in hand, so neither the
+// block sum nor the grid sum is a chain of FP64 additions.  Reduction 0 (phase 0) and the
+// rare reduction whose values leave the fixed-point window take the FP64 sums.
 #include <algorithm>
 
 #include "pcg_common.cuh"
+#include "pcg_fixed.cuh"
 
 namespace ccm {
 
@@ -49,6 +55,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
   __shared__ double sc_alpha, sc_beta, sc_igamma, sc_den, sc_rr, sc_bb;
   __shared__ double sc_igamma_next, sc_den_next;
   __shared__ int sc_it, sc_stop;
+  __shared__ FxShared fxs;
   // dynamic shared memory: with RES x~, r, p, s, w of the tile (TX*TY each), then the ring
   // [W: TY][E: TY][S: TX][N: TX], then with RES the tile's row kinds, then the list, then with
   // RES and f.lcache the five scaled coefficients of the first kNT listed cells (8-byte aligned:
@@ -343,6 +350,10 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
       }
       v[3] += bk * bk;
     }
+  // the fixed-point words start at zero (the previous launch leaves one buffer in use); the
+  // barriers of phase 0 order this before their first use
+  if (blockIdx.x == 0)
+    for (int q = threadIdx.x; q < 3 * kFxWords; q += kNT) f.fxacc[(size_t)q * kFxStride] = 0ULL;
   bool ok = grid_sync(a.bar, target);
   if (ok) {
     // w_0 = K~ r_0: every neighbour's r_0 is complete, read through the same ring path
@@ -356,6 +367,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
     reduce(v, 4, rows0);
     ok = grid_sync(a.bar, target);
   }
+  int fx_lo = 0;  // bottom of the fixed-point window of the next reduction (same in every block)
   if (ok) {
     double t[4];
     grid_sum<4>(rows0, nb, t, gsum);
@@ -373,6 +385,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
       }
     }
     __syncthreads();
+    fx_lo = fx_window(t[0], t[1], t[2]);
   }
   int cur = 0;
   while (ok && sc_stop == 0) {
@@ -444,23 +457,35 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
     __syncthreads();
     v[0] = v[1] = v[2] = 0.0;
     stencil(rn_, f.W[nxt], nxt, v);
-    double* const rows = (sc_it & 1) ? rows0 : rows1;  // reduction sc_it + 1
-    reduce(v, 3, rows);
+    // reduction sc_it + 1 in the rotating fixed-point buffers
+    const int ri = sc_it + 1, buf = ri % 3;
+    fx_arrive<kNT>(v, fx_lo, f.fxacc, buf, a.bar.absent, fxs);
     if constexpr (RES) {
       // x~ += alpha p_i is read by no other block and by nothing before the end: it runs between
       // this block's arrival at the grid barrier and its wait
-      grid_arrive(a.bar, target);
       if (col)
         for (int j = j0 + ty0; j < j1; j += RP) {
           const int l = lidx(ci, j);
           sx[l] += al * sp[l];
         }
-      if (!grid_wait(a.bar, target)) { ok = false; break; }
-    } else {
-      if (!grid_sync(a.bar, target)) { ok = false; break; }
     }
+    if (!fx_wait(f.fxacc, buf, (ri + 2) % 3, a.bar.budget, a.bar.err, fxs)) { ok = false; break; }
     double t[3];
-    grid_sum<3>(rows, nb, t, gsum);
+    if (fxs.s[kFxWords - 1] == 0) {
+      if (threadIdx.x < kFxQ) gsum[threadIdx.x] = fx_value(&fxs.s[threadIdx.x * kFxDigits], fx_lo);
+      __syncthreads();
+      t[0] = gsum[0];
+      t[1] = gsum[1];
+      t[2] = gsum[2];
+    } else {
+      // a value outside the window (every block sees the same count): this reduction again in
+      // FP64 through the partial rows and the counter barrier
+      double* const rows = (sc_it & 1) ? rows0 : rows1;
+      reduce(v, 3, rows);
+      if (!grid_sync(a.bar, target)) { ok = false; break; }
+      grid_sum<3>(rows, nb, t, gsum);
+    }
+    fx_lo = fx_window(t[0], t[1], t[2]);
     // beta = gamma / gamma_old; alpha = gamma / (delta - beta gamma / alpha_old).  The two
     // reciprocals are independent: 1/gamma (for the next beta) in warp 0, 1/den in warp 1,
     // which issue to different sub-partitions' FP64 pipes.
