@@ -120,8 +120,8 @@ KERNEL_SOURCES = {
     "k_pcg_poisson_m1": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_cheb.cuh", "pcg_mixed1.cu"),
     "k_pcg_poisson_m2": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_cheb.cuh", "pcg_mixed1.cu"),
     "k_pcg_poisson_mixed": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_cheb.cuh", "pcg_quad.cuh", "pcg_mixed.cu"),
-    "k_pcg_poisson_f1": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fused.cu"),
-    "k_pcg_poisson_f2": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fused.cu"),
+    "k_pcg_poisson_f1": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fixed.cuh", "pcg_fused.cu"),
+    "k_pcg_poisson_f2": ("ccm_internal.cuh", "pcg_common.cuh", "pcg_fixed.cuh", "pcg_fused.cu"),
     "k_pcg_poisson_cluster": ("pcg_common.cuh", "pcg_cluster.cu"),
 }
 
