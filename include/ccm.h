@@ -111,8 +111,10 @@ typedef struct {
    * 1..32 the projection of the new solution onto the span of the last L solutions in the
    * inner product of K (Fischer 1998), which lowers the iteration count of a smoothly
    * evolving flow.  Same stopping test either way.  Needs 2 L padded FP64 arrays more (the
-   * case's allocator).  Setting a state field (ccm_set_field) clears the history; batched
-   * steps (ccm_batch_*) do not use it; a singular (all-wall) system ignores it. */
+   * case's allocator).  Setting Phi or the step counter (ccm_set_field, as a restored
+   * checkpoint does) clears the history, so the restored run repeats a fresh run bit for bit;
+   * setting U, V or P keeps it (it only shortens the solves).  Batched steps (ccm_batch_*) do
+   * not use it; a singular (all-wall) system ignores it. */
   int guess_history;
 } ccm_config;
 

@@ -1091,7 +1091,10 @@ ccm_status ccm_set_field(ccm_case c, int field, const double* host, size_t count
   g_last_error.clear();
   if (!c || !host) return fail(CCM_E_INVALID, "null argument");
   if (!c->geometry) return fail(CCM_E_STATE, "set_geometry must come first");
-  c->gnb = 0;  // a new state: the initial-guess history no longer belongs to it
+  // the initial-guess history is only a guess for the next solves, good for any state; a new
+  // warm start or step counter (a restored checkpoint) starts a new one, so that a restored
+  // run repeats a fresh run from the same fields bit for bit
+  if (field == CCM_F_PHI || field == CCM_F_STEP) c->gnb = 0;
   if (field == CCM_F_STEP) {
     if (count < 1) return fail(CCM_E_INVALID, "count");
     c->nstep = (long long)host[0];

@@ -76,3 +76,25 @@ def test_history_is_cleared_by_a_new_state():
         assert np.array_equal(g.get_field(f), h.get_field(f)), f
     g.close()
     h.close()
+
+
+def test_history_survives_a_velocity_and_pressure_upload():
+    """Uploading U, V and P (the end-to-end loop's host round trip) keeps the history: the
+    steps continue with the same iteration counts and fields as without the round trip."""
+    case = I.cylinder_re40_128x64()
+    case.guess_history = 8
+    case.autotune = 0
+    a, b = ccm.Case(case), ccm.Case(case)
+    a.step(6)
+    b.step(6)
+    ia, ib = [], []
+    for _ in range(4):
+        for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P):
+            b.set_field(f, b.get_field(f))
+        ia.append(a.step(1)["iters_p"])
+        ib.append(b.step(1)["iters_p"])
+    assert ia == ib
+    for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P, ccm.CCM_F_PHI):
+        assert np.array_equal(a.get_field(f), b.get_field(f)), f
+    a.close()
+    b.close()
