@@ -631,10 +631,11 @@ def run_ours(args):
     g.enable_kernel_timing(False)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
+    e2e_iters = 0
     for _ in range(args.e2e_steps):
         for f, buf in zip(fields, hb):
             g.set_field(f, buf)
-        g.step(1)
+        e2e_iters += g.step(1)["iters_p"]
         for f, buf in zip(fields, hb):
             g.get_field(f, out=buf)
     e2e_s = time.perf_counter() - e0
@@ -734,7 +735,10 @@ def run_ours(args):
                                 launch_plan=launch_plan),
                     roofline=roof, roofline_detail=roof_alt, cpu_baseline=cpu,
                     e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes,
-                             steps=args.e2e_steps),
+                             steps=args.e2e_steps,
+                             # the steps after the timed ones, later on the trajectory: their Poisson
+                             # iteration count sets their cost, as iters_per_step does the headline's
+                             poisson_iters_per_step=(e2e_iters / args.e2e_steps) if args.e2e_steps > 0 else None),
                     gpu_launches=int(kt["kernel_launches"]), clocks=clocks,
                     wall_s=wall, step_ms_min=min(step_ms), step_ms_max=max(step_ms),
                     max_div=st["max_div"], kinetic=st["kinetic"], converged=bool(st["converged"]))

@@ -147,10 +147,10 @@ __device__ __forceinline__ void block_sum_warps(const double (&v)[NV], double (*
   __syncthreads();
 }
 
-// 1 / y by Newton's iteration x <- x + x (1 - y x) from a single-precision estimate of the
-// reciprocal of y's significand (quadratic convergence: ~24, ~48, >53 bits), scaled back by
-// y's power of two.  For normal, nonzero y; within a few units in the last place, which is
-// all the CG recurrences need.
+// 1 / y by Newton's iteration x <- x + x (1 - y x) from the correctly rounded single-precision
+// reciprocal of y's significand (quadratic convergence: 24, then 48, then beyond 53 bits, so
+// two steps), scaled back by y's power of two.  For normal, nonzero y; within a few units in
+// the last place, which is all the CG recurrences need.
 __device__ __forceinline__ double recip_newton(double y) {
   const long long bits = __double_as_longlong(y);
   const int e = (int)((bits >> 52) & 0x7ff) - 1023;
@@ -158,8 +158,6 @@ __device__ __forceinline__ double recip_newton(double y) {
   const double s = __longlong_as_double((long long)(1023 - e) << 52);                // 2^-e
   double x = (double)__frcp_rn((float)m);
   double r = fma(-m, x, 1.0);
-  x = fma(x, r, x);
-  r = fma(-m, x, 1.0);
   x = fma(x, r, x);
   r = fma(-m, x, 1.0);
   x = fma(x, r, x);

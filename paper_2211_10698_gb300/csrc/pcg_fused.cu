@@ -56,10 +56,11 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
   __shared__ double sc_igamma_next, sc_den_next;
   __shared__ int sc_it, sc_stop;
   __shared__ FxShared fxs;
-  // dynamic shared memory: with RES x~, r, p, s, w of the tile (TX*TY each), then the ring
-  // [W: TY][E: TY][S: TX][N: TX], then with RES the tile's row kinds, then the list, then with
-  // RES and f.lcache the five scaled coefficients of the first kNT listed cells (8-byte aligned:
-  // TX is a multiple of 32)
+  // dynamic shared memory: with RES x~, p, s, w of the tile (TX*TY each) and r~ of the tile in
+  // a one-cell frame ((TX+2)*(TY+2), the frame holding the ring), then the ring
+  // [W: TY][E: TY][S: TX][N: TX] (used without RES), then with RES the tile's row kinds, then
+  // the list, then with RES and f.lcache the five scaled coefficients of the first kNT listed
+  // cells (8-byte aligned: TX is a multiple of 32)
   extern __shared__ double dyn[];
   unsigned int target = 0;
   const ScaledSolve& a = f.a;
@@ -76,14 +77,19 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
   const bool col = ci < i1;
   const int TXY = TX * TY;
   double* const sx = dyn;  // the RES arrays (unused otherwise)
-  double* const sr = dyn + TXY;
-  double* const sp = dyn + 2 * TXY;
-  double* const ss = dyn + 3 * TXY;
-  double* const sw = dyn + 4 * TXY;
-  double* const ring = RES ? dyn + 5 * TXY : dyn;
+  double* const sp = dyn + TXY;
+  double* const ss = dyn + 2 * TXY;
+  double* const sw = dyn + 3 * TXY;
+  // RES: r~ of the tile with a one-cell frame that holds the ring, so that the stencil reads
+  // every neighbour from one array without a branch
+  const int TXP = TX + 2;
+  double* const sr = dyn + 4 * TXY;
+  double* const ring = RES ? dyn + 4 * TXY + TXP * (TY + 2) : dyn;
   int8_t* const skind = reinterpret_cast<int8_t*>(ring + 2 * (TX + TY));
   // tile-local index of own cell (i, j)
   auto lidx = [&](int i, int j) -> int { return (j - j0) * TX + (i - i0); };
+  // index of cell (i, j) of the tile or its frame in the framed r~ (RES)
+  auto lpad = [&](int i, int j) -> int { return (j - j0 + 1) * TXP + (i - i0 + 1); };
   // own cells on the tile's perimeter are read by the neighbouring tiles' rings
   auto perimeter = [&](int i, int j) -> bool { return i == i0 || i == i1 - 1 || j == j0 || j == j1 - 1; };
   // ring cells: W and E columns, then S and N rows, taken by threads t, t + kNT, ...
@@ -110,16 +116,16 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
   // r~ at neighbour (i, j) of an own cell after step 1: inside the tile from the next buffer,
   // on the ring from shared memory
   auto rnb = [&](const double* rn, int i, int j) -> double {
+    if constexpr (RES) return sr[lpad(i, j)];
     if (i < i0) return ring[j - j0];
     if (i >= i1) return ring[TY + (j - j0)];
     if (j < j0) return ring[2 * TY + (i - i0)];
     if (j >= j1) return ring[2 * TY + TX + (i - i0)];
-    if constexpr (RES) return sr[lidx(i, j)];
     else return rn[g.idx(i, j)];
   };
   // r~ of own cell (i, j) after step 1
   auto rown = [&](const double* rn, int i, int j) -> double {
-    if constexpr (RES) return sr[lidx(i, j)];
+    if constexpr (RES) return sr[lpad(i, j)];
     else return rn[g.idx(i, j)];
   };
   // w~ of own cell (i, j) into the tile (RES, which also publishes the perimeter's r, w and s
@@ -130,7 +136,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
       sw[l] = wk;
       if (perimeter(i, j)) {
         const size_t k = g.idx(i, j);
-        f.R[pub][k] = sr[l];
+        f.R[pub][k] = sr[lpad(i, j)];
         f.W[pub][k] = wk;
         f.S[pub][k] = ss[l];
       }
@@ -258,7 +264,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
         for (int j = j0 + ty0; j < j1; j += RP) {
           const int l = lidx(ci, j);
           const int8_t km = skind[l];
-          const double rc = sr[l], rw = rnb(rn, ci - 1, j), re = rnb(rn, ci + 1, j);
+          const double rc = sr[lpad(ci, j)], rw = rnb(rn, ci - 1, j), re = rnb(rn, ci + 1, j);
           const double rs = rnb(rn, ci, j - 1), rq = rnb(rn, ci, j + 1);
           const double wk = km == 0 ? 0.0 : rc - ax * (rw + re) - ay * (rs + rq);
           if (km != 2) {
@@ -337,7 +343,7 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
       if (RES) {
         const int l = lidx(ci, j);
         sx[l] = x0;
-        sr[l] = r0;
+        sr[lpad(ci, j)] = r0;
         ss[l] = 0.0;
         sp[l] = 0.0;
         skind[l] = kinds[k];
@@ -360,7 +366,9 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
     for (int t = threadIdx.x; t < nring; t += kNT) {
       int ri, rj, slot;
       const bool in = ring_cell(t, ri, rj, slot);
-      ring[slot] = in ? f.R[0][g.idx(ri, rj)] : 0.0;
+      const double rv0 = in ? f.R[0][g.idx(ri, rj)] : 0.0;
+      if constexpr (RES) sr[lpad(ri, rj)] = rv0;
+      else ring[slot] = rv0;
     }
     __syncthreads();
     stencil(f.R[0], f.W[0], 0, v);
@@ -398,12 +406,14 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
     double* __restrict__ sn_ = f.S[nxt];
     // this thread's first ring cell: the neighbours' iteration-i values, published before the
     // last grid barrier, are loaded now so the L2 round trip overlaps step 1
-    int pf_slot = 0;
+    int pf_slot = 0, pf_ri = 0, pf_rj = 0;
     bool pf_in = false;
     double pf_r = 0.0, pf_w = 0.0, pf_s = 0.0;
     if (threadIdx.x < nring) {
       int ri, rj;
       pf_in = ring_cell(threadIdx.x, ri, rj, pf_slot);
+      pf_ri = ri;
+      pf_rj = rj;
       if (pf_in) {
         const size_t k = g.idx(ri, rj);
         pf_r = rc_[k];
@@ -417,10 +427,11 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
       if (col)
         for (int j = j0 + ty0; j < j1; j += RP) {
           const int l = lidx(ci, j);
-          const double sk = sw[l] + be * ss[l], pk = sr[l] + be * sp[l];
+          const int lp = lpad(ci, j);
+          const double sk = sw[l] + be * ss[l], pk = sr[lp] + be * sp[l];
           ss[l] = sk;
           sp[l] = pk;
-          sr[l] -= al * sk;
+          sr[lp] -= al * sk;
         }
     } else if (col)
       for (int j = j0 + ty0; j < j1; j += 2 * RP) {
@@ -444,7 +455,11 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
         }
       }
     // ring cells: r_{i+1} from the neighbours' iteration-i vectors
-    if (threadIdx.x < nring) ring[pf_slot] = pf_in ? pf_r - al * (pf_w + be * pf_s) : 0.0;
+    if (threadIdx.x < nring) {
+      const double rv0 = pf_in ? pf_r - al * (pf_w + be * pf_s) : 0.0;
+      if constexpr (RES) sr[lpad(pf_ri, pf_rj)] = rv0;
+      else ring[pf_slot] = rv0;
+    }
     for (int t = threadIdx.x + kNT; t < nring; t += kNT) {
       int ri, rj, slot;
       double rv = 0.0;
@@ -452,7 +467,8 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
         const size_t k = g.idx(ri, rj);
         rv = rc_[k] - al * (wc_[k] + be * sc_[k]);
       }
-      ring[slot] = rv;
+      if constexpr (RES) sr[lpad(ri, rj)] = rv;
+      else ring[slot] = rv;
     }
     __syncthreads();
     v[0] = v[1] = v[2] = 0.0;
@@ -575,12 +591,13 @@ int fused_blocks() {
   return sms * per;
 }
 
-// Dynamic shared memory of a tile with its vectors resident (f2): x~, r, p, s, w, the ring, the
-// row kinds, a list of up to one entry per cell and, with `cache`, the coefficients of kNT
-// listed cells.
+// Dynamic shared memory of a tile with its vectors resident (f2): x~, p, s, w, r~ with its
+// one-cell frame, the ring, the row kinds, a list of up to one entry per cell and, with `cache`,
+// the coefficients of kNT listed cells.
 size_t fused_resident_smem(int TX, int TY, bool cache) {
   const size_t txy = (size_t)TX * (size_t)TY;
-  return 5 * sizeof(double) * txy + sizeof(double) * 2 * ((size_t)TX + (size_t)TY) + txy + sizeof(int) * txy +
+  return 4 * sizeof(double) * txy + sizeof(double) * ((size_t)TX + 2) * ((size_t)TY + 2) +
+         sizeof(double) * 2 * ((size_t)TX + (size_t)TY) + txy + sizeof(int) * txy +
          (cache ? 5 * sizeof(double) * kNT : 0);
 }
 
