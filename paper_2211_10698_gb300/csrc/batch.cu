@@ -36,6 +36,7 @@ struct ccm_batch_s {
   double* partials = nullptr;
   int* running = nullptr;
   unsigned int* bar_count = nullptr;
+  unsigned int* case_bar = nullptr;  // per-case barrier counters of the mixed Poisson launch
   int* bar_err = nullptr;
   double* host_sums = nullptr;  // pinned: 2 per case
   // batched explicit stages and Helmholtz solves: device tables and their pinned staging
@@ -62,8 +63,9 @@ struct ccm_batch_s {
   cudaStream_t cap_st = nullptr; // capture runs here (the legacy default stream cannot capture)
   // online tuning of the Poisson launch's block split (see split_candidates)
   bool tune = true;
-  int tune_next = 0;               // candidate the next tuned step uses (== count: done)
-  double tune_cost[3] = {0, 0, 0};
+  int tune_next = 0;               // candidate the next tuned step uses (== kSplitN: done)
+  double tune_cost[4] = {0, 0, 0, 0};
+  long long split_replays = 0;     // graph replays since the Poisson tables were uploaded
   double tune_cells = 0.0;           // cells of the batch the split was (is being) tuned on
   double split_exp = 0.0;          // the chosen exponent a of the weights cells x nx^a
   cudaEvent_t tev[2] = {nullptr, nullptr};
@@ -96,20 +98,36 @@ void allocate_blocks(const std::vector<double>& w, int blocks, std::vector<int>&
 
 }  // namespace
 
-// Block weights of the cooperative launches: cells x nx^a.  Each slot lasts as long as its most
-// loaded block; early in a solve every case is working, which favours equal cells per block
-// (a = 0), while the largest cases iterate longest, which favours giving them more (a > 0).
-// The Helmholtz launch uses a = 0 (about the same iteration count at every size); the Poisson
-// launch's a is tuned on the batch's own steps (split_candidates).
+// Block weights of the cooperative launches: cells x nx^a, or with a < 0 the expected work,
+// cells x the iterations of the case's last Poisson solve.  In a launch whose cases share
+// every barrier (FP64 CG, Helmholtz) each slot lasts as long as its most loaded block, which
+// favours equal cells per block (a = 0).  In the mixed Poisson launch every case has its own
+// barrier and runs at its own pace, so blocks in proportion to its work let the cases finish
+// together.  The Helmholtz launch uses a = 0 (about the same iteration count at every size);
+// the Poisson launch's weights are tuned on the batch's own steps (split_candidates).
 static std::vector<double> cell_weights(const std::vector<ccm_case>& cs, double a = 0.0) {
   std::vector<double> w(cs.size());
-  for (size_t i = 0; i < cs.size(); ++i) w[i] = (double)case_cells(cs[i]) * std::pow((double)case_nx(cs[i]), a);
+  for (size_t i = 0; i < cs.size(); ++i) {
+    if (a < 0.0) {
+      int it = 0;
+      if (cudaMemcpy(&it, case_inner_iters_dev(cs[i]), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        it = 0;
+      }
+      w[i] = (double)case_cells(cs[i]) * (double)std::max(it, 1);
+    } else {
+      w[i] = (double)case_cells(cs[i]) * std::pow((double)case_nx(cs[i]), a);
+    }
+  }
   return w;
 }
-// Exponents tried for the Poisson split, one batch step each (the steps advance the cases as
-// usual); the one with the least Poisson time per cell-iteration is kept.  Measured on 64
-// uneven cases: cells x nx^a with a = 0 beat the expected work (cells x iterations) by 13 %.
-static const double split_candidates[3] = {0.0, 0.5, 1.0};
+// Weights tried for the Poisson split, one batch step each (the steps advance the cases as
+// usual): cells x nx^a for a = 0, 1/2, 1 and the expected work (-1); the one with the least
+// Poisson time per cell-iteration is kept.  With the expected work, the weights follow the
+// cases' iteration counts: the tables are refreshed every kSplitRefresh graph replays.
+constexpr int kSplitN = 4;
+static const double split_candidates[kSplitN] = {0.0, 0.5, 1.0, -1.0};
+constexpr long long kSplitRefresh = 16;
 
 // Waits for the stream and turns a barrier give-up of any launch since the last check into
 // CCM_E_TIMEOUT.
@@ -165,7 +183,8 @@ static ccm_status upload_poisson_tables(ccm_batch b, bool mixed) {
 
 // One cooperative launch solves every case's Poisson system (tables already on the device).
 static cudaError_t launch_poisson_scaled(ccm_batch b, bool mixed) {
-  BatchControl ctl{b->partials, b->running, Barrier{b->bar_count, b->bar_err, 2000000000LL}};
+  BatchControl ctl{b->partials, b->running, Barrier{b->bar_count, b->bar_err, 2000000000LL}, b->case_bar,
+                   (int)b->cases.size()};
   return mixed ? run_mixed_batch(b->emx, b->block_case, ctl, b->blocks, b->st)
                : run_scaled_batch(b->esc, b->block_case, ctl, b->blocks, b->st);
 }
@@ -494,9 +513,9 @@ static ccm_status tuning_step(ccm_batch b, bool mixed) {
   }
   b->tune_cost[k] = ms > 0.0f && work > 0.0 ? ms / work : 1e300;
   b->tune_next = k + 1;
-  if (b->tune_next == 3) {
+  if (b->tune_next == kSplitN) {
     int best = 0;
-    for (int q = 1; q < 3; ++q)
+    for (int q = 1; q < kSplitN; ++q)
       if (b->tune_cost[q] < b->tune_cost[best]) best = q;
     b->split_exp = split_candidates[best];
   }
@@ -517,12 +536,13 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
     delete b;
     return bfail(CCM_E_INVALID, "a batch holds at most " + std::to_string(most) + " cases on this GPU");
   }
-  const size_t pieces[14] = {sizeof(BatchEntry<double>) * max_cases, sizeof(BatchEntry<float>) * max_cases,
+  const size_t pieces[15] = {sizeof(BatchEntry<double>) * max_cases, sizeof(BatchEntry<float>) * max_cases,
                              sizeof(ScaledBatchEntry) * max_cases, sizeof(MixedBatchEntry) * max_cases,
                              sizeof(int) * b->blocks, sizeof(double) * 6 * b->blocks, sizeof(int) * 2 * b->blocks,
                              sizeof(unsigned int) * kBarWords, sizeof(int) * 4, sizeof(StageCase) * max_cases,
                              sizeof(int) * (max_cases + 1), sizeof(HelmBatchEntry) * max_cases,
-                             sizeof(int) * b->blocks, sizeof(StageCase) * max_cases};
+                             sizeof(int) * b->blocks, sizeof(StageCase) * max_cases,
+                             sizeof(unsigned int) * kCaseBarStride * (size_t)max_cases};
   size_t bytes = 0;
   for (size_t n : pieces) bytes += (n + 255) & ~(size_t)255;
   cudaError_t e = cudaMalloc(&b->dev, bytes);
@@ -547,6 +567,7 @@ ccm_status ccm_batch_create(int max_cases, void* stream, ccm_batch* out) {
   b->helm = (HelmBatchEntry*)take(sizeof(HelmBatchEntry) * max_cases);
   b->helm_block_case = (int*)take(sizeof(int) * b->blocks);
   b->stages2 = (StageCase*)take(sizeof(StageCase) * max_cases);
+  b->case_bar = (unsigned int*)take(sizeof(unsigned int) * kCaseBarStride * (size_t)max_cases);
   const size_t hbytes = sizeof(StageCase) * max_cases + sizeof(HelmBatchEntry) * max_cases +
                         sizeof(int) * (max_cases + 1) + sizeof(int) * b->blocks;
   if ((e = cudaMallocHost(&b->host_sums, sizeof(double) * 2 * max_cases)) != cudaSuccess ||
@@ -649,7 +670,7 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
     n = 1;
   }
   // the next steps try the candidate splits of the Poisson launch, one each
-  for (; n < nsteps && scaled && b->tune && b->tune_next < 3; ++n) {
+  for (; n < nsteps && scaled && b->tune && b->tune_next < kSplitN; ++n) {
     drop_graphs(b);
     if ((s = tuning_step(b, mixed)) != CCM_OK) return s;
   }
@@ -658,6 +679,13 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
     if (!ok && (s = capture_graphs(b, mixed, &ok)) != CCM_OK) return s;
     if (ok) {
       for (; n < nsteps; ++n) {
+        if (b->split_exp < 0.0 && mixed && ++b->split_replays > kSplitRefresh) {
+          // the expected work moves with the cases' iteration counts: new weights for the
+          // Poisson tables the graphs read (uploaded once the previous replays have run)
+          if ((s = check_barrier(b, "batch graph")) != CCM_OK) return s;
+          if ((s = upload_poisson_tables(b, mixed)) != CCM_OK) return s;
+          b->split_replays = 1;
+        }
         const cudaError_t e = cudaGraphLaunch(b->gexec[b->gphase], b->st);
         if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
         b->gphase ^= 1;
@@ -690,7 +718,7 @@ ccm_status ccm_batch_set_tuning(ccm_batch b, int enable) {
   set_last_error("");
   if (!b) return bfail(CCM_E_INVALID, "null batch");
   b->tune = enable != 0;
-  if (!b->tune && b->tune_next < 3) b->split_exp = split_candidates[0];
+  if (!b->tune && b->tune_next < kSplitN) b->split_exp = split_candidates[0];
   return CCM_OK;
 }
 
@@ -698,7 +726,7 @@ ccm_status ccm_batch_split(ccm_batch b, double* exponent, int* tuned) {
   set_last_error("");
   if (!b || !exponent || !tuned) return bfail(CCM_E_INVALID, "null argument");
   *exponent = b->split_exp;
-  *tuned = b->tune_next >= 3 ? 1 : 0;
+  *tuned = b->tune_next >= kSplitN ? 1 : 0;
   return CCM_OK;
 }
 

@@ -217,10 +217,14 @@ struct BatchEntry {
   int block0, nblocks;
 };
 
+// Counters of the per-case barriers of k_mixed_batch, kCaseBarStride words apart.
+constexpr int kCaseBarStride = 32;
 struct BatchControl {
   double* partials;  // 6 values x blocks
   int* running;      // per block: its case is still iterating (two halves of gridDim.x)
   Barrier bar;
+  unsigned int* case_bar = nullptr;  // k_mixed_batch: one barrier counter per case
+  int ncases = 0;
 };
 
 // The Helmholtz operator of the predictor (Eq. pm_prediction, homogeneous part) as nine

@@ -181,6 +181,31 @@ __device__ __forceinline__ bool grid_sync(const Barrier& b, unsigned int& target
   return s_ok != 0;
 }
 
+// The same barrier among the n blocks that share the counter `count` (one case of a batched
+// launch, whose blocks wait for each other only); err, budget and the absent block as above.
+__device__ __forceinline__ bool range_sync(const Barrier& b, unsigned int* count, unsigned int n,
+                                           unsigned int& target) {
+  __shared__ int s_okr;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    target += n;
+    if ((int)blockIdx.x != b.absent)
+      asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+    const long long t0 = clock64();
+    while (ld_acquire_u32(count) < target) {
+      if (clock64() - t0 > b.budget) {
+        atomicExch(b.err, 1);
+        ok = 0;
+        break;
+      }
+    }
+    s_okr = ok;
+  }
+  __syncthreads();
+  return s_okr != 0;
+}
+
 // The same barrier in two halves, so that a block can do work that no other block reads
 // between its arrival and its wait: grid_arrive (all threads), then grid_wait (all threads).
 __device__ __forceinline__ void grid_arrive(const Barrier& b, unsigned int& target) {

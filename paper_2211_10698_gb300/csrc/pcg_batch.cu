@@ -11,8 +11,10 @@
 // FP64 solve: two barriers per CG iteration, as in pcg_scaled.cu.
 //
 // Mixed solve: each case steps through slots, one barrier after each, according to where it
-// is (so cases of different sizes, preconditioners and replacement histories share every
-// barrier):
+// is.  The barrier after a slot is the case's own (a counter per case that only its blocks
+// pass), so every case iterates at its own pace and its blocks leave the launch when it is
+// done; the host gives each case blocks in proportion to its expected work (cells x
+// iterations), so that the cases finish together:
 //   iteration      UPDATE (vector update A),
 //                  CHEB x (degree - 1) (Chebyshev steps from z1 = r / theta; none with Jacobi),
 //                  APPLY (w = K~ u and its sums), then the scalars and the replacement test
@@ -20,9 +22,8 @@
 //   replacement    FOLD (x += D^-1/2 e / sigma), RESID (FP64 residual and its norms; the
 //                  convergence test and the new normalisation sigma), FRESH (r = sigma r64;
 //                  Jacobi: also w = K~ r and its sums; Chebyshev: then CHEB and APPLY),
-//                  FORM (p, K~ p formed and (p, K~ p) summed; then alpha), WAIT (idle until
-//                  the next slot where iterations start: t = 0 mod the iteration's length)
-//   DONE           idle
+//                  FORM (p, K~ p formed and (p, K~ p) summed; then alpha)
+//   DONE           the case's blocks leave
 // The first pass starts in FOLD with p = s = e = 0.
 #include "batch_common.cuh"
 #include "pcg_quad.cuh"
@@ -231,8 +232,8 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
 // ---------------------------------------------------------------------------------------
 // Mixed-precision solve, batched.
 // ---------------------------------------------------------------------------------------
-// Slots of the mixed solve; a grid barrier follows each, and the sums a slot publishes are
-// reduced after it.
+// Slots of the mixed solve; the case's barrier follows each, and the sums a slot publishes
+// are reduced after it.
 enum : int {
   SL_FOLD = 0,    // x += D^-1/2 e / sigma, e = 0 (first pass: p = s = e = 0)
   SL_RESID = 1,   // r64 = D^-1/2 (b - K x) and its norms
@@ -241,8 +242,7 @@ enum : int {
   SL_APPLY = 4,   // w = K~ u and the sums (r, u), (w, u), (r, r)
   SL_FORM = 5,    // p = u + beta' p, s = w + beta' s and (p, s)
   SL_UPDATE = 6,  // vector update A
-  SL_DONE = 7,
-  SL_WAIT = 8     // idle until the slot where this case's iterations start (see below)
+  SL_DONE = 7     // the case's solve has ended
 };
 
 __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatchEntry* __restrict__ cases,
@@ -265,11 +265,10 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
   const int nx = g.nx;
   const int lb = blockIdx.x - E.block0, nbc = E.nblocks;
   const CaseRange ch(g.nx * g.ny, lb, nbc);
-  // The FP64 residual of a replacement costs several times an FP32 slot (its FP64 row and
-  // sums run on the narrow FP64 pipe), and every slot lasts as long as its slowest block, so
-  // while one case replaces, all others would wait.  It is therefore taken in parts of about
-  // 1024 cells per block, one part per slot (the same count in every block of the case).
-  const int nparts = min(16, max(1, (g.nx * g.ny / nbc + 1023) / 1024));
+  // The FP64 residual of a replacement is one slot: with per-case barriers no other case waits
+  // for it (the slot code still takes it in parts when asked to).
+  const int nparts = 1;
+  unsigned int* const case_bar = ctl.case_bar + (size_t)kCaseBarStride * block_case[blockIdx.x];
   // the FP32 phases work on aligned quads of the case's arrays (see QuadOpsF32)
   const Quads Q(g);
   const int u0 = (int)((long long)Q.nquad * lb / nbc), u1 = (int)((long long)Q.nquad * (lb + 1) / nbc);
@@ -284,13 +283,6 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
   // between zA and zB; u = M^-1 r is the last iterate.  With Jacobi u is r itself.
   const int cheb = A.cheb > 1 ? A.cheb : 1;
   constexpr float ith = (float)(1.0 / ChebCoef::theta);
-  // An iteration takes `period` slots (UPDATE, the Chebyshev steps, APPLY) and starts only at
-  // slots t = 0 mod period, so the iterations of cases with the same preconditioner run in
-  // phase: their updates (the costliest slot, about 40 B per cell) share slots, and so do
-  // their cheaper Chebyshev and APPLY slots.  Out of phase, nearly every slot would hold some
-  // case's update and last as long as one.  A case that ends a replacement waits for the next
-  // start; a replacement begins right after an APPLY, so its FOLD falls on an update slot.
-  const unsigned int period = cheb > 1 ? (unsigned int)cheb + 1u : 2u;
   const double tol2 = d.tol * d.tol;
 
   if (threadIdx.x == 0) {
@@ -311,9 +303,9 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
   // block reaches only once it has read them.
   for (unsigned int t = 0; ok; ++t) {
     const int sl = sc_slot, part = sc_part;
+    if (sl == SL_DONE) break;  // every block of the case sees the same slot
     const bool last_part = part == nparts - 1;
     double* prow = ctl.partials + (size_t)(3 * (t & 1)) * NB;
-    int* run = ctl.running + (size_t)(t & 1) * NB;
     if (sl == SL_FOLD) {
       if (sc_init) {
         const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -412,12 +404,10 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
           ops.update_u(p, uvec, r, w, s, e, Q.k(u), al, be, keep);
       }
     }
-    // whether any case still works is checked every fourth slot (the flags of slot t are read
-    // after its barrier and written again four slots later); a finished case idles meanwhile
-    const bool check = (t & 3u) == 3u;
-    if (check && threadIdx.x == 0) run[blockIdx.x] = sl != SL_DONE ? 1 : 0;
-    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
-    if (check && !any_running(run, NB)) break;
+    // the case's barrier (a case on one block needs only the block barrier: its own global
+    // writes are visible to its threads after it)
+    if (nbc == 1) __syncthreads();
+    else if (!range_sync(ctl.bar, case_bar, (unsigned int)nbc, target)) { ok = false; break; }
     // ---- after the barrier: the slot's sums, the scalars and the next slot
     const bool sums3 = (sl == SL_RESID && last_part) || sl == SL_APPLY || (sl == SL_FRESH && cheb == 1);
     double t3[3] = {0.0, 0.0, 0.0};
@@ -465,9 +455,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_mixed_batch(const MixedBatch
         sc_igamma = 1.0f / sc_gfresh;
         sc_ialpha = 1.0f / sc_alpha;
         sc_keep = 1;
-        sc_slot = (t + 1) % period == 0 ? SL_UPDATE : SL_WAIT;
-      } else if (sl == SL_WAIT) {
-        if ((t + 1) % period == 0) sc_slot = SL_UPDATE;
+        sc_slot = SL_UPDATE;
       } else if (sl == SL_UPDATE) {
         sc_fresh = 0;
         if (cheb > 1) {
@@ -565,7 +553,8 @@ cudaError_t run_scaled_batch(const ScaledBatchEntry* dev_cases, const int* dev_b
 
 cudaError_t run_mixed_batch(const MixedBatchEntry* dev_cases, const int* dev_block_case, BatchControl ctl,
                             int blocks, cudaStream_t st) {
-  cudaMemsetAsync(ctl.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
+  if (!ctl.case_bar || ctl.ncases < 1) return cudaErrorInvalidValue;
+  cudaMemsetAsync(ctl.case_bar, 0, sizeof(unsigned int) * kCaseBarStride * (size_t)ctl.ncases, st);
   void* params[] = {(void*)&dev_cases, (void*)&dev_block_case, &ctl};
   return cudaLaunchCooperativeKernel((const void*)k_mixed_batch, blocks, kPcgThreads, params, 0, st);
 }
