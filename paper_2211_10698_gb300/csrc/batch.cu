@@ -103,8 +103,9 @@ void allocate_blocks(const std::vector<double>& w, int blocks, std::vector<int>&
 // every barrier (FP64 CG, Helmholtz) each slot lasts as long as its most loaded block, which
 // favours equal cells per block (a = 0).  In the mixed Poisson launch every case has its own
 // barrier and runs at its own pace, so blocks in proportion to its work let the cases finish
-// together.  The Helmholtz launch uses a = 0 (about the same iteration count at every size);
-// the Poisson launch's weights are tuned on the batch's own steps (split_candidates).
+// together; the FP64 Poisson launch does the same.  The Helmholtz launch uses a = 0 (about
+// the same iteration count at every size); the Poisson launch's weights are tuned on the
+// batch's own steps (split_candidates).
 static std::vector<double> cell_weights(const std::vector<ccm_case>& cs, double a = 0.0) {
   std::vector<double> w(cs.size());
   for (size_t i = 0; i < cs.size(); ++i) {
@@ -679,7 +680,7 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
     if (!ok && (s = capture_graphs(b, mixed, &ok)) != CCM_OK) return s;
     if (ok) {
       for (; n < nsteps; ++n) {
-        if (b->split_exp < 0.0 && mixed && ++b->split_replays > kSplitRefresh) {
+        if (b->split_exp < 0.0 && ++b->split_replays > kSplitRefresh) {
           // the expected work moves with the cases' iteration counts: new weights for the
           // Poisson tables the graphs read (uploaded once the previous replays have run)
           if ((s = check_barrier(b, "batch graph")) != CCM_OK) return s;

@@ -4,9 +4,9 @@
 //
 // Block b serves case block_case[b]: each case owns a contiguous range of blocks, sized by
 // the host to its expected work, and reduces over its own blocks only, in the same fixed
-// order as a single solve.  Every block passes the same grid barriers, and after each one
-// every block counts the blocks whose case is still working (the same count in every block);
-// the launch ends when none is.
+// order as a single solve.  The barriers are the case's own (a counter per case that only its
+// blocks pass; a case on one block needs only the block barrier), so every case iterates at
+// its own pace and its blocks leave the launch when it has converged.
 //
 // FP64 solve: two barriers per CG iteration, as in pcg_scaled.cu.
 //
@@ -57,6 +57,14 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
   const int first = ch.t0 + threadIdx.x, stride = blockDim.x;
   const int kdummy = (int)g.idx(0, 0);
   const KRow<double> K{a.cu, a.cv, a.dk, a.kind, a.creg_x, a.creg_y, a.dreg, (size_t)P};
+  unsigned int* const case_bar = ctl.case_bar + (size_t)kCaseBarStride * block_case[blockIdx.x];
+  auto case_sync = [&]() -> bool {
+    if (nbc == 1) {
+      __syncthreads();
+      return true;
+    }
+    return range_sync(ctl.bar, case_bar, (unsigned int)nbc, target);
+  };
   const int8_t* __restrict__ kinds = a.kinds;
   const double* __restrict__ cus = a.cus;
   const double* __restrict__ cvs = a.cvs;
@@ -119,12 +127,12 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
     s[k] = 0.0;
     v[3] += bk * bk;
   }
-  bool ok = grid_sync(ctl.bar, target);
+  bool ok = case_sync();
   if (ok) {
     phase_b(v);
     block_sum_warps<4>(v, red, bsum);
     publish(ctl.partials, NB, bsum, 4);
-    ok = grid_sync(ctl.bar, target);
+    ok = case_sync();
   }
   if (ok) {
     double t[4];
@@ -145,8 +153,8 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
     __syncthreads();
   }
   while (ok) {
-    const bool run = sc_stop == 0;
-    if (run) {
+    if (sc_stop != 0) break;  // every block of the case sees the same scalars
+    {
       const double al = sc_alpha, be = sc_beta;
       CellWalk cw(first, stride, ch.t1, nx);
       Group<kGroup> gr;
@@ -174,18 +182,16 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_sc_batch(const ScaledBatchEn
         }
       }
     }
-    if (threadIdx.x == 0) ctl.running[blockIdx.x] = run ? 1 : 0;
-    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
-    if (!any_running(ctl.running, NB)) break;
-    if (run) {
+    if (!case_sync()) { ok = false; break; }
+    {
       v[0] = v[1] = v[2] = 0.0;
       phase_b(v);
       const double v3[3] = {v[0], v[1], v[2]};
       block_sum_warps<3>(v3, red, bsum);
       publish(ctl.partials, NB, bsum, 3);
     }
-    if (!grid_sync(ctl.bar, target)) { ok = false; break; }
-    if (run) {
+    if (!case_sync()) { ok = false; break; }
+    {
       double t[3];
       range_sum<3>(ctl.partials, NB, E.block0, nbc, t, gsum);
       // the two reciprocals in different warps (different sub-partitions' FP64 pipes):
@@ -546,7 +552,8 @@ int batch_scaled_blocks() {
 
 cudaError_t run_scaled_batch(const ScaledBatchEntry* dev_cases, const int* dev_block_case, BatchControl ctl,
                              int blocks, cudaStream_t st) {
-  cudaMemsetAsync(ctl.bar.count, 0, sizeof(unsigned int) * kBarWords, st);
+  if (!ctl.case_bar || ctl.ncases < 1) return cudaErrorInvalidValue;
+  cudaMemsetAsync(ctl.case_bar, 0, sizeof(unsigned int) * kCaseBarStride * (size_t)ctl.ncases, st);
   void* params[] = {(void*)&dev_cases, (void*)&dev_block_case, &ctl};
   return cudaLaunchCooperativeKernel((const void*)k_sc_batch, blocks, kPcgThreads, params, 0, st);
 }
