@@ -1329,10 +1329,18 @@ static ccm_status guess_after(ccm_case c) {
 static ccm_status enqueue_steps(ccm_case c, int nsteps) {
   ccm_status s;
   for (int n = 0; n < nsteps; ++n) {
-    if ((s = stage_predict(c)) != CCM_OK) return s;
-    if ((s = guess_before(c)) != CCM_OK) return s;
-    if ((s = poisson_solve(c, c->phi, c->rhs_p)) != CCM_OK) return s;
-    if ((s = guess_after(c)) != CCM_OK) return s;
+    StageRange step("ccm step");
+    {
+      StageRange r("predictor + Helmholtz + divergence");
+      if ((s = stage_predict(c)) != CCM_OK) return s;
+    }
+    {
+      StageRange r("Poisson");
+      if ((s = guess_before(c)) != CCM_OK) return s;
+      if ((s = poisson_solve(c, c->phi, c->rhs_p)) != CCM_OK) return s;
+      if ((s = guess_after(c)) != CCM_OK) return s;
+    }
+    StageRange r("projection");
     stage_project(c);
   }
   return check_cuda_errors("step");

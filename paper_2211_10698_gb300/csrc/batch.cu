@@ -642,6 +642,7 @@ int ccm_batch_size(ccm_batch b) { return b ? (int)b->cases.size() : 0; }
 
 ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
   set_last_error("");
+  StageRange range("ccm batch steps");
   if (!b) return bfail(CCM_E_INVALID, "null batch");
   if (nsteps < 0) return bfail(CCM_E_INVALID, "nsteps < 0");
   if (b->cases.empty()) return CCM_OK;

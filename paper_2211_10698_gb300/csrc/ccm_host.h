@@ -1,6 +1,7 @@
 // Host-side declarations shared by the libccm translation units: argument bundles of the
 // solver kernels and the launchers each .cu file provides.
 #pragma once
+#include <nvtx3/nvToolsExt.h>
 
 #include <functional>
 #include <string>
@@ -406,5 +407,14 @@ ccm_status case_mixed_residual(ccm_case c, double* host2);
 void case_mixed_correct(ccm_case c);
 void case_mixed_account(ccm_case c, long long inner, int outer, double rr, double bb, bool converged);
 int* case_inner_iters_dev(ccm_case c);
+
+// Named NVTX range of one stage of a step (header-only NVTX: without a profiler attached the
+// calls return at once), so that a timeline shows predictor, Helmholtz, Poisson and projection.
+struct StageRange {
+  explicit StageRange(const char* name) { nvtxRangePushA(name); }
+  ~StageRange() { nvtxRangePop(); }
+  StageRange(const StageRange&) = delete;
+  StageRange& operator=(const StageRange&) = delete;
+};
 
 }  // namespace ccm

@@ -12,6 +12,8 @@
 //      are copied to host memory and the case is destroyed, so a finished request holds no
 //      device memory; statistics, timestamps and the host copies stay until
 //      ccm_server_release.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -153,6 +155,7 @@ ccm_status ccm_server_run(ccm_server s, int rounds, int* active) {
   if (!s || rounds < 0) return CCM_E_INVALID;
   ccm_status worst = CCM_OK;
   for (int round = 0; round < rounds; ++round) {
+    nvtxRangePushA("ccm server round");  // popped at the end of the round
     // admission, in arrival order (a request that does not fit blocks the ones behind it)
     while (!s->queue.empty()) {
       Request* r = s->queue.front();
@@ -208,6 +211,7 @@ ccm_status ccm_server_run(ccm_server s, int rounds, int* active) {
       }
       order.swap(keep);
     }
+    nvtxRangePop();
   }
   if (active) {
     int a = (int)s->queue.size();
