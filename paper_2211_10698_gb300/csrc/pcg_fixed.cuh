@@ -135,18 +135,27 @@ __host__ __device__ __forceinline__ double fx_value(const long long* S, int lo) 
   if (U == 0) return 0.0;
   const unsigned long long hi = (unsigned long long)(U >> 64), lw = (unsigned long long)U;
   const int n = hi ? 128 - fx_clz64(hi) : 64 - fx_clz64(lw);  // bit length
+  // T = the significand, 53 bits, and the value T 2^(lo + sh)
   unsigned long long T;
   int sh = n - 53;
   if (sh <= 0) {
-    T = lw;
-    sh = 0;
+    T = lw << (-sh);  // exact
   } else {
     T = (unsigned long long)(U >> sh);
     const unsigned __int128 rem = U & (((unsigned __int128)1 << sh) - 1);
     const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-    if (rem > half || (rem == half && (T & 1))) T += 1;  // to nearest, ties to even (T <= 2^53)
+    if (rem > half || (rem == half && (T & 1))) T += 1;  // to nearest, ties to even
+    if (T >> 53) {  // rounded up to 2^53
+      T >>= 1;
+      sh += 1;
+    }
   }
-  const double r = fx_scale((double)T, lo + sh);  // exact: T <= 2^53
+  // assembled from its fields when the result is normal (integer work only), otherwise scaled
+  const int E = lo + sh + 52 + 1023;  // biased exponent of T 2^(lo + sh), T in [2^52, 2^53)
+  const unsigned long long sign = neg ? 1ULL << 63 : 0ULL;
+  if (E >= 1 && E <= 2046)
+    return fx_double((long long)(sign | ((unsigned long long)E << 52) | (T & 0xfffffffffffffULL)));
+  const double r = fx_scale((double)T, lo + sh);
   return neg ? -r : r;
 }
 
