@@ -488,10 +488,10 @@ def measure_configs(torch, stream, flush, only=None, keep=None):
     return out
 
 
-def measure_batch(torch, stream, flush, ncases=64, steps=10, warmup=5):
+def measure_batch(torch, stream, flush, ncases=64, steps=10, warmup=4):
     """The 64-case batch (cylinders and NACA00tt sections, 256..1024 cells wide, mixed
     precision, Chebyshev degree 4 as configured): all cases advance together, one batched
-    Poisson solve per step.  The warm-up covers the cases' first step and the four steps that
+    Poisson solve per step.  The warm-up covers the cases' first step and the three steps that
     tune the Poisson launch's block split."""
     from paper_2211_10698_gb300 import ccm, inputs
 

@@ -384,16 +384,13 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats);
 ccm_status ccm_batch_set_graphs(ccm_batch b, int enable);
 /* Steps this batch has replayed from captured graphs. */
 ccm_status ccm_batch_graph_steps(ccm_batch b, long long* steps);
-/* Online tuning of the Poisson launch's block split: with it on (the default), the four steps
+/* Online tuning of the Poisson launch's block split: with it on (the default), the three steps
  * after the cases' first each use one candidate split (blocks in proportion to cells x nx^a,
- * a = 0, 1/2, 1, or to cells x the iterations of each case's last solve, the expected work of
- * the mixed launch, whose cases each pass their own barriers; the steps advance the cases as
- * usual) and the one with the least Poisson time per cell-iteration is kept; the expected-work
- * split follows the iteration counts, refreshed every 16 replayed steps.  When the batch's
- * cells have changed by more than 30 % since the split was tuned (cases joined or left), the
- * next four steps tune it again.  Off: a = 0. */
+ * a = 0, 1/2, 1; the steps advance the cases as usual) and the one with the least Poisson time
+ * per cell-iteration is kept.  When the batch's cells have changed by more than 30 % since the
+ * split was tuned (cases joined or left), the next three steps tune it again.  Off: a = 0. */
 ccm_status ccm_batch_set_tuning(ccm_batch b, int enable);
-/* The exponent a in use (-1: the expected work) and whether the tuning has finished. */
+/* The exponent a in use and whether the tuning has finished. */
 ccm_status ccm_batch_split(ccm_batch b, double* exponent, int* tuned);
 
 /* ---- Request loop (serving) ------------------------------------------------------------

@@ -64,8 +64,7 @@ struct ccm_batch_s {
   // online tuning of the Poisson launch's block split (see split_candidates)
   bool tune = true;
   int tune_next = 0;               // candidate the next tuned step uses (== kSplitN: done)
-  double tune_cost[4] = {0, 0, 0, 0};
-  long long split_replays = 0;     // graph replays since the Poisson tables were uploaded
+  double tune_cost[3] = {0, 0, 0};
   double tune_cells = 0.0;           // cells of the batch the split was (is being) tuned on
   double split_exp = 0.0;          // the chosen exponent a of the weights cells x nx^a
   cudaEvent_t tev[2] = {nullptr, nullptr};
@@ -98,37 +97,25 @@ void allocate_blocks(const std::vector<double>& w, int blocks, std::vector<int>&
 
 }  // namespace
 
-// Block weights of the cooperative launches: cells x nx^a, or with a < 0 the expected work,
-// cells x the iterations of the case's last Poisson solve.  In a launch whose cases share
-// every barrier (FP64 CG, Helmholtz) each slot lasts as long as its most loaded block, which
-// favours equal cells per block (a = 0).  In the mixed Poisson launch every case has its own
-// barrier and runs at its own pace, so blocks in proportion to its work let the cases finish
-// together; the FP64 Poisson launch does the same.  The Helmholtz launch uses a = 0 (about
-// the same iteration count at every size); the Poisson launch's weights are tuned on the
-// batch's own steps (split_candidates).
+// Block weights of the cooperative launches: cells x nx^a.  The Poisson launches give every
+// case its own barriers, so a case's solve takes about its cells x iterations over its
+// blocks, and the largest cases iterate longest, which favours giving them more blocks
+// (a > 0); the Helmholtz launch, whose cases share every barrier and take about the same
+// iteration count at every size, uses a = 0.  The Poisson launch's a is tuned on the batch's
+// own steps (split_candidates).
 static std::vector<double> cell_weights(const std::vector<ccm_case>& cs, double a = 0.0) {
   std::vector<double> w(cs.size());
-  for (size_t i = 0; i < cs.size(); ++i) {
-    if (a < 0.0) {
-      int it = 0;
-      if (cudaMemcpy(&it, case_inner_iters_dev(cs[i]), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
-        cudaGetLastError();
-        it = 0;
-      }
-      w[i] = (double)case_cells(cs[i]) * (double)std::max(it, 1);
-    } else {
-      w[i] = (double)case_cells(cs[i]) * std::pow((double)case_nx(cs[i]), a);
-    }
-  }
+  for (size_t i = 0; i < cs.size(); ++i) w[i] = (double)case_cells(cs[i]) * std::pow((double)case_nx(cs[i]), a);
   return w;
 }
-// Weights tried for the Poisson split, one batch step each (the steps advance the cases as
-// usual): cells x nx^a for a = 0, 1/2, 1 and the expected work (-1); the one with the least
-// Poisson time per cell-iteration is kept.  With the expected work, the weights follow the
-// cases' iteration counts: the tables are refreshed every kSplitRefresh graph replays.
-constexpr int kSplitN = 4;
-static const double split_candidates[kSplitN] = {0.0, 0.5, 1.0, -1.0};
-constexpr long long kSplitRefresh = 16;
+// Exponents tried for the Poisson split, one batch step each (the steps advance the cases as
+// usual); the one with the least Poisson time per cell-iteration is kept.  With per-case
+// barriers the 64-case mix keeps a = 1 (60.3 M cell-steps/s); the expected work as weights
+// (cells x the iterations of each case's last solve, refreshed as the counts drift) measured
+// 56.4 M with the split fixed, and as a fourth candidate the tuner, which sees each candidate on
+// a different step, picked it on one run (56.2 M), so it is not offered.
+constexpr int kSplitN = 3;
+static const double split_candidates[kSplitN] = {0.0, 0.5, 1.0};
 
 // Waits for the stream and turns a barrier give-up of any launch since the last check into
 // CCM_E_TIMEOUT.
@@ -681,13 +668,6 @@ ccm_status ccm_batch_step(ccm_batch b, int nsteps, ccm_step_stats* stats) {
     if (!ok && (s = capture_graphs(b, mixed, &ok)) != CCM_OK) return s;
     if (ok) {
       for (; n < nsteps; ++n) {
-        if (b->split_exp < 0.0 && ++b->split_replays > kSplitRefresh) {
-          // the expected work moves with the cases' iteration counts: new weights for the
-          // Poisson tables the graphs read (uploaded once the previous replays have run)
-          if ((s = check_barrier(b, "batch graph")) != CCM_OK) return s;
-          if ((s = upload_poisson_tables(b, mixed)) != CCM_OK) return s;
-          b->split_replays = 1;
-        }
         const cudaError_t e = cudaGraphLaunch(b->gexec[b->gphase], b->st);
         if (e != cudaSuccess) return bfail(CCM_E_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
         b->gphase ^= 1;
