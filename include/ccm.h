@@ -271,6 +271,14 @@ ccm_status ccm_step(ccm_case c, int nsteps, ccm_step_stats* stats);
  * absent_block < -1. */
 ccm_status ccm_set_barrier_fault(ccm_case c, long long budget_cycles, int absent_block);
 
+/* Test hook for the exact fixed-point dot products of the FP64 one-barrier CG (the paper has
+ * no counterpart): with every = k > 0, every k-th reduction of a solve also takes the FP64
+ * fallback that a value outside the fixed-point window would trigger (FP64 partials and a
+ * counter barrier), so that path runs in tests; 0 (the default): only on such a value.  The
+ * fallback's sums round differently, so the fields agree with the normal path to the solver
+ * tolerance, not bit for bit.  CCM_E_INVALID for every < 0. */
+ccm_status ccm_set_sum_fallback(ccm_case c, int every);
+
 /* Time law of the body velocity (Sec. 4.6, Eq. pm_prediction and the boundary condition of U*
  * that follows it: conv and S^n take D^n, S* and cont(U*, D^{n+1}) of Eq. pm_poisson take the
  * next level D^{n+1}).  From the next step on the body velocity is D(t) = f(t) D0 with

@@ -109,6 +109,7 @@ def lib():
             "ccm_solve_pressure_noalloc": (c_int, [cp, c_void_p, c_void_p, POINTER(ccm_solve_stats)]),
             "ccm_set_barrier_fault": (c_int, [cp, c_longlong, c_int]),
             "ccm_set_body_motion": (c_int, [cp, c_double, c_double, c_double, c_double]),
+            "ccm_set_sum_fallback": (c_int, [cp, c_int]),
             "ccm_measure_fp64_rate": (c_int, [_DP]),
             "ccm_batch_create": (c_int, [c_int, c_void_p, POINTER(c_void_p)]),
             "ccm_batch_destroy": (c_int, [cp]),

@@ -113,6 +113,9 @@ struct ccm_case_s {
   // that skips its arrivals (failure-detection tests only; -1 otherwise)
   long long bar_budget = kBarrierBudget;
   int bar_absent = -1;
+  // tests only: every k-th fixed-point reduction of the FP64 one-barrier CG takes its FP64
+  // fallback (0: only when a value leaves the window)
+  int fx_fallback_every = 0;
   // stretched mesh: the face abscissas extended two faces beyond the box (host copies, and
   // their device arrays in the slab); empty for a uniform spacing
   std::vector<double> xfx, yfx;
@@ -299,6 +302,7 @@ ccm_status solve_poisson_fp64(ccm_case c, double* x, double* b) {
     FusedSolve f{};
     f.a = scaled_solve_of(v, x, b, c->pz, nullptr, nullptr, c->pp0, nullptr);
     f.fxacc = c->fxacc;
+    f.fx_fallback_every = c->fx_fallback_every;
     f.a.partials = c->partials;
     f.a.bar = case_barrier(c);
     f.a.out = PcgOut{&c->ds->iters_p, &c->ds->rr_p, &c->ds->bb_p, &c->ds->conv_p, &c->ds->total_p, &c->ds->nconv};
@@ -1411,6 +1415,14 @@ ccm_status ccm_set_barrier_fault(ccm_case c, long long budget_cycles, int absent
   if (budget_cycles < 0 || absent_block < -1) return fail(CCM_E_INVALID, "budget_cycles >= 0, absent_block >= -1");
   c->bar_budget = budget_cycles > 0 ? budget_cycles : kBarrierBudget;
   c->bar_absent = absent_block;
+  return CCM_OK;
+}
+
+ccm_status ccm_set_sum_fallback(ccm_case c, int every) {
+  g_last_error.clear();
+  if (!c) return fail(CCM_E_INVALID, "null case");
+  if (every < 0) return fail(CCM_E_INVALID, "every >= 0");
+  c->fx_fallback_every = every;
   return CCM_OK;
 }
 

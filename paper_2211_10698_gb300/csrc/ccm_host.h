@@ -106,6 +106,7 @@ constexpr int kFxAccWords = 3 * kFxWords * kFxStride;
 struct FusedSolve {
   ScaledSolve a;
   unsigned long long* fxacc;  // kFxAccWords words (cleared by the kernel itself)
+  int fx_fallback_every;      // tests only: every k-th reduction takes the FP64 fallback (0: on overflow only)
   double* R[2];
   double* W[2];
   double* S[2];

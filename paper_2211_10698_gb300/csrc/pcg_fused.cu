@@ -487,7 +487,10 @@ __device__ __forceinline__ void fused_body(const FusedSolve& f) {
     }
     if (!fx_wait(f.fxacc, buf, (ri + 2) % 3, a.bar.budget, a.bar.err, fxs)) { ok = false; break; }
     double t[3];
-    if (fxs.s[kFxWords - 1] == 0) {
+    // every block takes the same branch: the overflow count is the grid's, and the test hook
+    // depends on the reduction index only
+    const bool forced = f.fx_fallback_every > 0 && ri % f.fx_fallback_every == 0;
+    if (fxs.s[kFxWords - 1] == 0 && !forced) {
       if (threadIdx.x < kFxQ) gsum[threadIdx.x] = fx_value(&fxs.s[threadIdx.x * kFxDigits], fx_lo);
       __syncthreads();
       t[0] = gsum[0];

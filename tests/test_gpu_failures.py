@@ -120,3 +120,30 @@ def test_checkpoint_restore_continues_bitwise(precision, precond):
     assert g.get_field(ccm.CCM_F_STEP)[0, 0] == k + m
     g.close()
     ref.close()
+
+
+@pytest.mark.parametrize("plan", [(128, 27, 8, 152, 0, 0, 1), (64, 27, 16, 304, 0, 0, 0)])
+def test_fixed_point_sums_fallback_path(plan):
+    """The FP64 one-barrier CG sums its dot products as exact fixed-point digits and falls back
+    to FP64 partials and a counter barrier when a value leaves the digits' window (a sum that
+    grew 2^20-fold in one iteration).  The test hook forces that fallback on every third
+    reduction: the steps converge, and the fields equal those of the normal path to the solver
+    tolerance (resident and global-memory tiles, 1024x512 cylinder)."""
+    def run(every):
+        case = I.cylinder_re100_1024x512()
+        case.autotune = 0
+        g = ccm.Case(case)
+        g.set_launch_plan(plan)
+        assert ccm.lib().ccm_set_sum_fallback(g.h, every) == ccm.CCM_OK
+        st = g.step(3)
+        out = {f: g.get_field(f) for f in (ccm.CCM_F_U, ccm.CCM_F_V, ccm.CCM_F_P)}
+        g.close()
+        return st, out
+
+    s0, f0 = run(0)
+    s3, f3 = run(3)
+    assert s0["converged"] and s3["converged"]
+    assert abs(s3["iters_p"] - s0["iters_p"]) <= 0.02 * s0["iters_p"] + 3
+    for f in f0:
+        assert np.linalg.norm(f3[f] - f0[f]) / np.linalg.norm(f0[f]) < 1e-9, f
+    assert ccm.lib().ccm_set_sum_fallback(None, 1) == ccm.CCM_E_INVALID
