@@ -1434,8 +1434,9 @@ void orc_init_velocity(const orc_case* c, const double* caps, double u0, double 
  * full cell's area by default (pressure_update = 0): dividing by the fluid volume V_p of a
  * small cut cell (pressure_update = 1) makes the correction an unbounded gain there and the
  * step unstable (the paper does not say which volume).
- * The first step uses conv^{-1} = conv^0; P^{-1/2} = 0; the body is fixed and no-slip
- * (D = 0), the box boundary data are steady, gravity is zero.
+ * The first step uses conv^{-1} = conv^0; P^{-1/2} = 0; the body is fixed, the box boundary
+ * data are steady.  orc_step is the no-slip body (D = 0) without body acceleration; orc_step_g
+ * adds g, orc_step_gd a steady D and orc_step_gdt a D given at both time levels.
  * State arrays: u, v, p (P^{n-1/2}), phi (Phi^n, the warm start), cu, cv (conv^{n-1}).
  * `first` is 1 for the first step.  Intermediate results may be returned through
  * ustar/vstar and bdiv when not NULL.
