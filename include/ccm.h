@@ -27,6 +27,10 @@
  *    no-slip (Dirichlet data D = 0 in Eqs. divergence, diag, offdiag, convective) unless the
  *    fields CCM_F_DX / CCM_F_DY give its wall a velocity D (a rotating, sliding or porous
  *    body), steady or, through ccm_set_body_motion, scaled by a prescribed function of time.
+ *  - Equations are cited by their label in the paper's source.  Numbered in the order the
+ *    paper prints them: approximate (2), divergence (17), compatibility (18), diag (19),
+ *    offdiag (20), divD (21), convective (22), kinetic (26), semidiscrete (27),
+ *    pm_prediction (30), pm_poisson (31), pm_projection (32), pm_update (33).
  */
 #ifndef CCM_H
 #define CCM_H
@@ -305,7 +309,8 @@ ccm_status ccm_read_stats(ccm_case c, ccm_step_stats* stats);
  * step), force[4] = {Fp_x, Fp_y, Fv_x, Fv_y}: the pressure and viscous parts, in the case's
  * units (per unit depth).  The paper reports drag and lift (Sec. 5) without a discrete
  * definition; this is the body's share of the momentum that pres(P) and visc(2 mu S) give the
- * fluid (Secs. 4.1, 4.3), i.e. with A-differences across cells equal to -n |Gamma| (Eq. SCL):
+ * fluid (Secs. 4.1, 4.3), i.e. with A-differences across cells equal to -n |Gamma| (Eq.
+ * approximate, the surface conservation law):
  *   Fp_x = sum_cells P (A^x_{i-1/2,j} - A^x_{i+1/2,j}),  Fp_y likewise with A^y in y,
  *   Fv_x = -2 mu [sum_cells S_xx (B^xx_{i-1/2} - B^xx_{i+1/2}) + sum_nodes S_xy (B^xy_{j-1/2} - B^xy_{j+1/2})],
  *   Fv_y = -2 mu [sum_cells S_yy (B^yy_{j-1/2} - B^yy_{j+1/2}) + sum_nodes S_xy (B^yx_{i-1/2} - B^yx_{i+1/2})],

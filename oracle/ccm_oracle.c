@@ -1352,8 +1352,9 @@ double orc_max_div(const orc_case* c, const double* caps, const double* u, const
  * operators onto the capacities (summation by parts) leaves box-boundary fluxes plus terms in
  * the differences of A and B across cells, which vanish wherever the grid is uncut; those
  * terms are the body's share.  Per component, with F = (Fp_x, Fp_y, Fv_x, Fv_y):
- *   Fp_x = sum_cells P (A^x_left - A^x_right)        (= sum P n_x |Gamma| by Eq. SCL: the
- *   Fp_y = sum_cells P (A^y_bottom - A^y_top)           normal pointing out of the fluid)
+ *   Fp_x = sum_cells P (A^x_left - A^x_right)        (= sum P n_x |Gamma| by Eq. approximate,
+ *   Fp_y = sum_cells P (A^y_bottom - A^y_top)           the surface conservation law: the
+ *                                                       normal pointing out of the fluid)
  *   Fv_x = -2 mu [ sum_cells S_xx (B^xx_left - B^xx_right) + sum_nodes S_xy (B^xy_below - B^xy_above) ]
  *   Fv_y = -2 mu [ sum_cells S_yy (B^yy_below - B^yy_above) + sum_nodes S_xy (B^yx_left - B^yx_right) ]
  * over p-cells i in [0,nx), j in [0,ny); the S_xy sums run over the nodes whose two u-faces
