@@ -80,6 +80,9 @@ def _args():
     ap.add_argument("--cheb-degree", type=int, default=3)
     ap.add_argument("--batch-cases", type=int, default=64,
                     help="cases of the batched measurement (the first N of the seeded 64-case mix)")
+    ap.add_argument("--serving-window", default="32,100",
+                    help="NREQ,DIV: the serving measurement takes the first NREQ requests of the "
+                         "stream with their step counts divided by DIV")
     return ap.parse_args()
 
 
@@ -711,10 +714,11 @@ def run_ours(args):
     if rank == 0 and "serving" in want:
         try:
             torch.cuda.synchronize()
-            sv = dict(workload=f"request stream window: first 32 requests at 20/s, steps/100, "
+            nreq, sdiv = (int(x) for x in args.serving_window.split(","))
+            sv = dict(workload=f"request stream window: first {nreq} requests at 20/s, steps/{sdiv}, "
                                f"budget 150 GB, batches of up to 64, chunks of 5 steps")
-            sv["mixed"] = measure_serving("mixed")
-            sv["fp64"] = measure_serving("fp64")
+            sv["mixed"] = measure_serving("mixed", nreq=nreq, step_div=sdiv)
+            sv["fp64"] = measure_serving("fp64", nreq=nreq, step_div=sdiv)
             extras["serving"] = sv
         except Exception as e:
             extras["serving"] = {"error": str(e)}
